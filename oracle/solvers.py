@@ -1,0 +1,141 @@
+"""Oracle solvers: power method, preconditioned PDHG, CG and FISTA (test infrastructure only).
+
+Preconditioned PDHG for a simple g (Sec. 4.1), iteration k:
+    u <- (I + sigma_k P)^{-1} (u + sigma_k P (A xbar - y))
+    x_new <- prox_{tau_k g}(x - tau_k A^H u)
+    xbar <- x_new + theta_k (x_new - x)
+with sigma_0 = 1, tau_0 = 1/lambda_max(P A A^H) and the accelerated schedule
+    theta_k = 1/(1 + 2 sigma_k min_i p_i),  sigma_{k+1} = theta_k sigma_k,  tau_{k+1} = tau_k/theta_k.
+Readings where the paper is silent: x_0 = xbar_0 = 0, u_0 = 0; theta_k is computed from
+sigma_k before the k-th update; lambda_max is estimated by the power method on A^H P A
+(same non-zero spectrum as P A A^H) for 30 iterations (Sec. 6) from a given start vector
+(all ones by default), as ||A^H P A v|| / ||v|| at the last step, with no safety margin.
+
+Objective (Eq. obj): F(x) = 1/2 ||A x - y||^2 + g(x), g = lambda ||x||^2 / 2 or
+lambda ||W x||_1.  CG on (A^H A + lambda I) x = A^H y gives the l2 optimum; FISTA gives
+an independent l1 optimum.
+
+Parity: pinned by tests/test_oracle_solvers.py (power method against numpy.linalg.eigvalsh,
+PDHG l2 against the CG solution and the KKT relations u* = A x* - y and
+-A^H u* = lambda x*, PDHG l1 fixed point and agreement with FISTA, sigma*tau invariant).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import wavelet as wv
+
+__all__ = ["power_method", "pdhg_schedule", "objective", "pdhg", "cg_l2", "fista_l1",
+           "prox_l2", "make_prox"]
+
+
+def power_method(A, AH, p, x_shape, iters=30, v0=None):
+    """lambda_max(A^H P A) by the power method; returns (L, v)."""
+    v = np.ones(x_shape, dtype=np.complex128) if v0 is None else np.array(v0, dtype=np.complex128)
+    v = v / np.linalg.norm(v)
+    L = 0.0
+    for _ in range(iters):
+        w = AH(p * A(v))
+        L = float(np.linalg.norm(w))      # ||A^H P A v|| with ||v|| = 1
+        v = w / L
+    return L, v
+
+
+def pdhg_schedule(iters, L, pmin):
+    """(sigma_k, tau_k, theta_k) for k = 0..iters-1 (Sec. 4.1 accelerated schedule)."""
+    sig, tau = 1.0, 1.0 / L
+    out = []
+    for _ in range(iters):
+        theta = 1.0 / (1.0 + 2.0 * sig * pmin)
+        out.append((sig, tau, theta))
+        sig, tau = theta * sig, tau / theta
+    return out
+
+
+def prox_l2(z, t, lam):
+    """prox of t*lam*||x||^2/2: z / (1 + t lam)."""
+    return z / (1.0 + t * lam)
+
+
+def make_prox(reg, lam, levels=0):
+    if reg == "l2":
+        return lambda z, t: prox_l2(z, t, lam)
+    if reg == "l1_wavelet":
+        return lambda z, t: wv.prox_l1_wavelet(z, t * lam, levels)
+    raise ValueError(reg)
+
+
+def objective(A, x, y, reg, lam, levels=0):
+    """F(x) = 1/2 ||A x - y||^2 + g(x)."""
+    r = A(x) - y
+    f = 0.5 * float(np.vdot(r, r).real)
+    if reg == "l2":
+        f += 0.5 * lam * float(np.vdot(x, x).real)
+    else:
+        f += lam * float(np.sum(np.abs(wv.dwt(x, levels))))
+    return f
+
+
+def pdhg(A, AH, y, p, x_shape, reg, lam, iters, L, levels=0, trace=False, state=None):
+    """Preconditioned PDHG (Sec. 4.1).  Returns (x, u, xbar, objective trace or None)."""
+    prox = make_prox(reg, lam, levels)
+    y = np.asarray(y, dtype=np.complex128)
+    p = np.broadcast_to(np.asarray(p, dtype=np.float64), y.shape)
+    if state is None:
+        x = np.zeros(x_shape, dtype=np.complex128)
+        xbar = x.copy()
+        u = np.zeros_like(y)
+        k0 = 0
+    else:
+        x, xbar, u, k0 = (np.array(state[0], dtype=np.complex128), np.array(state[1], dtype=np.complex128),
+                          np.array(state[2], dtype=np.complex128), int(state[3]))
+    sched = pdhg_schedule(k0 + iters, L, float(p.min()))
+    objs = [] if trace else None
+    for k in range(k0, k0 + iters):
+        sig, tau, theta = sched[k]
+        u = (u + sig * p * (A(xbar) - y)) / (1.0 + sig * p)
+        x_new = prox(x - tau * AH(u), tau)
+        xbar = x_new + theta * (x_new - x)
+        x = x_new
+        if trace:
+            objs.append(objective(A, x, y, reg, lam, levels))
+    return x, u, xbar, objs
+
+
+def cg_l2(A, AH, y, lam, x_shape, iters=500, tol=1e-13):
+    """Conjugate gradient on (A^H A + lam I) x = A^H y (the l2 optimum)."""
+    b = AH(y)
+    x = np.zeros(x_shape, dtype=np.complex128)
+    r = b.copy()
+    d = r.copy()
+    rr = float(np.vdot(r, r).real)
+    bn = math.sqrt(float(np.vdot(b, b).real))
+    for _ in range(iters):
+        q = AH(A(d)) + lam * d
+        a = rr / float(np.vdot(d, q).real)
+        x = x + a * d
+        r = r - a * q
+        rr_new = float(np.vdot(r, r).real)
+        if math.sqrt(rr_new) < tol * bn:
+            break
+        d = r + (rr_new / rr) * d
+        rr = rr_new
+    return x
+
+
+def fista_l1(A, AH, y, lam, x_shape, levels, iters=2000, L=None):
+    """FISTA (Beck & Teboulle) for 1/2||Ax-y||^2 + lam ||W x||_1, step 1/L, L = lambda_max(A^H A)."""
+    if L is None:
+        L, _ = power_method(A, AH, 1.0, x_shape, iters=100)
+        L *= 1.0001
+    x = np.zeros(x_shape, dtype=np.complex128)
+    z = x.copy()
+    t = 1.0
+    for _ in range(iters):
+        x_new = wv.prox_l1_wavelet(z - AH(A(z) - y) / L, lam / L, levels)
+        t_new = (1 + math.sqrt(1 + 4 * t * t)) / 2
+        z = x_new + ((t - 1) / t_new) * (x_new - x)
+        x, t = x_new, t_new
+    return x
