@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of k-space-preconditioned PDHG (Ong, Uecker & Lustig, arXiv 1902.09657) on GB300.
+
+One timed step = one whole reconstruction of the 2D variable-density spiral l1-wavelet
+workload (256x256 image, 12 coils, 24 interleaves x 4096 samples, oversampling 1.25, KB width
+4, Daubechies-4 with 4 levels, lambda = 1e-3 max|A^H y|): trajectory binning, coil maps,
+multi-channel preconditioner, 30 power iterations, 100 PDHG iterations.  All inputs are
+synthetic (seeded phantom, Gaussian-bump coil maps, spiral trajectory, Gaussian noise).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank reconstructs its own
+replica of the workload (independent problems, weak scaling); ranks only meet in the
+barriers and the max-over-ranks of the timing.  --impl reference times the float64 CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "spiral2d_256"
+METRIC = "PDHG iterations/s, whole reconstruction (bin-sort + MC preconditioner + 30 power its + 100 l1-wavelet PDHG its)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip roofline/e2e/time-to-accuracy extras")
+    return ap.parse_args()
+
+
+def workload_config(w):
+    return {
+        "workload": f"{w.name}: {w.img_shape[0]}x{w.img_shape[1]} image, {w.ncoils} coils, "
+                    f"{w.traj_args['n_interleaves']}x{w.traj_args['n_samples']} spiral samples, alpha {w.oversamp}, "
+                    f"KB W{w.width}, db4 {w.wavelet_levels} levels, l1 lambda=1e-3*max|A^H y|, {w.iters} iterations",
+        "image": list(w.img_shape), "coils": w.ncoils,
+        "samples": int(w.traj_args["n_interleaves"] * w.traj_args["n_samples"]),
+        "iters": w.iters, "power_iters": 30, "preconditioner": "multi-channel",
+        "l2_between_steps": "flushed (256 MiB write)",
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(w, n_pdhg=3):
+    """Time the float64 oracle on a bounded sample of the workload and extrapolate the whole
+    reconstruction (preconditioner + 30 power iterations + w.iters PDHG iterations)."""
+    from oracle import nufft as onf, precond as opc, solvers as osv
+    traj, x, maps = w.traj(), w.phantom().astype(np.complex128), w.maps().astype(np.complex128)
+    y = onf.nufft_forward(x, maps, traj, w.oversamp, w.width)
+    y = y + 0.01 * np.abs(y).max() * w.noise()
+    A = lambda v: onf.nufft_forward(v, maps, traj, w.oversamp, w.width)
+    AH = lambda u: onf.nufft_adjoint(u, maps, traj, w.oversamp, w.width)
+    t0 = time.perf_counter()
+    p = opc.mc_precond_fast(maps, traj, w.oversamp, w.width)
+    t_pre = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=1)
+    t_pow = time.perf_counter() - t0
+    lam = w.lam_rel * float(np.abs(AH(y)).max())
+    t0 = time.perf_counter()
+    osv.pdhg(A, AH, y, p, x.shape, w.reg, lam, n_pdhg, L, levels=w.wavelet_levels)
+    t_it = (time.perf_counter() - t0) / n_pdhg
+    est = t_pre + 30 * t_pow + w.iters * t_it
+    return {"value": w.iters / est, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"float64 NumPy oracle on the full workload: MC preconditioner once ({t_pre:.2f} s), "
+                      f"1 power iteration ({t_pow:.2f} s), {n_pdhg} PDHG iterations ({t_it:.2f} s each); "
+                      f"whole reconstruction extrapolated to 30 power + {w.iters} PDHG iterations = {est:.1f} s",
+            "est_step_s": est}
+
+
+def run_reference(args, rank, world):
+    w = synth.workload(WORKLOAD)
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; each sample is independent
+    vals, ests = [], []
+    for _ in range(args.steps):
+        s = oracle_sample(w, n_pdhg=2)
+        vals.append(s["value"])
+        ests.append(s["est_step_s"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(ests),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "iters/s",
+                             "sample": s["sample"]},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def algorithmic_bytes(w, C, M, N, G):
+    """Algorithmic HBM bytes per PDHG iteration of each phase (each array touched once)."""
+    c8, m = 8, C * M
+    return {
+        "fwd_pre": N * 8 + C * N * 8 + C * G * 8,              # x, maps in; whole grid out
+        "interp_dual": C * G * 8 + m * (8 + 4 + 8 + 8) + M * 2 * 4,   # grid, y, p, u in/out, traj
+        "spread": m * c8 + M * 2 * 4 + C * G * 8,              # u, traj in; whole grid out
+        "adj_primal": C * N * 8 + C * N * 8 + N * 8 * 3,       # cropped grid, maps, x in/out, z out
+        "dwt_fwd": 2 * 2 * N * 8, "dwt_inv": 2 * 2 * N * 8, "soft": 2 * N * 8, "extrap": 4 * N * 8,
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1902_09657_gb300 import _build
+    from paper_1902_09657_gb300.api import Plan
+
+    _build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = synth.workload(WORKLOAD)
+    traj_h = torch.from_numpy(w.traj()).pin_memory()
+    x_true = torch.from_numpy(w.phantom())
+    maps_h = torch.from_numpy(w.maps()).pin_memory()
+    C, M = w.ncoils, traj_h.shape[0]
+    N = int(np.prod(w.img_shape))
+    traj_d, maps_d = traj_h.to(dev), maps_h.to(dev)
+    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, wavelet_levels=w.wavelet_levels, device=dev)
+    plan.set_trajectory(traj_d).set_maps(maps_d)
+    # synthetic measurements: A x + 1 % complex Gaussian noise
+    y_d = plan.sense_forward(x_true.to(dev))
+    noise = torch.from_numpy(w.noise().astype(np.complex64)).to(dev)
+    y_d = (y_d + 0.01 * y_d.abs().max() * noise).contiguous()
+    lam = w.lam_rel * float(plan.sense_adjoint(y_d).abs().max())
+    y_h = y_d.cpu().pin_memory()
+    G = 1
+    for n in w.img_shape:
+        g = math.ceil(w.oversamp * n - 1e-9)
+        G *= g + (g % 2)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step():
+        plan.set_trajectory(traj_d).set_maps(maps_d)
+        return plan.pdhg_solve(y_d, None, w.reg, lam, w.iters)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = plan.launch_count()
+    clocks = Clocks(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    clocks.start()
+    total_ms = 0.0
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    launches = plan.launch_count() - launches0
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * args.steps * w.iters / (total_ms / 1e3)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stream, flush,
+                            C, M, N, G, args)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w), "clocks": ck, "gpu_launches": int(launches)}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+def gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stream, flush, C, M, N, G, args):
+    import torch
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # --- end to end through the public API with host buffers
+    k = max(1, min(args.steps, 5))
+    tot = 0.0
+    for i in range(k + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        td = traj_h.to(dev, non_blocking=True)
+        md = maps_h.to(dev, non_blocking=True)
+        plan.set_trajectory(td).set_maps(md)
+        xh, _, _ = plan.pdhg_solve(y_h, None, w.reg, lam, w.iters)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            tot += e0.elapsed_time(e1)
+    bi = traj_h.numel() * 4 + maps_h.numel() * 8 + y_h.numel() * 8
+    out["e2e"] = {"value": k * w.iters / (tot / 1e3), "unit": "iters/s", "h2d_bytes_per_step": int(bi),
+                  "d2h_bytes_per_step": int(N * 8)}
+    # --- setup and solve-only split
+    plan.set_trajectory(traj_d).set_maps(maps_d)
+    torch.cuda.synchronize()
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(stream)
+    plan.set_trajectory(traj_d).set_maps(maps_d)
+    p = plan.make_preconditioner(True)
+    L = plan.max_eig(p, iters=30)
+    e1.record(stream)
+    plan.pdhg_solve(y_d, p, w.reg, lam, w.iters, lmax=L)
+    e2.record(stream)
+    e2.synchronize()
+    setup_ms, solve_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    out["setup_ms"] = setup_ms
+    out["solve_only_iters_per_s"] = w.iters / (solve_ms / 1e3)
+    # --- per-phase profile (events at every phase boundary, no graph) and the roofline
+    plan.set_profiling(True)
+    _, _, st = plan.pdhg_solve(y_d, p, w.reg, lam, w.iters, lmax=L)
+    plan.set_profiling(False)
+    ph = {n: v / w.iters for n, v in st["phase_ms"].items() if v > 0}
+    out["phase_ms_per_iter"] = {n: round(v, 5) for n, v in ph.items()}
+    ab = algorithmic_bytes(w, C, M, N, G)
+    own = {n: v for n, v in ph.items() if n in ab}
+    dom = max(own, key=own.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = ab[dom] / (own[dom] * 1e-3) / 1e9
+    out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+                       "algorithmic_bytes": int(ab[dom]), "avg_launch_ms": own[dom]}
+    # --- time to 1e-3 relative objective (F* = min over a 400-iteration float32 run)
+    _, tr, _ = plan.pdhg_solve(y_d, p, w.reg, lam, 400, lmax=L, trace=True)
+    Fstar = min(tr)
+    kk = next((i + 1 for i, f in enumerate(tr) if (f - Fstar) / abs(Fstar) < 1e-3), None)
+    per_it = solve_ms / w.iters
+    out["time_to_1e-3"] = {"iters": kk, "ms_solve_only": None if kk is None else kk * per_it,
+                           "ms_with_setup": None if kk is None else setup_ms + kk * per_it,
+                           "F_star": Fstar, "F_star_source": "min of a 400-iteration float32 GPU run"}
+    # --- CPU oracle baseline (bounded sample)
+    try:
+        out["cpu_baseline"] = {k2: v for k2, v in oracle_sample(w).items() if k2 != "est_step_s"}
+    except Exception as e:  # pragma: no cover
+        out["cpu_baseline"] = {"error": repr(e)}
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * kpdhg.h - C ABI of the GB300 (sm_103a) library for k-space-preconditioned PDHG
+ * reconstruction of multi-coil non-Cartesian MRI (Ong, Uecker & Lustig,
+ * "Accelerating Non-Cartesian MRI Reconstruction Convergence using k-space
+ * Preconditioning", arXiv 1902.09657).
+ *
+ * Problem statement (Sec. 2, Eq. model_i / model / obj):
+ *   y_c[i] = N^{-1/2} sum_n s_c[n] x[n] exp(-i 2 pi sum_d f_{i,d} n_d / N_d) + w_c[i],
+ *   x_hat = argmin_x 1/2 ||A x - y||^2 + g(x),  g = lambda ||x||^2/2  or  lambda ||W x||_1.
+ * A is applied as a Kaiser-Bessel NUFFT (Sec. 6: oversampling 1.25, width 4, following
+ * Beatty et al.).
+ *
+ * Conventions used by every entry point:
+ *   - Images are complex64 (interleaved re, im float32), row-major, slowest axis first
+ *     ((y, x) in 2D, (z, y, x) in 3D); pixel index j_d holds the centred position
+ *     n_d = j_d - N_d/2.
+ *   - Trajectories are float32 [M][ndim] in cycles per field of view, column d matching
+ *     image axis d; every coordinate must lie in [-N_d/2, N_d/2].
+ *   - k-space arrays (y, dual variable, preconditioner) are coil-major [C][M].
+ *   - Coil maps are [C][N] complex; storage type given by a kp_cdtype.
+ *   - All pointers named *_dev are device pointers owned by the caller, 16-byte aligned,
+ *     contiguous, and must stay valid until the stream work that uses them completes.
+ *     The library never frees caller memory; a plan owns only its own workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Work is
+ *     ordered on that stream.  Calls documented as "synchronous" wait for it to finish.
+ *   - No C++ exception crosses the boundary.  Every call returns a kp_status; on failure
+ *     kp_last_error() returns a thread-local message.
+ *   - A plan is not thread-safe: do not use one plan from two host threads or two
+ *     streams at the same time.
+ */
+#ifndef KPDHG_H
+#define KPDHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kp_plan_s* kp_plan;
+
+typedef enum {
+    KP_OK = 0,
+    KP_EINVAL = 1,       /* invalid argument (sizes, null pointer, coordinate range, p <= 0) */
+    KP_ENOMEM = 2,       /* device or host allocation failed */
+    KP_ECUDA = 3,        /* a CUDA runtime call failed */
+    KP_ECUFFT = 4,       /* a cuFFT call failed */
+    KP_EDIVERGED = 5,    /* objective exceeded 1e3 x its first value */
+    KP_ENONFINITE = 6,   /* NaN/Inf met (objective, power-method norm, or a non-positive
+                            preconditioner denominator in kp_make_preconditioner) */
+    KP_ETIMEOUT = 7,     /* a bounded device-side wait gave up */
+    KP_EINTERNAL = 8
+} kp_status;
+
+/* Complex storage types.  Arithmetic is always float32 with float64 reductions. */
+typedef enum {
+    KP_C64 = 0,          /* complex float32 */
+    KP_C32_BF16 = 1,     /* complex bfloat16 (re, im) */
+    KP_C32_FP16 = 2      /* complex float16 (re, im) */
+} kp_cdtype;
+
+typedef enum {
+    KP_REG_L2 = 0,           /* g(x) = lambda ||x||^2 / 2                       (Sec. 2) */
+    KP_REG_L1_WAVELET = 1    /* g(x) = lambda ||W x||_1, W periodised orthonormal
+                                8-tap Daubechies, `wavelet_levels` levels       (Sec. 2, 6) */
+} kp_reg;
+
+typedef struct {
+    int ndim;              /* 2 or 3 */
+    int64_t img[3];        /* N_d, slowest axis first; entries beyond ndim ignored */
+    int ncoils;            /* C >= 1 */
+    int64_t nsamples;      /* M >= 1 */
+    float oversamp;        /* grid oversampling alpha (1.25 in the paper); G_d = ceil(alpha N_d), even */
+    int kernel_width;      /* Kaiser-Bessel width W in grid units; 4 (the paper's) is supported */
+    int wavelet_levels;    /* levels of W for KP_REG_L1_WAVELET; each N_d divisible by 2^levels */
+} kp_params;
+
+#define KP_NPHASES 12      /* phases of one PDHG iteration reported by profiling */
+
+typedef struct {
+    int iters;             /* iterations run */
+    double lmax;           /* lambda_max(P A A^H) used for tau_0 */
+    double pmin;           /* min_i p_i used by the step-size schedule */
+    double sigma_last;     /* sigma, tau after the last iteration */
+    double tau_last;
+    double final_obj;      /* objective at the returned x if a trace was requested, else NaN */
+    double phase_ms[KP_NPHASES];  /* with profiling on: summed GPU time per phase (ms):
+                                     0 coil/apodise/pad, 1 FFT, 2 interpolation + dual update,
+                                     3 spreading, 4 split-tile reduction, 5 inverse FFT,
+                                     6 adjoint + primal step, 7 DWT, 8 soft threshold,
+                                     9 inverse DWT, 10 extrapolation, 11 iteration counter */
+} kp_stats;
+
+/* Human-readable name of a status; never NULL. */
+const char* kp_status_string(kp_status s);
+
+/* Thread-local message describing the last failure on this host thread ("" if none). */
+const char* kp_last_error(void);
+
+/* Create a plan: validates `params`, allocates all device workspace (grids, sort buffers,
+ * cuFFT plans) and uploads the apodisation and wavelet tables.  Synchronous.
+ * Errors: KP_EINVAL (ndim not 2/3, non-positive sizes, width != 4, oversamp < 1,
+ * levels incompatible with the image), KP_ENOMEM, KP_ECUFFT. */
+kp_status kp_plan_create(kp_plan* out, const kp_params* params, void* stream);
+
+/* Release a plan and all its workspace.  Synchronises the device first.  NULL is a no-op. */
+kp_status kp_plan_destroy(kp_plan plan);
+
+/* Set the trajectory (Sec. 2: sampling points f_i): converts to grid coordinates
+ * t = f G/N (float32), sorts samples by grid tile (counting sort) and builds the
+ * per-tile lists used by the spreading kernel.  traj_dev: float32 [M][ndim].
+ * Synchronous (it checks the coordinate range).  Errors: KP_EINVAL if any coordinate is
+ * outside [-N_d/2, N_d/2] or not finite. */
+kp_status kp_plan_set_trajectory(kp_plan plan, const float* traj_dev, void* stream);
+
+/* Set the coil sensitivity maps s_c (Sec. 2), [C][N] of type maps_t; copied into the
+ * plan (converted to the plan's storage: float32 for KP_C64, half types kept half).
+ * Asynchronous. */
+kp_status kp_plan_set_maps(kp_plan plan, const void* maps_dev, kp_cdtype maps_t, void* stream);
+
+/* y = A x (Sec. 2, Eq. model_i), NUFFT approximation: coil multiply, apodisation,
+ * oversampled FFT, Kaiser-Bessel interpolation.  x_dev: complex64 [N];
+ * y_dev: [C][M] of type y_t.  Asynchronous. */
+kp_status kp_sense_forward(kp_plan plan, const void* x_dev, void* y_dev, kp_cdtype y_t, void* stream);
+
+/* x = A^H y, the exact adjoint of kp_sense_forward (spreading, inverse FFT, apodisation,
+ * conjugate coil combine).  y_dev: [C][M] of type y_t; x_dev: complex64 [N].  Asynchronous. */
+kp_status kp_sense_adjoint(kp_plan plan, const void* y_dev, kp_cdtype y_t, void* x_dev, void* stream);
+
+/* l2-optimised diagonal k-space preconditioner (Sec. 5 and App. A), computed by the fast
+ * route of Sec. 5.1 (Fig. 2): autocorrelations of s_c s_d^* by FFT on a 2N grid,
+ * point-spread function h by a type-1 NUFFT of ones, one type-2 NUFFT per coil.
+ * multichannel = 1: Eq. mc_precond, p_c[i]^{-1} = 1/(||s_c||^2 N) sum_j sum_d
+ *   |sum_n s_c s_d^* e^{-i 2 pi (f_i - f_j) n/N}|^2;
+ * multichannel = 0: Eq. sc_precond with the 1/N^2 prefactor of the general form
+ *   (C = 1, s = 1), the same value written for every coil.
+ * p_dev: float32 [C][M], sample order of the trajectory.  Synchronous.
+ * Errors: KP_ENONFINITE if a denominator came out non-positive (NUFFT error). */
+kp_status kp_make_preconditioner(kp_plan plan, int multichannel, float* p_dev, void* stream);
+
+/* lambda_max(P A A^H) by `iters` power iterations on A^H P A (Sec. 6: 30 iterations),
+ * started from v0_dev (complex64 [N]) or from the all-ones image if v0_dev is NULL.
+ * p_dev: float32 [C][M] or NULL for P = I.  *lmax receives ||A^H P A v|| for the last
+ * normalised v.  Synchronous. */
+kp_status kp_max_eig(kp_plan plan, const float* p_dev, const void* v0_dev, int iters,
+                     double* lmax, void* stream);
+
+/* Preconditioned PDHG (Sec. 4.1):
+ *   u <- (I + sigma_k P)^{-1} (u + sigma_k P (A xbar - y))
+ *   x <- prox_{tau_k g}(x - tau_k A^H u),  xbar <- x + theta_k (x - x_old)
+ *   sigma_0 = 1, tau_0 = 1/lmax, theta_k = 1/(1 + 2 sigma_k min p),
+ *   sigma_{k+1} = theta_k sigma_k, tau_{k+1} = tau_k / theta_k;  x_0 = xbar_0 = 0, u_0 = 0.
+ * y_dev: [C][M] of type y_t.  p_dev: float32 [C][M]; NULL computes the multi-channel
+ * preconditioner first.  lmax <= 0 runs 30 power iterations from the all-ones image.
+ * x_dev: complex64 [N] output.  obj_trace: host double[iters] receiving F(x_k) after each
+ * iteration, or NULL (tracing adds a forward NUFFT per iteration).  stats: host or NULL.
+ * The iteration is replayed from a CUDA graph captured once per plan and regulariser.
+ * Synchronous.  Errors: KP_EINVAL (iters < 0, lambda < 0, wavelet levels 0 for l1,
+ * non-positive p or lmax found on the device), KP_ENONFINITE, KP_EDIVERGED. */
+kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev,
+                        kp_reg reg, float lambda, int iters, double lmax, void* x_dev,
+                        double* obj_trace, kp_stats* stats, void* stream);
+
+/* Periodised multilevel Daubechies-4 wavelet transform W (forward = 1) or W^H
+ * (forward = 0) of a complex64 [N] image, Mallat layout, plan's wavelet_levels.
+ * in_dev and out_dev may alias.  Asynchronous. */
+kp_status kp_wavelet(kp_plan plan, const void* in_dev, void* out_dev, int forward, void* stream);
+
+/* Profiling switch: when enable != 0, kp_pdhg_solve launches each iteration's kernels
+ * directly (no CUDA graph), records a CUDA event at every phase boundary on the caller's
+ * stream, and returns the per-phase GPU time in kp_stats.phase_ms. */
+kp_status kp_plan_set_profiling(kp_plan plan, int enable);
+
+/* Number of this library's own kernel launches issued through this plan so far (kernels
+ * inside replayed CUDA graphs included; cuFFT's kernels not included). */
+kp_status kp_plan_launch_count(kp_plan plan, int64_t* count);
+
+/* Number of grid tiles and the longest tile's sample count after kp_plan_set_trajectory
+ * (diagnostics for load balance). */
+kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_samples);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPDHG_H */

@@ -1,0 +1,201 @@
+"""Python binding of libkpdhg: a Plan object whose methods carry the C ABI's names.
+
+Every method only checks and marshals torch tensors (device pointers, sizes, the current
+CUDA stream) into one C call; all arithmetic runs in the library's CUDA kernels.
+Complex storage: torch.complex64 tensors map to KP_C64; float16 / bfloat16 tensors with a
+trailing dimension of 2 (re, im) map to KP_C32_FP16 / KP_C32_BF16.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _lib as L
+
+_REG = {"l2": L.KP_REG_L2, "l1_wavelet": L.KP_REG_L1_WAVELET}
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ctype_of(t: torch.Tensor):
+    if t.dtype == torch.complex64:
+        return L.KP_C64
+    if t.dtype == torch.float16 and t.shape[-1] == 2:
+        return L.KP_C32_FP16
+    if t.dtype == torch.bfloat16 and t.shape[-1] == 2:
+        return L.KP_C32_BF16
+    raise TypeError(f"unsupported complex storage {t.dtype} {tuple(t.shape)}")
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def to_storage(t: torch.Tensor, kind: str) -> torch.Tensor:
+    """complex64 -> storage tensor of the given kind ('c64', 'bf16', 'fp16')."""
+    if kind == "c64":
+        return t.to(torch.complex64).contiguous()
+    r = torch.view_as_real(t.to(torch.complex64).contiguous())
+    return r.to(torch.bfloat16 if kind == "bf16" else torch.float16).contiguous()
+
+
+class Plan:
+    """A reconstruction plan for one image size, coil count and sample count (kp_plan)."""
+
+    def __init__(self, img_shape, ncoils, nsamples, oversamp=1.25, kernel_width=4, wavelet_levels=0,
+                 device="cuda"):
+        self.lib = L.load()
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.img_shape = tuple(int(n) for n in img_shape)
+        self.ncoils = int(ncoils)
+        self.nsamples = int(nsamples)
+        self.ndim = len(self.img_shape)
+        prm = L.KpParams()
+        prm.ndim = self.ndim
+        for d, n in enumerate(self.img_shape):
+            prm.img[d] = n
+        prm.ncoils = self.ncoils
+        prm.nsamples = self.nsamples
+        prm.oversamp = float(oversamp)
+        prm.kernel_width = int(kernel_width)
+        prm.wavelet_levels = int(wavelet_levels)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.kp_plan_create(ctypes.byref(self._h), ctypes.byref(prm), _stream(self.device)),
+                    "kp_plan_create")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.kp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, t, name):
+        if not t.is_cuda or t.device != self.device:
+            raise ValueError(f"{name} must be on {self.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    @property
+    def N(self):
+        return math.prod(self.img_shape)
+
+    # -------------------------------------------------------------- set-up
+    def set_trajectory(self, traj):
+        """traj: float32 [M, ndim] in cycles/FOV on the plan's device."""
+        t = self._dev(traj, "traj")
+        if t.dtype != torch.float32 or tuple(t.shape) != (self.nsamples, self.ndim):
+            raise ValueError("traj must be float32 [M, ndim]")
+        L.check(self.lib.kp_plan_set_trajectory(self._h, _ptr(t), _stream(self.device)), "kp_plan_set_trajectory")
+        return self
+
+    def set_maps(self, maps):
+        """maps: [C, *img] complex64, or [C, *img, 2] float16/bfloat16."""
+        m = self._dev(maps, "maps")
+        kind = _ctype_of(m)
+        L.check(self.lib.kp_plan_set_maps(self._h, _ptr(m), kind, _stream(self.device)), "kp_plan_set_maps")
+        self._maps_ref = m
+        return self
+
+    def set_profiling(self, enable=True):
+        L.check(self.lib.kp_plan_set_profiling(self._h, int(bool(enable))), "kp_plan_set_profiling")
+        return self
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        L.check(self.lib.kp_plan_launch_count(self._h, ctypes.byref(n)), "kp_plan_launch_count")
+        return n.value
+
+    def tile_stats(self):
+        nt, mx = ctypes.c_int64(), ctypes.c_int64()
+        L.check(self.lib.kp_plan_tile_stats(self._h, ctypes.byref(nt), ctypes.byref(mx)), "kp_plan_tile_stats")
+        return nt.value, mx.value
+
+    # -------------------------------------------------------------- operators
+    def sense_forward(self, x, out=None, storage="c64"):
+        """y = A x: x complex64 [*img] -> y [C, M] (complex64 or half storage)."""
+        x = self._dev(x, "x")
+        if x.dtype != torch.complex64 or x.numel() != self.N:
+            raise ValueError("x must be complex64 of the image size")
+        if out is None:
+            if storage == "c64":
+                out = torch.empty((self.ncoils, self.nsamples), dtype=torch.complex64, device=self.device)
+            else:
+                dt = torch.bfloat16 if storage == "bf16" else torch.float16
+                out = torch.empty((self.ncoils, self.nsamples, 2), dtype=dt, device=self.device)
+        self._dev(out, "out")
+        L.check(self.lib.kp_sense_forward(self._h, _ptr(x), _ptr(out), _ctype_of(out), _stream(self.device)),
+                "kp_sense_forward")
+        return out
+
+    def sense_adjoint(self, y, out=None):
+        """x = A^H y: y [C, M] -> complex64 [*img]."""
+        y = self._dev(y, "y")
+        if out is None:
+            out = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
+        self._dev(out, "out")
+        L.check(self.lib.kp_sense_adjoint(self._h, _ptr(y), _ctype_of(y), _ptr(out), _stream(self.device)),
+                "kp_sense_adjoint")
+        return out
+
+    def make_preconditioner(self, multichannel=True, out=None):
+        """Diagonal k-space preconditioner p [C, M] float32 (multi- or single-channel)."""
+        if out is None:
+            out = torch.empty((self.ncoils, self.nsamples), dtype=torch.float32, device=self.device)
+        self._dev(out, "out")
+        L.check(self.lib.kp_make_preconditioner(self._h, int(bool(multichannel)), _ptr(out), _stream(self.device)),
+                "kp_make_preconditioner")
+        return out
+
+    def max_eig(self, p=None, v0=None, iters=30):
+        """lambda_max(P A A^H) by the power method."""
+        lm = ctypes.c_double()
+        pp = _ptr(self._dev(p, "p")) if p is not None else None
+        vv = _ptr(self._dev(v0, "v0")) if v0 is not None else None
+        L.check(self.lib.kp_max_eig(self._h, pp, vv, int(iters), ctypes.byref(lm), _stream(self.device)),
+                "kp_max_eig")
+        return lm.value
+
+    def wavelet(self, x, forward=True, out=None):
+        x = self._dev(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        L.check(self.lib.kp_wavelet(self._h, _ptr(x), _ptr(out), int(bool(forward)), _stream(self.device)),
+                "kp_wavelet")
+        return out
+
+    def pdhg_solve(self, y, p=None, reg="l2", lam=0.0, iters=30, lmax=0.0, trace=False, out=None):
+        """Preconditioned PDHG.  y may live on the host (it is then copied in, and x copied
+        back to the host).  Returns (x, objective trace or None, stats dict)."""
+        host = not y.is_cuda
+        yd = y.to(self.device, non_blocking=True) if host else y
+        self._dev(yd, "y")
+        pd = None
+        if p is not None:
+            pd = p.to(self.device, non_blocking=True) if not p.is_cuda else p
+            self._dev(pd, "p")
+        x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device) if out is None or host else out
+        tr = (ctypes.c_double * max(int(iters), 1))() if trace else None
+        st = L.KpStats()
+        status = self.lib.kp_pdhg_solve(self._h, _ptr(yd), _ctype_of(yd), _ptr(pd) if pd is not None else None,
+                                        _REG[reg], float(lam), int(iters), float(lmax), _ptr(x),
+                                        tr, ctypes.byref(st), _stream(self.device))
+        L.check(status, "kp_pdhg_solve")
+        if host:
+            x = x.to("cpu")
+        stats = dict(iters=st.iters, lmax=st.lmax, pmin=st.pmin, sigma_last=st.sigma_last,
+                     tau_last=st.tau_last, final_obj=st.final_obj,
+                     phase_ms={n: st.phase_ms[i] for i, n in enumerate(L.PHASES)})
+        return x, (list(tr)[: int(iters)] if trace else None), stats

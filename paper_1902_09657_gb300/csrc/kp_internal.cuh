@@ -1,0 +1,214 @@
+// Internal declarations shared by the CUDA translation units of libkpdhg.
+// Nothing here is part of the C ABI (include/kpdhg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/kpdhg.h"
+
+namespace kp {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+
+#define KP_TRY_CUDA(expr)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::kp::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+            return e_ == cudaErrorMemoryAllocation ? KP_ENOMEM : KP_ECUDA;         \
+        }                                                                          \
+    } while (0)
+
+#define KP_TRY_CUFFT(expr)                                                         \
+    do {                                                                           \
+        cufftResult r_ = (expr);                                                   \
+        if (r_ != CUFFT_SUCCESS) {                                                 \
+            ::kp::set_error(std::string(#expr) + ": cufft error " + std::to_string((int)r_)); \
+            return KP_ECUFFT;                                                      \
+        }                                                                          \
+    } while (0)
+
+#define KP_TRY(expr)                                                               \
+    do {                                                                           \
+        kp_status s_ = (expr);                                                     \
+        if (s_ != KP_OK) return s_;                                                \
+    } while (0)
+
+#define KP_LAUNCH_CHECK() KP_TRY_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- geometry
+constexpr int KW = 4;                // Kaiser-Bessel width supported by the kernels
+constexpr int MAXD = 3;
+
+// Geometry of one NUFFT operator, passed by value to kernels.  Arrays are indexed by
+// the *active* axes 0..D-1 (slowest first); 2D problems use D = 2.
+struct Geom {
+    int D;
+    int C;
+    int64_t M;
+    int n[MAXD];         // image size per axis
+    int g[MAXD];         // oversampled grid size per axis
+    float beta[MAXD];    // Kaiser-Bessel shape per axis
+    int64_t N;           // prod n
+    int64_t G;           // prod g
+    float rsqrtN;        // N^{-1/2}
+};
+
+// Spreading tiles: the grid is cut into tiles of ts[d] points per axis (edge tiles smaller).
+struct Tiles {
+    int ts[MAXD];
+    int nt[MAXD];        // tiles per axis
+    int64_t ntiles;
+};
+
+// ---------------------------------------------------------------- complex storage helpers
+__host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline float2 cmulc(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } // conj(a)*b
+
+template <typename T> __device__ inline float2 ldc(const T* p, size_t i);
+template <> __device__ inline float2 ldc<float2>(const float2* p, size_t i) { return p[i]; }
+template <> __device__ inline float2 ldc<__half2>(const __half2* p, size_t i) { return __half22float2(p[i]); }
+template <> __device__ inline float2 ldc<__nv_bfloat162>(const __nv_bfloat162* p, size_t i) { return __bfloat1622float2(p[i]); }
+
+template <typename T> __device__ inline void stc(T* p, size_t i, float2 v);
+template <> __device__ inline void stc<float2>(float2* p, size_t i, float2 v) { p[i] = v; }
+template <> __device__ inline void stc<__half2>(__half2* p, size_t i, float2 v) { p[i] = __float22half2_rn(v); }
+template <> __device__ inline void stc<__nv_bfloat162>(__nv_bfloat162* p, size_t i, float2 v) { p[i] = __float22bfloat162_rn(v); }
+
+inline size_t cdtype_bytes(kp_cdtype t) { return t == KP_C64 ? 8 : 4; }
+
+// ---------------------------------------------------------------- plan
+struct PrePlan;   // preconditioner workspace (kp_precond.cu)
+
+// Phases of one PDHG iteration, for event-based profiling (kp_plan_set_profiling).
+enum Phase { PH_FWD_PRE = 0, PH_FFT_FWD, PH_INTERP, PH_SPREAD, PH_SPREAD_RED, PH_FFT_INV, PH_ADJ, PH_DWT_FWD,
+             PH_SOFT, PH_DWT_INV, PH_EXTRAP, PH_OTHER, PH_N };
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int reg = -1;            // regulariser * 4 + measurement storage type
+    float lambda = -1.f;
+    int64_t n_items = -1;
+    int64_t launches = 0;    // own kernels per replay
+};
+
+}  // namespace kp
+
+struct kp_plan_s {
+    kp_params P;
+    kp::Geom geo;
+    kp::Tiles tiles;
+    bool unit_maps = false;          // s_c = 1 (used by the preconditioner's internal plans)
+    bool traj_set = false;
+    bool maps_set = false;
+    kp_cdtype maps_t = KP_C64;       // storage type of d_maps
+
+    // trajectory (sorted by tile)
+    float* d_t = nullptr;            // [D][M] grid coordinates t = f * g/n, sorted order
+    int* d_perm = nullptr;           // sorted position -> original sample index
+    int* d_key = nullptr;            // [M] tile key per original sample (scratch)
+    int* d_cnt = nullptr;            // [ntiles + 1]
+    int* d_off = nullptr;            // [ntiles + 1] exclusive scan of tile counts
+    int* d_ext_off = nullptr;        // [ntiles + 1] spreading lists: offsets
+    int* d_ext = nullptr;            // [M * 2^D] spreading lists: sorted sample positions
+    int* d_flag = nullptr;           // [4] device status words
+    int64_t max_tile = 0;
+    // spreading work items: {tile, begin, end, partial slot or -1}
+    int4* d_items = nullptr;
+    int64_t n_items = 0, items_cap = 0;
+    int* d_item_off = nullptr;       // [ntiles + 1]
+    int* d_slot_off = nullptr;       // [ntiles + 1] first partial slot of each split tile
+    int* d_nslots = nullptr;         // [ntiles + 1] partial slots per tile (0 = not split)
+    float2* d_partial = nullptr;     // [slots][C][tile points]
+    int64_t n_slots = 0;
+    size_t partial_cap = 0;
+    int chunk = 256;                 // samples per spreading work item
+
+    // operator data
+    void* d_maps = nullptr;          // [C][N] in maps_t storage
+    float* d_apod = nullptr;         // [sum n_d] 1/Phi_d(n_d) per axis
+    float2* d_grid = nullptr;        // [C][G] work grid
+    cufftHandle fft = 0;
+    bool fft_ok = false;
+
+    // solver state (sorted k-space order)
+    float2* d_u = nullptr;           // [C][M] dual variable
+    void* d_ys = nullptr;            // [C][M] sorted measurements (storage ys_t)
+    kp_cdtype ys_t = KP_C64;
+    float* d_ps = nullptr;           // [C][M] sorted preconditioner
+    float* d_puser = nullptr;        // [C][M] preconditioner in user order (when computed here)
+    float* d_f = nullptr;            // [M][D] copy of the trajectory (cycles/FOV), user order
+    int traj_version = 0;
+    float2* d_kt = nullptr;          // [C][M] scratch k-space (objective / power method)
+    float2* d_x = nullptr;           // [N] primal
+    float2* d_xbar = nullptr;        // [N] extrapolated primal
+    float2* d_z = nullptr;           // [N] prox input / wavelet work
+    float2* d_w = nullptr;           // [N] scratch image
+    double* d_red = nullptr;         // [8] reductions
+    float* d_sched = nullptr;        // [3 * cap] sigma, tau, theta per iteration
+    double* d_schedd = nullptr;      // [4] lmax, pmin, sigma_last, tau_last
+    int* d_iter = nullptr;           // iteration counter read by the captured graph
+    int sched_cap = 0;
+
+    // wavelet
+    float h[8];                      // Daubechies-4 scaling filter (host copy)
+
+    kp::Graph graphs[2];
+    // profiling: when on, PDHG runs without the graph and records an event at each phase
+    bool profiling = false;
+    cudaEvent_t* ev = nullptr;
+    int* ev_phase = nullptr;
+    int ev_cap = 0, ev_used = 0;
+    int64_t launches = 0;            // own kernel launches issued (graph replays included)
+    kp::PrePlan* pre = nullptr;
+    kp_plan_s* pre_nufft = nullptr;  // NUFFT plan on the 2N image (preconditioner)
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace kp {
+
+// Record a phase boundary when profiling (no-op otherwise).
+inline void mark(kp_plan p, int phase, cudaStream_t st) {
+    if (!p->profiling || p->ev_used >= p->ev_cap) return;
+    cudaEventRecord(p->ev[p->ev_used], st);
+    p->ev_phase[p->ev_used] = phase;
+    p->ev_used++;
+}
+
+// kp_plan.cu
+kp_status plan_create_internal(kp_plan* out, const kp_params* params, bool unit_maps, cudaStream_t st);
+kp_status plan_destroy_internal(kp_plan p);
+kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale, cudaStream_t st);
+
+// kp_nufft.cu
+// A x: x [N] complex64 -> out [C][M].  Output in sorted order (perm == nullptr) or user
+// order.  mode 0: plain; 1: multiply by p (sorted order); 2: PDHG dual update (uses p, y,
+// sched, iter).
+kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, const int* perm, cudaStream_t st);
+kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st);
+kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st);
+// A^H u: u [C][M] (sorted order if perm == nullptr, else user order) -> grid -> x.
+kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st);
+kp_status grid_to_image(kp_plan p, float2* x, cudaStream_t st);
+kp_status adjoint_primal(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st);
+
+// kp_pdhg.cu
+kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st);
+void daubechies4(float h[8]);
+kp_status upload_wavelet_filter(const float h[8]);
+void drop_graphs(kp_plan p);
+
+// kp_precond.cu
+void pre_destroy(kp_plan p);
+
+}  // namespace kp

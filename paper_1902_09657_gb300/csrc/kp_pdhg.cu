@@ -1,0 +1,616 @@
+// Preconditioned PDHG (Sec. 4.1), the power method for lambda_max(P A A^H) (Sec. 6) and the
+// periodised Daubechies-4 wavelet W used by the l1 prox (Sec. 2, Sec. 6).
+//
+// One PDHG iteration = fwd_pre -> FFT -> interp+dual (u update) -> spread -> IFFT ->
+// adj+primal (z = x - tau A^H u; l2 prox and extrapolation fused) [-> DWT -> soft -> IDWT ->
+// extrapolate for l1] -> advance the device iteration counter.  The step sizes
+// sigma_k, tau_k, theta_k are computed on the device in float64 from lambda_max and
+// min p, so one captured CUDA graph replays every iteration.
+#include "kp_internal.cuh"
+
+#include <cmath>
+#include <complex>
+#include <vector>
+
+namespace kp {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ================================================================ Daubechies-4 filter
+// Extremal-phase Daubechies scaling filter with 4 vanishing moments, by spectral
+// factorisation: the roots y_r of P(y) = 1 + 4y + 10y^2 + 20y^3 map to z_r with
+// z + 1/z = 2 - 4 y_r, |z_r| < 1; H(z) ~ (1 + z^{-1})^4 prod_r (1 - z_r z^{-1}), sum h = sqrt(2).
+void daubechies4(float hout[8]) {
+    using cd = std::complex<double>;
+    const double pc[4] = {1.0, 4.0, 10.0, 20.0};          // ascending powers of y
+    // Durand-Kerner iteration on the monic cubic y^3 + (10/20) y^2 + (4/20) y + 1/20.
+    auto P = [&](cd y) { return ((y + pc[2] / pc[3]) * y + pc[1] / pc[3]) * y + pc[0] / pc[3]; };
+    cd r[3] = {cd(0.4, 0.9), cd(0.4, 0.9) * cd(0.4, 0.9), cd(0.4, 0.9) * cd(0.4, 0.9) * cd(0.4, 0.9)};
+    for (int it = 0; it < 500; ++it) {
+        for (int i = 0; i < 3; ++i) {
+            cd den = 1.0;
+            for (int j = 0; j < 3; ++j)
+                if (j != i) den *= r[i] - r[j];
+            r[i] -= P(r[i]) / den;
+        }
+    }
+    std::vector<cd> poly = {1.0};
+    auto mul = [&](cd a0, cd a1) {           // poly *= (a0 + a1 z^{-1})
+        std::vector<cd> out(poly.size() + 1, 0.0);
+        for (size_t k = 0; k < poly.size(); ++k) {
+            out[k] += a0 * poly[k];
+            out[k + 1] += a1 * poly[k];
+        }
+        poly.swap(out);
+    };
+    for (int k = 0; k < 4; ++k) mul(1.0, 1.0);
+    for (int i = 0; i < 3; ++i) {
+        cd b = 2.0 - 4.0 * r[i];
+        cd disc = std::sqrt(b * b - 4.0);
+        cd z1 = (b + disc) / 2.0, z2 = (b - disc) / 2.0;
+        cd z = std::abs(z1) < 1.0 ? z1 : z2;
+        mul(1.0, -z);
+    }
+    double sum = 0;
+    for (int k = 0; k < 8; ++k) sum += poly[k].real();
+    for (int k = 0; k < 8; ++k) hout[k] = (float)(poly[k].real() * std::sqrt(2.0) / sum);
+}
+
+__constant__ float c_h[8];
+__constant__ float c_g[8];
+
+// Analysis filters: scaling h and wavelet g[n] = (-1)^n h[7 - n].
+kp_status upload_wavelet_filter(const float h[8]) {
+    float g[8];
+    for (int n = 0; n < 8; ++n) g[n] = (n & 1 ? -1.f : 1.f) * h[7 - n];
+    KP_TRY_CUDA(cudaMemcpyToSymbol(c_h, h, 8 * sizeof(float)));
+    KP_TRY_CUDA(cudaMemcpyToSymbol(c_g, g, 8 * sizeof(float)));
+    return KP_OK;
+}
+
+// ================================================================ wavelet line kernels
+constexpr int WV = 16;   // lines per CTA
+
+struct WLine {
+    int D;
+    int n[MAXD];     // full image size
+    int b[MAXD];     // current block (approximation) size
+    int axis;
+    int64_t nlines;  // prod_{d != axis} b[d]
+};
+
+__device__ __forceinline__ int64_t line_start(const WLine& wl, int64_t li) {
+    // coordinates over the non-axis dims, last dim fastest
+    int64_t flat = 0, stride = 1;
+    int64_t r = li;
+    for (int d = wl.D - 1; d >= 0; --d) {
+        if (d != wl.axis) {
+            int c = (int)(r % wl.b[d]);
+            r /= wl.b[d];
+            flat += c * stride;
+        }
+        stride *= wl.n[d];
+    }
+    return flat;
+}
+
+template <bool FWD>
+__global__ void k_dwt_axis(float2* __restrict__ img, WLine wl) {
+    extern __shared__ float2 sl[];   // [WV][L]
+    const int L = wl.b[wl.axis];
+    int64_t sa = 1;
+    for (int d = wl.axis + 1; d < wl.D; ++d) sa *= wl.n[d];
+    const bool inner = wl.axis == wl.D - 1;
+    const int64_t l0 = (int64_t)blockIdx.x * WV;
+    const int nthr = blockDim.x;
+    // load
+    for (int idx = threadIdx.x; idx < WV * L; idx += nthr) {
+        int v, l;
+        if (inner) { v = idx / L; l = idx % L; }
+        else { l = idx / WV; v = idx % WV; }
+        int64_t li = l0 + v;
+        if (li < wl.nlines) sl[v * L + l] = img[line_start(wl, li) + l * sa];
+    }
+    __syncthreads();
+    const int K = L / 2;
+    if (FWD) {
+        for (int idx = threadIdx.x; idx < WV * K; idx += nthr) {
+            int v, k;
+            if (inner) { v = idx / K; k = idx % K; }
+            else { k = idx / WV; v = idx % WV; }
+            int64_t li = l0 + v;
+            if (li >= wl.nlines) continue;
+            const float2* s = sl + v * L;
+            float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                int q = (2 * k + n) % L;
+                float2 xv = s[q];
+                a.x = fmaf(c_h[n], xv.x, a.x);
+                a.y = fmaf(c_h[n], xv.y, a.y);
+                d.x = fmaf(c_g[n], xv.x, d.x);
+                d.y = fmaf(c_g[n], xv.y, d.y);
+            }
+            int64_t st = line_start(wl, li);
+            img[st + k * sa] = a;
+            img[st + (K + k) * sa] = d;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < WV * L; idx += nthr) {
+            int v, j;
+            if (inner) { v = idx / L; j = idx % L; }
+            else { j = idx / WV; v = idx % WV; }
+            int64_t li = l0 + v;
+            if (li >= wl.nlines) continue;
+            const float2* s = sl + v * L;
+            float2 x = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                int n = (j & 1) + 2 * m;
+                int jm = ((j - n) % L + L) % L;
+                int k = jm >> 1;
+                float2 av = s[k], dv = s[K + k];
+                x.x = fmaf(c_h[n], av.x, fmaf(c_g[n], dv.x, x.x));
+                x.y = fmaf(c_h[n], av.y, fmaf(c_g[n], dv.y, x.y));
+            }
+            img[line_start(wl, li) + j * sa] = x;
+        }
+    }
+}
+
+kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const int levels = p->P.wavelet_levels;
+    if (in != out) KP_TRY_CUDA(cudaMemcpyAsync(out, in, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    static bool attr = false;
+    if (!attr) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_axis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_axis<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    auto pass = [&](int lev, int axis, bool fwd) -> kp_status {
+        WLine wl{};
+        wl.D = g.D;
+        wl.axis = axis;
+        wl.nlines = 1;
+        for (int d = 0; d < g.D; ++d) {
+            wl.n[d] = g.n[d];
+            wl.b[d] = g.n[d] >> lev;
+            if (d != axis) wl.nlines *= wl.b[d];
+        }
+        const int L = wl.b[axis];
+        const size_t smem = (size_t)WV * L * sizeof(float2);
+        const unsigned blocks = (unsigned)((wl.nlines + WV - 1) / WV);
+        if (fwd) k_dwt_axis<true><<<blocks, 256, smem, st>>>(out, wl);
+        else k_dwt_axis<false><<<blocks, 256, smem, st>>>(out, wl);
+        KP_LAUNCH_CHECK();
+        p->launches += 1;
+        return KP_OK;
+    };
+    mark(p, forward ? PH_DWT_FWD : PH_DWT_INV, st);
+    if (forward) {
+        for (int lev = 0; lev < levels; ++lev)
+            for (int ax = 0; ax < g.D; ++ax) KP_TRY(pass(lev, ax, true));
+    } else {
+        for (int lev = levels - 1; lev >= 0; --lev)
+            for (int ax = g.D - 1; ax >= 0; --ax) KP_TRY(pass(lev, ax, false));
+    }
+    return KP_OK;
+}
+
+// ================================================================ reductions and small kernels
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// out += sum of f(i) over i < n  (blocks of 256 threads)
+template <typename F>
+__device__ __forceinline__ void block_sum_to(double v, double* out) {
+    __shared__ double ws[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) atomicAdd(out, v);
+    }
+}
+
+__global__ void k_norm2(const float2* __restrict__ x, int64_t n, double* __restrict__ out) {
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = x[i];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    block_sum_to<int>(s, out);
+}
+
+__global__ void k_sumabs(const float2* __restrict__ x, int64_t n, double* __restrict__ out) {
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = x[i];
+        s += sqrt((double)v.x * v.x + (double)v.y * v.y);
+    }
+    block_sum_to<int>(s, out);
+}
+
+template <typename YT>
+__global__ void k_resid2(const float2* __restrict__ a, const YT* __restrict__ y, int64_t n, double* __restrict__ out) {
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = a[i];
+        float2 w = ldc<YT>(y, i);
+        double dx = (double)v.x - w.x, dy = (double)v.y - w.y;
+        s += dx * dx + dy * dy;
+    }
+    block_sum_to<int>(s, out);
+}
+
+// min over positive p (as int bits) and count of non-positive / non-finite entries
+__global__ void k_pmin(const float* __restrict__ p, int64_t n, int* __restrict__ minbits, int* __restrict__ bad) {
+    int m = 0x7f7fffff;
+    int nb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = p[i];
+        if (!(v > 0.f) || !isfinite(v)) ++nb;
+        else m = min(m, __float_as_int(v));
+    }
+    atomicMin(minbits, m);
+    if (nb) atomicAdd(bad, nb);
+}
+
+// v <- w / ||w||; lmax <- ||w|| (power method step, ||v_prev|| = 1)
+__global__ void k_normalize(const float2* __restrict__ w, float2* __restrict__ v, int64_t n,
+                            const double* __restrict__ n2, double* __restrict__ lmax_out) {
+    const double nrm = sqrt(*n2);
+    const float inv = nrm > 0 ? (float)(1.0 / nrm) : 0.f;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && lmax_out) *lmax_out = nrm;
+    if (i < n) {
+        float2 a = w[i];
+        v[i] = make_float2(a.x * inv, a.y * inv);
+    }
+}
+
+// Step sizes (Sec. 4.1): sigma_0 = 1, tau_0 = 1/L, theta_k = 1/(1 + 2 sigma_k pmin),
+// sigma_{k+1} = theta_k sigma_k, tau_{k+1} = tau_k / theta_k; float64 recursion.
+// schedd: [0] L, [1] pmin (written here from minbits), [2] sigma_last, [3] tau_last.
+__global__ void k_schedule(double* __restrict__ schedd, const int* __restrict__ minbits, int iters,
+                           float* __restrict__ sched, int* __restrict__ flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double L = schedd[0];
+    const double pmin = minbits ? (double)__int_as_float(*minbits) : schedd[1];
+    schedd[1] = pmin;
+    if (!(L > 0) || !isfinite(L) || !(pmin > 0) || !isfinite(pmin)) {
+        flag[0] = 1;
+        for (int k = 0; k < iters; ++k) { sched[3 * k] = 0.f; sched[3 * k + 1] = 0.f; sched[3 * k + 2] = 0.f; }
+        return;
+    }
+    double sig = 1.0, tau = 1.0 / L;
+    for (int k = 0; k < iters; ++k) {
+        const double th = 1.0 / (1.0 + 2.0 * sig * pmin);
+        sched[3 * k] = (float)sig;
+        sched[3 * k + 1] = (float)tau;
+        sched[3 * k + 2] = (float)th;
+        sig *= th;
+        tau /= th;
+    }
+    schedd[2] = sig;
+    schedd[3] = tau;
+}
+
+__global__ void k_advance(int* iter) { *iter += 1; }
+
+// complex soft threshold at tau_k * lambda (Sec. 2: prox of lambda ||W x||_1)
+__global__ void k_soft(float2* __restrict__ z, int64_t n, const float* __restrict__ sched,
+                       const int* __restrict__ iter, float lambda) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float t = sched[3 * (*iter) + 1] * lambda;
+    float2 c = z[i];
+    float m = sqrtf(c.x * c.x + c.y * c.y);
+    float s = m > t ? 1.f - t / m : 0.f;
+    z[i] = make_float2(c.x * s, c.y * s);
+}
+
+// x_new = z; xbar = x_new + theta (x_new - x); x = x_new (Sec. 4.1 extrapolation)
+__global__ void k_extrap(const float2* __restrict__ z, float2* __restrict__ x, float2* __restrict__ xbar, int64_t n,
+                         const float* __restrict__ sched, const int* __restrict__ iter) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float th = sched[3 * (*iter) + 2];
+    float2 xn = z[i], xo = x[i];
+    xbar[i] = make_float2(xn.x + th * (xn.x - xo.x), xn.y + th * (xn.y - xo.y));
+    x[i] = xn;
+}
+
+template <typename T>
+__global__ void k_permute(const T* __restrict__ in, T* __restrict__ out, const int* __restrict__ perm, int64_t M, int C) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const int64_t o = perm[s];
+    for (int c = 0; c < C; ++c) out[(size_t)c * M + s] = in[(size_t)c * M + o];
+}
+
+// ================================================================ host drivers
+static kp_status reduce_norm2(kp_plan p, const float2* x, int64_t n, double* out, cudaStream_t st) {
+    KP_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+    k_norm2<<<(unsigned)std::min<int64_t>(nblk(n, 256), 1216), 256, 0, st>>>(x, n, out);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    return KP_OK;
+}
+
+// Power method on A^H P A (Sec. 6: 30 iterations) using the sorted p in d_ps (or none).
+// Start vector in d_z (unnormalised); result L in d_schedd[0].
+static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cudaStream_t st) {
+    const Geom& g = p->geo;
+    KP_TRY(reduce_norm2(p, p->d_z, g.N, p->d_red, st));
+    k_normalize<<<nblk(g.N, 256), 256, 0, st>>>(p->d_z, p->d_z, g.N, p->d_red, nullptr);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    for (int it = 0; it < iters; ++it) {
+        KP_TRY(forward_scaled(p, p->d_z, p->d_kt, ps_sorted, st));
+        KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st));
+        KP_TRY(grid_to_image(p, p->d_w, st));
+        KP_TRY(reduce_norm2(p, p->d_w, g.N, p->d_red, st));
+        k_normalize<<<nblk(g.N, 256), 256, 0, st>>>(p->d_w, p->d_z, g.N, p->d_red, p->d_schedd);
+        KP_LAUNCH_CHECK();
+        p->launches += 1;
+    }
+    return KP_OK;
+}
+
+static kp_status issue_iteration(kp_plan p, int reg, float lambda, cudaStream_t st) {
+    const Geom& g = p->geo;
+    KP_TRY(forward_dual(p, p->d_xbar, st));
+    KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st));
+    KP_TRY(adjoint_primal(p, reg, lambda, st));
+    if (reg == KP_REG_L1_WAVELET) {
+        KP_TRY(wavelet_apply(p, p->d_z, p->d_z, true, st));
+        mark(p, PH_SOFT, st);
+        k_soft<<<nblk(g.N, 256), 256, 0, st>>>(p->d_z, g.N, p->d_sched, p->d_iter, lambda);
+        KP_LAUNCH_CHECK();
+        KP_TRY(wavelet_apply(p, p->d_z, p->d_z, false, st));
+        mark(p, PH_EXTRAP, st);
+        k_extrap<<<nblk(g.N, 256), 256, 0, st>>>(p->d_z, p->d_x, p->d_xbar, g.N, p->d_sched, p->d_iter);
+        KP_LAUNCH_CHECK();
+        p->launches += 2;
+    }
+    mark(p, PH_OTHER, st);
+    k_advance<<<1, 1, 0, st>>>(p->d_iter);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    return KP_OK;
+}
+
+static void drop_graph(Graph& gr) {
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (gr.graph) cudaGraphDestroy(gr.graph);
+    gr.exec = nullptr;
+    gr.graph = nullptr;
+}
+
+void drop_graphs(kp_plan p) {
+    for (auto& gr : p->graphs) drop_graph(gr);
+}
+
+// Capture one iteration on the plan's private stream; replay it on the caller's stream.
+static kp_status get_graph(kp_plan p, int reg, float lambda, Graph** out) {
+    Graph& gr = p->graphs[reg];
+    const int key = (int)p->ys_t * 4 + reg;
+    if (gr.exec && gr.reg == key && gr.lambda == lambda && gr.n_items == p->n_items) { *out = &gr; return KP_OK; }
+    drop_graph(gr);
+    cudaStream_t cs = p->cap_stream;
+    const int64_t before = p->launches;
+    KP_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    kp_status s = issue_iteration(p, reg, lambda, cs);
+    gr.launches = p->launches - before;
+    p->launches = before;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (s != KP_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    KP_TRY_CUDA(e);
+    gr.graph = graph;
+    KP_TRY_CUDA(cudaGraphInstantiate(&gr.exec, graph, 0));
+    gr.reg = key;
+    gr.lambda = lambda;
+    gr.n_items = p->n_items;
+    *out = &gr;
+    return KP_OK;
+}
+
+static kp_status objective(kp_plan p, int reg, float lambda, double* F, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const int64_t CM = (int64_t)g.C * g.M;
+    KP_TRY(forward_to(p, p->d_x, p->d_kt, KP_C64, nullptr, st));
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_red + 1, 0, 2 * sizeof(double), st));
+    const unsigned b = (unsigned)std::min<int64_t>(nblk(CM, 256), 1216);
+    switch (p->ys_t) {
+        case KP_C64: k_resid2<float2><<<b, 256, 0, st>>>(p->d_kt, (const float2*)p->d_ys, CM, p->d_red + 1); break;
+        case KP_C32_BF16: k_resid2<__nv_bfloat162><<<b, 256, 0, st>>>(p->d_kt, (const __nv_bfloat162*)p->d_ys, CM, p->d_red + 1); break;
+        default: k_resid2<__half2><<<b, 256, 0, st>>>(p->d_kt, (const __half2*)p->d_ys, CM, p->d_red + 1); break;
+    }
+    KP_LAUNCH_CHECK();
+    const unsigned bn = (unsigned)std::min<int64_t>(nblk(g.N, 256), 1216);
+    if (reg == KP_REG_L2) {
+        k_norm2<<<bn, 256, 0, st>>>(p->d_x, g.N, p->d_red + 2);
+    } else {
+        KP_TRY(wavelet_apply(p, p->d_x, p->d_w, true, st));
+        k_sumabs<<<bn, 256, 0, st>>>(p->d_w, g.N, p->d_red + 2);
+    }
+    KP_LAUNCH_CHECK();
+    double h[2];
+    KP_TRY_CUDA(cudaMemcpyAsync(h, p->d_red + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    *F = 0.5 * h[0] + (reg == KP_REG_L2 ? 0.5 * lambda * h[1] : lambda * h[1]);
+    return KP_OK;
+}
+
+static kp_status ensure_sched(kp_plan p, int iters) {
+    if (iters <= p->sched_cap) return KP_OK;
+    if (p->d_sched) cudaFree(p->d_sched);
+    p->d_sched = nullptr;
+    const int cap = std::max(iters, 128);
+    KP_TRY_CUDA(cudaMalloc(&p->d_sched, 3 * (size_t)cap * sizeof(float)));
+    p->sched_cap = cap;
+    for (auto& gr : p->graphs) drop_graph(gr);   // graphs bake the schedule pointer in
+    return KP_OK;
+}
+
+}  // namespace kp
+
+using namespace kp;
+
+extern "C" {
+
+kp_status kp_wavelet(kp_plan plan, const void* in_dev, void* out_dev, int forward, void* stream) {
+    if (!plan || !in_dev || !out_dev) { set_error("null argument"); return KP_EINVAL; }
+    if (plan->P.wavelet_levels < 1) { set_error("plan has wavelet_levels = 0"); return KP_EINVAL; }
+    return wavelet_apply(plan, (const float2*)in_dev, (float2*)out_dev, forward != 0, (cudaStream_t)stream);
+}
+
+kp_status kp_max_eig(kp_plan plan, const float* p_dev, const void* v0_dev, int iters, double* lmax, void* stream) {
+    if (!plan || !lmax) { set_error("null argument"); return KP_EINVAL; }
+    if (iters < 1) { set_error("iters must be >= 1"); return KP_EINVAL; }
+    if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geom& g = plan->geo;
+    if (p_dev) {
+        k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(p_dev, plan->d_ps, plan->d_perm, g.M, g.C);
+        KP_LAUNCH_CHECK();
+        plan->launches += 1;
+    }
+    if (v0_dev) KP_TRY_CUDA(cudaMemcpyAsync(plan->d_z, v0_dev, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    else { KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st)); plan->launches += 1; }
+    KP_TRY(power_method(plan, p_dev ? plan->d_ps : nullptr, iters, st));
+    KP_TRY_CUDA(cudaMemcpyAsync(lmax, plan->d_schedd, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (!(*lmax > 0) || !std::isfinite(*lmax)) { set_error("power method norm is zero or not finite"); return KP_ENONFINITE; }
+    return KP_OK;
+}
+
+static kp_status ensure_events(kp_plan p, int n) {
+    if (n <= p->ev_cap) return KP_OK;
+    for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
+    delete[] p->ev;
+    delete[] p->ev_phase;
+    p->ev = new cudaEvent_t[n];
+    p->ev_phase = new int[n];
+    p->ev_cap = 0;
+    for (int i = 0; i < n; ++i) {
+        KP_TRY_CUDA(cudaEventCreate(&p->ev[i]));
+        p->ev_cap = i + 1;
+    }
+    return KP_OK;
+}
+
+kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg, float lambda,
+                        int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats, void* stream) {
+    if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
+    if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
+    if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
+    if (!(lambda >= 0.f) || !std::isfinite(lambda)) { set_error("lambda must be finite and >= 0"); return KP_EINVAL; }
+    if (reg != KP_REG_L2 && reg != KP_REG_L1_WAVELET) { set_error("bad regulariser"); return KP_EINVAL; }
+    if (reg == KP_REG_L1_WAVELET && plan->P.wavelet_levels < 1) { set_error("l1-wavelet needs wavelet_levels >= 1"); return KP_EINVAL; }
+    if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geom& g = plan->geo;
+    KP_TRY(ensure_sched(plan, std::max(iters, 1)));
+    // measurements into sorted order
+    plan->ys_t = y_t;
+    if (y_t == KP_C64) k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>((const float2*)y_dev, (float2*)plan->d_ys, plan->d_perm, g.M, g.C);
+    else k_permute<unsigned><<<nblk(g.M, 256), 256, 0, st>>>((const unsigned*)y_dev, (unsigned*)plan->d_ys, plan->d_perm, g.M, g.C);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    // preconditioner
+    const float* pu = p_dev;
+    if (!pu) {
+        KP_TRY(kp_make_preconditioner(plan, 1, plan->d_puser, stream));
+        pu = plan->d_puser;
+    }
+    k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(pu, plan->d_ps, plan->d_perm, g.M, g.C);
+    KP_LAUNCH_CHECK();
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag, 0, 8 * sizeof(int), st));
+    {
+        static const int init = 0x7f7fffff;
+        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_flag + 4, &init, sizeof(int), cudaMemcpyHostToDevice, st));
+        const int64_t CM = (int64_t)g.C * g.M;
+        k_pmin<<<(unsigned)std::min<int64_t>(nblk(CM, 256), 1216), 256, 0, st>>>(plan->d_ps, CM, plan->d_flag + 4, plan->d_flag + 5);
+        KP_LAUNCH_CHECK();
+    }
+    plan->launches += 2;
+    // lambda_max(P A A^H)
+    if (lmax > 0) {
+        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_schedd, &lmax, sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+        KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st));
+        plan->launches += 1;
+        KP_TRY(power_method(plan, plan->d_ps, 30, st));
+    }
+    k_schedule<<<1, 1, 0, st>>>(plan->d_schedd, plan->d_flag + 4, std::max(iters, 1), plan->d_sched, plan->d_flag + 6);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    // x0 = xbar0 = 0, u0 = 0
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_x, 0, g.N * sizeof(float2), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
+    kp_status status = KP_OK;
+    double F0 = 0, F = NAN;
+    double phase_ms[PH_N] = {0};
+    if (iters > 0) {
+        Graph* gr = nullptr;
+        if (!plan->profiling) KP_TRY(get_graph(plan, (int)reg, lambda, &gr));
+        else KP_TRY(ensure_events(plan, 16 * PH_N + 2));
+        for (int k = 0; k < iters; ++k) {
+            if (gr) {
+                KP_TRY_CUDA(cudaGraphLaunch(gr->exec, st));
+                plan->launches += gr->launches;
+            } else {
+                // profiled iteration: direct launches with an event at every phase boundary
+                plan->ev_used = 0;
+                KP_TRY(issue_iteration(plan, (int)reg, lambda, st));
+                mark(plan, PH_N, st);
+                KP_TRY_CUDA(cudaEventSynchronize(plan->ev[plan->ev_used - 1]));
+                for (int e = 0; e + 1 < plan->ev_used; ++e) {
+                    float ms = 0.f;
+                    KP_TRY_CUDA(cudaEventElapsedTime(&ms, plan->ev[e], plan->ev[e + 1]));
+                    phase_ms[plan->ev_phase[e]] += ms;
+                }
+                plan->ev_used = 0;
+            }
+            if (obj_trace) {
+                KP_TRY(objective(plan, (int)reg, lambda, &F, st));
+                obj_trace[k] = F;
+                if (k == 0) F0 = F;
+                if (!std::isfinite(F)) { status = KP_ENONFINITE; break; }
+                if (k > 0 && F > 1e3 * F0 && F0 > 0) { status = KP_EDIVERGED; break; }
+            }
+        }
+    }
+    KP_TRY_CUDA(cudaMemcpyAsync(x_dev, plan->d_x, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    int flags[8];
+    double sd[4];
+    KP_TRY_CUDA(cudaMemcpyAsync(flags, plan->d_flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaMemcpyAsync(sd, plan->d_schedd, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->iters = iters;
+        stats->lmax = sd[0];
+        stats->pmin = sd[1];
+        stats->sigma_last = sd[2];
+        stats->tau_last = sd[3];
+        stats->final_obj = obj_trace ? F : NAN;
+        for (int i = 0; i < KP_NPHASES && i < PH_N; ++i) stats->phase_ms[i] = phase_ms[i];
+    }
+    if (flags[5] != 0) { set_error(std::to_string(flags[5]) + " preconditioner entries are not positive and finite"); return KP_EINVAL; }
+    if (flags[6] != 0) { set_error("lambda_max or min p is not positive and finite"); return KP_EINVAL; }
+    return status;
+}
+
+}  // extern "C"

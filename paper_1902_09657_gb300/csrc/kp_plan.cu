@@ -1,0 +1,492 @@
+// Plan life cycle, trajectory binning (counting sort by grid tile) and coil maps.
+//
+// The trajectory step converts each sample to grid coordinates t_d = f_d * (g_d / n_d)
+// (float32, Sec. 6 NUFFT with oversampling g/n), sorts samples by the grid tile that
+// holds their first Kaiser-Bessel tap, and builds, per tile, the list of samples whose
+// W^D footprint touches that tile (used by the spreading kernel, which owns one output
+// tile per CTA and therefore needs no global atomics and no zero-fill of the grid).
+#include "kp_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace kp {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ int wrap(int k, int g) { return k < 0 ? k + g : (k >= g ? k - g : k); }
+
+// Single-CTA exclusive scan of n ints: out[0..n] (out[n] = total).
+__global__ void k_scan_excl(const int* __restrict__ in, int* __restrict__ out, int64_t n) {
+    __shared__ long long part[1024];
+    const int T = blockDim.x;
+    const int64_t per = (n + T - 1) / T;
+    const int64_t beg = (int64_t)threadIdx.x * per;
+    const int64_t end = beg + per < n ? beg + per : n;
+    long long s = 0;
+    for (int64_t i = beg; i < end; ++i) s += in[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int64_t i = beg; i < end; ++i) {
+        out[i] = (int)run;
+        run += in[i];
+    }
+    if (threadIdx.x == T - 1) out[n] = (int)part[T - 1];
+}
+
+// Tile index of one sample from its first taps k0 (already wrapped into [0, g)).
+template <int D>
+__device__ __forceinline__ int64_t tile_of(const int* k0w, const Tiles& tl) {
+    int64_t key = 0;
+    for (int d = 0; d < D; ++d) key = key * tl.nt[d] + k0w[d] / tl.ts[d];
+    return key;
+}
+
+// Pass 1: validate, convert to grid coordinates, key by tile, histogram.
+template <int D>
+__global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geom geo, Tiles tl,
+                           int* __restrict__ key, int* __restrict__ cnt, int* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= geo.M) return;
+    int k0w[D];
+    bool bad = false;
+    for (int d = 0; d < D; ++d) {
+        float f = traj[i * D + d] * traj_scale;
+        float half = 0.5f * (float)geo.n[d];
+        if (!(f >= -half && f <= half)) bad = true;   // also catches NaN
+        float sc = (float)geo.g[d] / (float)geo.n[d];
+        float t = bad ? 0.f : f * sc;
+        int k0 = (int)ceilf(t - 0.5f * (float)KW);
+        k0w[d] = wrap(k0, geo.g[d]);
+    }
+    if (bad) atomicAdd(flag, 1);
+    int64_t kk = tile_of<D>(k0w, tl);
+    key[i] = (int)kk;
+    atomicAdd(&cnt[kk], 1);
+}
+
+// Pass 2: scatter sample i to its slot in the sorted order.
+template <int D>
+__global__ void k_traj_scatter(const float* __restrict__ traj, float traj_scale, Geom geo,
+                               const int* __restrict__ key, const int* __restrict__ off,
+                               int* __restrict__ fill, int* __restrict__ perm, float* __restrict__ t) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= geo.M) return;
+    int kk = key[i];
+    int pos = off[kk] + atomicAdd(&fill[kk], 1);
+    perm[pos] = (int)i;
+    for (int d = 0; d < D; ++d) {
+        float f = traj[i * D + d] * traj_scale;
+        float half = 0.5f * (float)geo.n[d];
+        if (!(f >= -half && f <= half)) f = 0.f;
+        float sc = (float)geo.g[d] / (float)geo.n[d];
+        t[(int64_t)d * geo.M + pos] = f * sc;
+    }
+}
+
+// Tiles touched by the footprint of sorted sample s, per axis (1 or 2 each).
+template <int D>
+__device__ __forceinline__ void footprint_tiles(const float* __restrict__ t, int64_t s, const Geom& geo,
+                                                const Tiles& tl, int lo[D], int hi[D]) {
+    for (int d = 0; d < D; ++d) {
+        float td = t[(int64_t)d * geo.M + s];
+        int k0 = (int)ceilf(td - 0.5f * (float)KW);
+        int a = wrap(k0, geo.g[d]);
+        int b = wrap(k0 + KW - 1, geo.g[d]);
+        lo[d] = a / tl.ts[d];
+        hi[d] = b / tl.ts[d];
+    }
+}
+
+template <int D, bool FILL>
+__global__ void k_ext(const float* __restrict__ t, Geom geo, Tiles tl, int* __restrict__ cnt,
+                      const int* __restrict__ off, int* __restrict__ ext) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= geo.M) return;
+    int lo[D], hi[D];
+    footprint_tiles<D>(t, s, geo, tl, lo, hi);
+    for (int m = 0; m < (1 << D); ++m) {
+        int64_t key = 0;
+        bool dup = false;
+        for (int d = 0; d < D; ++d) {
+            int bit = (m >> (D - 1 - d)) & 1;
+            if (bit && hi[d] == lo[d]) dup = true;
+            key = key * tl.nt[d] + (bit ? hi[d] : lo[d]);
+        }
+        if (dup) continue;
+        if (FILL) {
+            int pos = off[key] + atomicAdd(&cnt[key], 1);
+            ext[pos] = (int)s;
+        } else {
+            atomicAdd(&cnt[key], 1);
+        }
+    }
+}
+
+__global__ void k_max_count(const int* __restrict__ cnt, int64_t n, int* __restrict__ out) {
+    int m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, cnt[i]);
+    atomicMax(out, m);
+}
+
+// Spreading work items: each tile's list is cut into chunks of at most `chunk` samples;
+// tiles with more than one chunk get partial slots.  Empty tiles still get one item so
+// that their (zero) grid values are written.
+__global__ void k_chunks(const int* __restrict__ ext_off, int64_t ntiles, int chunk, int* __restrict__ nch,
+                         int* __restrict__ nsl) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    int cnt = ext_off[t + 1] - ext_off[t];
+    int nc = cnt <= chunk ? 1 : (cnt + chunk - 1) / chunk;
+    nch[t] = nc;
+    nsl[t] = nc > 1 ? nc : 0;
+}
+
+__global__ void k_items(const int* __restrict__ ext_off, const int* __restrict__ item_off,
+                        const int* __restrict__ slot_off, const int* __restrict__ nsl, int64_t ntiles, int chunk,
+                        int4* __restrict__ items) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    int beg = ext_off[t], end = ext_off[t + 1];
+    int nc = item_off[t + 1] - item_off[t];
+    for (int k = 0; k < nc; ++k) {
+        int b = beg + k * chunk;
+        int e = b + chunk < end ? b + chunk : end;
+        items[item_off[t] + k] = make_int4((int)t, b, e, nsl[t] > 0 ? slot_off[t] + k : -1);
+    }
+}
+
+template <typename T>
+__global__ void k_copy_maps(const T* __restrict__ in, T* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- host helpers
+static double kb_apod_host(double n, double g, double beta) {
+    // Fourier transform of the Kaiser-Bessel window at frequency n/g (width KW).
+    const double pi = 3.14159265358979323846;
+    double z2 = beta * beta - (pi * KW * n / g) * (pi * KW * n / g);
+    if (z2 > 0) { double z = std::sqrt(z2); return KW * std::sinh(z) / z; }
+    if (z2 < 0) { double z = std::sqrt(-z2); return KW * std::sin(z) / z; }
+    return KW;
+}
+
+template <typename T>
+static kp_status alloc(T** p, size_t count) {
+    KP_TRY_CUDA(cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 16));
+    return KP_OK;
+}
+
+kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_maps, cudaStream_t st) {
+    if (!out || !prm) { set_error("null argument"); return KP_EINVAL; }
+    *out = nullptr;
+    const int D = prm->ndim;
+    if (D != 2 && D != 3) { set_error("ndim must be 2 or 3"); return KP_EINVAL; }
+    if (prm->ncoils < 1 || prm->nsamples < 1) { set_error("ncoils and nsamples must be >= 1"); return KP_EINVAL; }
+    if (prm->nsamples > (int64_t)1 << 26) { set_error("nsamples too large (max 2^26)"); return KP_EINVAL; }
+    if (prm->kernel_width != KW) { set_error("kernel_width must be 4"); return KP_EINVAL; }
+    if (!(prm->oversamp >= 1.0f && prm->oversamp <= 4.0f)) { set_error("oversamp must be in [1, 4]"); return KP_EINVAL; }
+    if (prm->wavelet_levels < 0 || prm->wavelet_levels > 10) { set_error("wavelet_levels out of range"); return KP_EINVAL; }
+    for (int d = 0; d < D; ++d) {
+        if (prm->img[d] < 8 || prm->img[d] > 4096) { set_error("image sizes must be in [8, 4096]"); return KP_EINVAL; }
+        if (prm->wavelet_levels > 0 && (prm->img[d] % (1LL << prm->wavelet_levels)) != 0) {
+            set_error("every image size must be divisible by 2^wavelet_levels"); return KP_EINVAL;
+        }
+    }
+    kp_plan p = new (std::nothrow) kp_plan_s();
+    if (!p) { set_error("host allocation failed"); return KP_ENOMEM; }
+    p->P = *prm;
+    p->unit_maps = unit_maps;
+    Geom& g = p->geo;
+    g.D = D;
+    g.C = prm->ncoils;
+    g.M = prm->nsamples;
+    g.N = 1;
+    g.G = 1;
+    for (int d = 0; d < MAXD; ++d) { g.n[d] = 1; g.g[d] = 1; g.beta[d] = 0.f; }
+    for (int d = 0; d < D; ++d) {
+        int n = (int)prm->img[d];
+        int gg = (int)std::ceil((double)prm->oversamp * n - 1e-9);
+        gg += gg & 1;
+        g.n[d] = n;
+        g.g[d] = gg;
+        double a = (double)gg / n;
+        double b2 = (KW / a) * (KW / a) * (a - 0.5) * (a - 0.5) - 0.8;
+        if (b2 <= 0) { delete p; set_error("oversampling too small for a Kaiser-Bessel width of 4"); return KP_EINVAL; }
+        g.beta[d] = (float)(3.14159265358979323846 * std::sqrt(b2));
+        g.N *= n;
+        g.G *= gg;
+    }
+    g.rsqrtN = (float)(1.0 / std::sqrt((double)g.N));
+    if ((int64_t)g.C * g.G > ((int64_t)1 << 34)) { delete p; set_error("grid too large"); return KP_EINVAL; }
+    Tiles& tl = p->tiles;
+    tl.ntiles = 1;
+    for (int d = 0; d < MAXD; ++d) { tl.ts[d] = 1; tl.nt[d] = 1; }
+    for (int d = 0; d < D; ++d) {
+        tl.ts[d] = D == 2 ? 16 : 8;
+        tl.nt[d] = (g.g[d] + tl.ts[d] - 1) / tl.ts[d];
+        tl.ntiles *= tl.nt[d];
+    }
+    kp::daubechies4(p->h);
+    {
+        kp_status fs = upload_wavelet_filter(p->h);
+        if (fs != KP_OK) { delete p; return fs; }
+    }
+
+    const int64_t C = g.C, M = g.M, N = g.N, G = g.G;
+    kp_status s = KP_OK;
+#define KP_A(ptr, cnt) do { s = alloc(&(ptr), (size_t)(cnt)); if (s != KP_OK) { plan_destroy_internal(p); return s; } } while (0)
+    KP_A(p->d_t, (size_t)D * M);
+    KP_A(p->d_f, (size_t)D * M);
+    KP_A(p->d_perm, M);
+    KP_A(p->d_key, M);
+    KP_A(p->d_cnt, tl.ntiles + 1);
+    KP_A(p->d_off, tl.ntiles + 1);
+    KP_A(p->d_ext_off, tl.ntiles + 1);
+    KP_A(p->d_ext, (size_t)M << D);
+    KP_A(p->d_item_off, tl.ntiles + 1);
+    KP_A(p->d_slot_off, tl.ntiles + 1);
+    KP_A(p->d_nslots, tl.ntiles + 1);
+    KP_A(p->d_flag, 8);
+    {
+        float* ap = nullptr;
+        int tot = 0;
+        for (int d = 0; d < D; ++d) tot += g.n[d];
+        KP_A(ap, tot);
+        p->d_apod = ap;
+        std::vector<float> h(tot);
+        int o = 0;
+        for (int d = 0; d < D; ++d) {
+            for (int j = 0; j < g.n[d]; ++j) {
+                double nn = (double)(j - g.n[d] / 2);
+                h[o + j] = (float)(1.0 / kb_apod_host(nn, g.g[d], g.beta[d]));
+            }
+            o += g.n[d];
+        }
+        KP_TRY_CUDA(cudaMemcpy(ap, h.data(), tot * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (!unit_maps) {
+        char* mp = nullptr;
+        KP_A(mp, (size_t)C * N * 8);
+        p->d_maps = mp;
+    }
+    KP_A(p->d_grid, (size_t)C * G);
+    KP_A(p->d_u, (size_t)C * M);
+    {
+        char* yp = nullptr;
+        KP_A(yp, (size_t)C * M * 8);
+        p->d_ys = yp;
+    }
+    KP_A(p->d_ps, (size_t)C * M);
+    KP_A(p->d_puser, (size_t)C * M);
+    KP_A(p->d_kt, (size_t)C * M);
+    KP_A(p->d_x, N);
+    KP_A(p->d_xbar, N);
+    KP_A(p->d_z, N);
+    KP_A(p->d_w, N);
+    KP_A(p->d_red, 16);
+    KP_A(p->d_schedd, 8);
+    KP_A(p->d_iter, 4);
+#undef KP_A
+    int dims[3] = {g.g[0], g.g[1], g.g[2]};
+    cufftResult fr = cufftPlanMany(&p->fft, D, dims, nullptr, 1, (int)G, nullptr, 1, (int)G, CUFFT_C2C, (int)C);
+    if (fr != CUFFT_SUCCESS) {
+        plan_destroy_internal(p);
+        set_error("cufftPlanMany failed: " + std::to_string((int)fr));
+        return fr == CUFFT_ALLOC_FAILED ? KP_ENOMEM : KP_ECUFFT;
+    }
+    p->fft_ok = true;
+    if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_destroy_internal(p);
+        set_error("cudaStreamCreate failed");
+        return KP_ECUDA;
+    }
+    (void)st;
+    *out = p;
+    return KP_OK;
+}
+
+kp_status plan_destroy_internal(kp_plan p) {
+    if (!p) return KP_OK;
+    cudaDeviceSynchronize();
+    drop_graphs(p);
+    pre_destroy(p);
+    if (p->fft_ok) cufftDestroy(p->fft);
+    void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
+                    p->d_items, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_partial,
+                    p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
+                    p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_red, p->d_sched, p->d_schedd, p->d_iter};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
+    delete[] p->ev;
+    delete[] p->ev_phase;
+    delete p;
+    return KP_OK;
+}
+
+kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale, cudaStream_t st) {
+    if (!p || !traj) { set_error("null argument"); return KP_EINVAL; }
+    const Geom& g = p->geo;
+    const Tiles& tl = p->tiles;
+    const int T = 256;
+    drop_graphs(p);
+    p->traj_set = false;
+    p->traj_version++;
+    if (traj != p->d_f)
+        KP_TRY_CUDA(cudaMemcpyAsync(p->d_f, traj, (size_t)g.D * g.M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag, 0, 8 * sizeof(int), st));
+    if (g.D == 2) k_traj_key<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, tl, p->d_key, p->d_cnt, p->d_flag);
+    else k_traj_key<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, tl, p->d_key, p->d_cnt, p->d_flag);
+    KP_LAUNCH_CHECK();
+    k_max_count<<<64, 256, 0, st>>>(p->d_cnt, tl.ntiles, p->d_flag + 1);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_off, tl.ntiles);
+    KP_LAUNCH_CHECK();
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
+    if (g.D == 2) k_traj_scatter<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t);
+    else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t);
+    KP_LAUNCH_CHECK();
+    // spreading lists
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
+    if (g.D == 2) k_ext<2, false><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, nullptr, nullptr);
+    else k_ext<3, false><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, nullptr, nullptr);
+    KP_LAUNCH_CHECK();
+    k_max_count<<<64, 256, 0, st>>>(p->d_cnt, tl.ntiles, p->d_flag + 2);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_ext_off, tl.ntiles);
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
+    if (g.D == 2) k_ext<2, true><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
+    else k_ext<3, true><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
+    KP_LAUNCH_CHECK();
+    int flag[4];
+    KP_TRY_CUDA(cudaMemcpyAsync(flag, p->d_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (flag[0] != 0) {
+        set_error(std::to_string(flag[0]) + " trajectory coordinates outside [-N/2, N/2] or not finite");
+        p->traj_set = false;
+        return KP_EINVAL;
+    }
+    p->max_tile = flag[2];
+    // work items for the spreading kernel
+    const unsigned tb = nblk(tl.ntiles, 256);
+    k_chunks<<<tb, 256, 0, st>>>(p->d_ext_off, tl.ntiles, p->chunk, p->d_cnt, p->d_nslots);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_nslots, p->d_slot_off, tl.ntiles);
+    KP_LAUNCH_CHECK();
+    int tot[2];
+    KP_TRY_CUDA(cudaMemcpyAsync(&tot[0], p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaMemcpyAsync(&tot[1], p->d_slot_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    p->n_items = tot[0];
+    p->n_slots = tot[1];
+    if (p->n_items > p->items_cap) {
+        if (p->d_items) cudaFree(p->d_items);
+        p->d_items = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_items, p->n_items * sizeof(int4)));
+        p->items_cap = p->n_items;
+    }
+    int64_t P = 1;
+    for (int d = 0; d < g.D; ++d) P *= tl.ts[d];
+    const size_t need = (size_t)p->n_slots * g.C * P * sizeof(float2);
+    if (need > p->partial_cap) {
+        if (p->d_partial) cudaFree(p->d_partial);
+        p->d_partial = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_partial, need));
+        p->partial_cap = need;
+    }
+    k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, p->chunk, p->d_items);
+    KP_LAUNCH_CHECK();
+    p->launches += 12;
+    p->traj_set = true;
+    return KP_OK;
+}
+
+}  // namespace kp
+
+using namespace kp;
+
+extern "C" {
+
+const char* kp_status_string(kp_status s) {
+    switch (s) {
+        case KP_OK: return "KP_OK";
+        case KP_EINVAL: return "KP_EINVAL";
+        case KP_ENOMEM: return "KP_ENOMEM";
+        case KP_ECUDA: return "KP_ECUDA";
+        case KP_ECUFFT: return "KP_ECUFFT";
+        case KP_EDIVERGED: return "KP_EDIVERGED";
+        case KP_ENONFINITE: return "KP_ENONFINITE";
+        case KP_ETIMEOUT: return "KP_ETIMEOUT";
+        case KP_EINTERNAL: return "KP_EINTERNAL";
+    }
+    return "KP_UNKNOWN";
+}
+
+const char* kp_last_error(void) { return g_last_error.c_str(); }
+
+kp_status kp_plan_create(kp_plan* out, const kp_params* params, void* stream) {
+    g_last_error.clear();
+    return plan_create_internal(out, params, false, (cudaStream_t)stream);
+}
+
+kp_status kp_plan_destroy(kp_plan plan) { return plan_destroy_internal(plan); }
+
+kp_status kp_plan_set_trajectory(kp_plan plan, const float* traj_dev, void* stream) {
+    g_last_error.clear();
+    if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    return set_trajectory_internal(plan, traj_dev, 1.0f, (cudaStream_t)stream);
+}
+
+kp_status kp_plan_set_maps(kp_plan plan, const void* maps_dev, kp_cdtype maps_t, void* stream) {
+    g_last_error.clear();
+    if (!plan || !maps_dev) { set_error("null argument"); return KP_EINVAL; }
+    if (plan->unit_maps) { set_error("plan has unit maps"); return KP_EINVAL; }
+    if (maps_t != KP_C64 && maps_t != KP_C32_BF16 && maps_t != KP_C32_FP16) { set_error("bad maps type"); return KP_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = (int64_t)plan->geo.C * plan->geo.N;
+    if (maps_t == KP_C64) k_copy_maps<float2><<<nblk(n, 256), 256, 0, st>>>((const float2*)maps_dev, (float2*)plan->d_maps, n);
+    else k_copy_maps<unsigned><<<nblk(n, 256), 256, 0, st>>>((const unsigned*)maps_dev, (unsigned*)plan->d_maps, n);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    plan->maps_t = maps_t;
+    plan->maps_set = true;
+    // cached graphs bake the maps type in: drop them
+    drop_graphs(plan);
+    return KP_OK;
+}
+
+kp_status kp_plan_launch_count(kp_plan plan, int64_t* count) {
+    if (!plan || !count) { set_error("null argument"); return KP_EINVAL; }
+    *count = plan->launches + (plan->pre_nufft ? plan->pre_nufft->launches : 0);
+    return KP_OK;
+}
+
+kp_status kp_plan_set_profiling(kp_plan plan, int enable) {
+    if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    plan->profiling = enable != 0;
+    return KP_OK;
+}
+
+kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_samples) {
+    if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    if (ntiles) *ntiles = plan->tiles.ntiles;
+    if (max_tile_samples) *max_tile_samples = plan->max_tile;
+    return KP_OK;
+}
+
+}  // extern "C"

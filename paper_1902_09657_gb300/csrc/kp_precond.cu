@@ -1,0 +1,301 @@
+// l2-optimised diagonal k-space preconditioner (Sec. 5, App. A), fast route of Sec. 5.1:
+//
+//   q_cd = s_c s_d^*  zero-padded to the 2N grid  -> FFT -> R_c = sum_d |Q_cd|^2 (float64)
+//   r_c  = IFFT(R_c) / (2^D N)                      (autocorrelation sum, lags in [-N_d, N_d))
+//   h    = N^{-1/2} sum_j e^{+i 2 pi f_j k/N}        (type-1 NUFFT of ones at 2 f_j on the 2N image)
+//   p_c[i] = ||s_c||^2 sqrt(N) / Re(sum_k r_c[k] h[k] e^{-i 2 pi f_i k / N})   (type-2 NUFFT at 2 f_i)
+//
+// With the 2N-image NUFFT carrying (2^D N)^{-1/2} in both directions, the last line is
+// p_c[i] = ||s_c||^2 / (2^D Re(fwd_2N(r_c * adj_2N(1))[i])).  Pairs (c, d) and (d, c) share
+// one FFT: |Q_dc|^2[m] = |Q_cd|^2[-m].  Single channel (Eq. sc_precond): C = 1, s = 1.
+#include "kp_internal.cuh"
+
+#include <vector>
+
+namespace kp {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct PrePlan {
+    int D = 0;
+    int nb[MAXD] = {1, 1, 1};
+    int64_t Nb = 0;
+    int C = 0;            // coils of the owning plan
+    int B = 0;            // pairs per FFT batch
+    double* d_R = nullptr;      // [C][Nb]
+    float2* d_q = nullptr;      // [B][Nb]
+    float2* d_r = nullptr;      // [Nb]
+    float2* d_h = nullptr;      // [Nb]
+    float2* d_v = nullptr;      // [Nb]
+    double* d_norm = nullptr;   // [C]
+    int2* d_pairs = nullptr;    // [C(C+1)/2]
+    int npairs = 0;
+    cufftHandle fft_pairs = 0, fft_one = 0;
+    bool ok_pairs = false, ok_one = false;
+    int traj_version = -1;
+};
+
+void pre_destroy(kp_plan p) {
+    if (p->pre_nufft) { plan_destroy_internal(p->pre_nufft); p->pre_nufft = nullptr; }
+    PrePlan* q = p->pre;
+    if (!q) return;
+    if (q->ok_pairs) cufftDestroy(q->fft_pairs);
+    if (q->ok_one) cufftDestroy(q->fft_one);
+    void* bufs[] = {q->d_R, q->d_q, q->d_r, q->d_h, q->d_v, q->d_norm, q->d_pairs};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete q;
+    p->pre = nullptr;
+}
+
+static kp_status pre_create(kp_plan p, cudaStream_t st) {
+    if (p->pre) return KP_OK;
+    PrePlan* q = new (std::nothrow) PrePlan();
+    if (!q) { set_error("host allocation failed"); return KP_ENOMEM; }
+    p->pre = q;
+    const Geom& g = p->geo;
+    q->D = g.D;
+    q->C = g.C;
+    q->Nb = 1;
+    for (int d = 0; d < g.D; ++d) { q->nb[d] = 2 * g.n[d]; q->Nb *= q->nb[d]; }
+    q->npairs = g.C * (g.C + 1) / 2;
+    const int bmax = g.D == 2 ? 16 : 2;
+    q->B = q->npairs < bmax ? q->npairs : bmax;
+    KP_TRY_CUDA(cudaMalloc(&q->d_R, (size_t)g.C * q->Nb * sizeof(double)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_q, (size_t)q->B * q->Nb * sizeof(float2)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_r, (size_t)q->Nb * sizeof(float2)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_h, (size_t)q->Nb * sizeof(float2)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_v, (size_t)q->Nb * sizeof(float2)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_norm, (size_t)g.C * sizeof(double)));
+    std::vector<int2> pairs;
+    for (int c = 0; c < g.C; ++c)
+        for (int d = c; d < g.C; ++d) pairs.push_back(make_int2(c, d));
+    KP_TRY_CUDA(cudaMalloc(&q->d_pairs, pairs.size() * sizeof(int2)));
+    KP_TRY_CUDA(cudaMemcpy(q->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    int dims[3] = {q->nb[0], q->nb[1], q->nb[2]};
+    KP_TRY_CUFFT(cufftPlanMany(&q->fft_pairs, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, q->B));
+    q->ok_pairs = true;
+    KP_TRY_CUFFT(cufftPlanMany(&q->fft_one, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, 1));
+    q->ok_one = true;
+    // NUFFT on the 2N image with unit maps and one coil
+    kp_params prm = p->P;
+    prm.ncoils = 1;
+    prm.wavelet_levels = 0;
+    for (int d = 0; d < g.D; ++d) prm.img[d] = 2 * g.n[d];
+    KP_TRY(plan_create_internal(&p->pre_nufft, &prm, true, st));
+    return KP_OK;
+}
+
+// Zero-padded product q = s_c s_d^* (or 1 with unit maps) on the 2N grid, pixel n at n mod 2N.
+template <typename MT>
+__global__ void k_make_q(const MT* __restrict__ maps, const int2* __restrict__ pairs, int pair0, int npairs_valid,
+                         Geom geo, int D, int nb0, int nb1, int nb2, int64_t Nb, int B, float2* __restrict__ q) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nb) return;
+    const int nb[3] = {nb0, nb1, nb2};
+    int ii[MAXD];
+    int64_t r = m;
+    for (int d = D - 1; d >= 0; --d) { ii[d] = (int)(r % nb[d]); r /= nb[d]; }
+    int64_t j = 0;
+    bool inside = true;
+    for (int d = 0; d < D; ++d) {
+        int n = geo.n[d], h = n / 2;
+        int jd = ii[d] < n - h ? ii[d] + h : (ii[d] >= nb[d] - h ? ii[d] - nb[d] + h : -1);
+        if (jd < 0) inside = false;
+        j = j * n + (jd < 0 ? 0 : jd);
+    }
+    for (int b = 0; b < B; ++b) {
+        float2 v = make_float2(0.f, 0.f);
+        if (inside && b < npairs_valid) {
+            if (maps) {
+                int2 cd = pairs[pair0 + b];
+                float2 sc = ldc<MT>(maps, (size_t)cd.x * geo.N + j);
+                float2 sd = ldc<MT>(maps, (size_t)cd.y * geo.N + j);
+                v = cmulc(sd, sc);   // s_c s_d^*
+            } else {
+                v = make_float2(1.f, 0.f);
+            }
+        }
+        q[(size_t)b * Nb + m] = v;
+    }
+}
+
+// R_c[m] += |Q_cd[m]|^2, R_d[m] += |Q_cd[-m]|^2 for each pair of the batch (float64).
+__global__ void k_accum_R(const float2* __restrict__ Q, const int2* __restrict__ pairs, int pair0, int npairs_valid,
+                          int D, int nb0, int nb1, int nb2, int64_t Nb, double* __restrict__ R, bool unit) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nb) return;
+    const int nb[3] = {nb0, nb1, nb2};
+    // index of -m
+    int64_t r = m, mneg = 0, stride = 1;
+    for (int d = D - 1; d >= 0; --d) {
+        int i = (int)(r % nb[d]);
+        r /= nb[d];
+        int in = i == 0 ? 0 : nb[d] - i;
+        mneg += in * stride;
+        stride *= nb[d];
+    }
+    for (int b = 0; b < npairs_valid; ++b) {
+        int2 cd = unit ? make_int2(0, 0) : pairs[pair0 + b];
+        float2 a = Q[(size_t)b * Nb + m];
+        R[(size_t)cd.x * Nb + m] += (double)a.x * a.x + (double)a.y * a.y;
+        if (cd.y != cd.x) {
+            float2 bq = Q[(size_t)b * Nb + mneg];
+            R[(size_t)cd.y * Nb + m] += (double)bq.x * bq.x + (double)bq.y * bq.y;
+        }
+    }
+}
+
+__global__ void k_R_to_c(const double* __restrict__ R, int64_t Nb, float2* __restrict__ out) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < Nb) out[m] = make_float2((float)(R[m] / (double)Nb), 0.f);
+}
+
+// v[j] = r[(j - n) mod 2n] * h[j] on the centred 2N image (lag k_d = j_d - n_d).
+__global__ void k_rh(const float2* __restrict__ r, const float2* __restrict__ h, int D, int nb0, int nb1, int nb2,
+                     int64_t Nb, float2* __restrict__ v) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Nb) return;
+    const int nb[3] = {nb0, nb1, nb2};
+    int64_t rr = j, ri = 0, stride = 1;
+    for (int d = D - 1; d >= 0; --d) {
+        int jd = (int)(rr % nb[d]);
+        rr /= nb[d];
+        int k = jd - nb[d] / 2;
+        int idx = k < 0 ? k + nb[d] : k;
+        ri += idx * stride;
+        stride *= nb[d];
+    }
+    v[j] = cmul(r[ri], h[j]);
+}
+
+template <typename MT>
+__global__ void k_coil_norm2(const MT* __restrict__ maps, int64_t N, int C, double* __restrict__ out) {
+    __shared__ double ws[32];
+    const int c = blockIdx.y;
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = ldc<MT>(maps, (size_t)c * N + i);
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) atomicAdd(&out[c], s);
+    }
+}
+
+__global__ void k_set_norm(double* out, int C, double v) {
+    int c = threadIdx.x;
+    if (c < C) out[c] = v;
+}
+
+// p[c][i] = ||s_c||^2 / (2^D Re(den[s])) with den in the 2N plan's sorted order.
+__global__ void k_p_out(const float2* __restrict__ den, const int* __restrict__ perm, int64_t M, const double* __restrict__ norm,
+                        int cnorm, int c_first, int c_count, int D, float* __restrict__ p, int* __restrict__ bad) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const double dv = (double)den[s].x * (double)(1 << D);
+    const int64_t i = perm[s];
+    float val;
+    if (dv > 0 && isfinite(dv)) {
+        val = (float)(norm[cnorm] / dv);
+    } else {
+        val = 0.f;
+        atomicAdd(bad, 1);
+    }
+    for (int c = c_first; c < c_first + c_count; ++c) p[(size_t)c * M + i] = val;
+}
+
+}  // namespace kp
+
+using namespace kp;
+
+extern "C" kp_status kp_make_preconditioner(kp_plan plan, int multichannel, float* p_dev, void* stream) {
+    if (!plan || !p_dev) { set_error("null argument"); return KP_EINVAL; }
+    if (!plan->traj_set || (multichannel && !plan->maps_set)) { set_error("trajectory (and maps) must be set"); return KP_EINVAL; }
+    if (plan->unit_maps) { set_error("not available on an internal plan"); return KP_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    KP_TRY(pre_create(plan, st));
+    PrePlan* q = plan->pre;
+    kp_plan nu = plan->pre_nufft;
+    const Geom& g = plan->geo;
+    const bool mc = multichannel != 0;
+    const int C = mc ? g.C : 1;
+    if (q->traj_version != plan->traj_version) {
+        KP_TRY(set_trajectory_internal(nu, plan->d_f, 2.0f, st));
+        q->traj_version = plan->traj_version;
+    }
+    // ||s_c||^2
+    if (mc) {
+        KP_TRY_CUDA(cudaMemsetAsync(q->d_norm, 0, C * sizeof(double), st));
+        dim3 grid(64, C);
+        switch (plan->maps_t) {
+            case KP_C64: k_coil_norm2<float2><<<grid, 256, 0, st>>>((const float2*)plan->d_maps, g.N, C, q->d_norm); break;
+            case KP_C32_BF16: k_coil_norm2<__nv_bfloat162><<<grid, 256, 0, st>>>((const __nv_bfloat162*)plan->d_maps, g.N, C, q->d_norm); break;
+            default: k_coil_norm2<__half2><<<grid, 256, 0, st>>>((const __half2*)plan->d_maps, g.N, C, q->d_norm); break;
+        }
+    } else {
+        k_set_norm<<<1, 32, 0, st>>>(q->d_norm, 1, (double)g.N);
+    }
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    // R_c = sum_d |FFT(q_cd)|^2
+    KP_TRY_CUDA(cudaMemsetAsync(q->d_R, 0, (size_t)C * q->Nb * sizeof(double), st));
+    KP_TRY_CUFFT(cufftSetStream(q->fft_pairs, st));
+    KP_TRY_CUFFT(cufftSetStream(q->fft_one, st));
+    const int npairs = mc ? q->npairs : 1;
+    for (int p0 = 0; p0 < npairs; p0 += q->B) {
+        const int nv = npairs - p0 < q->B ? npairs - p0 : q->B;
+        switch (mc ? plan->maps_t : KP_C64) {
+            case KP_C64:
+                k_make_q<float2><<<nblk(q->Nb, 256), 256, 0, st>>>(mc ? (const float2*)plan->d_maps : nullptr, q->d_pairs, p0, nv, g,
+                                                                   g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->B, q->d_q);
+                break;
+            case KP_C32_BF16:
+                k_make_q<__nv_bfloat162><<<nblk(q->Nb, 256), 256, 0, st>>>((const __nv_bfloat162*)plan->d_maps, q->d_pairs, p0, nv, g,
+                                                                           g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->B, q->d_q);
+                break;
+            default:
+                k_make_q<__half2><<<nblk(q->Nb, 256), 256, 0, st>>>((const __half2*)plan->d_maps, q->d_pairs, p0, nv, g,
+                                                                    g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->B, q->d_q);
+                break;
+        }
+        KP_LAUNCH_CHECK();
+        KP_TRY_CUFFT(cufftExecC2C(q->fft_pairs, (cufftComplex*)q->d_q, (cufftComplex*)q->d_q, CUFFT_FORWARD));
+        k_accum_R<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_q, q->d_pairs, p0, nv, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb,
+                                                    q->d_R, !mc);
+        KP_LAUNCH_CHECK();
+        plan->launches += 2;
+    }
+    // h = adjoint NUFFT of ones on the 2N image
+    KP_TRY(fill_image(nu->d_kt, nu->geo.M, make_float2(1.f, 0.f), st));
+    plan->launches += 1;
+    KP_TRY(adjoint_to_grid(nu, nu->d_kt, KP_C64, nullptr, st));
+    KP_TRY(grid_to_image(nu, q->d_h, st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag + 7, 0, sizeof(int), st));
+    for (int c = 0; c < C; ++c) {
+        k_R_to_c<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_R + (size_t)c * q->Nb, q->Nb, q->d_r);
+        KP_LAUNCH_CHECK();
+        KP_TRY_CUFFT(cufftExecC2C(q->fft_one, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r, CUFFT_INVERSE));
+        k_rh<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_r, q->d_h, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v);
+        KP_LAUNCH_CHECK();
+        KP_TRY(forward_to(nu, q->d_v, nu->d_kt, KP_C64, nullptr, st));
+        k_p_out<<<nblk(g.M, 256), 256, 0, st>>>(nu->d_kt, nu->d_perm, g.M, q->d_norm, c, mc ? c : 0, mc ? 1 : g.C, g.D,
+                                                p_dev, plan->d_flag + 7);
+        KP_LAUNCH_CHECK();
+        plan->launches += 3;
+    }
+    int bad = 0;
+    KP_TRY_CUDA(cudaMemcpyAsync(&bad, plan->d_flag + 7, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (bad) {
+        set_error(std::to_string(bad) + " preconditioner denominators were not positive (set to 0)");
+        return KP_ENONFINITE;
+    }
+    return KP_OK;
+}

@@ -1,0 +1,68 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, and exports every
+function include/kpdhg.h declares; the ctypes structs match the header's layout."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kpdhg.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kp_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit")
+    from paper_1902_09657_gb300 import _build, _lib
+    _build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for fn in ("kp_plan_create", "kp_plan_set_trajectory", "kp_plan_set_maps", "kp_make_preconditioner",
+               "kp_sense_forward", "kp_sense_adjoint", "kp_max_eig", "kp_pdhg_solve", "kp_plan_destroy"):
+        assert fn in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    assert lib.kp_status_string(0) == b"KP_OK"
+    assert lib.kp_status_string(1) == b"KP_EINVAL"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    from paper_1902_09657_gb300 import _lib
+    assert lib.kp_plan_create(None, None, None) == _lib.KP_EINVAL
+    assert lib.kp_plan_destroy(None) == _lib.KP_OK
+    assert lib.kp_sense_forward(None, None, None, 0, None) == _lib.KP_EINVAL
+    prm = _lib.KpParams()
+    prm.ndim = 4
+    h = ctypes.c_void_p()
+    assert lib.kp_plan_create(ctypes.byref(h), ctypes.byref(prm), None) == _lib.KP_EINVAL
+    assert b"ndim" in lib.kp_last_error()
+
+
+def test_struct_layout_matches_header():
+    from paper_1902_09657_gb300 import _lib
+    # kp_params: int, (pad), int64[3], int, (pad), int64, float, int, int, (pad) -> 64 bytes
+    assert ctypes.sizeof(_lib.KpParams) == 64
+    assert _lib.KpParams.nsamples.offset == 40
+    assert ctypes.sizeof(_lib.KpStats) == 8 + 5 * 8 + 12 * 8
+
+
+def test_sources_use_blackwell_target():
+    from paper_1902_09657_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)

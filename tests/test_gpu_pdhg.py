@@ -1,0 +1,111 @@
+"""GPU parity of the power method and preconditioned PDHG (Sec. 4.1, Sec. 6) against the
+float64 oracle running the same iteration from the same inputs.
+
+Solver parity is checked two ways: (a) the oracle's p and lambda_max are passed to both
+sides, so only the iteration is compared (tolerance 1e-5 relative l2 on x after the
+workload's iteration count); (b) the GPU computes p and lambda_max itself (MC
+preconditioner, 30 power iterations from the all-ones image) and the whole chain is compared
+(tolerance 1e-4: the preconditioner's own 1e-4 bound carries through the step sizes)."""
+import numpy as np
+import pytest
+
+from oracle import nufft as onf, precond as opc, solvers as osv
+from tests.gpu_util import need_gpu, rel, workload_problem, simulate, to_dev, make_plan
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _ops(maps, traj, alpha):
+    m = maps.astype(np.complex128)
+    A = lambda v: onf.nufft_forward(v, m, traj, alpha, 4)
+    AH = lambda u: onf.nufft_adjoint(u, m, traj, alpha, 4)
+    return A, AH
+
+
+def _small_spiral(n=64, C=4, L=8, ns=1024):
+    w = synth.Workload("spiral_small", (n, n), C, 1.25, 4, "l1_wavelet", 1e-3, 100, 3, "spiral",
+                       dict(n_interleaves=L, n_samples=ns, kmax=n / 2.0))
+    return w, w.phantom(), w.maps(), w.traj()
+
+
+def test_power_method_matches_oracle():
+    need_gpu()
+    w, x, maps, traj = _small_spiral()
+    A, AH = _ops(maps, traj, 1.25)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
+    L_ref, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0])
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    L = plan.max_eig(to_dev(p.astype(np.float32)), iters=30)
+    assert abs(L - L_ref) < 1e-5 * L_ref
+
+
+@pytest.mark.parametrize("reg,lam,iters,levels", [("l2", 1e-3, 100, 0), ("l1_wavelet", 1e-3, 100, 3)])
+def test_pdhg_iteration_parity_small(reg, lam, iters, levels):
+    need_gpu()
+    w, x, maps, traj = _small_spiral()
+    y = simulate(w, x, maps, traj)
+    A, AH = _ops(maps, traj, 1.25)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    if reg == "l1_wavelet":
+        lam = lam * float(np.abs(AH(y.astype(np.complex128))).max())
+    x_ref, _, _, objs = osv.pdhg(A, AH, y, p, x.shape, reg, lam, iters, L, levels=levels, trace=True)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=levels)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    xg, tr, st = plan.pdhg_solve(to_dev(y), to_dev(p.astype(np.float32)), reg, lam, iters, lmax=L, trace=True)
+    assert rel(xg.cpu().numpy(), x_ref) < 1e-5
+    assert abs(tr[-1] - objs[-1]) < 1e-5 * abs(objs[-1])
+    assert abs(st["lmax"] - L) < 1e-12 * L and abs(st["pmin"] - p.min()) < 1e-6 * p.min()
+
+
+@pytest.mark.parametrize("name,alpha,iters", [("radial2d_128", 2.0, 30), ("spiral2d_256", 1.25, 8)])
+def test_pdhg_full_chain_workloads(name, alpha, iters):
+    """Whole chain on the full-size 2D workloads: GPU builds p (MC) and lambda_max itself."""
+    need_gpu()
+    w, x, maps, traj = workload_problem(name)
+    y = simulate(w, x, maps, traj)
+    A, AH = _ops(maps, traj, alpha)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, alpha, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    lam = w.lam_rel
+    if w.reg == "l1_wavelet":
+        lam = lam * float(np.abs(AH(y.astype(np.complex128))).max())
+    x_ref, _, _, _ = osv.pdhg(A, AH, y, p, x.shape, w.reg, lam, iters, L, levels=w.wavelet_levels)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], alpha, w.wavelet_levels)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    xg, _, st = plan.pdhg_solve(to_dev(y), None, w.reg, lam, iters)
+    assert abs(st["lmax"] - L) < 1e-4 * L
+    assert rel(xg.cpu().numpy(), x_ref) < 1e-4
+
+
+def test_pdhg_host_buffers_roundtrip():
+    """pdhg_solve with host (CPU) y: the binding copies in and out; same result as device y."""
+    need_gpu()
+    w, x, maps, traj = _small_spiral(n=32, C=2, L=4, ns=512)
+    y = simulate(w, x, maps, traj)
+    plan = make_plan(x.shape, 2, traj.shape[0], levels=2)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    import torch
+    xa, _, _ = plan.pdhg_solve(torch.from_numpy(y).pin_memory(), None, "l1_wavelet", 1e-3, 20)
+    xb, _, _ = plan.pdhg_solve(to_dev(y), None, "l1_wavelet", 1e-3, 20)
+    assert xa.device.type == "cpu"
+    assert rel(xa.numpy(), xb.cpu().numpy()) < 1e-6
+
+
+def test_pdhg_rejects_bad_inputs():
+    need_gpu()
+    from paper_1902_09657_gb300._lib import KpError
+    w, x, maps, traj = _small_spiral(n=32, C=2, L=4, ns=512)
+    y = simulate(w, x, maps, traj)
+    plan = make_plan(x.shape, 2, traj.shape[0], levels=0)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    with pytest.raises(KpError):
+        plan.pdhg_solve(to_dev(y), None, "l1_wavelet", 1e-3, 5)        # no wavelet levels
+    bad_p = np.ones((2, traj.shape[0]), np.float32)
+    bad_p[1, 3] = -1.0
+    with pytest.raises(KpError):
+        plan.pdhg_solve(to_dev(y), to_dev(bad_p), "l2", 1e-3, 5)
+    x0, _, _ = plan.pdhg_solve(to_dev(y), None, "l2", 1e-3, 0)       # zero iterations -> x0 = 0
+    assert float(x0.abs().max()) == 0.0
