@@ -18,8 +18,9 @@ apodisation by its continuous Fourier transform
 
 (sin form when the radicand is negative), zero padding with pixel n_d stored at
 grid index n_d mod G_d, a forward DFT of size G, and W^d-tap interpolation with
-taps k_d = ceil(t_d - W/2) + j, j = 0..W-1 (the first-tap decision is taken in
-float32, the same precision the GPU takes it in), read at index k_d mod G_d.
+taps k_d = ceil(t_d - W/2) + j, j = 0..W-1, evaluated as ceil(t_d) - W/2 + j (exact for
+even W, no rounding; t_d itself is the float32 value the GPU uses), read at index
+k_d mod G_d.  Every tap then has |t_d - k_d| <= W/2.
 The adjoint is the exact transpose, step by step in reverse order.
 
 Parity: pinned by tests/test_oracle_nufft.py (brute-force NUDFT on tiny inputs,
@@ -87,9 +88,11 @@ def grid_coords(traj, img_shape, gshape):
 
 
 def first_tap(t, W):
-    """k0 = ceil(t - W/2), decided in float32."""
+    """k0 = ceil(t) - W/2 for even W: the same integer as ceil(t - W/2) in exact arithmetic,
+    computed without rounding (t - W/2 in float32 can round onto an integer when |t| < W/2,
+    which would push the first tap just outside the window)."""
     t = np.asarray(t, dtype=np.float32)
-    return np.ceil(t - np.float32(W / 2.0)).astype(np.int64)
+    return np.ceil(t).astype(np.int64) - W // 2
 
 
 def _centred(n):

@@ -71,7 +71,7 @@ struct Tiles {
 
 // ---------------------------------------------------------------- complex storage helpers
 __host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__host__ __device__ inline float2 cmulc(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } // conj(a)*b
+__host__ __device__ inline float2 cmulc(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); } // conj(a)*b
 
 template <typename T> __device__ inline float2 ldc(const T* p, size_t i);
 template <> __device__ inline float2 ldc<float2>(const float2* p, size_t i) { return p[i]; }

@@ -9,7 +9,8 @@
 //           warp never collide; single-chunk tiles store straight to the grid, split tiles
 //           store partial tiles that a reduction pass sums) -> cuFFT C2C inverse ->
 //           adj_post (crop, 1/Phi, conj(s_c) coil combine, N^{-1/2}).
-// The grid coordinates t = f g/n and the first tap k0 = ceil(t - 2) are float32.
+// The grid coordinates t = f g/n are float32; the first tap is k0 = ceil(t) - W/2, which equals
+// ceil(t - W/2) exactly and involves no rounding, so |t - k| <= W/2 for every tap.
 #include "kp_internal.cuh"
 
 namespace kp {
@@ -37,7 +38,7 @@ __device__ __forceinline__ void make_taps(const float* __restrict__ t, int64_t s
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         float td = t[(int64_t)d * geo.M + s];
-        int k0 = (int)ceilf(td - 0.5f * (float)KW);
+        int k0 = (int)ceilf(td) - KW / 2;
         int stride = 1;
         for (int e = d + 1; e < D; ++e) stride *= geo.g[e];
 #pragma unroll
@@ -266,7 +267,7 @@ k_spread(const float* __restrict__ t, const UT* __restrict__ u, const int* __res
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 td[d] = t[(int64_t)d * geo.M + s];
-                k0[d] = (int)ceilf(td[d] - 0.5f * (float)KW);
+                k0[d] = (int)ceilf(td[d]) - KW / 2;
             }
             if (TAPS < 32) {
                 // 2D: two lanes per tap, each taking every other coil

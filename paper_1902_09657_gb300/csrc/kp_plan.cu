@@ -66,7 +66,7 @@ __global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geo
         if (!(f >= -half && f <= half)) bad = true;   // also catches NaN
         float sc = (float)geo.g[d] / (float)geo.n[d];
         float t = bad ? 0.f : f * sc;
-        int k0 = (int)ceilf(t - 0.5f * (float)KW);
+        int k0 = (int)ceilf(t) - KW / 2;
         k0w[d] = wrap(k0, geo.g[d]);
     }
     if (bad) atomicAdd(flag, 1);
@@ -100,7 +100,7 @@ __device__ __forceinline__ void footprint_tiles(const float* __restrict__ t, int
                                                 const Tiles& tl, int lo[D], int hi[D]) {
     for (int d = 0; d < D; ++d) {
         float td = t[(int64_t)d * geo.M + s];
-        int k0 = (int)ceilf(td - 0.5f * (float)KW);
+        int k0 = (int)ceilf(td) - KW / 2;
         int a = wrap(k0, geo.g[d]);
         int b = wrap(k0 + KW - 1, geo.g[d]);
         lo[d] = a / tl.ts[d];

@@ -93,7 +93,12 @@ def test_grid_shape_and_beta():
     assert 6.9 < nf.kb_beta(4, 1.25) < 7.1
 
 
-def test_first_tap_decision_is_float32():
-    t = np.array([2.0 ** -30, 0.5, -1.0, 3.999999], dtype=np.float32)
-    # t - 2 rounds to -2 in float32 for the tiny t, so the first tap is -2
-    assert list(nf.first_tap(t, 4)) == [-2, -1, -3, 2]
+def test_first_tap_is_exact_and_inside_window():
+    """k0 = ceil(t - W/2) exactly, even where t - W/2 would round in float32 (tiny t)."""
+    t = np.array([2.0 ** -30, 0.5, -1.0, 3.999999, -0.99999994, 0.0], dtype=np.float32)
+    assert list(nf.first_tap(t, 4)) == [-1, -1, -3, 2, -2, -2]
+    t = np.random.default_rng(0).uniform(-3, 3, 10000).astype(np.float32)
+    t[:100] = np.float32(1e-9) * np.arange(100, dtype=np.float32)
+    k0 = nf.first_tap(t, 4)
+    u0 = t.astype(np.float64) - k0
+    assert np.all(u0 > 1.0 - 1e-12) and np.all(u0 <= 2.0)
