@@ -237,7 +237,18 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     tl.ntiles = 1;
     for (int d = 0; d < MAXD; ++d) { tl.ts[d] = 1; tl.nt[d] = 1; }
     for (int d = 0; d < D; ++d) {
-        tl.ts[d] = D == 2 ? 16 : 8;
+        // Tile edge: the largest size <= 16 (2D) / 8 (3D) whose last, ragged tile still has at
+        // least W - 1 points, so a footprint of W consecutive grid points (with wrap-around)
+        // touches at most two tiles per axis.
+        const int base = D == 2 ? 16 : 8, lo = D == 2 ? 8 : 4;
+        int ts = g.g[d];
+        if (g.g[d] > base) {
+            for (int c = base; c >= lo; --c) {
+                const int r = g.g[d] % c;
+                if (r == 0 || r >= KW - 1) { ts = c; break; }
+            }
+        }
+        tl.ts[d] = ts;
         tl.nt[d] = (g.g[d] + tl.ts[d] - 1) / tl.ts[d];
         tl.ntiles *= tl.nt[d];
     }
