@@ -175,6 +175,25 @@ kp_status kp_plan_set_profiling(kp_plan plan, int enable);
  * inside replayed CUDA graphs included; cuFFT's kernels not included). */
 kp_status kp_plan_launch_count(kp_plan plan, int64_t* count);
 
+/* x = A^H y like kp_sense_adjoint, but with no plan and no device allocation: for callers
+ * that reserve all device memory up front and may not let a library allocate afterwards
+ * (for example a real-time reconstruction service with a fixed memory pool).  The paper has
+ * no counterpart; this is a deployment variant of the adjoint.
+ * params: sizes as for kp_plan_create (wavelet_levels ignored); traj_dev float32 [M][ndim];
+ * maps_dev complex64 [C][N]; y_dev complex64 [C][M]; x_dev complex64 [N] (output).
+ * Work space is one fixed 4 MiB device array built into the library (2^19 complex64 values,
+ * held on every GPU that loads the library until exit); problems needing more than
+ * C x (G + G / g_last x n_last) values are rejected with KP_EINVAL (G = prod g_d, g_d the
+ * oversampled grid).  Its device address is looked up on the first call on each device,
+ * with that device current; make that first call before any stream capture.  The grid is
+ * cleared at the start of every call; calls that overlap on the GPU share the array and race,
+ * so issue them one at a time.  The inverse DFT is evaluated directly (no cuFFT plan), so the
+ * result matches kp_sense_adjoint to float32 rounding.  Samples with a coordinate outside
+ * [-N_d/2, N_d/2] or not finite are skipped (this path cannot report them without a
+ * synchronisation; kp_plan_set_trajectory validates a trajectory).  Asynchronous. */
+kp_status kp_sense_adjoint_noalloc(const kp_params* params, const float* traj_dev, const void* maps_dev,
+                                   const void* y_dev, void* x_dev, void* stream);
+
 /* Number of grid tiles and the longest tile's sample count after kp_plan_set_trajectory
  * (diagnostics for load balance). */
 kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_samples);

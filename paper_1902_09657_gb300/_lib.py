@@ -58,6 +58,7 @@ _SIGS = {
     "kp_wavelet": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "kp_plan_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "kp_plan_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "kp_sense_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(KpParams), _vp, _vp, _vp, _vp, _vp]),
     "kp_plan_tile_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
 }
 
