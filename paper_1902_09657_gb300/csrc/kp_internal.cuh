@@ -63,11 +63,19 @@ struct Geom {
 };
 
 // Spreading tiles: the grid is cut into tiles of ts[d] points per axis (edge tiles smaller).
+// Tiles partition the shifted index p = (i + sh) mod g of each axis, sh = ts/2, so that
+// the densely sampled k-space centre (grid index 0) falls in the middle of a tile.
 struct Tiles {
     int ts[MAXD];
     int nt[MAXD];        // tiles per axis
+    int sh[MAXD];        // index shift
     int64_t ntiles;
 };
+
+// shifted tile coordinate of grid index i (0 <= i < g)
+__host__ __device__ __forceinline__ int tshift(int i, int sh, int g) { int p = i + sh; return p >= g ? p - g : p; }
+// grid index of shifted coordinate p (0 <= p < g)
+__host__ __device__ __forceinline__ int tunshift(int p, int sh, int g) { int i = p - sh; return i < 0 ? i + g : i; }
 
 // ---------------------------------------------------------------- complex storage helpers
 __host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -128,15 +136,19 @@ struct kp_plan_s {
     int* d_item_off = nullptr;       // [ntiles + 1]
     int* d_slot_off = nullptr;       // [ntiles + 1] first partial slot of each split tile
     int* d_nslots = nullptr;         // [ntiles + 1] partial slots per tile (0 = not split)
-    float2* d_partial = nullptr;     // [slots][C][tile points]
-    int64_t n_slots = 0;
-    size_t partial_cap = 0;
-    int chunk = 256;                 // samples per spreading work item
+    int* d_split = nullptr;          // tiles whose list spans several work items
+    int64_t n_split = 0, split_cap = 0;
+    int* d_k0 = nullptr;             // [D][M] wrapped first tap per sorted sample
+    float* d_wt = nullptr;           // [D * W][M] Kaiser-Bessel weights per sorted sample
+    int chunk = 256;                 // samples per work item (spreading and interpolation)
+    int4* d_iitems = nullptr;        // interpolation work items {tile, begin, end, -1} over d_off ranges
+    int64_t n_iitems = 0, iitems_cap = 0;
 
     // operator data
     void* d_maps = nullptr;          // [C][N] in maps_t storage
     float* d_apod = nullptr;         // [sum n_d] 1/Phi_d(n_d) per axis
-    float2* d_grid = nullptr;        // [C][G] work grid
+    float2* d_grid = nullptr;        // [C][G] forward work grid
+    float2* d_grid2 = nullptr;       // [C][G] adjoint (spreading) grid
     cufftHandle fft = 0;
     bool fft_ok = false;
 
@@ -152,7 +164,9 @@ struct kp_plan_s {
     float2* d_x = nullptr;           // [N] primal
     float2* d_xbar = nullptr;        // [N] extrapolated primal
     float2* d_z = nullptr;           // [N] prox input / wavelet work
-    float2* d_w = nullptr;           // [N] scratch image
+    float2* d_w = nullptr;           // [N] scratch image / wavelet coefficients
+    float2* d_wl0 = nullptr;         // [N / 2^D] wavelet approximation ping-pong buffers
+    float2* d_wl1 = nullptr;
     double* d_red = nullptr;         // [8] reductions
     float* d_sched = nullptr;        // [3 * cap] sigma, tau, theta per iteration
     double* d_schedd = nullptr;      // [4] lmax, pmin, sigma_last, tau_last
@@ -193,6 +207,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
 // A x: x [N] complex64 -> out [C][M].  Output in sorted order (perm == nullptr) or user
 // order.  mode 0: plain; 1: multiply by p (sorted order); 2: PDHG dual update (uses p, y,
 // sched, iter).
+kp_status build_tap_tables(kp_plan p, cudaStream_t st);
 kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, const int* perm, cudaStream_t st);
 kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st);
 kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st);
@@ -204,6 +219,7 @@ kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st);
 
 // kp_pdhg.cu
 kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st);
+kp_status wavelet_prox_extrap(kp_plan p, float lambda, cudaStream_t st);
 void daubechies4(float h[8]);
 kp_status upload_wavelet_filter(const float h[8]);
 void drop_graphs(kp_plan p);

@@ -4,11 +4,15 @@
 // Forward:  fwd_pre (coil multiply, 1/Phi apodisation, centred zero padding; writes the
 //           whole grid) -> cuFFT C2C forward, batch C -> interp (W^D taps per sample,
 //           one thread per sorted sample, all coils, N^{-1/2}).
-// Adjoint:  spread (one CTA per (tile, chunk) work item; a warp takes one sample at a
-//           time with its lanes over (tap, coil) pairs, so shared-memory atomics within a
-//           warp never collide; single-chunk tiles store straight to the grid, split tiles
-//           store partial tiles that a reduction pass sums) -> cuFFT C2C inverse ->
-//           adj_post (crop, 1/Phi, conj(s_c) coil combine, N^{-1/2}).
+// Adjoint:  spread into a second grid (one CTA per (tile, chunk) work item; each sample is
+//           taken by a group of lanes, one lane per tap, looping over coils, so shared-memory
+//           atomics of one sample never collide; single-chunk tiles store straight to the
+//           grid, chunks of split tiles add their tile with global atomics into a region
+//           cleared just before) -> cuFFT C2C inverse -> adj_post (crop, 1/Phi, conj(s_c)
+//           coil combine, N^{-1/2}).
+// The Kaiser-Bessel weights and first taps of every sample are tabulated once per
+// trajectory (sorted order, structure of arrays), so no Bessel function is evaluated
+// inside the iteration.
 // The grid coordinates t = f g/n are float32; the first tap is k0 = ceil(t) - W/2, which equals
 // ceil(t - W/2) exactly and involves no rounding, so |t - k| <= W/2 for every tap.
 #include "kp_internal.cuh"
@@ -34,22 +38,47 @@ struct Taps {
 };
 
 template <int D>
-__device__ __forceinline__ void make_taps(const float* __restrict__ t, int64_t s, const Geom& geo, Taps<D>& tp) {
+__device__ __forceinline__ void make_taps(const int* __restrict__ k0t, const float* __restrict__ wt, int64_t s,
+                                          const Geom& geo, Taps<D>& tp) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        float td = t[(int64_t)d * geo.M + s];
-        int k0 = (int)ceilf(td) - KW / 2;
+        const int k0w = k0t[(int64_t)d * geo.M + s];
         int stride = 1;
         for (int e = d + 1; e < D; ++e) stride *= geo.g[e];
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
-            int k = k0 + j;
-            tp.w[d][j] = kbw(td - (float)k, geo.beta[d]);
-            int ix = wrapg(k, geo.g[d]);
+            int ix = k0w + j;
+            if (ix >= geo.g[d]) ix -= geo.g[d];
+            tp.w[d][j] = wt[(int64_t)(d * KW + j) * geo.M + s];
             tp.idx[d][j] = ix;
             tp.off[d][j] = ix * stride;
         }
     }
+}
+
+// Tap tables of the sorted samples: wrapped first tap k0 = ceil(t) - W/2 (mod g) and the
+// Kaiser-Bessel weights phi(t - k) of the W taps per axis.
+template <int D>
+__global__ void k_tap_tables(const float* __restrict__ t, Geom geo, int* __restrict__ k0t, float* __restrict__ wt) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= geo.M) return;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float td = t[(int64_t)d * geo.M + s];
+        const int k0 = (int)ceilf(td) - KW / 2;
+        k0t[(int64_t)d * geo.M + s] = wrapg(k0, geo.g[d]);
+#pragma unroll
+        for (int j = 0; j < KW; ++j) wt[(int64_t)(d * KW + j) * geo.M + s] = kbw(td - (float)(k0 + j), geo.beta[d]);
+    }
+}
+
+kp_status build_tap_tables(kp_plan p, cudaStream_t st) {
+    const Geom& g = p->geo;
+    if (g.D == 2) k_tap_tables<2><<<nblk(g.M, 256), 256, 0, st>>>(p->d_t, g, p->d_k0, p->d_wt);
+    else k_tap_tables<3><<<nblk(g.M, 256), 256, 0, st>>>(p->d_t, g, p->d_k0, p->d_wt);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    return KP_OK;
 }
 
 // sum over taps of w * grid[c] for one coil.
@@ -130,214 +159,269 @@ __global__ void k_fwd_pre(const float2* __restrict__ x, const MT* __restrict__ m
     }
 }
 
-// ---------------------------------------------------------------- forward: interp variants
-template <int D, typename OT>
-__global__ void k_interp_out(const float* __restrict__ t, const float2* __restrict__ grid, Geom geo,
-                             const int* __restrict__ perm, OT* __restrict__ out) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= geo.M) return;
-    Taps<D> tp;
-    make_taps<D>(t, s, geo, tp);
-    int64_t o = perm ? perm[s] : s;
-    for (int c = 0; c < geo.C; ++c) {
-        float2 v = gather_coil<D>(grid + (size_t)c * geo.G, tp);
-        v.x *= geo.rsqrtN;
-        v.y *= geo.rsqrtN;
-        stc<OT>(out, (size_t)c * geo.M + o, v);
-    }
-}
+// ---------------------------------------------------------------- forward: interpolation
+// One CTA per (tile chunk, coil group): the grid region the tile's samples read
+// ((ts + W - 1)^D points per coil, periodic) is staged in shared memory with coalesced loads,
+// then each thread interpolates one sample for the group's coils from shared memory.
+constexpr int IP_CH = 4;           // coils per CTA (blockIdx.y selects the group)
+constexpr int IP_THREADS = 256;
 
-template <int D>
-__global__ void k_interp_scaled(const float* __restrict__ t, const float2* __restrict__ grid, Geom geo,
-                                const float* __restrict__ ps, float2* __restrict__ out) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= geo.M) return;
-    Taps<D> tp;
-    make_taps<D>(t, s, geo, tp);
-    for (int c = 0; c < geo.C; ++c) {
-        size_t o = (size_t)c * geo.M + s;
-        float2 v = gather_coil<D>(grid + (size_t)c * geo.G, tp);
-        float sc = geo.rsqrtN * (ps ? ps[o] : 1.f);
-        out[o] = make_float2(v.x * sc, v.y * sc);
-    }
-}
+struct InterpIO {
+    void* out;           // mode 0: [C][M] storage type T, index perm[s] (or s)
+    const int* perm;
+    float2* outs;        // mode 1: [C][M] sorted, scaled by p
+    const float* ps;     // modes 1, 2: sorted preconditioner
+    const void* ys;      // mode 2: sorted measurements, storage type T
+    float2* u;           // mode 2: dual variable, sorted
+    const float* sched;
+    const int* iter;
+};
 
-// PDHG dual step (Sec. 4.1): u <- (u + sigma p (A xbar - y)) / (1 + sigma p).
-template <int D, typename YT>
-__global__ void k_interp_dual(const float* __restrict__ t, const float2* __restrict__ grid, Geom geo,
-                              const YT* __restrict__ ys, const float* __restrict__ ps, float2* __restrict__ u,
-                              const float* __restrict__ sched, const int* __restrict__ iter) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= geo.M) return;
-    const float sigma = sched[3 * (*iter)];
-    Taps<D> tp;
-    make_taps<D>(t, s, geo, tp);
-    for (int c = 0; c < geo.C; ++c) {
-        size_t o = (size_t)c * geo.M + s;
-        float2 v = gather_coil<D>(grid + (size_t)c * geo.G, tp);
-        float2 y = ldc<YT>(ys, o);
-        float sp = sigma * ps[o];
-        float inv = 1.f / (1.f + sp);
-        float2 uo = u[o];
-        float2 un;
-        un.x = (uo.x + sp * (v.x * geo.rsqrtN - y.x)) * inv;
-        un.y = (uo.y + sp * (v.y * geo.rsqrtN - y.y)) * inv;
-        u[o] = un;
+template <int D, int MODE, typename T>
+__global__ void __launch_bounds__(IP_THREADS)
+k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const float* __restrict__ wt,
+              const float2* __restrict__ grid, Geom geo, Tiles tl, InterpIO io) {
+    extern __shared__ float2 sg[];    // [IP_CH][R^D]
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z;
+    const int c0 = blockIdx.y * IP_CH;
+    const int cc = min(IP_CH, geo.C - c0);
+    int o[MAXD], R[MAXD], rs[MAXD];
+    {
+        int r = tile;
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            R[d] = tl.ts[d] + KW - 1;
+        }
+        int st = 1;
+        for (int d = D - 1; d >= 0; --d) { rs[d] = st; st *= R[d]; }
+    }
+    int Rtot = 1;
+    for (int d = 0; d < D; ++d) Rtot *= R[d];
+    for (int idx = threadIdx.x; idx < cc * Rtot; idx += blockDim.x) {
+        const int c = idx / Rtot;
+        int r = idx - c * Rtot;
+        int64_t flat = 0;
+        int lrev[MAXD];
+        for (int d = D - 1; d >= 0; --d) { lrev[d] = r % R[d]; r /= R[d]; }
+        for (int d = 0; d < D; ++d) {
+            int pp = o[d] + lrev[d];
+            if (pp >= geo.g[d]) pp -= geo.g[d];
+            flat = flat * geo.g[d] + tunshift(pp, tl.sh[d], geo.g[d]);
+        }
+        sg[c * Rtot + (idx - c * Rtot)] = __ldg(grid + (size_t)(c0 + c) * geo.G + flat);
+    }
+    __syncthreads();
+    float sigma = 0.f;
+    if (MODE == 2) sigma = io.sched[3 * (*io.iter)];
+    for (int s = beg + threadIdx.x; s < end; s += blockDim.x) {
+        float w[D][KW];
+        int lb = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+            lb += (p0 - o[d]) * rs[d];
+#pragma unroll
+            for (int j = 0; j < KW; ++j) w[d][j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+        }
+        for (int c = 0; c < cc; ++c) {
+            const float2* base = sg + c * Rtot + lb;
+            float2 acc = make_float2(0.f, 0.f);
+            if (D == 2) {
+#pragma unroll
+                for (int a = 0; a < KW; ++a)
+#pragma unroll
+                    for (int b = 0; b < KW; ++b) {
+                        const float ww = w[0][a] * w[D - 1][b];
+                        const float2 v = base[a * rs[0] + b];
+                        acc.x = fmaf(ww, v.x, acc.x);
+                        acc.y = fmaf(ww, v.y, acc.y);
+                    }
+            } else {
+#pragma unroll
+                for (int a = 0; a < KW; ++a)
+#pragma unroll
+                    for (int b = 0; b < KW; ++b) {
+                        const float wab = w[0][a] * w[1 % D][b];
+#pragma unroll
+                        for (int e = 0; e < KW; ++e) {
+                            const float ww = wab * w[D - 1][e];
+                            const float2 v = base[a * rs[0] + b * rs[1 % D] + e];
+                            acc.x = fmaf(ww, v.x, acc.x);
+                            acc.y = fmaf(ww, v.y, acc.y);
+                        }
+                    }
+            }
+            acc.x *= geo.rsqrtN;
+            acc.y *= geo.rsqrtN;
+            const size_t os = (size_t)(c0 + c) * geo.M + s;
+            if (MODE == 0) {
+                const int64_t oi = io.perm ? io.perm[s] : s;
+                stc<T>((T*)io.out, (size_t)(c0 + c) * geo.M + oi, acc);
+            } else if (MODE == 1) {
+                const float sc = io.ps ? io.ps[os] : 1.f;
+                io.outs[os] = make_float2(acc.x * sc, acc.y * sc);
+            } else {
+                // PDHG dual step (Sec. 4.1): u <- (u + sigma p (A xbar - y)) / (1 + sigma p)
+                const float2 y = ldc<T>((const T*)io.ys, os);
+                const float sp = sigma * io.ps[os];
+                const float inv = 1.f / (1.f + sp);
+                const float2 uo = io.u[os];
+                io.u[os] = make_float2((uo.x + sp * (acc.x - y.x)) * inv, (uo.y + sp * (acc.y - y.y)) * inv);
+            }
+        }
     }
 }
 
 // ---------------------------------------------------------------- adjoint: spread
-constexpr int SP_CH = 16;          // coils per shared-memory pass
-constexpr int SP_THREADS = 256;
+// One CTA per (spreading work item, coil group).  The item's samples (their coil values,
+// first taps and weights) are staged in shared memory by all threads at once; then each
+// warp takes one sample at a time, its lanes covering distinct (tap, coil) pairs, and adds
+// into its own private copy of the tile, so no atomics are needed.  The private copies are
+// summed and the tile is stored (or, for a tile split over several items, added with global
+// atomics into a region cleared beforehand).  Tile coordinates are shifted (Tiles::sh).
+constexpr int SP_CH = 4;           // coils per CTA
+constexpr int SP_THREADS = 128;    // 4 warps, 4 private tile copies
+constexpr int SP_CHUNK = 256;      // samples per work item (== plan chunk)
 
 struct SpreadLayout {
-    int ls[MAXD];      // shared-memory strides of the local tile index (padded against bank conflicts)
-    int plane;         // floats per coil plane (re and im planes are separate)
-    int P;             // unpadded tile points
+    int ls[MAXD];      // shared-memory strides of the local tile index
+    int plane;         // floats per (warp, coil, re/im) plane
+    int P;             // tile points
 };
 
 static SpreadLayout spread_layout(const Tiles& tl, int D) {
     SpreadLayout L{};
-    int last = D - 1;
-    L.ls[last] = 1;
-    int ext = tl.ts[last] + 4;
-    for (int d = last - 1; d >= 0; --d) {
-        L.ls[d] = ext;
-        ext *= tl.ts[d] + (d > 0 ? 1 : 0);
-    }
-    int pl = ext;
-    pl = ((pl + 31) / 32) * 32 + 16;
-    L.plane = pl;
-    L.P = 1;
-    for (int d = 0; d < D; ++d) L.P *= tl.ts[d];
+    int st = 1;
+    for (int d = D - 1; d >= 0; --d) { L.ls[d] = st; st *= tl.ts[d]; }
+    L.P = st;
+    L.plane = st;
     return L;
-}
-
-// Weight and shared-memory offset of tap q (axis-major digits, last axis fastest) of a
-// sample, or false if that tap falls outside the tile.
-template <int D>
-__device__ __forceinline__ bool tap_local(int q, const int* k0, const float* td, const int* o, const int* e,
-                                          const Geom& geo, const SpreadLayout& L, float& w, int& lo) {
-    w = 1.f;
-    lo = 0;
-    bool ok = true;
-#pragma unroll
-    for (int d = D - 1; d >= 0; --d) {
-        int j = q % KW;
-        q /= KW;
-        int k = k0[d] + j;
-        int l = wrapg(k, geo.g[d]) - o[d];
-        if (l < 0 || l >= e[d]) ok = false;
-        w *= kbw(td[d] - (float)k, geo.beta[d]);
-        lo += l * L.ls[d];
-    }
-    return ok;
 }
 
 template <int D, typename UT>
 __global__ void __launch_bounds__(SP_THREADS)
-k_spread(const float* __restrict__ t, const UT* __restrict__ u, const int* __restrict__ perm,
-         const int* __restrict__ ext, const int4* __restrict__ items, Geom geo, Tiles tl, SpreadLayout L,
-         float2* __restrict__ grid, float2* __restrict__ partial) {
-    extern __shared__ float sacc[];   // [CH][2][plane]
+k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+         const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
+         Tiles tl, SpreadLayout L, float2* __restrict__ grid) {
+    extern __shared__ float smem[];
+    constexpr int NW = SP_THREADS / 32;
+    float* acc = smem;                                              // [NW][SP_CH][2][P]
+    float2* su = (float2*)(acc + NW * SP_CH * 2 * L.plane);         // [SP_CHUNK][SP_CH]
+    float* sw = (float*)(su + SP_CHUNK * SP_CH);                    // [SP_CHUNK][D*KW]
+    int* sl = (int*)(sw + SP_CHUNK * D * KW);                       // [SP_CHUNK][D] local first tap (may be < 0)
     const int4 it = items[blockIdx.x];
-    const int tile = it.x, beg = it.y, end = it.z, slot = it.w;
+    const int tile = it.x, beg = it.y, end = it.z;
+    const bool split = it.w >= 0;
+    const int c0 = blockIdx.y * SP_CH;
+    const int cc = min(SP_CH, geo.C - c0);
     int o[MAXD], e[MAXD];
     {
         int r = tile;
         for (int d = D - 1; d >= 0; --d) {
-            int tc = r % tl.nt[d];
+            const int tc = r % tl.nt[d];
             r /= tl.nt[d];
             o[d] = tc * tl.ts[d];
             e[d] = min(tl.ts[d], geo.g[d] - o[d]);
         }
     }
-    constexpr int TAPS = D == 2 ? KW * KW : KW * KW * KW;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c0 = 0; c0 < geo.C; c0 += SP_CH) {
-        const int cc = min(SP_CH, geo.C - c0);
-        for (int i = threadIdx.x; i < cc * 2 * L.plane; i += blockDim.x) sacc[i] = 0.f;
-        __syncthreads();
-        for (int ei = beg + warp; ei < end; ei += nw) {
-            const int s = ext[ei];
-            const int64_t un = perm ? perm[s] : s;
-            // per-axis tap positions relative to the tile, and weights
-            float td[D];
-            int k0[D];
+    const int n = end - beg;
+    for (int i = threadIdx.x; i < NW * SP_CH * 2 * L.plane; i += blockDim.x) acc[i] = 0.f;
+    // stage the item's samples
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = ext[beg + i];
+        const int64_t un = perm ? perm[s] : s;
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                td[d] = t[(int64_t)d * geo.M + s];
-                k0[d] = (int)ceilf(td[d]) - KW / 2;
-            }
-            if (TAPS < 32) {
-                // 2D: two lanes per tap, each taking every other coil
-                constexpr int LPT = TAPS < 32 ? 32 / TAPS : 1;
-                const int q = lane % TAPS;
-                float w;
-                int lo;
-                if (tap_local<D>(q, k0, td, o, e, geo, L, w, lo)) {
-                    for (int c = lane / TAPS; c < cc; c += LPT) {
-                        float2 uv = ldc<UT>(u, (size_t)(c0 + c) * geo.M + un);
-                        float* pl = sacc + (size_t)c * 2 * L.plane;
-                        atomicAdd(pl + lo, w * uv.x);
-                        atomicAdd(pl + L.plane + lo, w * uv.y);
-                    }
-                }
-            } else {
-                for (int q = lane; q < TAPS; q += 32) {
-                    float w;
-                    int lo;
-                    if (!tap_local<D>(q, k0, td, o, e, geo, L, w, lo)) continue;
-                    for (int c = 0; c < cc; ++c) {
-                        float2 uv = ldc<UT>(u, (size_t)(c0 + c) * geo.M + un);
-                        float* pl = sacc + (size_t)c * 2 * L.plane;
-                        atomicAdd(pl + lo, w * uv.x);
-                        atomicAdd(pl + L.plane + lo, w * uv.y);
-                    }
-                }
-            }
+        for (int c = 0; c < SP_CH; ++c)
+            su[i * SP_CH + c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];
+            // the footprint may start in the previous tile (or wrap around the axis)
+            if (p0 > e[d]) p0 -= geo.g[d];
+            sl[i * D + d] = p0;
+#pragma unroll
+            for (int j = 0; j < KW; ++j) sw[i * D * KW + d * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
         }
-        __syncthreads();
-        // write out the tile (or its partial)
-        for (int i = threadIdx.x; i < cc * L.P; i += blockDim.x) {
-            const int c = i / L.P;
-            int r = i % L.P;
-            int lidx[MAXD];
-            for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
-            bool in = true;
+    }
+    __syncthreads();
+    constexpr int TAPS = D == 2 ? KW * KW : KW * KW * KW;
+    constexpr int LPT = TAPS < 32 ? 32 / TAPS : 1;     // lanes per tap (2D: 2, coils split between them)
+    constexpr int TPL = TAPS > 32 ? TAPS / 32 : 1;     // taps per lane (3D: 2)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* my = acc + warp * SP_CH * 2 * L.plane;
+    for (int i = warp; i < n; i += NW) {
+#pragma unroll
+        for (int tq = 0; tq < TPL; ++tq) {
+            int q = (TAPS < 32 ? lane % TAPS : lane) + 32 * tq;
+            float w = 1.f;
             int lo = 0;
-            int64_t gflat = 0;
-            for (int d = 0; d < D; ++d) {
-                if (lidx[d] >= e[d]) in = false;
-                lo += lidx[d] * L.ls[d];
-                gflat = gflat * geo.g[d] + o[d] + lidx[d];
+            bool ok = true;
+#pragma unroll
+            for (int d = D - 1; d >= 0; --d) {
+                const int j = q % KW;
+                q /= KW;
+                int pp = o[d] + sl[i * D + d] + j;      // shifted coordinate of the tap
+                if (pp < 0) pp += geo.g[d];
+                else if (pp >= geo.g[d]) pp -= geo.g[d];
+                const int l = pp - o[d];
+                if (l < 0 || l >= e[d]) ok = false;
+                w *= sw[i * D * KW + d * KW + j];
+                lo += l * L.ls[d];
             }
-            const float* pl = sacc + (size_t)c * 2 * L.plane;
-            float2 v = make_float2(pl[lo], pl[L.plane + lo]);
-            if (slot < 0) {
-                if (in) grid[(size_t)(c0 + c) * geo.G + gflat] = v;
-            } else {
-                partial[((size_t)slot * geo.C + c0 + c) * L.P + (i % L.P)] = v;
+            if (!ok) continue;
+            for (int c = (TAPS < 32 ? lane / TAPS : 0); c < cc; c += LPT) {
+                const float2 uv = su[i * SP_CH + c];
+                float* pl = my + c * 2 * L.plane;
+                pl[lo] += w * uv.x;
+                pl[L.plane + lo] += w * uv.y;
             }
         }
-        __syncthreads();
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cc * L.P; i += blockDim.x) {
+        const int c = i / L.P;
+        const int r0 = i - c * L.P;
+        int r = r0;
+        int lidx[MAXD];
+        for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
+        bool in = true;
+        int64_t gflat = 0;
+        for (int d = 0; d < D; ++d) {
+            if (lidx[d] >= e[d]) in = false;
+            gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
+        }
+        if (!in) continue;
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const float* pl = acc + (w * SP_CH + c) * 2 * L.plane;
+            v.x += pl[r0];
+            v.y += pl[L.plane + r0];
+        }
+        float2* dst = grid + (size_t)(c0 + c) * geo.G + gflat;
+        if (split) {
+            atomicAdd(&dst->x, v.x);
+            atomicAdd(&dst->y, v.y);
+        } else {
+            *dst = v;
+        }
     }
 }
 
-// Sum the partial tiles of split tiles into the grid.
+// Clear the grid region of every split tile (all coils) before the spreading kernel adds
+// the tile's chunks into it.
 template <int D>
-__global__ void k_spread_reduce(const int* __restrict__ slot_off, const int* __restrict__ nslots,
-                                const float2* __restrict__ partial, Geom geo, Tiles tl, int P,
-                                float2* __restrict__ grid) {
-    const int tile = blockIdx.x;
-    const int ns = nslots[tile];
-    if (ns == 0) return;
-    const int s0 = slot_off[tile];
+__global__ void k_zero_split(const int* __restrict__ split_tiles, Geom geo, Tiles tl, int P, float2* __restrict__ grid) {
+    const int tile = split_tiles[blockIdx.x];
     int o[MAXD], e[MAXD];
     {
         int r = tile;
         for (int d = D - 1; d >= 0; --d) {
-            int tc = r % tl.nt[d];
+            const int tc = r % tl.nt[d];
             r /= tl.nt[d];
             o[d] = tc * tl.ts[d];
             e[d] = min(tl.ts[d], geo.g[d] - o[d]);
@@ -352,16 +436,9 @@ __global__ void k_spread_reduce(const int* __restrict__ slot_off, const int* __r
         int64_t gflat = 0;
         for (int d = 0; d < D; ++d) {
             if (lidx[d] >= e[d]) in = false;
-            gflat = gflat * geo.g[d] + o[d] + lidx[d];
+            gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
         }
-        if (!in) continue;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int k = 0; k < ns; ++k) {
-            float2 v = partial[((size_t)(s0 + k) * geo.C + c) * P + (i % P)];
-            acc.x += v.x;
-            acc.y += v.y;
-        }
-        grid[(size_t)c * geo.G + gflat] = acc;
+        if (in) grid[(size_t)c * geo.G + gflat] = make_float2(0.f, 0.f);
     }
 }
 
@@ -470,66 +547,79 @@ static kp_status fwd_grid(kp_plan p, const float2* x, cudaStream_t st) {
     return KP_OK;
 }
 
-kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, const int* perm, cudaStream_t st) {
-    KP_TRY(fwd_grid(p, x, st));
+template <int MODE>
+static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaStream_t st) {
     const Geom& g = p->geo;
+    size_t rt = 1;
+    for (int d = 0; d < g.D; ++d) rt *= p->tiles.ts[d] + KW - 1;
+    const size_t smem = (size_t)IP_CH * rt * sizeof(float2);
+    const dim3 grid((unsigned)p->n_iitems, (g.C + IP_CH - 1) / IP_CH);
+    static bool attr[2][3][3] = {};
     mark(p, PH_INTERP, st);
     p->launches += 1;
-    KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(out_t, OT,
-        k_interp_out<DD, OT><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_grid, g, perm, (OT*)out)));
+    if (p->n_iitems == 0) return KP_OK;
+    KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(t, T,
+        if (!attr[DD - 2][MODE][t]) {
+            KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_tile<DD, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            attr[DD - 2][MODE][t] = true;
+        }
+        k_interp_tile<DD, MODE, T><<<grid, IP_THREADS, smem, st>>>(p->d_iitems, p->d_k0, p->d_wt, p->d_grid, g, p->tiles, io)));
     KP_LAUNCH_CHECK();
     return KP_OK;
+}
+
+kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, const int* perm, cudaStream_t st) {
+    KP_TRY(fwd_grid(p, x, st));
+    InterpIO io{};
+    io.out = out;
+    io.perm = perm;
+    return launch_interp<0>(p, out_t, io, st);
 }
 
 kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st) {
     KP_TRY(fwd_grid(p, x, st));
-    const Geom& g = p->geo;
-    mark(p, PH_INTERP, st);
-    p->launches += 1;
-    KP_DISPATCH_D(g.D, DD, k_interp_scaled<DD><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_grid, g, ps, out_sorted));
-    KP_LAUNCH_CHECK();
-    return KP_OK;
+    InterpIO io{};
+    io.outs = out_sorted;
+    io.ps = ps;
+    return launch_interp<1>(p, KP_C64, io, st);
 }
 
 kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st) {
     KP_TRY(fwd_grid(p, xbar, st));
-    const Geom& g = p->geo;
-    mark(p, PH_INTERP, st);
-    p->launches += 1;
-    KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(p->ys_t, YT,
-        k_interp_dual<DD, YT><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_grid, g, (const YT*)p->d_ys, p->d_ps,
-                                                             p->d_u, p->d_sched, p->d_iter)));
-    KP_LAUNCH_CHECK();
-    return KP_OK;
+    InterpIO io{};
+    io.ys = p->d_ys;
+    io.ps = p->d_ps;
+    io.u = p->d_u;
+    io.sched = p->d_sched;
+    io.iter = p->d_iter;
+    return launch_interp<2>(p, p->ys_t, io, st);
 }
 
 kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st) {
     const Geom& g = p->geo;
     const SpreadLayout L = spread_layout(p->tiles, g.D);
-    const int cc = g.C < SP_CH ? g.C : SP_CH;
-    const size_t smem = (size_t)cc * 2 * L.plane * sizeof(float);
+    const size_t smem = (size_t)(SP_THREADS / 32) * SP_CH * 2 * L.plane * sizeof(float) +
+                        (size_t)SP_CHUNK * (SP_CH * sizeof(float2) + g.D * KW * sizeof(float) + g.D * sizeof(int));
     static bool attr_set[2][3] = {{false}};
     mark(p, PH_SPREAD, st);
+    if (p->n_split > 0) {
+        KP_DISPATCH_D(g.D, DD, k_zero_split<DD><<<(unsigned)p->n_split, 256, 0, st>>>(p->d_split, g, p->tiles, L.P,
+                                                                                      p->d_grid2));
+        KP_LAUNCH_CHECK();
+        p->launches += 1;
+    }
     p->launches += 1;
     KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
         if (!attr_set[DD - 2][u_t]) {
             KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
             attr_set[DD - 2][u_t] = true;
         }
-        k_spread<DD, UT><<<(unsigned)p->n_items, SP_THREADS, smem, st>>>(p->d_t, (const UT*)u, perm, p->d_ext,
-                                                                        p->d_items, g, p->tiles, L, p->d_grid,
-                                                                        p->d_partial)));
+        k_spread<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SP_CH - 1) / SP_CH), SP_THREADS, smem, st>>>(p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext,
+                                                                        p->d_items, g, p->tiles, L, p->d_grid2)));
     KP_LAUNCH_CHECK();
-    if (p->n_slots > 0) {
-        mark(p, PH_SPREAD_RED, st);
-        p->launches += 1;
-        KP_DISPATCH_D(g.D, DD, k_spread_reduce<DD><<<(unsigned)p->tiles.ntiles, 256, 0, st>>>(
-            p->d_slot_off, p->d_nslots, p->d_partial, g, p->tiles, L.P, p->d_grid));
-        KP_LAUNCH_CHECK();
-    }
     mark(p, PH_FFT_INV, st);
     KP_TRY_CUFFT(cufftSetStream(p->fft, st));
-    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_grid, CUFFT_INVERSE));
+    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
     return KP_OK;
 }
 
@@ -539,7 +629,7 @@ kp_status grid_to_image(kp_plan p, float2* x, cudaStream_t st) {
     mark(p, PH_ADJ, st);
     p->launches += 1;
     KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
-        k_adj_image<DD, MT><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid, p->unit_maps ? nullptr : (const MT*)p->d_maps,
+        k_adj_image<DD, MT><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid2, p->unit_maps ? nullptr : (const MT*)p->d_maps,
                                                            p->d_apod, g, x)));
     KP_LAUNCH_CHECK();
     return KP_OK;
@@ -552,11 +642,11 @@ kp_status adjoint_primal(kp_plan p, int reg, float lambda, cudaStream_t st) {
     p->launches += 1;
     if (reg == KP_REG_L2) {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
-            k_adj_primal<DD, MT, 0><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
+            k_adj_primal<DD, MT, 0><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid2, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
                                                                    p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda)));
     } else {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
-            k_adj_primal<DD, MT, 1><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
+            k_adj_primal<DD, MT, 1><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid2, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
                                                                    p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda)));
     }
     KP_LAUNCH_CHECK();

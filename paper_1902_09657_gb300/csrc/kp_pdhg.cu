@@ -56,148 +56,6 @@ void daubechies4(float hout[8]) {
     for (int k = 0; k < 8; ++k) hout[k] = (float)(poly[k].real() * std::sqrt(2.0) / sum);
 }
 
-__constant__ float c_h[8];
-__constant__ float c_g[8];
-
-// Analysis filters: scaling h and wavelet g[n] = (-1)^n h[7 - n].
-kp_status upload_wavelet_filter(const float h[8]) {
-    float g[8];
-    for (int n = 0; n < 8; ++n) g[n] = (n & 1 ? -1.f : 1.f) * h[7 - n];
-    KP_TRY_CUDA(cudaMemcpyToSymbol(c_h, h, 8 * sizeof(float)));
-    KP_TRY_CUDA(cudaMemcpyToSymbol(c_g, g, 8 * sizeof(float)));
-    return KP_OK;
-}
-
-// ================================================================ wavelet line kernels
-constexpr int WV = 16;   // lines per CTA
-
-struct WLine {
-    int D;
-    int n[MAXD];     // full image size
-    int b[MAXD];     // current block (approximation) size
-    int axis;
-    int64_t nlines;  // prod_{d != axis} b[d]
-};
-
-__device__ __forceinline__ int64_t line_start(const WLine& wl, int64_t li) {
-    // coordinates over the non-axis dims, last dim fastest
-    int64_t flat = 0, stride = 1;
-    int64_t r = li;
-    for (int d = wl.D - 1; d >= 0; --d) {
-        if (d != wl.axis) {
-            int c = (int)(r % wl.b[d]);
-            r /= wl.b[d];
-            flat += c * stride;
-        }
-        stride *= wl.n[d];
-    }
-    return flat;
-}
-
-template <bool FWD>
-__global__ void k_dwt_axis(float2* __restrict__ img, WLine wl) {
-    extern __shared__ float2 sl[];   // [WV][L]
-    const int L = wl.b[wl.axis];
-    int64_t sa = 1;
-    for (int d = wl.axis + 1; d < wl.D; ++d) sa *= wl.n[d];
-    const bool inner = wl.axis == wl.D - 1;
-    const int64_t l0 = (int64_t)blockIdx.x * WV;
-    const int nthr = blockDim.x;
-    // load
-    for (int idx = threadIdx.x; idx < WV * L; idx += nthr) {
-        int v, l;
-        if (inner) { v = idx / L; l = idx % L; }
-        else { l = idx / WV; v = idx % WV; }
-        int64_t li = l0 + v;
-        if (li < wl.nlines) sl[v * L + l] = img[line_start(wl, li) + l * sa];
-    }
-    __syncthreads();
-    const int K = L / 2;
-    if (FWD) {
-        for (int idx = threadIdx.x; idx < WV * K; idx += nthr) {
-            int v, k;
-            if (inner) { v = idx / K; k = idx % K; }
-            else { k = idx / WV; v = idx % WV; }
-            int64_t li = l0 + v;
-            if (li >= wl.nlines) continue;
-            const float2* s = sl + v * L;
-            float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                int q = (2 * k + n) % L;
-                float2 xv = s[q];
-                a.x = fmaf(c_h[n], xv.x, a.x);
-                a.y = fmaf(c_h[n], xv.y, a.y);
-                d.x = fmaf(c_g[n], xv.x, d.x);
-                d.y = fmaf(c_g[n], xv.y, d.y);
-            }
-            int64_t st = line_start(wl, li);
-            img[st + k * sa] = a;
-            img[st + (K + k) * sa] = d;
-        }
-    } else {
-        for (int idx = threadIdx.x; idx < WV * L; idx += nthr) {
-            int v, j;
-            if (inner) { v = idx / L; j = idx % L; }
-            else { j = idx / WV; v = idx % WV; }
-            int64_t li = l0 + v;
-            if (li >= wl.nlines) continue;
-            const float2* s = sl + v * L;
-            float2 x = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                int n = (j & 1) + 2 * m;
-                int jm = ((j - n) % L + L) % L;
-                int k = jm >> 1;
-                float2 av = s[k], dv = s[K + k];
-                x.x = fmaf(c_h[n], av.x, fmaf(c_g[n], dv.x, x.x));
-                x.y = fmaf(c_h[n], av.y, fmaf(c_g[n], dv.y, x.y));
-            }
-            img[line_start(wl, li) + j * sa] = x;
-        }
-    }
-}
-
-kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st) {
-    const Geom& g = p->geo;
-    const int levels = p->P.wavelet_levels;
-    if (in != out) KP_TRY_CUDA(cudaMemcpyAsync(out, in, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    static bool attr = false;
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_axis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_axis<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
-    auto pass = [&](int lev, int axis, bool fwd) -> kp_status {
-        WLine wl{};
-        wl.D = g.D;
-        wl.axis = axis;
-        wl.nlines = 1;
-        for (int d = 0; d < g.D; ++d) {
-            wl.n[d] = g.n[d];
-            wl.b[d] = g.n[d] >> lev;
-            if (d != axis) wl.nlines *= wl.b[d];
-        }
-        const int L = wl.b[axis];
-        const size_t smem = (size_t)WV * L * sizeof(float2);
-        const unsigned blocks = (unsigned)((wl.nlines + WV - 1) / WV);
-        if (fwd) k_dwt_axis<true><<<blocks, 256, smem, st>>>(out, wl);
-        else k_dwt_axis<false><<<blocks, 256, smem, st>>>(out, wl);
-        KP_LAUNCH_CHECK();
-        p->launches += 1;
-        return KP_OK;
-    };
-    mark(p, forward ? PH_DWT_FWD : PH_DWT_INV, st);
-    if (forward) {
-        for (int lev = 0; lev < levels; ++lev)
-            for (int ax = 0; ax < g.D; ++ax) KP_TRY(pass(lev, ax, true));
-    } else {
-        for (int lev = levels - 1; lev >= 0; --lev)
-            for (int ax = g.D - 1; ax >= 0; --ax) KP_TRY(pass(lev, ax, false));
-    }
-    return KP_OK;
-}
-
 // ================================================================ reductions and small kernels
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -305,29 +163,6 @@ __global__ void k_schedule(double* __restrict__ schedd, const int* __restrict__ 
 
 __global__ void k_advance(int* iter) { *iter += 1; }
 
-// complex soft threshold at tau_k * lambda (Sec. 2: prox of lambda ||W x||_1)
-__global__ void k_soft(float2* __restrict__ z, int64_t n, const float* __restrict__ sched,
-                       const int* __restrict__ iter, float lambda) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float t = sched[3 * (*iter) + 1] * lambda;
-    float2 c = z[i];
-    float m = sqrtf(c.x * c.x + c.y * c.y);
-    float s = m > t ? 1.f - t / m : 0.f;
-    z[i] = make_float2(c.x * s, c.y * s);
-}
-
-// x_new = z; xbar = x_new + theta (x_new - x); x = x_new (Sec. 4.1 extrapolation)
-__global__ void k_extrap(const float2* __restrict__ z, float2* __restrict__ x, float2* __restrict__ xbar, int64_t n,
-                         const float* __restrict__ sched, const int* __restrict__ iter) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float th = sched[3 * (*iter) + 2];
-    float2 xn = z[i], xo = x[i];
-    xbar[i] = make_float2(xn.x + th * (xn.x - xo.x), xn.y + th * (xn.y - xo.y));
-    x[i] = xn;
-}
-
 template <typename T>
 __global__ void k_permute(const T* __restrict__ in, T* __restrict__ out, const int* __restrict__ perm, int64_t M, int C) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -370,17 +205,7 @@ static kp_status issue_iteration(kp_plan p, int reg, float lambda, cudaStream_t 
     KP_TRY(forward_dual(p, p->d_xbar, st));
     KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st));
     KP_TRY(adjoint_primal(p, reg, lambda, st));
-    if (reg == KP_REG_L1_WAVELET) {
-        KP_TRY(wavelet_apply(p, p->d_z, p->d_z, true, st));
-        mark(p, PH_SOFT, st);
-        k_soft<<<nblk(g.N, 256), 256, 0, st>>>(p->d_z, g.N, p->d_sched, p->d_iter, lambda);
-        KP_LAUNCH_CHECK();
-        KP_TRY(wavelet_apply(p, p->d_z, p->d_z, false, st));
-        mark(p, PH_EXTRAP, st);
-        k_extrap<<<nblk(g.N, 256), 256, 0, st>>>(p->d_z, p->d_x, p->d_xbar, g.N, p->d_sched, p->d_iter);
-        KP_LAUNCH_CHECK();
-        p->launches += 2;
-    }
+    if (reg == KP_REG_L1_WAVELET) KP_TRY(wavelet_prox_extrap(p, lambda, st));
     mark(p, PH_OTHER, st);
     k_advance<<<1, 1, 0, st>>>(p->d_iter);
     KP_LAUNCH_CHECK();

@@ -49,7 +49,7 @@ template <int D>
 __device__ __forceinline__ int64_t tile_of(const int* k0w, const Tiles& tl) {
     int64_t key = 0;
     for (int d = 0; d < D; ++d) key = key * tl.nt[d] + k0w[d] / tl.ts[d];
-    return key;
+    return key;   // k0w already shifted
 }
 
 // Pass 1: validate, convert to grid coordinates, key by tile, histogram.
@@ -67,7 +67,7 @@ __global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geo
         float sc = (float)geo.g[d] / (float)geo.n[d];
         float t = bad ? 0.f : f * sc;
         int k0 = (int)ceilf(t) - KW / 2;
-        k0w[d] = wrap(k0, geo.g[d]);
+        k0w[d] = tshift(wrap(k0, geo.g[d]), tl.sh[d], geo.g[d]);
     }
     if (bad) atomicAdd(flag, 1);
     int64_t kk = tile_of<D>(k0w, tl);
@@ -101,8 +101,8 @@ __device__ __forceinline__ void footprint_tiles(const float* __restrict__ t, int
     for (int d = 0; d < D; ++d) {
         float td = t[(int64_t)d * geo.M + s];
         int k0 = (int)ceilf(td) - KW / 2;
-        int a = wrap(k0, geo.g[d]);
-        int b = wrap(k0 + KW - 1, geo.g[d]);
+        int a = tshift(wrap(k0, geo.g[d]), tl.sh[d], geo.g[d]);
+        int b = tshift(wrap(k0 + KW - 1, geo.g[d]), tl.sh[d], geo.g[d]);
         lo[d] = a / tl.ts[d];
         hi[d] = b / tl.ts[d];
     }
@@ -151,6 +151,26 @@ __global__ void k_chunks(const int* __restrict__ ext_off, int64_t ntiles, int ch
     int nc = cnt <= chunk ? 1 : (cnt + chunk - 1) / chunk;
     nch[t] = nc;
     nsl[t] = nc > 1 ? nc : 0;
+}
+
+__global__ void k_ichunks(const int* __restrict__ off, int64_t ntiles, int chunk, int* __restrict__ nch) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int cnt = off[t + 1] - off[t];
+    nch[t] = (cnt + chunk - 1) / chunk;
+}
+
+__global__ void k_iitems(const int* __restrict__ off, const int* __restrict__ item_off, int64_t ntiles, int chunk,
+                         int4* __restrict__ items) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int beg = off[t], end = off[t + 1];
+    const int nc = item_off[t + 1] - item_off[t];
+    for (int k = 0; k < nc; ++k) {
+        const int b = beg + k * chunk;
+        const int e = b + chunk < end ? b + chunk : end;
+        items[item_off[t] + k] = make_int4((int)t, b, e, -1);
+    }
 }
 
 __global__ void k_items(const int* __restrict__ ext_off, const int* __restrict__ item_off,
@@ -235,7 +255,7 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     if ((int64_t)g.C * g.G > ((int64_t)1 << 34)) { delete p; set_error("grid too large"); return KP_EINVAL; }
     Tiles& tl = p->tiles;
     tl.ntiles = 1;
-    for (int d = 0; d < MAXD; ++d) { tl.ts[d] = 1; tl.nt[d] = 1; }
+    for (int d = 0; d < MAXD; ++d) { tl.ts[d] = 1; tl.nt[d] = 1; tl.sh[d] = 0; }
     for (int d = 0; d < D; ++d) {
         // Tile edge: the largest size <= 16 (2D) / 8 (3D) whose last, ragged tile still has at
         // least W - 1 points, so a footprint of W consecutive grid points (with wrap-around)
@@ -249,6 +269,7 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
             }
         }
         tl.ts[d] = ts;
+        tl.sh[d] = ts < g.g[d] ? ts / 2 : 0;
         tl.nt[d] = (g.g[d] + tl.ts[d] - 1) / tl.ts[d];
         tl.ntiles *= tl.nt[d];
     }
@@ -270,6 +291,8 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     KP_A(p->d_ext_off, tl.ntiles + 1);
     KP_A(p->d_ext, (size_t)M << D);
     KP_A(p->d_item_off, tl.ntiles + 1);
+    KP_A(p->d_k0, (size_t)D * M);
+    KP_A(p->d_wt, (size_t)D * KW * M);
     KP_A(p->d_slot_off, tl.ntiles + 1);
     KP_A(p->d_nslots, tl.ntiles + 1);
     KP_A(p->d_flag, 8);
@@ -296,6 +319,7 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
         p->d_maps = mp;
     }
     KP_A(p->d_grid, (size_t)C * G);
+    KP_A(p->d_grid2, (size_t)C * G);
     KP_A(p->d_u, (size_t)C * M);
     {
         char* yp = nullptr;
@@ -309,6 +333,10 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     KP_A(p->d_xbar, N);
     KP_A(p->d_z, N);
     KP_A(p->d_w, N);
+    if (prm->wavelet_levels > 0) {
+        KP_A(p->d_wl0, (N >> D) + 1);
+        KP_A(p->d_wl1, (N >> D) + 1);
+    }
     KP_A(p->d_red, 16);
     KP_A(p->d_schedd, 8);
     KP_A(p->d_iter, 4);
@@ -338,9 +366,10 @@ kp_status plan_destroy_internal(kp_plan p) {
     pre_destroy(p);
     if (p->fft_ok) cufftDestroy(p->fft);
     void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
-                    p->d_items, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_partial,
+                    p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
+                    p->d_grid2,
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
-                    p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_red, p->d_sched, p->d_schedd, p->d_iter};
+                    p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -373,6 +402,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     if (g.D == 2) k_traj_scatter<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t);
     else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t);
     KP_LAUNCH_CHECK();
+    KP_TRY(build_tap_tables(p, st));
     // spreading lists
     KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
     if (g.D == 2) k_ext<2, false><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, nullptr, nullptr);
@@ -402,26 +432,47 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     int tot[2];
     KP_TRY_CUDA(cudaMemcpyAsync(&tot[0], p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaMemcpyAsync(&tot[1], p->d_slot_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int> nsl(tl.ntiles);
+    KP_TRY_CUDA(cudaMemcpyAsync(nsl.data(), p->d_nslots, tl.ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));
     p->n_items = tot[0];
-    p->n_slots = tot[1];
     if (p->n_items > p->items_cap) {
         if (p->d_items) cudaFree(p->d_items);
         p->d_items = nullptr;
         KP_TRY_CUDA(cudaMalloc(&p->d_items, p->n_items * sizeof(int4)));
         p->items_cap = p->n_items;
     }
-    int64_t P = 1;
-    for (int d = 0; d < g.D; ++d) P *= tl.ts[d];
-    const size_t need = (size_t)p->n_slots * g.C * P * sizeof(float2);
-    if (need > p->partial_cap) {
-        if (p->d_partial) cudaFree(p->d_partial);
-        p->d_partial = nullptr;
-        KP_TRY_CUDA(cudaMalloc(&p->d_partial, need));
-        p->partial_cap = need;
+    std::vector<int> split;
+    for (int64_t t = 0; t < tl.ntiles; ++t)
+        if (nsl[t] > 0) split.push_back((int)t);
+    p->n_split = (int64_t)split.size();
+    if (p->n_split > p->split_cap) {
+        if (p->d_split) cudaFree(p->d_split);
+        p->d_split = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_split, p->n_split * sizeof(int)));
+        p->split_cap = p->n_split;
     }
+    if (p->n_split > 0)
+        KP_TRY_CUDA(cudaMemcpy(p->d_split, split.data(), split.size() * sizeof(int), cudaMemcpyHostToDevice));
     k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, p->chunk, p->d_items);
     KP_LAUNCH_CHECK();
+    // interpolation items (own samples of each tile; d_item_off is free again)
+    k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->chunk, p->d_cnt);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
+    KP_LAUNCH_CHECK();
+    int nii = 0;
+    KP_TRY_CUDA(cudaMemcpyAsync(&nii, p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    p->n_iitems = nii;
+    if (p->n_iitems > p->iitems_cap) {
+        if (p->d_iitems) cudaFree(p->d_iitems);
+        p->d_iitems = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_iitems, p->n_iitems * sizeof(int4)));
+        p->iitems_cap = p->n_iitems;
+    }
+    k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_item_off, tl.ntiles, p->chunk, p->d_iitems);
+    KP_LAUNCH_CHECK();
+    p->launches += 3;
     p->launches += 12;
     p->traj_set = true;
     return KP_OK;
