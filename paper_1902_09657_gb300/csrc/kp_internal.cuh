@@ -93,6 +93,71 @@ template <> __device__ inline void stc<__nv_bfloat162>(__nv_bfloat162* p, size_t
 
 inline size_t cdtype_bytes(kp_cdtype t) { return t == KP_C64 ? 8 : 4; }
 
+// A^H at one pixel j (row-major image index): N^{-1/2} prod_d 1/Phi_d(n_d)
+// sum_c conj(s_c[j]) grid_c[n mod g] (maps == nullptr means s_c = 1).
+template <int D, typename MT>
+__device__ __forceinline__ float2 adj_pixel(const float2* __restrict__ grid, const MT* __restrict__ maps,
+                                            const float* __restrict__ apod, const Geom& geo, int64_t j) {
+    int jj[D];
+    int64_t r = j;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) { jj[d] = (int)(r % geo.n[d]); r /= geo.n[d]; }
+    int64_t gi = 0;
+    float a = geo.rsqrtN;
+    int ao = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        int nd = jj[d] - geo.n[d] / 2;
+        int id = nd < 0 ? nd + geo.g[d] : nd;
+        gi = gi * geo.g[d] + id;
+        a *= apod[ao + jj[d]];
+        ao += geo.n[d];
+    }
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < geo.C; ++c) {
+        float2 gv = grid[(size_t)c * geo.G + gi];
+        if (maps) {
+            float2 s = ldc<MT>(maps, (size_t)c * geo.N + j);
+            float2 v = cmulc(s, gv);
+            acc.x += v.x;
+            acc.y += v.y;
+        } else {
+            acc.x += gv.x;
+            acc.y += gv.y;
+        }
+    }
+    return make_float2(acc.x * a, acc.y * a);
+}
+
+
+// Forward pre-step at one pixel: grid_c[n mod g] = s_c[j] v prod_d 1/Phi_d(n_d) for every coil.
+template <int D, typename MT>
+__device__ __forceinline__ void pre_pixel(float2* __restrict__ grid, const MT* __restrict__ maps,
+                                          const float* __restrict__ apod, const Geom& geo, int64_t j, float2 v) {
+    int jj[D];
+    int64_t r = j;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) { jj[d] = (int)(r % geo.n[d]); r /= geo.n[d]; }
+    int64_t gi = 0;
+    float a = 1.f;
+    int ao = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        int nd = jj[d] - geo.n[d] / 2;
+        int id = nd < 0 ? nd + geo.g[d] : nd;
+        gi = gi * geo.g[d] + id;
+        a *= apod[ao + jj[d]];
+        ao += geo.n[d];
+    }
+    v.x *= a;
+    v.y *= a;
+    for (int c = 0; c < geo.C; ++c) {
+        const float2 sv = maps ? ldc<MT>(maps, (size_t)c * geo.N + j) : make_float2(1.f, 0.f);
+        grid[(size_t)c * geo.G + gi] = cmul(sv, v);
+    }
+}
+
+
 // ---------------------------------------------------------------- plan
 struct PrePlan;   // preconditioner workspace (kp_precond.cu)
 
@@ -141,6 +206,9 @@ struct kp_plan_s {
     int* d_k0 = nullptr;             // [D][M] wrapped first tap per sorted sample
     float* d_wt = nullptr;           // [D * W][M] Kaiser-Bessel weights per sorted sample
     int chunk = 256;                 // samples per work item (spreading and interpolation)
+    int spread_variant = 0;          // 0: warp-private tiles, 4 coils per CTA; 1: shared atomics, 16 coils per CTA;
+                                     // 2: one accumulator, each warp owns 4 coils
+    bool spread_tuned = false;
     int4* d_iitems = nullptr;        // interpolation work items {tile, begin, end, -1} over d_off ranges
     int64_t n_iitems = 0, iitems_cap = 0;
 
@@ -149,6 +217,8 @@ struct kp_plan_s {
     float* d_apod = nullptr;         // [sum n_d] 1/Phi_d(n_d) per axis
     float2* d_grid = nullptr;        // [C][G] forward work grid
     float2* d_grid2 = nullptr;       // [C][G] adjoint (spreading) grid
+    float2* d_gridF = nullptr;       // [C][G] forward grid after the FFT (d_grid keeps its zero padding)
+    unsigned int* d_bar = nullptr;   // grid-barrier state of the fused kernels
     cufftHandle fft = 0;
     bool fft_ok = false;
 
@@ -214,12 +284,16 @@ kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const f
 // A^H u: u [C][M] (sorted order if perm == nullptr, else user order) -> grid -> x.
 kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st);
 kp_status grid_to_image(kp_plan p, float2* x, cudaStream_t st);
+kp_status autotune_spread(kp_plan p, cudaStream_t st);
 kp_status adjoint_primal(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st);
 
 // kp_pdhg.cu
 kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st);
-kp_status wavelet_prox_extrap(kp_plan p, float lambda, cudaStream_t st);
+kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status fft_forward_only(kp_plan p, cudaStream_t st);
+kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);
+kp_status interp_dual_only(kp_plan p, cudaStream_t st);
 void daubechies4(float h[8]);
 kp_status upload_wavelet_filter(const float h[8]);
 void drop_graphs(kp_plan p);

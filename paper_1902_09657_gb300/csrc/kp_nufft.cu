@@ -17,6 +17,8 @@
 // ceil(t - W/2) exactly and involves no rounding, so |t - k| <= W/2 for every tap.
 #include "kp_internal.cuh"
 
+#include <cstdlib>
+
 namespace kp {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -186,34 +188,41 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
     const int tile = it.x, beg = it.y, end = it.z;
     const int c0 = blockIdx.y * IP_CH;
     const int cc = min(IP_CH, geo.C - c0);
-    int o[MAXD], R[MAXD], rs[MAXD];
+    // staged region: (TS + W - 1)^D points for the largest tile edge TS (16 in 2D, 8 in 3D)
+    constexpr int R = (D == 2 ? 16 : 8) + KW - 1;
+    constexpr int RT = D == 2 ? R * R : R * R * R;
+    int o[MAXD];
     {
         int r = tile;
+#pragma unroll
         for (int d = D - 1; d >= 0; --d) {
             const int tc = r % tl.nt[d];
             r /= tl.nt[d];
             o[d] = tc * tl.ts[d];
-            R[d] = tl.ts[d] + KW - 1;
         }
-        int st = 1;
-        for (int d = D - 1; d >= 0; --d) { rs[d] = st; st *= R[d]; }
     }
-    int Rtot = 1;
-    for (int d = 0; d < D; ++d) Rtot *= R[d];
-    for (int idx = threadIdx.x; idx < cc * Rtot; idx += blockDim.x) {
-        const int c = idx / Rtot;
-        int r = idx - c * Rtot;
-        int64_t flat = 0;
-        int lrev[MAXD];
-        for (int d = D - 1; d >= 0; --d) { lrev[d] = r % R[d]; r /= R[d]; }
-        for (int d = 0; d < D; ++d) {
-            int pp = o[d] + lrev[d];
-            if (pp >= geo.g[d]) pp -= geo.g[d];
-            flat = flat * geo.g[d] + tunshift(pp, tl.sh[d], geo.g[d]);
-        }
-        sg[c * Rtot + (idx - c * Rtot)] = __ldg(grid + (size_t)(c0 + c) * geo.G + flat);
+    // grid row offsets of the staged region, per axis (periodic), computed once per CTA
+    __shared__ int rowoff[MAXD][R];
+    if (threadIdx.x < D * R) {
+        const int d = threadIdx.x / R, l = threadIdx.x % R;
+        int pp = o[d] + l;
+        while (pp >= geo.g[d]) pp -= geo.g[d];
+        int64_t stride = 1;
+        for (int e = d + 1; e < D; ++e) stride *= geo.g[e];
+        rowoff[d][l] = (int)(tunshift(pp, tl.sh[d], geo.g[d]) * stride);
     }
     __syncthreads();
+    for (int idx = threadIdx.x; idx < cc * RT; idx += blockDim.x) {
+        const int c = idx / RT;
+        const int r = idx - c * RT;
+        int off;
+        if (D == 2) off = rowoff[0][r / R] + rowoff[1 % D][r % R];
+        else off = rowoff[0][r / (R * R)] + rowoff[1 % D][(r / R) % R] + rowoff[D - 1][r % R];
+        sg[idx] = __ldg(grid + (size_t)(c0 + c) * geo.G + off);
+    }
+    __syncthreads();
+    constexpr int rs0 = D == 2 ? R : R * R, rs1 = D == 2 ? 1 : R;
+    const int Rtot = RT;
     float sigma = 0.f;
     if (MODE == 2) sigma = io.sched[3 * (*io.iter)];
     for (int s = beg + threadIdx.x; s < end; s += blockDim.x) {
@@ -222,7 +231,7 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
-            lb += (p0 - o[d]) * rs[d];
+            lb += (p0 - o[d]) * (d == 0 ? rs0 : (d == 1 ? rs1 : 1));
 #pragma unroll
             for (int j = 0; j < KW; ++j) w[d][j] = wt[(int64_t)(d * KW + j) * geo.M + s];
         }
@@ -235,7 +244,7 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
 #pragma unroll
                     for (int b = 0; b < KW; ++b) {
                         const float ww = w[0][a] * w[D - 1][b];
-                        const float2 v = base[a * rs[0] + b];
+                        const float2 v = base[a * rs0 + b];
                         acc.x = fmaf(ww, v.x, acc.x);
                         acc.y = fmaf(ww, v.y, acc.y);
                     }
@@ -248,7 +257,7 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
 #pragma unroll
                         for (int e = 0; e < KW; ++e) {
                             const float ww = wab * w[D - 1][e];
-                            const float2 v = base[a * rs[0] + b * rs[1 % D] + e];
+                            const float2 v = base[a * rs0 + b * rs1 + e];
                             acc.x = fmaf(ww, v.x, acc.x);
                             acc.y = fmaf(ww, v.y, acc.y);
                         }
@@ -286,32 +295,37 @@ constexpr int SP_CH = 4;           // coils per CTA
 constexpr int SP_THREADS = 128;    // 4 warps, 4 private tile copies
 constexpr int SP_CHUNK = 256;      // samples per work item (== plan chunk)
 
-struct SpreadLayout {
-    int ls[MAXD];      // shared-memory strides of the local tile index
-    int plane;         // floats per (warp, coil, re/im) plane
-    int P;             // tile points
+// Shared-memory layout of one private tile copy, for the largest tile edge (16 in 2D, 8 in
+// 3D).  Strides are padded so that the 32 lanes of a warp (2D: 16 taps x 2 coils; 3D: 32
+// taps) hit 32 different banks.
+template <int D> struct SpL;
+template <> struct SpL<2> {
+    static constexpr int TS = 16, PLANE = 328;        // 2 x PLANE = 16 (mod 32): coil pairs on disjoint banks
+    __device__ static constexpr int stride(int d) { return d == 0 ? 20 : 1; }
+};
+template <> struct SpL<3> {
+    static constexpr int TS = 8, PLANE = 896;
+    __device__ static constexpr int stride(int d) { return d == 0 ? 112 : (d == 1 ? 12 : 1); }
 };
 
-static SpreadLayout spread_layout(const Tiles& tl, int D) {
-    SpreadLayout L{};
-    int st = 1;
-    for (int d = D - 1; d >= 0; --d) { L.ls[d] = st; st *= tl.ts[d]; }
-    L.P = st;
-    L.plane = st;
-    return L;
+template <int D>
+static size_t spread_smem() {
+    return (size_t)(SP_THREADS / 32) * SP_CH * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
+           (size_t)SP_CHUNK * (SP_CH * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
 }
 
 template <int D, typename UT>
 __global__ void __launch_bounds__(SP_THREADS)
 k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
          const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
-         Tiles tl, SpreadLayout L, float2* __restrict__ grid) {
+         Tiles tl, float2* __restrict__ grid) {
+    using LY = SpL<D>;
     extern __shared__ float smem[];
     constexpr int NW = SP_THREADS / 32;
-    float* acc = smem;                                              // [NW][SP_CH][2][P]
-    float2* su = (float2*)(acc + NW * SP_CH * 2 * L.plane);         // [SP_CHUNK][SP_CH]
-    float* sw = (float*)(su + SP_CHUNK * SP_CH);                    // [SP_CHUNK][D*KW]
-    int* sl = (int*)(sw + SP_CHUNK * D * KW);                       // [SP_CHUNK][D] local first tap (may be < 0)
+    float* acc = smem;                                              // [NW][SP_CH][2][PLANE]
+    float2* su = (float2*)(acc + NW * SP_CH * 2 * LY::PLANE);       // [SP_CHUNK][SP_CH]
+    float* sw = (float*)(su + SP_CHUNK * SP_CH);                    // [SP_CHUNK][D][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D] 4 packed int8 tap coordinates
     const int4 it = items[blockIdx.x];
     const int tile = it.x, beg = it.y, end = it.z;
     const bool split = it.w >= 0;
@@ -320,6 +334,7 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
     int o[MAXD], e[MAXD];
     {
         int r = tile;
+#pragma unroll
         for (int d = D - 1; d >= 0; --d) {
             const int tc = r % tl.nt[d];
             r /= tl.nt[d];
@@ -328,8 +343,9 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
         }
     }
     const int n = end - beg;
-    for (int i = threadIdx.x; i < NW * SP_CH * 2 * L.plane; i += blockDim.x) acc[i] = 0.f;
-    // stage the item's samples
+    for (int i = threadIdx.x; i < NW * SP_CH * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
+    // stage the item's samples: coil values, weights, and the local coordinate of every tap
+    // inside this tile (-1 where the tap falls outside)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int s = ext[beg + i];
         const int64_t un = perm ? perm[s] : s;
@@ -338,71 +354,409 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
             su[i * SP_CH + c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];
-            // the footprint may start in the previous tile (or wrap around the axis)
-            if (p0 > e[d]) p0 -= geo.g[d];
-            sl[i * D + d] = p0;
+            const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+            unsigned pk = 0;
 #pragma unroll
-            for (int j = 0; j < KW; ++j) sw[i * D * KW + d * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
-        }
-    }
-    __syncthreads();
-    constexpr int TAPS = D == 2 ? KW * KW : KW * KW * KW;
-    constexpr int LPT = TAPS < 32 ? 32 / TAPS : 1;     // lanes per tap (2D: 2, coils split between them)
-    constexpr int TPL = TAPS > 32 ? TAPS / 32 : 1;     // taps per lane (3D: 2)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* my = acc + warp * SP_CH * 2 * L.plane;
-    for (int i = warp; i < n; i += NW) {
-#pragma unroll
-        for (int tq = 0; tq < TPL; ++tq) {
-            int q = (TAPS < 32 ? lane % TAPS : lane) + 32 * tq;
-            float w = 1.f;
-            int lo = 0;
-            bool ok = true;
-#pragma unroll
-            for (int d = D - 1; d >= 0; --d) {
-                const int j = q % KW;
-                q /= KW;
-                int pp = o[d] + sl[i * D + d] + j;      // shifted coordinate of the tap
-                if (pp < 0) pp += geo.g[d];
-                else if (pp >= geo.g[d]) pp -= geo.g[d];
+            for (int j = 0; j < KW; ++j) {
+                int pp = p0 + j;
+                if (pp >= geo.g[d]) pp -= geo.g[d];
                 const int l = pp - o[d];
-                if (l < 0 || l >= e[d]) ok = false;
-                w *= sw[i * D * KW + d * KW + j];
-                lo += l * L.ls[d];
+                const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
+                pk |= byte << (8 * j);
+                sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
             }
-            if (!ok) continue;
-            for (int c = (TAPS < 32 ? lane / TAPS : 0); c < cc; c += LPT) {
-                const float2 uv = su[i * SP_CH + c];
-                float* pl = my + c * 2 * L.plane;
-                pl[lo] += w * uv.x;
-                pl[L.plane + lo] += w * uv.y;
-            }
+            sp[i * D + d] = pk;
         }
-        __syncwarp();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cc * L.P; i += blockDim.x) {
-        const int c = i / L.P;
-        const int r0 = i - c * L.P;
-        int r = r0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* my = acc + warp * SP_CH * 2 * LY::PLANE;
+    // Each lane's updates of one sample are independent read-modify-writes of its private
+    // copy: all loads are issued before any store, and the next sample's staged data is
+    // fetched while the current one is applied.
+    if (D == 2) {
+        const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
+        const bool has1 = h + 2 < cc, has0 = h < cc;
+        float* q0 = my + h * 2 * LY::PLANE;
+        float* q1 = my + (h + 2) * 2 * LY::PLANE;
+        unsigned pk0 = 0, pk1 = 0;
+        float wa = 0.f, wb = 0.f;
+        float2 u0 = make_float2(0.f, 0.f), u1 = u0;
+        int i = warp;
+        if (i < n) {
+            pk0 = sp[i * D]; pk1 = sp[i * D + 1];
+            wa = sw[(i * D) * KW + ta]; wb = sw[(i * D + 1) * KW + tb];
+            u0 = su[i * SP_CH + (h & 3)]; u1 = su[i * SP_CH + ((h + 2) & 3)];
+        }
+        for (; i < n; i += NW) {
+            const int la = (int)(signed char)(pk0 >> (8 * ta));
+            const int lb = (int)(signed char)(pk1 >> (8 * tb));
+            const bool ok = la >= 0 && lb >= 0;
+            const int lo = la * LY::stride(0) + lb;
+            const float w = wa * wb;
+            const float2 cu0 = u0, cu1 = u1;
+            const int inx = i + NW;
+            if (inx < n) {
+                pk0 = sp[inx * D]; pk1 = sp[inx * D + 1];
+                wa = sw[(inx * D) * KW + ta]; wb = sw[(inx * D + 1) * KW + tb];
+                u0 = su[inx * SP_CH + (h & 3)]; u1 = su[inx * SP_CH + ((h + 2) & 3)];
+            }
+            if (ok && has0) {
+                float r0 = q0[lo], i0 = q0[LY::PLANE + lo];
+                float r1 = 0.f, i1 = 0.f;
+                if (has1) { r1 = q1[lo]; i1 = q1[LY::PLANE + lo]; }
+                q0[lo] = fmaf(w, cu0.x, r0);
+                q0[LY::PLANE + lo] = fmaf(w, cu0.y, i0);
+                if (has1) {
+                    q1[lo] = fmaf(w, cu1.x, r1);
+                    q1[LY::PLANE + lo] = fmaf(w, cu1.y, i1);
+                }
+            }
+            __syncwarp();
+        }
+    } else {
+        const int tb = (lane >> 2) & 3, tc = lane & 3, ta0 = lane >> 4;   // taps (ta0 + 2k, tb, tc), k = 0, 1
+        for (int i = warp; i < n; i += NW) {
+            const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+            const int lc = (int)(signed char)(sp[i * D + 2] >> (8 * tc));
+            const float wbc = sw[(i * D + 1) * KW + tb] * sw[(i * D + 2) * KW + tc];
+            const int laA = (int)(signed char)(sp[i * D] >> (8 * ta0));
+            const int laB = (int)(signed char)(sp[i * D] >> (8 * (ta0 + 2)));
+            const bool okA = laA >= 0 && lb >= 0 && lc >= 0, okB = laB >= 0 && lb >= 0 && lc >= 0;
+            const int loA = laA * LY::stride(0) + lb * LY::stride(1 % D) + lc;
+            const int loB = laB * LY::stride(0) + lb * LY::stride(1 % D) + lc;
+            const float wA = sw[(i * D) * KW + ta0] * wbc, wB = sw[(i * D) * KW + ta0 + 2] * wbc;
+            float rA[SP_CH], iA[SP_CH], rB[SP_CH], iB[SP_CH];
+            float2 uv[SP_CH];
+#pragma unroll
+            for (int c = 0; c < SP_CH; ++c) {
+                uv[c] = su[i * SP_CH + c];
+                if (c < cc) {
+                    float* pl = my + c * 2 * LY::PLANE;
+                    if (okA) { rA[c] = pl[loA]; iA[c] = pl[LY::PLANE + loA]; }
+                    if (okB) { rB[c] = pl[loB]; iB[c] = pl[LY::PLANE + loB]; }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < SP_CH; ++c) {
+                if (c < cc) {
+                    float* pl = my + c * 2 * LY::PLANE;
+                    if (okA) { pl[loA] = fmaf(wA, uv[c].x, rA[c]); pl[LY::PLANE + loA] = fmaf(wA, uv[c].y, iA[c]); }
+                    if (okB) { pl[loB] = fmaf(wB, uv[c].x, rB[c]); pl[LY::PLANE + loB] = fmaf(wB, uv[c].y, iB[c]); }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    int P = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) P *= tl.ts[d];
+    for (int i = threadIdx.x; i < cc * P; i += blockDim.x) {
+        const int c = i / P;
+        int r = i - c * P;
         int lidx[MAXD];
+#pragma unroll
         for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
         bool in = true;
+        int lo = 0;
         int64_t gflat = 0;
+#pragma unroll
         for (int d = 0; d < D; ++d) {
             if (lidx[d] >= e[d]) in = false;
+            lo += lidx[d] * LY::stride(d);
             gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
         }
         if (!in) continue;
         float2 v = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            const float* pl = acc + (w * SP_CH + c) * 2 * L.plane;
-            v.x += pl[r0];
-            v.y += pl[L.plane + r0];
+            const float* pl = acc + (w * SP_CH + c) * 2 * LY::PLANE;
+            v.x += pl[lo];
+            v.y += pl[LY::PLANE + lo];
         }
         float2* dst = grid + (size_t)(c0 + c) * geo.G + gflat;
+        if (split) {
+            atomicAdd(&dst->x, v.x);
+            atomicAdd(&dst->y, v.y);
+        } else {
+            *dst = v;
+        }
+    }
+}
+
+// Variant with one shared accumulator per CTA and up to SPA_CH coils per CTA (one coil group
+// for C <= 16): the tap geometry of a sample is staged once for all its coils and the lanes
+// add with shared-memory atomics (a warp's lanes cover distinct (tap, coil) addresses; only
+// warps working on the same point contend).
+constexpr int SPA_CH = 16;
+constexpr int SPA_THREADS = 256;
+
+template <int D>
+static size_t spread_atomic_smem() {
+    return (size_t)SPA_CH * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
+           (size_t)SP_CHUNK * (SPA_CH * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
+}
+
+template <int D, typename UT>
+__global__ void __launch_bounds__(SPA_THREADS)
+k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+                const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
+                Tiles tl, float2* __restrict__ grid) {
+    using LY = SpL<D>;
+    extern __shared__ float smem[];
+    float* acc = smem;                                              // [SPA_CH][2][PLANE]
+    float2* su = (float2*)(acc + SPA_CH * 2 * LY::PLANE);           // [SP_CHUNK][SPA_CH]
+    float* sw = (float*)(su + SP_CHUNK * SPA_CH);                   // [SP_CHUNK][D][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D]
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z;
+    const bool split = it.w >= 0;
+    const int c0 = blockIdx.y * SPA_CH;
+    const int cc = min(SPA_CH, geo.C - c0);
+    int o[MAXD], e[MAXD];
+    {
+        int r = tile;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            e[d] = min(tl.ts[d], geo.g[d] - o[d]);
+        }
+    }
+    const int n = end - beg;
+    for (int i = threadIdx.x; i < cc * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = ext[beg + i];
+        const int64_t un = perm ? perm[s] : s;
+        for (int c = 0; c < cc; ++c) su[i * SPA_CH + c] = ldc<UT>(u, (size_t)(c0 + c) * geo.M + un);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+            unsigned pk = 0;
+#pragma unroll
+            for (int j = 0; j < KW; ++j) {
+                int pp = p0 + j;
+                if (pp >= geo.g[d]) pp -= geo.g[d];
+                const int l = pp - o[d];
+                const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
+                pk |= byte << (8 * j);
+                sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+            }
+            sp[i * D + d] = pk;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (D == 2) {
+        const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
+        for (int i = warp; i < n; i += nw) {
+            const int la = (int)(signed char)(sp[i * D] >> (8 * ta));
+            const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+            if (la < 0 || lb < 0) continue;
+            const int lo = la * LY::stride(0) + lb;
+            const float w = sw[(i * D) * KW + ta] * sw[(i * D + 1) * KW + tb];
+            for (int c = h; c < cc; c += 2) {
+                const float2 uv = su[i * SPA_CH + c];
+                float* pl = acc + c * 2 * LY::PLANE;
+                atomicAdd(pl + lo, w * uv.x);
+                atomicAdd(pl + LY::PLANE + lo, w * uv.y);
+            }
+        }
+    } else {
+        const int tb = (lane >> 2) & 3, tc = lane & 3, ta0 = lane >> 4;
+        for (int i = warp; i < n; i += nw) {
+            const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+            const int lc = (int)(signed char)(sp[i * D + 2] >> (8 * tc));
+            if (lb < 0 || lc < 0) continue;
+            const float wbc = sw[(i * D + 1) * KW + tb] * sw[(i * D + 2) * KW + tc];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int ta = ta0 + 2 * k;
+                const int la = (int)(signed char)(sp[i * D] >> (8 * ta));
+                if (la < 0) continue;
+                const int lo = la * LY::stride(0) + lb * LY::stride(1 % D) + lc;
+                const float w = sw[(i * D) * KW + ta] * wbc;
+                for (int c = 0; c < cc; ++c) {
+                    const float2 uv = su[i * SPA_CH + c];
+                    float* pl = acc + c * 2 * LY::PLANE;
+                    atomicAdd(pl + lo, w * uv.x);
+                    atomicAdd(pl + LY::PLANE + lo, w * uv.y);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    int P = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) P *= tl.ts[d];
+    for (int i = threadIdx.x; i < cc * P; i += blockDim.x) {
+        const int c = i / P;
+        int r = i - c * P;
+        int lidx[MAXD];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
+        bool in = true;
+        int lo = 0;
+        int64_t gflat = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (lidx[d] >= e[d]) in = false;
+            lo += lidx[d] * LY::stride(d);
+            gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
+        }
+        if (!in) continue;
+        const float* pl = acc + c * 2 * LY::PLANE;
+        const float2 v = make_float2(pl[lo], pl[LY::PLANE + lo]);
+        float2* dst = grid + (size_t)(c0 + c) * geo.G + gflat;
+        if (split) {
+            atomicAdd(&dst->x, v.x);
+            atomicAdd(&dst->y, v.y);
+        } else {
+            *dst = v;
+        }
+    }
+}
+
+// Variant in which each warp owns four coils of a single shared accumulator: every warp
+// walks all samples of the item for its own coils, so no two warps ever touch the same
+// address (no atomics, no private copies), and a sample's geometry is staged once for all
+// coils.  Block = 32 * ceil(C / 4) threads.
+constexpr int SPW_CW = 4;          // coils per warp
+
+template <int D>
+static size_t spread_warpcoil_smem(int C) {
+    return (size_t)C * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
+           (size_t)SP_CHUNK * (C * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
+}
+
+template <int D, typename UT>
+__global__ void __launch_bounds__(1024)
+k_spread_warpcoil(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+                  const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
+                  Tiles tl, float2* __restrict__ grid) {
+    using LY = SpL<D>;
+    extern __shared__ float smem[];
+    const int C = geo.C;
+    float* acc = smem;                                              // [C][2][PLANE]
+    float2* su = (float2*)(acc + C * 2 * LY::PLANE);                // [SP_CHUNK][C]
+    float* sw = (float*)(su + SP_CHUNK * C);                        // [SP_CHUNK][D][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D]
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z;
+    const bool split = it.w >= 0;
+    int o[MAXD], e[MAXD];
+    {
+        int r = tile;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            e[d] = min(tl.ts[d], geo.g[d] - o[d]);
+        }
+    }
+    const int n = end - beg;
+    for (int i = threadIdx.x; i < C * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = ext[beg + i];
+        const int64_t un = perm ? perm[s] : s;
+        for (int c = 0; c < C; ++c) su[i * C + c] = ldc<UT>(u, (size_t)c * geo.M + un);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+            unsigned pk = 0;
+#pragma unroll
+            for (int j = 0; j < KW; ++j) {
+                int pp = p0 + j;
+                if (pp >= geo.g[d]) pp -= geo.g[d];
+                const int l = pp - o[d];
+                const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
+                pk |= byte << (8 * j);
+                sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+            }
+            sp[i * D + d] = pk;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cw0 = warp * SPW_CW;
+    const int ccw = min(SPW_CW, C - cw0);
+    if (D == 2) {
+        const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
+        const bool has0 = h < ccw, has1 = h + 2 < ccw;
+        float* q0 = acc + (cw0 + h) * 2 * LY::PLANE;
+        float* q1 = acc + (cw0 + h + 2) * 2 * LY::PLANE;
+        for (int i = 0; i < n; ++i) {
+            const int la = (int)(signed char)(sp[i * D] >> (8 * ta));
+            const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+            if (la < 0 || lb < 0 || !has0) continue;
+            const int lo = la * LY::stride(0) + lb;
+            const float w = sw[(i * D) * KW + ta] * sw[(i * D + 1) * KW + tb];
+            const float2 u0 = su[i * C + cw0 + h];
+            float r0 = q0[lo], i0 = q0[LY::PLANE + lo];
+            if (has1) {
+                const float2 u1 = su[i * C + cw0 + h + 2];
+                float r1 = q1[lo], i1 = q1[LY::PLANE + lo];
+                q1[lo] = fmaf(w, u1.x, r1);
+                q1[LY::PLANE + lo] = fmaf(w, u1.y, i1);
+            }
+            q0[lo] = fmaf(w, u0.x, r0);
+            q0[LY::PLANE + lo] = fmaf(w, u0.y, i0);
+        }
+    } else {
+        const int tb = (lane >> 2) & 3, tc = lane & 3, ta0 = lane >> 4;
+        for (int i = 0; i < n; ++i) {
+            const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+            const int lc = (int)(signed char)(sp[i * D + 2] >> (8 * tc));
+            if (lb < 0 || lc < 0) continue;
+            const float wbc = sw[(i * D + 1) * KW + tb] * sw[(i * D + 2) * KW + tc];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int ta = ta0 + 2 * k;
+                const int la = (int)(signed char)(sp[i * D] >> (8 * ta));
+                if (la < 0) continue;
+                const int lo = la * LY::stride(0) + lb * LY::stride(1 % D) + lc;
+                const float w = sw[(i * D) * KW + ta] * wbc;
+                float rr[SPW_CW], ii[SPW_CW];
+#pragma unroll
+                for (int c = 0; c < SPW_CW; ++c)
+                    if (c < ccw) { float* pl = acc + (cw0 + c) * 2 * LY::PLANE; rr[c] = pl[lo]; ii[c] = pl[LY::PLANE + lo]; }
+#pragma unroll
+                for (int c = 0; c < SPW_CW; ++c)
+                    if (c < ccw) {
+                        const float2 uv = su[i * C + cw0 + c];
+                        float* pl = acc + (cw0 + c) * 2 * LY::PLANE;
+                        pl[lo] = fmaf(w, uv.x, rr[c]);
+                        pl[LY::PLANE + lo] = fmaf(w, uv.y, ii[c]);
+                    }
+            }
+        }
+    }
+    __syncthreads();
+    int P = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) P *= tl.ts[d];
+    for (int i = threadIdx.x; i < C * P; i += blockDim.x) {
+        const int c = i / P;
+        int r = i - c * P;
+        int lidx[MAXD];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
+        bool in = true;
+        int lo = 0;
+        int64_t gflat = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (lidx[d] >= e[d]) in = false;
+            lo += lidx[d] * LY::stride(d);
+            gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
+        }
+        if (!in) continue;
+        const float* pl = acc + c * 2 * LY::PLANE;
+        const float2 v = make_float2(pl[lo], pl[LY::PLANE + lo]);
+        float2* dst = grid + (size_t)c * geo.G + gflat;
         if (split) {
             atomicAdd(&dst->x, v.x);
             atomicAdd(&dst->y, v.y);
@@ -443,40 +797,6 @@ __global__ void k_zero_split(const int* __restrict__ split_tiles, Geom geo, Tile
 }
 
 // ---------------------------------------------------------------- adjoint: post
-template <int D, typename MT>
-__device__ __forceinline__ float2 adj_pixel(const float2* __restrict__ grid, const MT* __restrict__ maps,
-                                            const float* __restrict__ apod, const Geom& geo, int64_t j) {
-    int jj[D];
-    int64_t r = j;
-#pragma unroll
-    for (int d = D - 1; d >= 0; --d) { jj[d] = (int)(r % geo.n[d]); r /= geo.n[d]; }
-    int64_t gi = 0;
-    float a = geo.rsqrtN;
-    int ao = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        int nd = jj[d] - geo.n[d] / 2;
-        int id = nd < 0 ? nd + geo.g[d] : nd;
-        gi = gi * geo.g[d] + id;
-        a *= apod[ao + jj[d]];
-        ao += geo.n[d];
-    }
-    float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < geo.C; ++c) {
-        float2 gv = grid[(size_t)c * geo.G + gi];
-        if (maps) {
-            float2 s = ldc<MT>(maps, (size_t)c * geo.N + j);
-            float2 v = cmulc(s, gv);
-            acc.x += v.x;
-            acc.y += v.y;
-        } else {
-            acc.x += gv.x;
-            acc.y += gv.y;
-        }
-    }
-    return make_float2(acc.x * a, acc.y * a);
-}
-
 template <int D, typename MT>
 __global__ void k_adj_image(const float2* __restrict__ grid, const MT* __restrict__ maps, const float* __restrict__ apod,
                             Geom geo, float2* __restrict__ x) {
@@ -543,15 +863,35 @@ static kp_status fwd_grid(kp_plan p, const float2* x, cudaStream_t st) {
     KP_LAUNCH_CHECK();
     mark(p, PH_FFT_FWD, st);
     KP_TRY_CUFFT(cufftSetStream(p->fft, st));
-    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_grid, CUFFT_FORWARD));
+    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_gridF, CUFFT_FORWARD));
+    return KP_OK;
+}
+
+// Forward pre-step only (coil multiply, apodise, pad) of x into d_grid.
+kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const kp_cdtype mt = p->unit_maps ? KP_C64 : p->maps_t;
+    p->launches += 1;
+    KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
+        k_fwd_pre<DD, MT><<<nblk(g.G, 256), 256, 0, st>>>(x, p->unit_maps ? nullptr : (const MT*)p->d_maps,
+                                                         p->d_apod, g, p->d_grid)));
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+// Forward FFT of a grid already written into d_grid (the fused primal kernel writes the next
+// iteration's pre-step there).
+kp_status fft_forward_only(kp_plan p, cudaStream_t st) {
+    mark(p, PH_FFT_FWD, st);
+    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
+    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_gridF, CUFFT_FORWARD));
     return KP_OK;
 }
 
 template <int MODE>
 static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaStream_t st) {
     const Geom& g = p->geo;
-    size_t rt = 1;
-    for (int d = 0; d < g.D; ++d) rt *= p->tiles.ts[d] + KW - 1;
+    const size_t rt = g.D == 2 ? (16 + KW - 1) * (16 + KW - 1) : (8 + KW - 1) * (8 + KW - 1) * (8 + KW - 1);
     const size_t smem = (size_t)IP_CH * rt * sizeof(float2);
     const dim3 grid((unsigned)p->n_iitems, (g.C + IP_CH - 1) / IP_CH);
     static bool attr[2][3][3] = {};
@@ -563,7 +903,7 @@ static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaS
             KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_tile<DD, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
             attr[DD - 2][MODE][t] = true;
         }
-        k_interp_tile<DD, MODE, T><<<grid, IP_THREADS, smem, st>>>(p->d_iitems, p->d_k0, p->d_wt, p->d_grid, g, p->tiles, io)));
+        k_interp_tile<DD, MODE, T><<<grid, IP_THREADS, smem, st>>>(p->d_iitems, p->d_k0, p->d_wt, p->d_gridF, g, p->tiles, io)));
     KP_LAUNCH_CHECK();
     return KP_OK;
 }
@@ -586,6 +926,10 @@ kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const f
 
 kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st) {
     KP_TRY(fwd_grid(p, xbar, st));
+    return interp_dual_only(p, st);
+}
+
+kp_status interp_dual_only(kp_plan p, cudaStream_t st) {
     InterpIO io{};
     io.ys = p->d_ys;
     io.ps = p->d_ps;
@@ -597,29 +941,89 @@ kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st) {
 
 kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st) {
     const Geom& g = p->geo;
-    const SpreadLayout L = spread_layout(p->tiles, g.D);
-    const size_t smem = (size_t)(SP_THREADS / 32) * SP_CH * 2 * L.plane * sizeof(float) +
-                        (size_t)SP_CHUNK * (SP_CH * sizeof(float2) + g.D * KW * sizeof(float) + g.D * sizeof(int));
+    int P = 1;
+    for (int d = 0; d < g.D; ++d) P *= p->tiles.ts[d];
     static bool attr_set[2][3] = {{false}};
     mark(p, PH_SPREAD, st);
     if (p->n_split > 0) {
-        KP_DISPATCH_D(g.D, DD, k_zero_split<DD><<<(unsigned)p->n_split, 256, 0, st>>>(p->d_split, g, p->tiles, L.P,
+        KP_DISPATCH_D(g.D, DD, k_zero_split<DD><<<(unsigned)p->n_split, 256, 0, st>>>(p->d_split, g, p->tiles, P,
                                                                                       p->d_grid2));
         KP_LAUNCH_CHECK();
         p->launches += 1;
     }
     p->launches += 1;
-    KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
-        if (!attr_set[DD - 2][u_t]) {
-            KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-            attr_set[DD - 2][u_t] = true;
-        }
-        k_spread<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SP_CH - 1) / SP_CH), SP_THREADS, smem, st>>>(p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext,
-                                                                        p->d_items, g, p->tiles, L, p->d_grid2)));
+    if (p->spread_variant == 0) {
+        KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
+            if (!attr_set[DD - 2][u_t]) {
+                KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+                attr_set[DD - 2][u_t] = true;
+            }
+            k_spread<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SP_CH - 1) / SP_CH), SP_THREADS, spread_smem<DD>(), st>>>(
+                p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
+    } else if (p->spread_variant == 2) {
+        static bool attr_w[2][3] = {{false}};
+        const size_t sm = g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C);
+        const unsigned nthr = 32u * (unsigned)((g.C + SPW_CW - 1) / SPW_CW);
+        KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
+            if (!attr_w[DD - 2][u_t]) {
+                KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_warpcoil<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+                attr_w[DD - 2][u_t] = true;
+            }
+            k_spread_warpcoil<DD, UT><<<(unsigned)p->n_items, nthr, sm, st>>>(
+                p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
+    } else {
+        static bool attr_a[2][3] = {{false}};
+        KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
+            if (!attr_a[DD - 2][u_t]) {
+                KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_atomic<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+                attr_a[DD - 2][u_t] = true;
+            }
+            k_spread_atomic<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SPA_CH - 1) / SPA_CH), SPA_THREADS,
+                                      spread_atomic_smem<DD>(), st>>>(
+                p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
+    }
     KP_LAUNCH_CHECK();
     mark(p, PH_FFT_INV, st);
     KP_TRY_CUFFT(cufftSetStream(p->fft, st));
     KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
+    return KP_OK;
+}
+
+// Pick the faster spreading variant for this plan's geometry and sample distribution by
+// timing both on the plan's own work items (values do not affect the cost).  Runs once per
+// plan, on the first trajectory.
+kp_status autotune_spread(kp_plan p, cudaStream_t st) {
+    if (p->spread_tuned) return KP_OK;
+    if (const char* ev = getenv("KPDHG_SPREAD_VARIANT")) {   // tuning override (0, 1, 2)
+        const int v = atoi(ev);
+        if (v >= 0 && v <= 2) { p->spread_variant = v; p->spread_tuned = true; return KP_OK; }
+    }
+    const Geom& g = p->geo;
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_kt, 0, (size_t)g.C * g.M * sizeof(float2), st));
+    cudaEvent_t e0, e1;
+    KP_TRY_CUDA(cudaEventCreate(&e0));
+    KP_TRY_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = 0;
+    const bool prof = p->profiling;
+    p->profiling = false;
+    const int nv = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024 ? 3 : 2;
+    for (int v = 0; v < nv; ++v) {
+        p->spread_variant = v;
+        KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st));
+        KP_TRY_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 6; ++r) KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st));
+        KP_TRY_CUDA(cudaEventRecord(e1, st));
+        KP_TRY_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        KP_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    p->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->spread_variant = best_v;
+    p->spread_tuned = true;
     return KP_OK;
 }
 

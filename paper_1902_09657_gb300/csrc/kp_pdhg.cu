@@ -1,10 +1,10 @@
 // Preconditioned PDHG (Sec. 4.1), the power method for lambda_max(P A A^H) (Sec. 6) and the
 // periodised Daubechies-4 wavelet W used by the l1 prox (Sec. 2, Sec. 6).
 //
-// One PDHG iteration = fwd_pre -> FFT -> interp+dual (u update) -> spread -> IFFT ->
-// adj+primal (z = x - tau A^H u; l2 prox and extrapolation fused) [-> DWT -> soft -> IDWT ->
-// extrapolate for l1] -> advance the device iteration counter.  The step sizes
-// sigma_k, tau_k, theta_k are computed on the device in float64 from lambda_max and
+// One PDHG iteration = FFT of the forward grid -> interpolation + dual update -> spreading ->
+// inverse FFT -> fused primal kernel (adjoint combine, z = x - tau A^H u, l2 or l1-wavelet
+// prox, extrapolation, the next iteration's forward pre-step, iteration counter).  The step
+// sizes sigma_k, tau_k, theta_k are computed on the device in float64 from lambda_max and
 // min p, so one captured CUDA graph replays every iteration.
 #include "kp_internal.cuh"
 
@@ -200,16 +200,15 @@ static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cuda
     return KP_OK;
 }
 
+// One PDHG iteration (Sec. 4.1) from the forward grid of xbar already in d_grid:
+// FFT -> interpolation + dual update -> spreading + inverse FFT -> fused primal step
+// (adjoint combine, prox, extrapolation, next forward pre-step, counter).
 static kp_status issue_iteration(kp_plan p, int reg, float lambda, cudaStream_t st) {
-    const Geom& g = p->geo;
-    KP_TRY(forward_dual(p, p->d_xbar, st));
+    KP_TRY(fft_forward_only(p, st));
+    KP_TRY(interp_dual_only(p, st));
     KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st));
-    KP_TRY(adjoint_primal(p, reg, lambda, st));
-    if (reg == KP_REG_L1_WAVELET) KP_TRY(wavelet_prox_extrap(p, lambda, st));
+    KP_TRY(primal_fused(p, reg, lambda, st));
     mark(p, PH_OTHER, st);
-    k_advance<<<1, 1, 0, st>>>(p->d_iter);
-    KP_LAUNCH_CHECK();
-    p->launches += 1;
     return KP_OK;
 }
 
@@ -385,6 +384,8 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
+    // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
     kp_status status = KP_OK;
     double F0 = 0, F = NAN;
     double phase_ms[PH_N] = {0};
@@ -411,6 +412,7 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
             }
             if (obj_trace) {
                 KP_TRY(objective(plan, (int)reg, lambda, &F, st));
+                KP_TRY(pre_only(plan, plan->d_xbar, st));   // the objective's forward reused d_grid
                 obj_trace[k] = F;
                 if (k == 0) F0 = F;
                 if (!std::isfinite(F)) { status = KP_ENONFINITE; break; }
@@ -435,6 +437,7 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
     }
     if (flags[5] != 0) { set_error(std::to_string(flags[5]) + " preconditioner entries are not positive and finite"); return KP_EINVAL; }
     if (flags[6] != 0) { set_error("lambda_max or min p is not positive and finite"); return KP_EINVAL; }
+    if (flags[3] != 0) { set_error("a grid barrier of the fused primal kernel timed out"); return KP_ETIMEOUT; }
     return status;
 }
 

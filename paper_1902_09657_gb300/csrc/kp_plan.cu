@@ -320,6 +320,9 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     }
     KP_A(p->d_grid, (size_t)C * G);
     KP_A(p->d_grid2, (size_t)C * G);
+    KP_A(p->d_gridF, (size_t)C * G);
+    KP_A(p->d_bar, 4);
+    KP_TRY_CUDA(cudaMemset(p->d_bar, 0, 4 * sizeof(unsigned int)));
     KP_A(p->d_u, (size_t)C * M);
     {
         char* yp = nullptr;
@@ -367,7 +370,7 @@ kp_status plan_destroy_internal(kp_plan p) {
     if (p->fft_ok) cufftDestroy(p->fft);
     void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
                     p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
-                    p->d_grid2,
+                    p->d_grid2, p->d_gridF, p->d_bar,
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
                     p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter};
     for (void* b : bufs)
@@ -472,10 +475,9 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     }
     k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_item_off, tl.ntiles, p->chunk, p->d_iitems);
     KP_LAUNCH_CHECK();
-    p->launches += 3;
-    p->launches += 12;
+    p->launches += 15;
     p->traj_set = true;
-    return KP_OK;
+    return autotune_spread(p, st);
 }
 
 }  // namespace kp
@@ -546,6 +548,11 @@ kp_status kp_plan_set_profiling(kp_plan plan, int enable) {
 
 kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_samples) {
     if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    if (max_tile_samples && *max_tile_samples == -1) {   // query of the chosen spreading variant
+        *max_tile_samples = plan->spread_variant;
+        if (ntiles) *ntiles = plan->n_items;
+        return KP_OK;
+    }
     if (ntiles) *ntiles = plan->tiles.ntiles;
     if (max_tile_samples) *max_tile_samples = plan->max_tile;
     return KP_OK;

@@ -9,12 +9,15 @@
 // ping-pong buffers.  Inverse level l reads the level-l approximation and the details and
 // writes the level-(l-1) approximation (or the image at l = 0).  The soft threshold S_t is
 // applied as the forward kernels write the coefficients, and PDHG's extrapolation
-// xbar = x + theta (x - x_old) is fused into the last inverse level, so the whole prox is
-// 2 L launches.
+// xbar = x + theta (x - x_old) is fused into the last inverse level.  Inside a PDHG iteration
+// the level passes run in one persistent cooperative kernel (k_primal_fused, end of file),
+// separated by grid barriers; the standalone level kernels serve kp_wavelet.
 //
 // Filters: analysis a[k] = sum_n h[n] x[2k+n], d[k] = sum_n g[n] x[2k+n] (indices mod the
 // block length), g[n] = (-1)^n h[7-n]; synthesis is the transpose.
 #include "kp_internal.cuh"
+
+#include <algorithm>
 
 namespace kp {
 
@@ -46,6 +49,11 @@ struct LevelArgs {
     float lambda;
     float2* x;           // extrapolation targets (inverse, first level, prox mode)
     float2* xbar;
+    float2* fgrid;       // when set (inverse, first level): write s_c xbar / Phi into the forward grid
+    const void* maps;
+    const float* apod;
+    Geom geo;
+    int tiles_total;     // number of tiles of the level
 };
 
 template <int D>
@@ -56,35 +64,35 @@ __device__ __forceinline__ int64_t voff(const View& v, const int* i) {
     return o;
 }
 
-// Filter one axis of a shared-memory block: in has extents ein[], out has extents eout[]
-// (equal except along `ax`).  Forward: out[.., q, ..] for q < K is a[k0 + q], for q >= K is
-// d[k0 + q - K], from in[.., 2q' + n, ..].
-template <int D, int K>
-__device__ __forceinline__ void fwd_axis(const float2* __restrict__ in, const int* ein, float2* __restrict__ out,
-                                         const int* eout, int ax) {
-    int tot = 1;
-#pragma unroll
-    for (int d = 0; d < D; ++d) tot *= eout[d];
-    for (int o = threadIdx.x; o < tot; o += blockDim.x) {
-        int idx[D];
+// Filter one axis of a shared-memory block with compile-time extents: the input block has
+// extents (I0, I1, I2) (the last D used); the output equals it except along AX, which becomes
+// 2K.  Forward: out q < K is a[k0 + q], q >= K is d[k0 + q - K], from in[2 (q mod K) + n].
+template <int D, int K, int AX, int I0, int I1, int I2>
+__device__ __forceinline__ void fwd_axis_c(const float2* __restrict__ in, float2* __restrict__ out) {
+    constexpr int EI[3] = {I0, I1, I2};
+    constexpr int O0 = AX == 0 ? 2 * K : I0, O1 = AX == 1 ? 2 * K : I1, O2 = AX == 2 ? 2 * K : I2;
+    constexpr int EO[3] = {O0, O1, O2};
+    constexpr int TOT = D == 2 ? O0 * O1 : O0 * O1 * O2;
+    constexpr int SAX = AX == D - 1 ? 1 : (AX == D - 2 ? EI[D - 1] : EI[1] * EI[2]);
+    for (int o = threadIdx.x; o < TOT; o += blockDim.x) {
+        int idx[3];
         int r = o;
 #pragma unroll
-        for (int d = D - 1; d >= 0; --d) { idx[d] = r % eout[d]; r /= eout[d]; }
-        const int q = idx[ax];
+        for (int d = D - 1; d >= 0; --d) { idx[d] = r % EO[d]; r /= EO[d]; }
+        const int q = idx[AX];
         const bool det = q >= K;
         const int k = det ? q - K : q;
-        int base = 0, stride = 1, sax = 1;
+        int base = 0, stride = 1;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) {
-            if (d == ax) sax = stride;
-            base += (d == ax ? 2 * k : idx[d]) * stride;
-            stride *= ein[d];
+            base += (d == AX ? 2 * k : idx[d]) * stride;
+            stride *= EI[d];
         }
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
             const float c = det ? c_wg[n] : c_wh[n];
-            const float2 v = in[base + n * sax];
+            const float2 v = in[base + n * SAX];
             acc.x = fmaf(c, v.x, acc.x);
             acc.y = fmaf(c, v.y, acc.y);
         }
@@ -92,35 +100,35 @@ __device__ __forceinline__ void fwd_axis(const float2* __restrict__ in, const in
     }
 }
 
-// Inverse along one axis: in holds [a (K+4) | d (K+4)] coefficients for k = kb .. kb+K+3,
-// out holds 2K outputs for j = 2 kb + 8 .. (so that j - n for n < 8 stays >= 2 kb).
-template <int D, int K>
-__device__ __forceinline__ void inv_axis(const float2* __restrict__ in, const int* ein, float2* __restrict__ out,
-                                         const int* eout, int ax) {
-    int tot = 1;
-#pragma unroll
-    for (int d = 0; d < D; ++d) tot *= eout[d];
+// Inverse along AX: the input holds [a (K+4) | d (K+4)] coefficients per axis position for
+// k = kb .. kb+K+3; the output holds 2K values for j = 2 kb + 8 ...
+template <int D, int K, int AX, int I0, int I1, int I2>
+__device__ __forceinline__ void inv_axis_c(const float2* __restrict__ in, float2* __restrict__ out) {
+    constexpr int EI[3] = {I0, I1, I2};
+    constexpr int O0 = AX == 0 ? 2 * K : I0, O1 = AX == 1 ? 2 * K : I1, O2 = AX == 2 ? 2 * K : I2;
+    constexpr int EO[3] = {O0, O1, O2};
+    constexpr int TOT = D == 2 ? O0 * O1 : O0 * O1 * O2;
+    constexpr int SAX = AX == D - 1 ? 1 : (AX == D - 2 ? EI[D - 1] : EI[1] * EI[2]);
     constexpr int E = K + 4;
-    for (int o = threadIdx.x; o < tot; o += blockDim.x) {
-        int idx[D];
+    for (int o = threadIdx.x; o < TOT; o += blockDim.x) {
+        int idx[3];
         int r = o;
 #pragma unroll
-        for (int d = D - 1; d >= 0; --d) { idx[d] = r % eout[d]; r /= eout[d]; }
-        const int jl = idx[ax];            // output j = j0 + jl, j0 = 2 kb + 8
-        int base = 0, stride = 1, sax = 1;
+        for (int d = D - 1; d >= 0; --d) { idx[d] = r % EO[d]; r /= EO[d]; }
+        const int jl = idx[AX];
+        int base = 0, stride = 1;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) {
-            if (d == ax) sax = stride;
-            base += (d == ax ? 0 : idx[d]) * stride;
-            stride *= ein[d];
+            base += (d == AX ? 0 : idx[d]) * stride;
+            stride *= EI[d];
         }
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int n = (jl & 1) + 2 * m;
-            const int kl = (jl + 8 - n) >> 1;    // (j - n)/2 - kb, in [0, K+4)
-            const float2 av = in[base + kl * sax];
-            const float2 dv = in[base + (E + kl) * sax];
+            const int kl = (jl + 8 - n) >> 1;
+            const float2 av = in[base + kl * SAX];
+            const float2 dv = in[base + (E + kl) * SAX];
             acc.x = fmaf(c_wh[n], av.x, fmaf(c_wg[n], dv.x, acc.x));
             acc.y = fmaf(c_wh[n], av.y, fmaf(c_wg[n], dv.y, acc.y));
         }
@@ -135,12 +143,11 @@ __device__ __forceinline__ float2 soft(float2 c, float t) {
 }
 
 template <int D, int T>
-__global__ void __launch_bounds__(256) k_dwt_fwd_level(LevelArgs a) {
-    extern __shared__ float2 sm[];
+__device__ __forceinline__ void fwd_level_tile(const LevelArgs& a, int tile, float2* sm) {
     constexpr int EI = 2 * T + 6;
     int tc[D];
     {
-        int r = blockIdx.x;
+        int r = tile;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) { tc[d] = r % a.tiles[d]; r /= a.tiles[d]; }
     }
@@ -166,24 +173,23 @@ __global__ void __launch_bounds__(256) k_dwt_fwd_level(LevelArgs a) {
         buf0[o] = a.src.p[voff<D>(a.src, i)];
     }
     __syncthreads();
-    // filter axis by axis, last axis first
-    int ecur[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) ecur[d] = EI;
-    float2* in = buf0;
-    float2* out = buf1;
-#pragma unroll
-    for (int ax = D - 1; ax >= 0; --ax) {
-        int eout[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) eout[d] = d == ax ? 2 * T : ecur[d];
-        fwd_axis<D, T>(in, ecur, out, eout, ax);
+    // filter axis by axis, last axis first (buf0 -> buf1 -> buf0 [-> buf1 in 3D])
+    constexpr int T2 = 2 * T;
+    float2* in;
+    if (D == 2) {
+        fwd_axis_c<D, T, 1, EI, EI, 1>(buf0, buf1);
         __syncthreads();
-#pragma unroll
-        for (int d = 0; d < D; ++d) ecur[d] = eout[d];
-        float2* t = in;
-        in = out;
-        out = t;
+        fwd_axis_c<D, T, 0, EI, T2, 1>(buf1, buf0);
+        __syncthreads();
+        in = buf0;
+    } else {
+        fwd_axis_c<D, T, 2, EI, EI, EI>(buf0, buf1);
+        __syncthreads();
+        fwd_axis_c<D, T, 1, EI, EI, T2>(buf1, buf0);
+        __syncthreads();
+        fwd_axis_c<D, T, 0, EI, T2, T2>(buf0, buf1);
+        __syncthreads();
+        in = buf1;
     }
     // in now holds (2T)^D values: per axis q < T -> a[k0+q], q >= T -> d[k0+q-T]
     const float thr = a.sched ? a.sched[3 * (*a.iter) + 1] * a.lambda : 0.f;
@@ -215,15 +221,15 @@ __global__ void __launch_bounds__(256) k_dwt_fwd_level(LevelArgs a) {
             a.coef.p[voff<D>(a.coef, pos)] = v;
         }
     }
+    __syncthreads();   // shared memory is reused by the next tile
 }
 
-template <int D, int T>
-__global__ void __launch_bounds__(256) k_dwt_inv_level(LevelArgs a) {
-    extern __shared__ float2 sm[];
+template <int D, int T, typename MT>
+__device__ __forceinline__ void inv_level_tile(const LevelArgs& a, int tile, float2* sm) {
     constexpr int E = T + 4;      // coefficients per subband per axis
     int tc[D];
     {
-        int r = blockIdx.x;
+        int r = tile;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) { tc[d] = r % a.tiles[d]; r /= a.tiles[d]; }
     }
@@ -257,23 +263,22 @@ __global__ void __launch_bounds__(256) k_dwt_inv_level(LevelArgs a) {
         buf0[o] = v;
     }
     __syncthreads();
-    int ecur[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) ecur[d] = 2 * E;
-    float2* in = buf0;
-    float2* out = buf1;
-#pragma unroll
-    for (int ax = D - 1; ax >= 0; --ax) {
-        int eout[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) eout[d] = d == ax ? 2 * T : ecur[d];
-        inv_axis<D, T>(in, ecur, out, eout, ax);
+    constexpr int T2 = 2 * T, E2 = 2 * E;
+    float2* in;
+    if (D == 2) {
+        inv_axis_c<D, T, 1, E2, E2, 1>(buf0, buf1);
         __syncthreads();
-#pragma unroll
-        for (int d = 0; d < D; ++d) ecur[d] = eout[d];
-        float2* t = in;
-        in = out;
-        out = t;
+        inv_axis_c<D, T, 0, E2, T2, 1>(buf1, buf0);
+        __syncthreads();
+        in = buf0;
+    } else {
+        inv_axis_c<D, T, 2, E2, E2, E2>(buf0, buf1);
+        __syncthreads();
+        inv_axis_c<D, T, 1, E2, E2, T2>(buf1, buf0);
+        __syncthreads();
+        inv_axis_c<D, T, 0, E2, T2, T2>(buf0, buf1);
+        __syncthreads();
+        in = buf1;
     }
     // inv_axis produced outputs for j = 2 kb + 8 + jl = 2 T tc + jl
     const float th = (a.lev_first && a.x) ? a.sched[3 * (*a.iter) + 2] : 0.f;
@@ -296,12 +301,27 @@ __global__ void __launch_bounds__(256) k_dwt_inv_level(LevelArgs a) {
         const int64_t off = voff<D>(a.dst, j);
         if (a.lev_first && a.x) {
             const float2 xo = a.x[off];
-            a.xbar[off] = make_float2(v.x + th * (v.x - xo.x), v.y + th * (v.y - xo.y));
+            const float2 xb = make_float2(v.x + th * (v.x - xo.x), v.y + th * (v.y - xo.y));
+            a.xbar[off] = xb;
             a.x[off] = v;
+            if (a.fgrid) pre_pixel<D, MT>(a.fgrid, (const MT*)a.maps, a.apod, a.geo, off, xb);
         } else {
             a.dst.p[off] = v;
         }
     }
+    __syncthreads();   // shared memory is reused by the next tile
+}
+
+template <int D, int T>
+__global__ void __launch_bounds__(256) k_dwt_fwd_level(LevelArgs a) {
+    extern __shared__ float2 sm[];
+    fwd_level_tile<D, T>(a, blockIdx.x, sm);
+}
+
+template <int D, int T>
+__global__ void __launch_bounds__(256) k_dwt_inv_level(LevelArgs a) {
+    extern __shared__ float2 sm[];
+    inv_level_tile<D, T, float2>(a, blockIdx.x, sm);
 }
 
 static inline int wt_tile(int D) { return D == 2 ? 16 : 8; }
@@ -356,8 +376,8 @@ static kp_status launch_inv(const LevelArgs& a, int nblocks, cudaStream_t st) {
 
 // Forward W (coefficients in Mallat layout into `coef`), optionally soft-thresholded at
 // tau_k lambda (prox mode, sched != null).
-static kp_status wavelet_forward(kp_plan p, const float2* in, float2* coef, const float* sched, float lambda,
-                                 cudaStream_t st) {
+// Forward W (coefficients in Mallat layout into `coef`), no threshold.
+static kp_status wavelet_forward(kp_plan p, const float2* in, float2* coef, cudaStream_t st) {
     const Geom& g = p->geo;
     const int L = p->P.wavelet_levels;
     const int T = wt_tile(g.D);
@@ -378,9 +398,7 @@ static kp_status wavelet_forward(kp_plan p, const float2* in, float2* coef, cons
         a.dst = dense_view(ll[lev & 1], hdim, g.D);
         a.coef = full_view(coef, g);
         a.lev_last = lev == L - 1;
-        a.sched = sched;
         a.iter = p->d_iter;
-        a.lambda = lambda;
         if (g.D == 2) KP_TRY((launch_fwd<2, 16>(a, nb, st)));
         else KP_TRY((launch_fwd<3, 8>(a, nb, st)));
         p->launches += 1;
@@ -388,10 +406,8 @@ static kp_status wavelet_forward(kp_plan p, const float2* in, float2* coef, cons
     return KP_OK;
 }
 
-// Inverse W from Mallat-layout coefficients; in prox mode (x != null) the last level writes
-// x_new and the extrapolation xbar = x_new + theta_k (x_new - x).
-static kp_status wavelet_inverse(kp_plan p, const float2* coef, float2* out, float2* x, float2* xbar,
-                                 const float* sched, cudaStream_t st) {
+// Inverse W from Mallat-layout coefficients.
+static kp_status wavelet_inverse(kp_plan p, const float2* coef, float2* out, cudaStream_t st) {
     const Geom& g = p->geo;
     const int L = p->P.wavelet_levels;
     const int T = wt_tile(g.D);
@@ -410,13 +426,10 @@ static kp_status wavelet_inverse(kp_plan p, const float2* coef, float2* out, flo
         }
         a.src = dense_view(ll[lev & 1], hdim, g.D);
         a.coef = full_view(const_cast<float2*>(coef), g);
-        a.dst = lev == 0 ? full_view(x ? x : out, g) : dense_view(ll[(lev - 1) & 1], bdim, g.D);
+        a.dst = lev == 0 ? full_view(out, g) : dense_view(ll[(lev - 1) & 1], bdim, g.D);
         a.lev_last = lev == L - 1;
         a.lev_first = lev == 0;
-        a.sched = sched;
         a.iter = p->d_iter;
-        a.x = (lev == 0) ? x : nullptr;
-        a.xbar = (lev == 0) ? xbar : nullptr;
         if (g.D == 2) KP_TRY((launch_inv<2, 16>(a, nb, st)));
         else KP_TRY((launch_inv<3, 8>(a, nb, st)));
         p->launches += 1;
@@ -425,26 +438,238 @@ static kp_status wavelet_inverse(kp_plan p, const float2* coef, float2* out, flo
 }
 
 kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st) {
-    if (forward) {
-        if (in == out) {
-            // the level kernels read the image while writing coefficients: stage a copy
-            KP_TRY_CUDA(cudaMemcpyAsync(p->d_w, in, p->geo.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-            in = p->d_w;
-        }
-        return wavelet_forward(p, in, out, nullptr, 0.f, st);
-    }
     if (in == out) {
+        // the level kernels read the input while writing the output: stage a copy
         KP_TRY_CUDA(cudaMemcpyAsync(p->d_w, in, p->geo.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
         in = p->d_w;
     }
-    return wavelet_inverse(p, in, out, nullptr, nullptr, nullptr, st);
+    if (forward) return wavelet_forward(p, in, out, st);
+    return wavelet_inverse(p, in, out, st);
 }
 
-// PDHG l1-wavelet prox with extrapolation: z -> coefficients (thresholded) -> x_new, xbar.
-kp_status wavelet_prox_extrap(kp_plan p, float lambda, cudaStream_t st) {
-    KP_TRY(wavelet_forward(p, p->d_z, p->d_w, p->d_sched, lambda, st));
-    KP_TRY(wavelet_inverse(p, p->d_w, nullptr, p->d_x, p->d_xbar, p->d_sched, st));
+}  // namespace kp
+
+namespace kp {
+
+// ================================================================ fused primal step
+// One persistent cooperative kernel per PDHG iteration after the inverse FFT (Sec. 4.1):
+//   z = x - tau_k A^H u  (coil combine + apodisation of the adjoint grid)
+//   l2:  x_new = z / (1 + tau_k lambda)
+//   l1:  x_new = W^H S_{tau_k lambda}(W z), level by level with grid barriers in between
+//   xbar = x_new + theta_k (x_new - x),  x = x_new,
+//   forward pre-step of the next iteration: grid_c = s_c xbar / Phi (image region only),
+//   iteration counter += 1.
+// Grid barrier: arrival counter + generation word in device memory; every wait is bounded
+// (about a second of SM clock), after which the kernel records a timeout in *err and carries
+// on (the host reports KP_ETIMEOUT).
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &b->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > 2000000000LL) {   // about one second at GB300 clocks
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+struct PrimalArgs {
+    const float2* grid2;   // adjoint grid after the inverse FFT
+    const void* maps;
+    const float* apod;
+    Geom geo;
+    float2* x;
+    float2* xbar;
+    float2* z;
+    float2* coef;          // wavelet coefficients
+    float2* ll0;
+    float2* ll1;
+    float2* fgrid;         // forward grid of the next iteration (image region written)
+    const float* sched;
+    int* iter;
+    float lambda;
+    int levels;
+    GridBarrier* bar;
+    int* err;
+};
+
+template <int D, int T>
+__device__ __forceinline__ LevelArgs level_args(const PrimalArgs& a, int lev, bool fwd, int k) {
+    LevelArgs la{};
+    const Geom& g = a.geo;
+    int bdim[MAXD], hdim[MAXD];
+    int nb = 1;
+    for (int d = 0; d < D; ++d) {
+        bdim[d] = g.n[d] >> lev;
+        hdim[d] = bdim[d] / 2;
+        la.b[d] = bdim[d];
+        la.tiles[d] = fwd ? (hdim[d] + T - 1) / T : (bdim[d] + 2 * T - 1) / (2 * T);
+        nb *= la.tiles[d];
+    }
+    la.tiles_total = nb;
+    auto full = [&](float2* p) { View v{}; v.p = p; int64_t s = 1; for (int d = D - 1; d >= 0; --d) { v.s[d] = s; s *= g.n[d]; } return v; };
+    auto dense = [&](float2* p, const int* dims) { View v{}; v.p = p; int64_t s = 1; for (int d = D - 1; d >= 0; --d) { v.s[d] = s; s *= dims[d]; } return v; };
+    float2* ll[2] = {a.ll0, a.ll1};
+    la.coef = full(a.coef);
+    la.lev_last = lev == a.levels - 1;
+    la.sched = a.sched;
+    la.iter = a.iter;
+    la.lambda = a.lambda;
+    la.geo = g;
+    if (fwd) {
+        la.src = lev == 0 ? full(a.z) : dense(ll[(lev - 1) & 1], bdim);
+        la.dst = dense(ll[lev & 1], hdim);
+    } else {
+        la.src = dense(ll[lev & 1], hdim);
+        la.dst = lev == 0 ? full(a.x) : dense(ll[(lev - 1) & 1], bdim);
+        la.lev_first = lev == 0;
+        la.x = lev == 0 ? a.x : nullptr;
+        la.xbar = lev == 0 ? a.xbar : nullptr;
+        la.fgrid = lev == 0 ? a.fgrid : nullptr;
+        la.maps = a.maps;
+        la.apod = a.apod;
+    }
+    (void)k;
+    return la;
+}
+
+constexpr int PF_THREADS = 512;
+
+template <int D, int T, typename MT, int REG>
+__global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
+    extern __shared__ float2 sm[];
+    const Geom& g = a.geo;
+    const int k = *a.iter;
+    const float tau = a.sched[3 * k + 1], theta = a.sched[3 * k + 2];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += stride) {
+        const float2 ah = adj_pixel<D, MT>(a.grid2, (const MT*)a.maps, a.apod, g, j);
+        const float2 xo = a.x[j];
+        const float2 zz = make_float2(xo.x - tau * ah.x, xo.y - tau * ah.y);
+        if (REG == 0) {
+            const float sc = 1.f / (1.f + tau * a.lambda);
+            const float2 xn = make_float2(zz.x * sc, zz.y * sc);
+            const float2 xb = make_float2(xn.x + theta * (xn.x - xo.x), xn.y + theta * (xn.y - xo.y));
+            a.x[j] = xn;
+            a.xbar[j] = xb;
+            pre_pixel<D, MT>(a.fgrid, (const MT*)a.maps, a.apod, g, j, xb);
+        } else {
+            a.z[j] = zz;
+        }
+    }
+    if (REG == 1) {
+        grid_barrier(a.bar, a.err);
+        for (int lev = 0; lev < a.levels; ++lev) {
+            const LevelArgs la = level_args<D, T>(a, lev, true, k);
+            for (int t = blockIdx.x; t < la.tiles_total; t += gridDim.x) fwd_level_tile<D, T>(la, t, sm);
+            grid_barrier(a.bar, a.err);
+        }
+        for (int lev = a.levels - 1; lev >= 0; --lev) {
+            const LevelArgs la = level_args<D, T>(a, lev, false, k);
+            for (int t = blockIdx.x; t < la.tiles_total; t += gridDim.x) inv_level_tile<D, T, MT>(la, t, sm);
+            if (lev > 0) grid_barrier(a.bar, a.err);
+        }
+    }
+    grid_barrier(a.bar, a.err);   // every block has read the iteration counter
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.iter = k + 1;
+}
+
+template <int D, int T>
+static size_t primal_smem() {
+    constexpr int EI = 2 * T + 6, E = T + 4;
+    size_t f = 1, f1 = 1, v = 1, v1 = 1;
+    for (int d = 0; d < D; ++d) {
+        f *= EI; f1 *= (d == D - 1 ? 2 * T : EI);
+        v *= 2 * E; v1 *= (d == D - 1 ? 2 * T : 2 * E);
+    }
+    return std::max(f + f1, v + v1) * sizeof(float2);
+}
+
+template <int D, int T, typename MT, int REG>
+static kp_status launch_primal(kp_plan p, const PrimalArgs& a, cudaStream_t st) {
+    auto kern = k_primal_fused<D, T, MT, REG>;
+    const size_t smem = REG == 1 ? primal_smem<D, T>() : 0;
+    static int blocks_cache[4] = {0, 0, 0, 0};
+    int& nblk = blocks_cache[(D - 2) * 2 + REG];
+    if (nblk == 0) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        int dev = 0, sms = 0, per = 0;
+        KP_TRY_CUDA(cudaGetDevice(&dev));
+        KP_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        KP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, PF_THREADS, smem));
+        if (per < 1) { set_error("fused primal kernel does not fit on an SM"); return KP_EINTERNAL; }
+        nblk = sms;   // one CTA per SM: the barrier's arrival count stays small
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)nblk);
+    cfg.blockDim = dim3(PF_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    KP_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    p->launches += 1;
     return KP_OK;
+}
+
+kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st) {
+    const Geom& g = p->geo;
+    PrimalArgs a{};
+    a.grid2 = p->d_grid2;
+    a.maps = p->d_maps;
+    a.apod = p->d_apod;
+    a.geo = g;
+    a.x = p->d_x;
+    a.xbar = p->d_xbar;
+    a.z = p->d_z;
+    a.coef = p->d_w;
+    a.ll0 = p->d_wl0;
+    a.ll1 = p->d_wl1;
+    a.fgrid = p->d_grid;
+    a.sched = p->d_sched;
+    a.iter = p->d_iter;
+    a.lambda = lambda;
+    a.levels = p->P.wavelet_levels;
+    a.bar = (GridBarrier*)p->d_bar;
+    a.err = p->d_flag + 3;
+    mark(p, PH_ADJ, st);
+    const kp_cdtype mt = p->maps_t;
+#define KP_PRIMAL(DD, TT)                                                                          \
+    do {                                                                                           \
+        if (reg == KP_REG_L2) {                                                                    \
+            if (mt == KP_C64) return launch_primal<DD, TT, float2, 0>(p, a, st);                   \
+            if (mt == KP_C32_BF16) return launch_primal<DD, TT, __nv_bfloat162, 0>(p, a, st);      \
+            return launch_primal<DD, TT, __half2, 0>(p, a, st);                                    \
+        }                                                                                          \
+        if (mt == KP_C64) return launch_primal<DD, TT, float2, 1>(p, a, st);                       \
+        if (mt == KP_C32_BF16) return launch_primal<DD, TT, __nv_bfloat162, 1>(p, a, st);          \
+        return launch_primal<DD, TT, __half2, 1>(p, a, st);                                        \
+    } while (0)
+    if (g.D == 2) KP_PRIMAL(2, 16);
+    KP_PRIMAL(3, 8);
+#undef KP_PRIMAL
 }
 
 }  // namespace kp
