@@ -109,3 +109,75 @@ def test_pdhg_rejects_bad_inputs():
         plan.pdhg_solve(to_dev(y), to_dev(bad_p), "l2", 1e-3, 5)
     x0, _, _ = plan.pdhg_solve(to_dev(y), None, "l2", 1e-3, 0)       # zero iterations -> x0 = 0
     assert float(x0.abs().max()) == 0.0
+
+
+def _small_3d(n=16, C=3, spokes=300, nr=16, levels=2):
+    w = synth.Workload("ute_small", (n, n, n), C, 1.25, 4, "l1_wavelet", 1e-3, 20, levels, "radial3d",
+                       dict(n_spokes=spokes, n_readout=nr, kmax=n / 2.0))
+    return w, w.phantom(), w.maps(), w.traj()
+
+
+@pytest.mark.parametrize("reg,lam", [("l2", 1e-3), ("l1_wavelet", 1e-3)])
+def test_pdhg_3d_parity(reg, lam):
+    """3D centre-out radial (Fibonacci sphere), 16^3 x 3 coils, 2 wavelet levels."""
+    need_gpu()
+    w, x, maps, traj = _small_3d()
+    y = simulate(w, x, maps, traj)
+    A, AH = _ops(maps, traj, 1.25)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    if reg == "l1_wavelet":
+        lam = lam * float(np.abs(AH(y.astype(np.complex128))).max())
+    x_ref, _, _, _ = osv.pdhg(A, AH, y, p, x.shape, reg, lam, 20, L, levels=2)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    pg = plan.make_preconditioner(True).cpu().numpy()
+    assert rel(pg, p) < 1e-4
+    xg, _, st = plan.pdhg_solve(to_dev(y), to_dev(p.astype(np.float32)), reg, lam, 20, lmax=L)
+    assert rel(xg.cpu().numpy(), x_ref) < 1e-5
+
+
+@pytest.mark.parametrize("ystore,mstore,tol", [("bf16", "fp16", 2e-3), ("fp16", "bf16", 2e-3), ("bf16", "bf16", 3e-3)])
+def test_pdhg_half_storage(ystore, mstore, tol):
+    """Mixed precision: measurements and coil maps stored in 16-bit floats, float32 arithmetic,
+    against the float64 oracle on the unrounded inputs (spec tolerance 2e-3; bf16 maps
+    and data together carry twice the rounding and get 3e-3)."""
+    need_gpu()
+    from paper_1902_09657_gb300.api import to_storage
+    w, x, maps, traj = _small_spiral()
+    y = simulate(w, x, maps, traj)
+    A, AH = _ops(maps, traj, 1.25)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    lam = 1e-3 * float(np.abs(AH(y.astype(np.complex128))).max())
+    x_ref, _, _, _ = osv.pdhg(A, AH, y, p, x.shape, "l1_wavelet", lam, 30, L, levels=3)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=3)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_storage(to_dev(maps), mstore))
+    xg, _, _ = plan.pdhg_solve(to_storage(to_dev(y), ystore), to_dev(p.astype(np.float32)), "l1_wavelet", lam, 30,
+                               lmax=L)
+    assert rel(xg.cpu().numpy(), x_ref) < tol
+
+
+def test_ute3d_full_size_properties():
+    """Full-size 3D UTE workload (192^3, 8 coils, 24,000 x 256 samples): adjoint identity of the
+    GPU operator pair, a positive finite multi-channel preconditioner, and three l1-wavelet
+    PDHG iterations with a finite, decreasing objective."""
+    need_gpu()
+    import torch
+    w, x, maps, traj = workload_problem("ute3d_192")
+    C, M = maps.shape[0], traj.shape[0]
+    plan = make_plan(x.shape, C, M, 1.25, 3)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    xd = to_dev(x)
+    y = plan.sense_forward(xd)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.randn(C, M, dtype=torch.complex64, device="cuda", generator=g)
+    lhs = torch.vdot(u.flatten().to(torch.complex128), y.flatten().to(torch.complex128))
+    xa = plan.sense_adjoint(u)
+    rhs = torch.vdot(xa.flatten().to(torch.complex128), xd.flatten().to(torch.complex128))
+    assert abs(complex(lhs - rhs)) < 1e-4 * abs(complex(lhs))
+    p = plan.make_preconditioner(True)
+    assert bool(torch.isfinite(p).all()) and float(p.min()) > 0
+    lam = 1e-3 * float(plan.sense_adjoint(y).abs().max())
+    _, tr, st = plan.pdhg_solve(y, p, "l1_wavelet", lam, 3, trace=True)
+    assert all(np.isfinite(tr)) and tr[2] < tr[0]
