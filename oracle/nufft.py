@@ -79,8 +79,12 @@ def kb_apod(n, G, W, beta):
     return out
 
 
-def grid_coords(traj, img_shape, gshape):
-    """t_{i,d} = f_{i,d} * (G_d / N_d), computed in float32 as the GPU does."""
+def grid_coords(traj, img_shape, gshape, exact=False):
+    """t_{i,d} = f_{i,d} * (G_d / N_d), computed in float32 as the GPU does (exact=True: float64,
+    used only by finite-difference checks, whose steps float32 coordinates cannot resolve)."""
+    if exact:
+        traj = np.asarray(traj, dtype=np.float64)
+        return traj * np.array([g / n for g, n in zip(gshape, img_shape)])[None, :]
     traj = np.asarray(traj, dtype=np.float32)
     scale = np.array([np.float32(g) / np.float32(n) for g, n in zip(gshape, img_shape)],
                      dtype=np.float32)
@@ -91,7 +95,7 @@ def first_tap(t, W):
     """k0 = ceil(t) - W/2 for even W: the same integer as ceil(t - W/2) in exact arithmetic,
     computed without rounding (t - W/2 in float32 can round onto an integer when |t| < W/2,
     which would push the first tap just outside the window)."""
-    t = np.asarray(t, dtype=np.float32)
+    t = np.asarray(t)
     return np.ceil(t).astype(np.int64) - W // 2
 
 
@@ -148,9 +152,9 @@ def nudft_adjoint(y, maps, traj):
 class _Taps:
     """Per-sample interpolation taps: flat grid indices [T, M] and weights [T, M]."""
 
-    def __init__(self, traj, img_shape, gshape, W):
+    def __init__(self, traj, img_shape, gshape, W, exact=False):
         d = len(img_shape)
-        t32 = grid_coords(traj, img_shape, gshape)
+        t32 = grid_coords(traj, img_shape, gshape, exact)
         k0 = first_tap(t32, W)
         t = t32.astype(np.float64)
         per_dim_idx, per_dim_w = [], []
@@ -191,7 +195,7 @@ def _pad_index(img_shape, gshape):
     return np.ix_(*[np.mod(_centred(n), g) for n, g in zip(img_shape, gshape)])
 
 
-def nufft_forward(x, maps, traj, oversamp=1.25, W=4):
+def nufft_forward(x, maps, traj, oversamp=1.25, W=4, exact_coords=False):
     """NUFFT approximation of A x: coil multiply, apodise, pad, DFT, interpolate. [C, M]."""
     img_shape = x.shape
     d = len(img_shape)
@@ -202,14 +206,14 @@ def nufft_forward(x, maps, traj, oversamp=1.25, W=4):
     grid = np.zeros((C,) + gshape, dtype=np.complex128)
     grid[(slice(None),) + _pad_index(img_shape, gshape)] = img
     Xhat = np.fft.fftn(grid, axes=tuple(range(1, d + 1))).reshape(C, -1)
-    taps = _Taps(traj, img_shape, gshape, W)
+    taps = _Taps(traj, img_shape, gshape, W, exact_coords)
     y = np.zeros((C, taps.w.shape[1]), dtype=np.complex128)
     for j in range(taps.w.shape[0]):
         y += taps.w[j][None, :] * Xhat[:, taps.flat[j]]
     return y / math.sqrt(N)
 
 
-def nufft_adjoint(y, maps, traj, oversamp=1.25, W=4):
+def nufft_adjoint(y, maps, traj, oversamp=1.25, W=4, exact_coords=False):
     """Exact transpose of nufft_forward: spread, inverse DFT (unnormalised), crop, apodise, coil combine."""
     img_shape = maps.shape[1:]
     d = len(img_shape)
@@ -217,7 +221,7 @@ def nufft_adjoint(y, maps, traj, oversamp=1.25, W=4):
     N = int(np.prod(img_shape))
     G = int(np.prod(gshape))
     C = maps.shape[0]
-    taps = _Taps(traj, img_shape, gshape, W)
+    taps = _Taps(traj, img_shape, gshape, W, exact_coords)
     flat = taps.flat.ravel()
     grid = np.empty((C, G), dtype=np.complex128)
     for c in range(C):
