@@ -161,6 +161,34 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
                         kp_reg reg, float lambda, int iters, double lmax, void* x_dev,
                         double* obj_trace, kp_stats* stats, void* stream);
 
+/* Trajectory gradient through y = A x (differentiable reconstruction; Sec. 6 operator with the
+ * Kaiser-Bessel derivative phi'): gtraj[i][d] = Re sum_c conj(gy_c[i]) d y_c[i] / d f_{i,d},
+ * taps held fixed (y jumps where a coordinate crosses a grid line, at the window edge).
+ * x_dev complex64 [N]; gy_dev complex64 [C][M] (user order); gtraj_dev float32 [M][ndim]
+ * (overwritten).  Asynchronous. */
+kp_status kp_sense_forward_traj_grad(kp_plan plan, const void* x_dev, const void* gy_dev, float* gtraj_dev,
+                                     void* stream);
+
+/* Trajectory gradient through x = A^H u: gtraj[i][d] = Re sum_n conj(gx[n]) d x[n] / d f_{i,d}
+ * = Re sum_c conj(u_c[i]) d (A gx)_c[i] / d f_{i,d}.  u_dev [C][M], gx_dev [N], gtraj_dev
+ * [M][ndim] (overwritten).  Asynchronous. */
+kp_status kp_sense_adjoint_traj_grad(kp_plan plan, const void* u_dev, const void* gx_dev, float* gtraj_dev,
+                                     void* stream);
+
+/* Unrolled l2 PDHG for differentiation: `iters` iterations of Sec. 4.1 with
+ * g = lambda ||x||^2 / 2 (same schedule, start and preconditioner rules as kp_pdhg_solve,
+ * complex64 y), keeping xbar_k, u_{k+1} and x_{k+1} of every iteration in the plan (per-
+ * iteration checkpoints, (2N + CM) complex values each).  x_dev receives x_K.  Synchronous. */
+kp_status kp_unrolled_forward(kp_plan plan, const void* y_dev, const float* p_dev, float lambda, int iters,
+                              double lmax, void* x_dev, void* stream);
+
+/* Reverse sweep of the last kp_unrolled_forward: given gx = dL/dRe x_K + i dL/dIm x_K
+ * (complex64 [N]), returns dL/dy (complex64 [C][M], user order, or NULL), dL/dlambda (host,
+ * or NULL) and dL/df (float32 [M][ndim], or NULL), with p, lambda_max and the step sizes held
+ * constant.  Synchronous. */
+kp_status kp_unrolled_backward(kp_plan plan, const void* gx_dev, void* gy_dev, double* glambda, float* gtraj_dev,
+                               void* stream);
+
 /* Periodised multilevel Daubechies-4 wavelet transform W (forward = 1) or W^H
  * (forward = 0) of a complex64 [N] image, Mallat layout, plan's wavelet_levels.
  * in_dev and out_dev may alias.  Asynchronous. */

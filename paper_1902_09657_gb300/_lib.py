@@ -59,6 +59,10 @@ _SIGS = {
     "kp_plan_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "kp_plan_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     "kp_sense_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(KpParams), _vp, _vp, _vp, _vp, _vp]),
+    "kp_sense_forward_traj_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "kp_sense_adjoint_traj_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "kp_unrolled_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int, ctypes.c_double, _vp, _vp]),
+    "kp_unrolled_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
     "kp_plan_tile_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
 }
 

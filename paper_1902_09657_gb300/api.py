@@ -82,8 +82,12 @@ class Plan:
             pass
 
     def _dev(self, t, name):
+        """Check placement and layout; materialise lazy conjugate / negative views (autograd
+        hands those to backward functions), whose raw memory is not the tensor's value."""
         if not t.is_cuda or t.device != self.device:
             raise ValueError(f"{name} must be on {self.device}")
+        if t.is_conj() or t.is_neg():
+            t = t.resolve_conj().resolve_neg()
         if not t.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
         return t
@@ -145,7 +149,7 @@ class Plan:
         y = self._dev(y, "y")
         if out is None:
             out = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
-        self._dev(out, "out")
+        out = self._dev(out, "out")
         L.check(self.lib.kp_sense_adjoint(self._h, _ptr(y), _ctype_of(y), _ptr(out), _stream(self.device)),
                 "kp_sense_adjoint")
         return out
@@ -162,11 +166,51 @@ class Plan:
     def max_eig(self, p=None, v0=None, iters=30):
         """lambda_max(P A A^H) by the power method."""
         lm = ctypes.c_double()
-        pp = _ptr(self._dev(p, "p")) if p is not None else None
-        vv = _ptr(self._dev(v0, "v0")) if v0 is not None else None
+        p = self._dev(p, "p") if p is not None else None
+        v0 = self._dev(v0, "v0") if v0 is not None else None
+        pp = _ptr(p) if p is not None else None
+        vv = _ptr(v0) if v0 is not None else None
         L.check(self.lib.kp_max_eig(self._h, pp, vv, int(iters), ctypes.byref(lm), _stream(self.device)),
                 "kp_max_eig")
         return lm.value
+
+    def sense_forward_traj_grad(self, x, gy):
+        """dL/dtraj [M, ndim] through y = A x for the upstream gradient gy."""
+        out = torch.empty((self.nsamples, self.ndim), dtype=torch.float32, device=self.device)
+        x, gy = self._dev(x, "x"), self._dev(gy, "gy")
+        L.check(self.lib.kp_sense_forward_traj_grad(self._h, _ptr(x), _ptr(gy),
+                                                    _ptr(out), _stream(self.device)), "kp_sense_forward_traj_grad")
+        return out
+
+    def sense_adjoint_traj_grad(self, u, gx):
+        """dL/dtraj [M, ndim] through x = A^H u for the upstream gradient gx."""
+        out = torch.empty((self.nsamples, self.ndim), dtype=torch.float32, device=self.device)
+        u, gx = self._dev(u, "u"), self._dev(gx, "gx")
+        L.check(self.lib.kp_sense_adjoint_traj_grad(self._h, _ptr(u), _ptr(gx),
+                                                    _ptr(out), _stream(self.device)), "kp_sense_adjoint_traj_grad")
+        return out
+
+    def unrolled_forward(self, y, p=None, lam=0.0, iters=10, lmax=0.0):
+        """Unrolled l2 PDHG keeping per-iteration checkpoints; returns x_K."""
+        x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
+        p = self._dev(p, "p") if p is not None else None
+        y = self._dev(y, "y")
+        pp = _ptr(p) if p is not None else None
+        L.check(self.lib.kp_unrolled_forward(self._h, _ptr(y), pp, float(lam), int(iters), float(lmax),
+                                             _ptr(x), _stream(self.device)), "kp_unrolled_forward")
+        return x
+
+    def unrolled_backward(self, gx, want_y=True, want_traj=True):
+        """Reverse sweep of the last unrolled_forward: (dL/dy, dL/dlambda, dL/dtraj)."""
+        gy = torch.empty((self.ncoils, self.nsamples), dtype=torch.complex64, device=self.device) if want_y else None
+        gt = torch.empty((self.nsamples, self.ndim), dtype=torch.float32, device=self.device) if want_traj else None
+        gl = ctypes.c_double()
+        gx = self._dev(gx.contiguous(), "gx")
+        L.check(self.lib.kp_unrolled_backward(self._h, _ptr(gx),
+                                              _ptr(gy) if gy is not None else None, ctypes.byref(gl),
+                                              _ptr(gt) if gt is not None else None, _stream(self.device)),
+                "kp_unrolled_backward")
+        return gy, gl.value, gt
 
     def wavelet(self, x, forward=True, out=None):
         x = self._dev(x, "x")
@@ -181,11 +225,11 @@ class Plan:
         back to the host).  Returns (x, objective trace or None, stats dict)."""
         host = not y.is_cuda
         yd = y.to(self.device, non_blocking=True) if host else y
-        self._dev(yd, "y")
+        yd = self._dev(yd, "y")
         pd = None
         if p is not None:
             pd = p.to(self.device, non_blocking=True) if not p.is_cuda else p
-            self._dev(pd, "p")
+            pd = self._dev(pd, "p")
         x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device) if out is None or host else out
         tr = (ctypes.c_double * max(int(iters), 1))() if trace else None
         st = L.KpStats()

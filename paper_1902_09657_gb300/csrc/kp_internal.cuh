@@ -246,6 +246,13 @@ struct kp_plan_s {
     // wavelet
     float h[8];                      // Daubechies-4 scaling filter (host copy)
 
+    // unrolled PDHG checkpoints: per iteration xbar_k [N], u_{k+1} [C][M] (sorted), x_{k+1} [N]
+    float2* d_tape = nullptr;
+    size_t tape_cap = 0;
+    int tape_iters = 0;
+    float tape_lambda = 0.f;
+    float2* d_bk = nullptr;          // [2][C][M] reverse-sweep k-space work (g_r, g_y)
+
     kp::Graph graphs[2];
     // profiling: when on, PDHG runs without the graph and records an event at each phase
     bool profiling = false;
@@ -291,8 +298,12 @@ kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st);
 // kp_pdhg.cu
 kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st);
 kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
+                      cudaStream_t st);
+kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);
+kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status interp_dual_only(kp_plan p, cudaStream_t st);
 void daubechies4(float h[8]);
 kp_status upload_wavelet_filter(const float h[8]);

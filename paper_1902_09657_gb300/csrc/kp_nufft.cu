@@ -867,6 +867,9 @@ static kp_status fwd_grid(kp_plan p, const float2* x, cudaStream_t st) {
     return KP_OK;
 }
 
+// Forward grid spectrum of x (pre-step into d_grid, FFT into d_gridF), no interpolation.
+kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st) { return fwd_grid(p, x, st); }
+
 // Forward pre-step only (coil multiply, apodise, pad) of x into d_grid.
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st) {
     const Geom& g = p->geo;

@@ -286,6 +286,60 @@ static kp_status ensure_sched(kp_plan p, int iters) {
     return KP_OK;
 }
 
+// Everything a PDHG run needs before its first iteration (Sec. 4.1): measurements and
+// preconditioner in sorted order, min p, lambda_max (given, or 30 power iterations), the
+// step-size schedule, zero initial iterates and the forward grid of xbar_0 = 0.
+kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
+                      cudaStream_t st) {
+    const Geom& g = plan->geo;
+    void* stream = (void*)st;
+    KP_TRY(ensure_sched(plan, std::max(iters, 1)));
+    // measurements into sorted order
+    plan->ys_t = y_t;
+    if (y_t == KP_C64) k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>((const float2*)y_dev, (float2*)plan->d_ys, plan->d_perm, g.M, g.C);
+    else k_permute<unsigned><<<nblk(g.M, 256), 256, 0, st>>>((const unsigned*)y_dev, (unsigned*)plan->d_ys, plan->d_perm, g.M, g.C);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    // preconditioner
+    const float* pu = p_dev;
+    if (!pu) {
+        KP_TRY(kp_make_preconditioner(plan, 1, plan->d_puser, stream));
+        pu = plan->d_puser;
+    }
+    k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(pu, plan->d_ps, plan->d_perm, g.M, g.C);
+    KP_LAUNCH_CHECK();
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag, 0, 8 * sizeof(int), st));
+    {
+        static const int init = 0x7f7fffff;
+        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_flag + 4, &init, sizeof(int), cudaMemcpyHostToDevice, st));
+        const int64_t CM = (int64_t)g.C * g.M;
+        k_pmin<<<(unsigned)std::min<int64_t>(nblk(CM, 256), 1216), 256, 0, st>>>(plan->d_ps, CM, plan->d_flag + 4, plan->d_flag + 5);
+        KP_LAUNCH_CHECK();
+    }
+    plan->launches += 2;
+    // lambda_max(P A A^H)
+    if (lmax > 0) {
+        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_schedd, &lmax, sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+        KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st));
+        plan->launches += 1;
+        KP_TRY(power_method(plan, plan->d_ps, 30, st));
+    }
+    k_schedule<<<1, 1, 0, st>>>(plan->d_schedd, plan->d_flag + 4, std::max(iters, 1), plan->d_sched, plan->d_flag + 6);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    // x0 = xbar0 = 0, u0 = 0
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_x, 0, g.N * sizeof(float2), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
+    // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
+    return KP_OK;
+}
+
+kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st) { return issue_iteration(p, reg, lambda, st); }
+
 }  // namespace kp
 
 using namespace kp;
@@ -344,48 +398,7 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
     if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
     const Geom& g = plan->geo;
-    KP_TRY(ensure_sched(plan, std::max(iters, 1)));
-    // measurements into sorted order
-    plan->ys_t = y_t;
-    if (y_t == KP_C64) k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>((const float2*)y_dev, (float2*)plan->d_ys, plan->d_perm, g.M, g.C);
-    else k_permute<unsigned><<<nblk(g.M, 256), 256, 0, st>>>((const unsigned*)y_dev, (unsigned*)plan->d_ys, plan->d_perm, g.M, g.C);
-    KP_LAUNCH_CHECK();
-    plan->launches += 1;
-    // preconditioner
-    const float* pu = p_dev;
-    if (!pu) {
-        KP_TRY(kp_make_preconditioner(plan, 1, plan->d_puser, stream));
-        pu = plan->d_puser;
-    }
-    k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(pu, plan->d_ps, plan->d_perm, g.M, g.C);
-    KP_LAUNCH_CHECK();
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag, 0, 8 * sizeof(int), st));
-    {
-        static const int init = 0x7f7fffff;
-        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_flag + 4, &init, sizeof(int), cudaMemcpyHostToDevice, st));
-        const int64_t CM = (int64_t)g.C * g.M;
-        k_pmin<<<(unsigned)std::min<int64_t>(nblk(CM, 256), 1216), 256, 0, st>>>(plan->d_ps, CM, plan->d_flag + 4, plan->d_flag + 5);
-        KP_LAUNCH_CHECK();
-    }
-    plan->launches += 2;
-    // lambda_max(P A A^H)
-    if (lmax > 0) {
-        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_schedd, &lmax, sizeof(double), cudaMemcpyHostToDevice, st));
-    } else {
-        KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st));
-        plan->launches += 1;
-        KP_TRY(power_method(plan, plan->d_ps, 30, st));
-    }
-    k_schedule<<<1, 1, 0, st>>>(plan->d_schedd, plan->d_flag + 4, std::max(iters, 1), plan->d_sched, plan->d_flag + 6);
-    KP_LAUNCH_CHECK();
-    plan->launches += 1;
-    // x0 = xbar0 = 0, u0 = 0
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_x, 0, g.N * sizeof(float2), st));
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
-    // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
+    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st));
     kp_status status = KP_OK;
     double F0 = 0, F = NAN;
     double phase_ms[PH_N] = {0};

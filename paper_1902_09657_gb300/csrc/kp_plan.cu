@@ -370,7 +370,7 @@ kp_status plan_destroy_internal(kp_plan p) {
     if (p->fft_ok) cufftDestroy(p->fft);
     void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
                     p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
-                    p->d_grid2, p->d_gridF, p->d_bar,
+                    p->d_grid2, p->d_gridF, p->d_bar, p->d_tape, p->d_bk,
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
                     p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter};
     for (void* b : bufs)
