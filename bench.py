@@ -38,13 +38,19 @@ METRIC = "PDHG iterations/s, whole reconstruction (bin-sort + MC preconditioner 
 
 
 def parse():
+    return parse_args_list(None)
+
+
+def parse_args_list(argv):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip roofline/e2e/time-to-accuracy extras")
-    return ap.parse_args()
+    ap.add_argument("--no-side-workloads", action="store_true",
+                    help="skip the 64-case batch, 3D UTE gridding and unrolled-gradient side measurements")
+    return ap.parse_args(argv)
 
 
 def workload_config(w):
@@ -107,6 +113,23 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- multi-rank
+def max_over_ranks(total_ms, world, device="cpu"):
+    """Slowest rank's timed-region length (every rank runs its own replica: weak scaling)."""
+    if world == 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, steps, iters, total_ms):
+    """PDHG iterations per second summed over all ranks' replicas, timed by the slowest."""
+    return world * steps * iters / (total_ms / 1e3)
 
 
 # ----------------------------------------------------------------------------- oracle arm
@@ -233,12 +256,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ck = clocks.stop()
     launches = plan.launch_count() - launches0
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * w.iters / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = whole_job_value(world, args.steps, w.iters, total_ms)
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -320,12 +339,132 @@ def gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stre
     out["time_to_1e-3"] = {"iters": kk, "ms_solve_only": None if kk is None else kk * per_it,
                            "ms_with_setup": None if kk is None else setup_ms + kk * per_it,
                            "F_star": Fstar, "F_star_source": "min of a 400-iteration float32 GPU run"}
+    if not args.no_side_workloads:
+        for key, fn in (("batched_64", side_batched), ("gridding_3d", side_gridding_3d),
+                        ("unrolled_grad", side_unrolled)):
+            try:
+                out[key] = fn(dev, stream, flush)
+            except Exception as e:  # reported, never hidden
+                out[key] = {"error": repr(e)}
+            torch.cuda.empty_cache()
     # --- CPU oracle baseline (bounded sample)
     try:
         out["cpu_baseline"] = {k2: v for k2, v in oracle_sample(w).items() if k2 != "est_step_s"}
     except Exception as e:  # pragma: no cover
         out["cpu_baseline"] = {"error": repr(e)}
     return out
+
+
+def _timed(fn, stream, flush, reps):
+    """Mean device time (ms) of fn() over reps runs, L2 flushed before each."""
+    import torch
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def _measure_y(plan, x, gen):
+    import torch
+    y = plan.sense_forward(x)
+    n = torch.randn(y.shape, dtype=torch.complex64, device=y.device, generator=gen)
+    return (y + 0.01 * y.abs().max() * n).contiguous()
+
+
+def side_batched(dev, stream, flush, n_cases=64, iters=20):
+    """64 uneven cases (96..320 image, 4..32 coils, radial/spiral, l2/l1): one kp_batch solve
+    (per-case MC preconditioner + 30 power iterations, then `iters` graph-replayed iterations of
+    all cases at once) against the same cases solved one after another."""
+    import torch
+    from paper_1902_09657_gb300.api import Batch, Plan
+    gen = torch.Generator(device=dev).manual_seed(11)
+    cases = synth.batched_cases(n_cases)
+    plans, ys, lams, regs = [], [], [], []
+    samples = 0
+    for w in cases:
+        traj = torch.from_numpy(w.traj()).to(dev)
+        plan = Plan(w.img_shape, w.ncoils, traj.shape[0], oversamp=w.oversamp, wavelet_levels=w.wavelet_levels,
+                    device=dev)
+        plan.set_trajectory(traj).set_maps(torch.from_numpy(w.maps()).to(dev))
+        y = _measure_y(plan, torch.from_numpy(w.phantom()).to(dev), gen)
+        lam = w.lam_rel * (float(plan.sense_adjoint(y).abs().max()) if w.reg == "l1_wavelet" else 1.0)
+        plans.append(plan)
+        ys.append(y)
+        lams.append(lam)
+        regs.append(w.reg)
+        samples += w.ncoils * traj.shape[0]
+    batch = Batch(plans)
+    batch.solve(ys, None, regs, lams, iters)          # captures the all-case graph
+    t_batch = _timed(lambda: batch.solve(ys, None, regs, lams, iters), stream, flush, 3)
+
+    def sequential():
+        for pl, y, r, lm in zip(plans, ys, regs, lams):
+            pl.pdhg_solve(y, None, r, lm, iters)
+    sequential()
+    t_seq = _timed(sequential, stream, flush, 3)
+    batch.close()
+    for pl in plans:
+        pl.close()
+    return {"cases": n_cases, "iters": iters, "coil_samples": int(samples),
+            "batched_ms": t_batch, "batched_cases_per_s": n_cases / (t_batch / 1e3),
+            "sequential_ms": t_seq, "sequential_cases_per_s": n_cases / (t_seq / 1e3),
+            "what": "whole reconstructions (MC preconditioner, 30 power its, PDHG its) per second"}
+
+
+def side_gridding_3d(dev, stream, flush):
+    """3D UTE operator pair (192^3 image, 8 coils, 24000 spokes x 256): forward and adjoint
+    NUFFT times and interpolation / spreading rates."""
+    import torch
+    from paper_1902_09657_gb300.api import Plan
+    w = synth.workload("ute3d_192")
+    traj = torch.from_numpy(w.traj()).to(dev)
+    M, C = traj.shape[0], w.ncoils
+    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, device=dev)
+    plan.set_trajectory(traj).set_maps(torch.from_numpy(w.maps()).to(dev))
+    x = torch.from_numpy(w.phantom()).to(dev)
+    y = plan.sense_forward(x)
+    xo = torch.empty_like(x)
+    for _ in range(3):
+        plan.sense_forward(x, out=y)
+        plan.sense_adjoint(y, out=xo)
+    t_f = _timed(lambda: plan.sense_forward(x, out=y), stream, flush, 5)
+    t_a = _timed(lambda: plan.sense_adjoint(y, out=xo), stream, flush, 5)
+    plan.close()
+    return {"image": list(w.img_shape), "coils": C, "samples": M, "forward_ms": t_f, "adjoint_ms": t_a,
+            "forward_coil_samples_per_s": C * M / (t_f / 1e3), "adjoint_coil_samples_per_s": C * M / (t_a / 1e3)}
+
+
+def side_unrolled(dev, stream, flush):
+    """Differentiable unrolled l2 PDHG (256^2 spiral, 16 coils, 16 x 4096, 10 iterations):
+    forward with per-iteration checkpoints, and the reverse sweep giving dL/dy, dL/dlambda and
+    the trajectory gradient."""
+    import torch
+    from paper_1902_09657_gb300.api import Plan
+    w = synth.workload("spiral2d_256_unrolled")
+    traj = torch.from_numpy(w.traj()).to(dev)
+    M, C = traj.shape[0], w.ncoils
+    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, device=dev)
+    plan.set_trajectory(traj).set_maps(torch.from_numpy(w.maps()).to(dev))
+    gen = torch.Generator(device=dev).manual_seed(5)
+    y = _measure_y(plan, torch.from_numpy(w.phantom()).to(dev), gen)
+    p = plan.make_preconditioner(True)
+    L = plan.max_eig(p, iters=30)
+    gx = torch.randn(w.img_shape, dtype=torch.complex64, device=dev, generator=gen)
+    for _ in range(3):
+        plan.unrolled_forward(y, p, w.lam_rel, w.iters, L)
+        plan.unrolled_backward(gx)
+    t_f = _timed(lambda: plan.unrolled_forward(y, p, w.lam_rel, w.iters, L), stream, flush, 5)
+    t_b = _timed(lambda: plan.unrolled_backward(gx), stream, flush, 5)
+    plan.close()
+    return {"iters": w.iters, "forward_ms": t_f, "backward_ms": t_b,
+            "backward_outputs": "dL/dy, dL/dlambda, dL/dtraj"}
 
 
 def main():

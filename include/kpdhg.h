@@ -222,6 +222,31 @@ kp_status kp_plan_launch_count(kp_plan plan, int64_t* count);
 kp_status kp_sense_adjoint_noalloc(const kp_params* params, const float* traj_dev, const void* maps_dev,
                                    const void* y_dev, void* x_dev, void* stream);
 
+/* Batched reconstruction of independent cases (the paper solves one problem at a time; a
+ * batch is many Sec. 4.1 solves sharing the GPU).  A batch refers to `ncases` existing plans
+ * (each with its own sizes, trajectory and maps; the plans stay owned by the caller, must
+ * outlive the batch, and must not be used by another call while a batch solve runs).
+ * Errors: KP_EINVAL (null pointer, ncases < 1), KP_ECUDA. */
+typedef struct kp_batch_s* kp_batch;
+kp_status kp_batch_create(kp_batch* out, kp_plan* plans, int ncases);
+
+/* Runs `iters` iterations of Sec. 4.1 on every case of the batch.  Arrays of length ncases:
+ * y_devs[i] ([C_i][M_i] of type y_types[i]), p_devs[i] (float32 [C_i][M_i], or NULL entries /
+ * a NULL array for the multi-channel preconditioner), regs[i], lambdas[i], x_devs[i]
+ * (complex64 [N_i] output).  Start, step sizes and power method follow kp_pdhg_solve per case.
+ * Set-up runs case by case; the iteration of all cases is one CUDA graph (captured on the
+ * first call and again when regs, lambdas or y types change) in which every case runs on its
+ * own forked stream, so the cases overlap on the GPU; the graph is replayed `iters` times on
+ * `stream`.  Each case's result equals that case's kp_pdhg_solve up to float32 rounding order.
+ * Synchronous.  Errors: KP_EINVAL (iters < 0, l1 case without wavelet levels, non-positive p
+ * or lambda_max of some case), KP_ECUDA, KP_ECUFFT. */
+kp_status kp_batch_solve(kp_batch batch, const void* const* y_devs, const kp_cdtype* y_types,
+                         const float* const* p_devs, const kp_reg* regs, const float* lambdas, int iters,
+                         void* const* x_devs, void* stream);
+
+/* Frees the batch's streams, events and graph (not the plans).  Waits for the device. */
+kp_status kp_batch_destroy(kp_batch batch);
+
 /* Number of grid tiles and the longest tile's sample count after kp_plan_set_trajectory
  * (diagnostics for load balance). */
 kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_samples);

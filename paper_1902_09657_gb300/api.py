@@ -243,3 +243,52 @@ class Plan:
                      tau_last=st.tau_last, final_obj=st.final_obj,
                      phase_ms={n: st.phase_ms[i] for i, n in enumerate(L.PHASES)})
         return x, (list(tr)[: int(iters)] if trace else None), stats
+
+
+class Batch:
+    """Independent cases (one Plan each, any sizes) solved together: per-case set-up, then one
+    CUDA graph per iteration advancing every case on its own stream (kp_batch)."""
+
+    def __init__(self, plans):
+        self.lib = L.load()
+        self.plans = list(plans)
+        if not self.plans:
+            raise ValueError("a batch needs at least one plan")
+        self.device = self.plans[0].device
+        if any(p.device != self.device for p in self.plans):
+            raise ValueError("all plans of a batch must be on one device")
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p._h.value for p in self.plans])
+        self._h = ctypes.c_void_p()
+        L.check(self.lib.kp_batch_create(ctypes.byref(self._h), arr, n), "kp_batch_create")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.kp_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, ys, ps=None, regs="l2", lams=0.0, iters=30):
+        """ys: list of [C_i, M_i] device tensors; ps: list (entries may be None) or None;
+        regs / lams: one value or one per case.  Returns the list of complex64 images."""
+        n = len(self.plans)
+        if len(ys) != n:
+            raise ValueError("one y per case")
+        regs = [regs] * n if isinstance(regs, str) else list(regs)
+        lams = [lams] * n if isinstance(lams, (int, float)) else list(lams)
+        ys = [pl._dev(y, "y") for pl, y in zip(self.plans, ys)]
+        ps = [None] * n if ps is None else [pl._dev(p, "p") if p is not None else None for pl, p in zip(self.plans, ps)]
+        xs = [torch.empty(pl.img_shape, dtype=torch.complex64, device=self.device) for pl in self.plans]
+        VP = ctypes.c_void_p * n
+        st = self.lib.kp_batch_solve(
+            self._h, VP(*[y.data_ptr() for y in ys]), (ctypes.c_int * n)(*[_ctype_of(y) for y in ys]),
+            VP(*[p.data_ptr() if p is not None else None for p in ps]),
+            (ctypes.c_int * n)(*[_REG[r] for r in regs]), (ctypes.c_float * n)(*[float(v) for v in lams]),
+            int(iters), VP(*[x.data_ptr() for x in xs]), _stream(self.device))
+        L.check(st, "kp_batch_solve")
+        return xs

@@ -1,0 +1,156 @@
+// Batched reconstruction: many independent cases (each its own plan: image size, coils,
+// trajectory, maps, regulariser, lambda) solved together.  Set-up (preconditioner, power
+// method, schedule) runs per case; the PDHG iteration of every case is captured once into a
+// single CUDA graph, each case on its own forked stream, so one graph launch advances all
+// cases by one iteration and their kernels run concurrently on the GPU.  Cases use the
+// non-cooperative iteration (several cooperative grids would compete for co-residency).
+#include "kp_internal.cuh"
+
+#include <vector>
+
+struct kp_batch_s {
+    std::vector<kp_plan> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> key_reg;
+    std::vector<float> key_lam;
+    std::vector<int> key_yt;
+    std::vector<uint64_t> key_gen;   // plans' graph generations at capture
+    std::vector<int64_t> per_replay;  // kernels each case adds per graph replay
+};
+
+namespace kp {
+static void batch_drop_graph(kp_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+}  // namespace kp
+
+using namespace kp;
+
+extern "C" {
+
+kp_status kp_batch_create(kp_batch* out, kp_plan* plans, int ncases) {
+    if (!out || !plans || ncases < 1) { set_error("null argument or ncases < 1"); return KP_EINVAL; }
+    *out = nullptr;
+    kp_batch b = new (std::nothrow) kp_batch_s();
+    if (!b) { set_error("host allocation failed"); return KP_ENOMEM; }
+    for (int i = 0; i < ncases; ++i) {
+        if (!plans[i]) { delete b; set_error("null plan in batch"); return KP_EINVAL; }
+        b->plans.push_back(plans[i]);
+    }
+    b->streams.assign(ncases, nullptr);
+    b->joins.assign(ncases, nullptr);
+    kp_status s = KP_OK;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        s = KP_ECUDA;
+    for (int i = 0; s == KP_OK && i < ncases; ++i) {
+        if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) != cudaSuccess)
+            s = KP_ECUDA;
+    }
+    if (s != KP_OK) {
+        kp_batch_destroy(b);
+        set_error("stream or event creation failed");
+        return s;
+    }
+    *out = b;
+    return KP_OK;
+}
+
+kp_status kp_batch_destroy(kp_batch b) {
+    if (!b) return KP_OK;
+    cudaDeviceSynchronize();
+    batch_drop_graph(b);
+    for (auto s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : b->joins)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return KP_OK;
+}
+
+kp_status kp_batch_solve(kp_batch b, const void* const* y_devs, const kp_cdtype* y_types, const float* const* p_devs,
+                         const kp_reg* regs, const float* lambdas, int iters, void* const* x_devs, void* stream) {
+    if (!b || !y_devs || !y_types || !regs || !lambdas || !x_devs) { set_error("null argument"); return KP_EINVAL; }
+    if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)b->plans.size();
+    for (int i = 0; i < n; ++i) {
+        kp_plan p = b->plans[i];
+        if (!p->traj_set || !p->maps_set) { set_error("every plan needs a trajectory and maps"); return KP_EINVAL; }
+        if (regs[i] == KP_REG_L1_WAVELET && p->P.wavelet_levels < 1) { set_error("l1-wavelet case without levels"); return KP_EINVAL; }
+        KP_TRY(solve_setup(p, y_devs[i], y_types[i], p_devs ? p_devs[i] : nullptr, 0.0, std::max(iters, 1), st));
+    }
+    // (re)capture the all-case iteration graph when the regularisers, lambdas, data types or
+    // any plan's buffers (trajectory, maps, schedule length) changed
+    std::vector<int> kr(regs, regs + n), ky(n);
+    std::vector<float> kl(lambdas, lambdas + n);
+    std::vector<uint64_t> kg(n);
+    for (int i = 0; i < n; ++i) {
+        ky[i] = (int)y_types[i];
+        kg[i] = b->plans[i]->graph_gen;
+    }
+    if (!b->exec || kr != b->key_reg || kl != b->key_lam || ky != b->key_yt || kg != b->key_gen) {
+        batch_drop_graph(b);
+        // capture issues nothing: remember each plan's launch count and restore it afterwards;
+        // each replay then adds the kernels its part of the graph holds
+        std::vector<int64_t> before(n);
+        for (int i = 0; i < n; ++i) before[i] = b->plans[i]->launches;
+        KP_TRY_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        kp_status s = KP_OK;
+        if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) s = KP_ECUDA;
+        for (int i = 0; s == KP_OK && i < n; ++i) {
+            if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) { s = KP_ECUDA; break; }
+            s = pdhg_iteration_concurrent(b->plans[i], (int)regs[i], lambdas[i], b->streams[i]);
+            if (s == KP_OK && (cudaEventRecord(b->joins[i], b->streams[i]) != cudaSuccess ||
+                               cudaStreamWaitEvent(b->cap, b->joins[i], 0) != cudaSuccess))
+                s = KP_ECUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+        b->per_replay.assign(n, 0);
+        for (int i = 0; i < n; ++i) {
+            b->per_replay[i] = b->plans[i]->launches - before[i];
+            b->plans[i]->launches = before[i];
+        }
+        if (s != KP_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+        KP_TRY_CUDA(e);
+        b->graph = graph;
+        KP_TRY_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+        b->key_reg = kr;
+        b->key_lam = kl;
+        b->key_yt = ky;
+        b->key_gen = kg;
+    }
+    for (int k = 0; k < iters; ++k) {
+        KP_TRY_CUDA(cudaGraphLaunch(b->exec, st));
+        for (int i = 0; i < n; ++i) b->plans[i]->launches += b->per_replay[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        kp_plan p = b->plans[i];
+        KP_TRY_CUDA(cudaMemcpyAsync(x_devs[i], p->d_x, p->geo.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    }
+    std::vector<int> flags(8 * (size_t)n);
+    for (int i = 0; i < n; ++i)
+        KP_TRY_CUDA(cudaMemcpyAsync(&flags[8 * (size_t)i], b->plans[i]->d_flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+        if (flags[8 * (size_t)i + 5] != 0 || flags[8 * (size_t)i + 6] != 0) {
+            set_error("case " + std::to_string(i) + ": preconditioner or lambda_max not positive and finite");
+            return KP_EINVAL;
+        }
+    }
+    return KP_OK;
+}
+
+}  // extern "C"

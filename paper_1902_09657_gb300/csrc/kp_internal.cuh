@@ -184,6 +184,7 @@ struct kp_plan_s {
     bool traj_set = false;
     bool maps_set = false;
     kp_cdtype maps_t = KP_C64;       // storage type of d_maps
+    uint64_t graph_gen = 0;          // bumped whenever captured graphs become stale
 
     // trajectory (sorted by tile)
     float* d_t = nullptr;            // [D][M] grid coordinates t = f * g/n, sorted order
@@ -301,6 +302,8 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
                       cudaStream_t st);
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st);

@@ -221,6 +221,7 @@ static void drop_graph(Graph& gr) {
 
 void drop_graphs(kp_plan p) {
     for (auto& gr : p->graphs) drop_graph(gr);
+    p->graph_gen++;
 }
 
 // Capture one iteration on the plan's private stream; replay it on the caller's stream.
@@ -282,7 +283,7 @@ static kp_status ensure_sched(kp_plan p, int iters) {
     const int cap = std::max(iters, 128);
     KP_TRY_CUDA(cudaMalloc(&p->d_sched, 3 * (size_t)cap * sizeof(float)));
     p->sched_cap = cap;
-    for (auto& gr : p->graphs) drop_graph(gr);   // graphs bake the schedule pointer in
+    drop_graphs(p);   // graphs bake the schedule pointer in
     return KP_OK;
 }
 
@@ -339,6 +340,22 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
 }
 
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st) { return issue_iteration(p, reg, lambda, st); }
+
+// The same iteration without the cooperative primal kernel (for several plans running
+// concurrently): adjoint + primal step kernel, wavelet level kernels (threshold, extrapolation
+// and the next pre-step fused into them) or the pre-step kernel for l2, counter kernel.
+kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st) {
+    KP_TRY(fft_forward_only(p, st));
+    KP_TRY(interp_dual_only(p, st));
+    KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st));
+    KP_TRY(adjoint_primal(p, reg, lambda, st));
+    if (reg == KP_REG_L1_WAVELET) KP_TRY(wavelet_prox_levels(p, lambda, st));
+    else KP_TRY(pre_only(p, p->d_xbar, st));
+    k_advance<<<1, 1, 0, st>>>(p->d_iter);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    return KP_OK;
+}
 
 }  // namespace kp
 

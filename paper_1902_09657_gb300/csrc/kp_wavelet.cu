@@ -324,7 +324,29 @@ __global__ void __launch_bounds__(256) k_dwt_inv_level(LevelArgs a) {
     inv_level_tile<D, T, float2>(a, blockIdx.x, sm);
 }
 
+template <int D, int T, typename MT>
+__global__ void __launch_bounds__(256) k_dwt_inv_level_t(LevelArgs a) {
+    extern __shared__ float2 sm[];
+    inv_level_tile<D, T, MT>(a, blockIdx.x, sm);
+}
+
 static inline int wt_tile(int D) { return D == 2 ? 16 : 8; }
+
+template <int D, int T, typename MT>
+static kp_status launch_inv_t(const LevelArgs& a, int nblocks, cudaStream_t st) {
+    constexpr int E = T + 4;
+    size_t tot = 1, tot1 = 1;
+    for (int d = 0; d < D; ++d) { tot *= 2 * E; tot1 *= (d == D - 1 ? 2 * T : 2 * E); }
+    const size_t smem = (tot + tot1) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level_t<D, T, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    k_dwt_inv_level_t<D, T, MT><<<nblocks, 256, smem, st>>>(a);
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
 
 static View full_view(float2* p, const Geom& g) {
     View v{};
@@ -432,6 +454,77 @@ static kp_status wavelet_inverse(kp_plan p, const float2* coef, float2* out, cud
         a.iter = p->d_iter;
         if (g.D == 2) KP_TRY((launch_inv<2, 16>(a, nb, st)));
         else KP_TRY((launch_inv<3, 8>(a, nb, st)));
+        p->launches += 1;
+    }
+    return KP_OK;
+}
+
+// l1-wavelet prox of the PDHG primal step with the standalone level kernels (for runs in
+// which several plans share the GPU concurrently, where a cooperative grid-wide kernel per
+// plan is not used): z -> thresholded coefficients -> x_new, xbar and the forward grid.
+kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const int L = p->P.wavelet_levels;
+    const int T = wt_tile(g.D);
+    float2* ll[2] = {p->d_wl0, p->d_wl1};
+    for (int lev = 0; lev < L; ++lev) {
+        LevelArgs a{};
+        int bdim[MAXD], hdim[MAXD];
+        int nb = 1;
+        for (int d = 0; d < g.D; ++d) {
+            bdim[d] = g.n[d] >> lev;
+            hdim[d] = bdim[d] / 2;
+            a.b[d] = bdim[d];
+            a.tiles[d] = (hdim[d] + T - 1) / T;
+            nb *= a.tiles[d];
+        }
+        a.src = lev == 0 ? full_view(p->d_z, g) : dense_view(ll[(lev - 1) & 1], bdim, g.D);
+        a.dst = dense_view(ll[lev & 1], hdim, g.D);
+        a.coef = full_view(p->d_w, g);
+        a.lev_last = lev == L - 1;
+        a.sched = p->d_sched;
+        a.iter = p->d_iter;
+        a.lambda = lambda;
+        if (g.D == 2) KP_TRY((launch_fwd<2, 16>(a, nb, st)));
+        else KP_TRY((launch_fwd<3, 8>(a, nb, st)));
+        p->launches += 1;
+    }
+    for (int lev = L - 1; lev >= 0; --lev) {
+        LevelArgs a{};
+        int bdim[MAXD], hdim[MAXD];
+        int nb = 1;
+        for (int d = 0; d < g.D; ++d) {
+            bdim[d] = g.n[d] >> lev;
+            hdim[d] = bdim[d] / 2;
+            a.b[d] = bdim[d];
+            a.tiles[d] = (bdim[d] + 2 * T - 1) / (2 * T);
+            nb *= a.tiles[d];
+        }
+        a.src = dense_view(ll[lev & 1], hdim, g.D);
+        a.coef = full_view(p->d_w, g);
+        a.dst = lev == 0 ? full_view(p->d_x, g) : dense_view(ll[(lev - 1) & 1], bdim, g.D);
+        a.lev_last = lev == L - 1;
+        a.lev_first = lev == 0;
+        a.sched = p->d_sched;
+        a.iter = p->d_iter;
+        if (lev == 0) {
+            a.x = p->d_x;
+            a.xbar = p->d_xbar;
+            a.fgrid = p->d_grid;
+            a.maps = p->d_maps;
+            a.apod = p->d_apod;
+            a.geo = g;
+        }
+        const kp_cdtype mt = p->maps_t;
+        if (g.D == 2) {
+            if (mt == KP_C64) KP_TRY((launch_inv_t<2, 16, float2>(a, nb, st)));
+            else if (mt == KP_C32_BF16) KP_TRY((launch_inv_t<2, 16, __nv_bfloat162>(a, nb, st)));
+            else KP_TRY((launch_inv_t<2, 16, __half2>(a, nb, st)));
+        } else {
+            if (mt == KP_C64) KP_TRY((launch_inv_t<3, 8, float2>(a, nb, st)));
+            else if (mt == KP_C32_BF16) KP_TRY((launch_inv_t<3, 8, __nv_bfloat162>(a, nb, st)));
+            else KP_TRY((launch_inv_t<3, 8, __half2>(a, nb, st)));
+        }
         p->launches += 1;
     }
     return KP_OK;

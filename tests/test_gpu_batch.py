@@ -1,0 +1,149 @@
+"""Batched reconstruction (kp_batch): many independent cases, each with its own image size,
+coil count, trajectory, regulariser and lambda, advanced together by one CUDA graph per
+Sec. 4.1 iteration.  Each case must match (a) the float64 oracle's PDHG from the same p and
+lambda_max and (b) the single-case solver kp_pdhg_solve on the same plan."""
+import numpy as np
+import pytest
+
+from oracle import nufft as onf, precond as opc, solvers as osv
+from tests.gpu_util import need_gpu, rel, simulate, to_dev, make_plan
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(i, n, C, kind, spokes, reg, levels):
+    if kind == "radial":
+        targs = dict(n_spokes=spokes, n_readout=2 * n, kmax=n / 2.0)
+    else:
+        targs = dict(n_interleaves=spokes, n_samples=2 * n, kmax=n / 2.0)
+    return synth.Workload(f"b{i}", (n, n), C, 1.25, 4, reg, 1e-3, 20, levels, kind, targs, seed=500 + i)
+
+
+# uneven sizes, both trajectory kinds, both regularisers; 48 has a ragged tile, 40 needs a
+# different tile size than 64
+CASES = [(0, 64, 4, "spiral", 6, "l1_wavelet", 3), (1, 48, 3, "radial", 40, "l2", 0),
+         (2, 40, 5, "radial", 24, "l1_wavelet", 2), (3, 32, 2, "spiral", 4, "l2", 0)]
+
+
+def _setup(cases):
+    plans, ys, ps, Ls, lams, oracle_in = [], [], [], [], [], []
+    for spec in cases:
+        w = _case(*spec)
+        x, maps, traj = w.phantom(), w.maps(), w.traj()
+        y = simulate(w, x, maps, traj)
+        m = maps.astype(np.complex128)
+        A = lambda v, m=m, traj=traj: onf.nufft_forward(v, m, traj, 1.25, 4)
+        AH = lambda u, m=m, traj=traj: onf.nufft_adjoint(u, m, traj, 1.25, 4)
+        p = opc.mc_precond_fast(m, traj, 1.25, 4)
+        L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+        lam = 1e-3
+        if w.reg == "l1_wavelet":
+            lam = lam * float(np.abs(AH(y.astype(np.complex128))).max())
+        plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=w.wavelet_levels)
+        plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+        plans.append(plan)
+        ys.append(y)
+        ps.append(p)
+        Ls.append(L)
+        lams.append(lam)
+        oracle_in.append((w, A, AH, x.shape))
+    return plans, ys, ps, Ls, lams, oracle_in
+
+
+def test_batch_matches_oracle_and_single_solves():
+    need_gpu()
+    from paper_1902_09657_gb300.api import Batch
+    plans, ys, ps, Ls, lams, oin = _setup(CASES)
+    iters = 40
+    regs = [c[5] for c in CASES]
+    batch = Batch(plans)
+    yd = [to_dev(y) for y in ys]
+    pd = [to_dev(p.astype(np.float32)) for p in ps]
+    xs = batch.solve(yd, pd, regs, lams, iters)
+    for i, (w, A, AH, shape) in enumerate(oin):
+        x_ref, _, _, _ = osv.pdhg(A, AH, ys[i], ps[i], shape, regs[i], lams[i], iters, Ls[i],
+                                  levels=w.wavelet_levels)
+        # the batch runs its own power method: lambda_max agrees to 1e-5, which the step sizes carry
+        assert rel(xs[i].cpu().numpy(), x_ref) < 1e-4, i
+        xg, _, st = plans[i].pdhg_solve(yd[i], pd[i], regs[i], lams[i], iters)
+        assert rel(xs[i].cpu().numpy(), xg.cpu().numpy()) < 2e-6, i
+    batch.close()
+
+
+def test_batch_graph_reuse_and_recapture():
+    """A second solve replays the cached graph (same result); a new lambda or regulariser
+    re-captures; a changed trajectory (new tiles and buffers) re-captures too."""
+    need_gpu()
+    from paper_1902_09657_gb300.api import Batch
+    cases = CASES[1:3]
+    plans, ys, ps, Ls, lams, oin = _setup(cases)
+    regs = [c[5] for c in cases]
+    batch = Batch(plans)
+    yd = [to_dev(y) for y in ys]
+    xa = batch.solve(yd, None, regs, lams, 15)
+    xb = batch.solve(yd, None, regs, lams, 15)
+    for a, b in zip(xa, xb):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+    lams2 = [2 * v for v in lams]
+    xc = batch.solve(yd, None, regs, lams2, 15)
+    for i in range(2):
+        xg, _, _ = plans[i].pdhg_solve(yd[i], None, regs[i], lams2[i], 15)
+        assert rel(xc[i].cpu().numpy(), xg.cpu().numpy()) < 2e-6
+    # new trajectory on case 0 (same sample count): the batch must not replay stale buffers
+    w = _case(*cases[0])
+    rng = np.random.default_rng(7)
+    traj2 = (w.traj() + rng.uniform(-0.3, 0.3, w.traj().shape)).clip(-w.img_shape[0] / 2, w.img_shape[0] / 2 - 1e-3)
+    plans[0].set_trajectory(to_dev(traj2.astype(np.float32)))
+    xd = batch.solve(yd, None, regs, lams, 15)
+    xg, _, _ = plans[0].pdhg_solve(yd[0], None, regs[0], lams[0], 15)
+    assert rel(xd[0].cpu().numpy(), xg.cpu().numpy()) < 2e-6
+    assert rel(xd[1].cpu().numpy(), xa[1].cpu().numpy()) < 1e-6
+    batch.close()
+
+
+def test_batch_launch_count_and_bad_inputs():
+    need_gpu()
+    from paper_1902_09657_gb300.api import Batch
+    from paper_1902_09657_gb300._lib import KpError
+    cases = CASES[:2]
+    plans, ys, ps, Ls, lams, oin = _setup(cases)
+    regs = [c[5] for c in cases]
+    batch = Batch(plans)
+    yd = [to_dev(y) for y in ys]
+    batch.solve(yd, None, regs, lams, 3)
+    before = [p.launch_count() for p in plans]
+    batch.solve(yd, None, regs, lams, 7)
+    grown = [p.launch_count() - b for p, b in zip(plans, before)]
+    assert all(g > 7 for g in grown)          # per-iteration kernels are counted on replay
+    with pytest.raises(KpError):
+        batch.solve(yd, None, ["l1_wavelet", "l1_wavelet"], lams, 3)   # case 1 has no wavelet levels
+    bad = np.ones(ps[0].shape, np.float32)
+    bad[0, 5] = 0.0
+    with pytest.raises(KpError):
+        batch.solve(yd, [to_dev(bad), None], regs, lams, 3)
+    batch.close()
+
+
+def test_batch_uneven_workload_cases():
+    """The first cases of the 64-case uneven workload (image 96..320, 4..32 coils): batched
+    results equal the per-case solver's."""
+    need_gpu()
+    from paper_1902_09657_gb300.api import Batch, Plan
+    import torch
+    cases = synth.batched_cases(6)
+    plans, yd, lams = [], [], []
+    g = torch.Generator(device="cuda").manual_seed(3)
+    for w in cases:
+        traj = w.traj()
+        plan = Plan(w.img_shape, w.ncoils, traj.shape[0], wavelet_levels=w.wavelet_levels)
+        plan.set_trajectory(to_dev(traj)).set_maps(to_dev(w.maps()))
+        y = torch.randn((w.ncoils, traj.shape[0]), dtype=torch.complex64, device="cuda", generator=g)
+        plans.append(plan)
+        yd.append(y)
+        lams.append(1e-3 * (float(plan.sense_adjoint(y).abs().max()) if w.reg == "l1_wavelet" else 1.0))
+    regs = [w.reg for w in cases]
+    xs = Batch(plans).solve(yd, None, regs, lams, 20)
+    for i in range(len(cases)):
+        xg, _, _ = plans[i].pdhg_solve(yd[i], None, regs[i], lams[i], 20)
+        assert rel(xs[i].cpu().numpy(), xg.cpu().numpy()) < 2e-6, i
