@@ -34,7 +34,15 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 WORKLOAD = "spiral2d_256"
-METRIC = "PDHG iterations/s, whole reconstruction (bin-sort + MC preconditioner + 30 power its + 100 l1-wavelet PDHG its)"
+def metric_name(w):
+    reg = "l1-wavelet" if w.reg == "l1_wavelet" else "l2"
+    return (f"PDHG iterations/s, whole reconstruction (bin-sort + MC preconditioner + 30 power its + "
+            f"{w.iters} {reg} PDHG its)")
+
+
+def lambda_for(w, ahy_max=None):
+    """l2: lambda itself; l1: lam_rel * max|A^H y|."""
+    return w.lam_rel * ahy_max if w.reg == "l1_wavelet" else w.lam_rel
 
 
 def parse():
@@ -47,6 +55,8 @@ def parse_args_list(argv):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
+                    help="timed workload (default: the 2D spiral l1-wavelet reconstruction)")
     ap.add_argument("--no-extras", action="store_true", help="skip roofline/e2e/time-to-accuracy extras")
     ap.add_argument("--no-side-workloads", action="store_true",
                     help="skip the 64-case batch, 3D UTE gridding and unrolled-gradient side measurements")
@@ -54,12 +64,20 @@ def parse_args_list(argv):
 
 
 def workload_config(w):
+    ta = w.traj_args
+    if w.traj_kind == "spiral":
+        traj = f"{ta['n_interleaves']}x{ta['n_samples']} spiral samples"
+        m = ta["n_interleaves"] * ta["n_samples"]
+    else:
+        traj = f"{ta['n_spokes']}x{ta['n_readout']} {w.traj_kind} samples"
+        m = ta["n_spokes"] * ta["n_readout"]
+    shape = "x".join(str(n) for n in w.img_shape)
+    reg = ("l1 lambda=1e-3*max|A^H y|, db4 %d levels" % w.wavelet_levels if w.reg == "l1_wavelet"
+           else "l2 lambda=%g" % w.lam_rel)
     return {
-        "workload": f"{w.name}: {w.img_shape[0]}x{w.img_shape[1]} image, {w.ncoils} coils, "
-                    f"{w.traj_args['n_interleaves']}x{w.traj_args['n_samples']} spiral samples, alpha {w.oversamp}, "
-                    f"KB W{w.width}, db4 {w.wavelet_levels} levels, l1 lambda=1e-3*max|A^H y|, {w.iters} iterations",
-        "image": list(w.img_shape), "coils": w.ncoils,
-        "samples": int(w.traj_args["n_interleaves"] * w.traj_args["n_samples"]),
+        "workload": f"{w.name}: {shape} image, {w.ncoils} coils, {traj}, alpha {w.oversamp}, KB W{w.width}, "
+                    f"{reg}, {w.iters} iterations",
+        "image": list(w.img_shape), "coils": w.ncoils, "samples": int(m),
         "iters": w.iters, "power_iters": 30, "preconditioner": "multi-channel",
         "l2_between_steps": "flushed (256 MiB write)",
     }
@@ -148,7 +166,7 @@ def oracle_sample(w, n_pdhg=3):
     t0 = time.perf_counter()
     L, _ = osv.power_method(A, AH, p, x.shape, iters=1)
     t_pow = time.perf_counter() - t0
-    lam = w.lam_rel * float(np.abs(AH(y)).max())
+    lam = lambda_for(w, ahy_max=float(np.abs(AH(y)).max()))
     t0 = time.perf_counter()
     osv.pdhg(A, AH, y, p, x.shape, w.reg, lam, n_pdhg, L, levels=w.wavelet_levels)
     t_it = (time.perf_counter() - t0) / n_pdhg
@@ -161,7 +179,7 @@ def oracle_sample(w, n_pdhg=3):
 
 
 def run_reference(args, rank, world):
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     if rank != 0:
         return
     for _ in range(args.warmup):
@@ -172,7 +190,7 @@ def run_reference(args, rank, world):
         vals.append(s["value"])
         ests.append(s["est_step_s"])
     v = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_name(w), "value": v, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(ests),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w),
@@ -183,14 +201,15 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def algorithmic_bytes(w, C, M, N, G):
+def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
     """Algorithmic HBM bytes per PDHG iteration of each phase (each array touched once)."""
-    c8, m = 8, C * M
+    c8, m, D = 8, C * M, len(w.img_shape)
     return {
-        "fwd_pre": N * 8 + C * N * 8 + C * G * 8,              # x, maps in; whole grid out
-        "interp_dual": C * G * 8 + m * (8 + 4 + 8 + 8) + M * 2 * 4,   # grid, y, p, u in/out, traj
-        "spread": m * c8 + M * 2 * 4 + C * G * 8,              # u, traj in; whole grid out
-        "adj_primal": C * N * 8 + C * N * 8 + N * 8 * 3,       # cropped grid, maps, x in/out, z out
+        "fwd_pre": N * 8 + C * N * maps_bytes + C * G * 8,     # x, maps in; whole grid out
+        "interp_dual": C * G * 8 + m * (8 + 4 + 8 + 8) + M * D * 4,   # grid, y, p, u in/out, traj
+        "spread": m * c8 + M * D * 4 + C * G * 8,              # u, traj in; whole grid out
+        "adj_primal": C * N * 8 + C * N * maps_bytes + N * 8 * 3,   # cropped grid, maps, x in/out, z out
+        "fft_fwd": 2 * C * G * 8, "fft_inv": 2 * C * G * 8,     # one read + one write pass
         "dwt_fwd": 2 * 2 * N * 8, "dwt_inv": 2 * 2 * N * 8, "soft": 2 * N * 8, "extrap": 4 * N * 8,
     }
 
@@ -203,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
     _build.build()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     traj_h = torch.from_numpy(w.traj()).pin_memory()
     x_true = torch.from_numpy(w.phantom())
     maps_h = torch.from_numpy(w.maps()).pin_memory()
@@ -216,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
     y_d = plan.sense_forward(x_true.to(dev))
     noise = torch.from_numpy(w.noise().astype(np.complex64)).to(dev)
     y_d = (y_d + 0.01 * y_d.abs().max() * noise).contiguous()
-    lam = w.lam_rel * float(plan.sense_adjoint(y_d).abs().max())
+    lam = lambda_for(w, ahy_max=float(plan.sense_adjoint(y_d).abs().max()))
     y_h = y_d.cpu().pin_memory()
     G = 1
     for n in w.img_shape:
@@ -265,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
                             C, M, N, G, args)
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric_name(w), "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(w), "clocks": ck, "gpu_launches": int(launches)}
@@ -318,7 +337,7 @@ def gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stre
     ph = {n: v / w.iters for n, v in st["phase_ms"].items() if v > 0}
     out["phase_ms_per_iter"] = {n: round(v, 5) for n, v in ph.items()}
     ab = algorithmic_bytes(w, C, M, N, G)
-    own = {n: v for n, v in ph.items() if n in ab}
+    own = {n: v for n, v in ph.items() if n in ab and not n.startswith("fft")}
     dom = max(own, key=own.get)
     peaks = {}
     try:
@@ -403,6 +422,7 @@ def side_batched(dev, stream, flush, n_cases=64, iters=20):
     batch = Batch(plans)
     batch.solve(ys, None, regs, lams, iters)          # captures the all-case graph
     t_batch = _timed(lambda: batch.solve(ys, None, regs, lams, iters), stream, flush, 3)
+    t_setup = _timed(lambda: batch.solve(ys, None, regs, lams, 0), stream, flush, 3)
 
     def sequential():
         for pl, y, r, lm in zip(plans, ys, regs, lams):
@@ -414,31 +434,59 @@ def side_batched(dev, stream, flush, n_cases=64, iters=20):
         pl.close()
     return {"cases": n_cases, "iters": iters, "coil_samples": int(samples),
             "batched_ms": t_batch, "batched_cases_per_s": n_cases / (t_batch / 1e3),
+            "batched_setup_ms": t_setup, "batched_iteration_ms": (t_batch - t_setup) / iters,
             "sequential_ms": t_seq, "sequential_cases_per_s": n_cases / (t_seq / 1e3),
             "what": "whole reconstructions (MC preconditioner, 30 power its, PDHG its) per second"}
 
 
 def side_gridding_3d(dev, stream, flush):
-    """3D UTE operator pair (192^3 image, 8 coils, 24000 spokes x 256): forward and adjoint
-    NUFFT times and interpolation / spreading rates."""
+    """3D UTE workload (192^3 image, 8 coils, 24000 spokes x 256, FP16 coil maps, db4 3 levels):
+    forward / adjoint operator times, the MC preconditioner's construction time, 30 graph-
+    replayed l1-wavelet PDHG iterations, and a per-phase profile with each phase's achieved
+    bandwidth for its algorithmic bytes (the HBM-scale case: grids of 885 MB)."""
     import torch
-    from paper_1902_09657_gb300.api import Plan
+    from paper_1902_09657_gb300.api import Plan, to_storage
     w = synth.workload("ute3d_192")
     traj = torch.from_numpy(w.traj()).to(dev)
     M, C = traj.shape[0], w.ncoils
-    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, device=dev)
-    plan.set_trajectory(traj).set_maps(torch.from_numpy(w.maps()).to(dev))
+    N = int(np.prod(w.img_shape))
+    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, wavelet_levels=w.wavelet_levels, device=dev)
+    plan.set_trajectory(traj).set_maps(to_storage(torch.from_numpy(w.maps()).to(dev), "fp16"))
     x = torch.from_numpy(w.phantom()).to(dev)
-    y = plan.sense_forward(x)
+    gen = torch.Generator(device=dev).manual_seed(3)
+    y = _measure_y(plan, x, gen)
+    yo = torch.empty_like(y)
     xo = torch.empty_like(x)
     for _ in range(3):
-        plan.sense_forward(x, out=y)
+        plan.sense_forward(x, out=yo)
         plan.sense_adjoint(y, out=xo)
-    t_f = _timed(lambda: plan.sense_forward(x, out=y), stream, flush, 5)
+    t_f = _timed(lambda: plan.sense_forward(x, out=yo), stream, flush, 5)
     t_a = _timed(lambda: plan.sense_adjoint(y, out=xo), stream, flush, 5)
+    p = plan.make_preconditioner(True)
+    t_p = _timed(lambda: plan.make_preconditioner(True, out=p), stream, flush, 3)
+    L = plan.max_eig(p, iters=30)
+    lam = lambda_for(w, ahy_max=float(plan.sense_adjoint(y).abs().max()))
+    plan.pdhg_solve(y, p, w.reg, lam, w.iters, lmax=L)
+    t_s = _timed(lambda: plan.pdhg_solve(y, p, w.reg, lam, w.iters, lmax=L), stream, flush, 3)
+    plan.set_profiling(True)
+    k = 5
+    _, _, st = plan.pdhg_solve(y, p, w.reg, lam, k, lmax=L)
+    plan.set_profiling(False)
+    G = 1
+    for n in w.img_shape:
+        g = math.ceil(w.oversamp * n - 1e-9)
+        G *= g + (g % 2)
+    ab = algorithmic_bytes(w, C, M, N, G, maps_bytes=4)
+    ph = {n: v / k for n, v in st["phase_ms"].items() if v > 0}
+    rates = {n: {"ms": round(v, 4), "GB_per_s": round(ab[n] / (v * 1e-3) / 1e9, 1)} if n in ab else {"ms": round(v, 4)}
+             for n, v in ph.items()}
     plan.close()
-    return {"image": list(w.img_shape), "coils": C, "samples": M, "forward_ms": t_f, "adjoint_ms": t_a,
-            "forward_coil_samples_per_s": C * M / (t_f / 1e3), "adjoint_coil_samples_per_s": C * M / (t_a / 1e3)}
+    return {"image": list(w.img_shape), "coils": C, "samples": M, "maps": "fp16",
+            "forward_ms": t_f, "adjoint_ms": t_a,
+            "forward_coil_samples_per_s": C * M / (t_f / 1e3), "adjoint_coil_samples_per_s": C * M / (t_a / 1e3),
+            "make_preconditioner_ms": t_p, "lmax": L,
+            "pdhg_iters_per_s": w.iters / (t_s / 1e3), "pdhg_ms": t_s, "iters": w.iters,
+            "phase_per_iter": rates}
 
 
 def side_unrolled(dev, stream, flush):

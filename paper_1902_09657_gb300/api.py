@@ -127,6 +127,13 @@ class Plan:
         L.check(self.lib.kp_plan_tile_stats(self._h, ctypes.byref(nt), ctypes.byref(mx)), "kp_plan_tile_stats")
         return nt.value, mx.value
 
+    def spread_config(self):
+        """Autotuned spreading choice: dict(variant, chunk, items, split_tiles)."""
+        v, c, ni, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(self.lib.kp_plan_spread_config(self._h, ctypes.byref(v), ctypes.byref(c), ctypes.byref(ni),
+                                               ctypes.byref(ns)), "kp_plan_spread_config")
+        return dict(variant=v.value, chunk=c.value, items=ni.value, split_tiles=ns.value)
+
     # -------------------------------------------------------------- operators
     def sense_forward(self, x, out=None, storage="c64"):
         """y = A x: x complex64 [*img] -> y [C, M] (complex64 or half storage)."""

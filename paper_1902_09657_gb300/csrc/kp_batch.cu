@@ -89,7 +89,16 @@ kp_status kp_batch_solve(kp_batch b, const void* const* y_devs, const kp_cdtype*
         kp_plan p = b->plans[i];
         if (!p->traj_set || !p->maps_set) { set_error("every plan needs a trajectory and maps"); return KP_EINVAL; }
         if (regs[i] == KP_REG_L1_WAVELET && p->P.wavelet_levels < 1) { set_error("l1-wavelet case without levels"); return KP_EINVAL; }
-        KP_TRY(solve_setup(p, y_devs[i], y_types[i], p_devs ? p_devs[i] : nullptr, 0.0, std::max(iters, 1), st));
+    }
+    // per-case set-up (preconditioner, power method, schedule, zero iterates), each case on its
+    // own stream so the cases' set-up kernels overlap; the caller's stream waits for all
+    KP_TRY_CUDA(cudaEventRecord(b->fork, st));
+    for (int i = 0; i < n; ++i) {
+        KP_TRY_CUDA(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        KP_TRY(solve_setup(b->plans[i], y_devs[i], y_types[i], p_devs ? p_devs[i] : nullptr, 0.0, std::max(iters, 1),
+                           b->streams[i]));
+        KP_TRY_CUDA(cudaEventRecord(b->joins[i], b->streams[i]));
+        KP_TRY_CUDA(cudaStreamWaitEvent(st, b->joins[i], 0));
     }
     // (re)capture the all-case iteration graph when the regularisers, lambdas, data types or
     // any plan's buffers (trajectory, maps, schedule length) changed

@@ -206,7 +206,8 @@ struct kp_plan_s {
     int64_t n_split = 0, split_cap = 0;
     int* d_k0 = nullptr;             // [D][M] wrapped first tap per sorted sample
     float* d_wt = nullptr;           // [D * W][M] Kaiser-Bessel weights per sorted sample
-    int chunk = 256;                 // samples per work item (spreading and interpolation)
+    int chunk = 256;                 // samples per interpolation work item
+    int spread_chunk = 256;          // samples per spreading work item (autotuned, multiple of 256)
     int spread_variant = 0;          // 0: warp-private tiles, 4 coils per CTA; 1: shared atomics, 16 coils per CTA;
                                      // 2: one accumulator, each warp owns 4 coils
     bool spread_tuned = false;
@@ -303,6 +304,8 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
                       cudaStream_t st);
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st);
+kp_status make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st);
 kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);

@@ -18,6 +18,7 @@
 #include "kp_internal.cuh"
 
 #include <cstdlib>
+#include <vector>
 
 namespace kp {
 
@@ -304,8 +305,10 @@ template <> struct SpL<2> {
     __device__ static constexpr int stride(int d) { return d == 0 ? 20 : 1; }
 };
 template <> struct SpL<3> {
-    static constexpr int TS = 8, PLANE = 896;
-    __device__ static constexpr int stride(int d) { return d == 0 ? 112 : (d == 1 ? 12 : 1); }
+    // (la, lb, lc) -> 68 la + 8 lb + lc: for 4 consecutive lb, 4 consecutive lc and two
+    // consecutive la the banks (4 la + 8 lb + lc) mod 32 are all distinct
+    static constexpr int TS = 8, PLANE = 544;
+    __device__ static constexpr int stride(int d) { return d == 0 ? 68 : (d == 1 ? 8 : 1); }
 };
 
 template <int D>
@@ -342,12 +345,17 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
             e[d] = min(tl.ts[d], geo.g[d] - o[d]);
         }
     }
-    const int n = end - beg;
     for (int i = threadIdx.x; i < NW * SP_CH * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
-    // stage the item's samples: coil values, weights, and the local coordinate of every tap
-    // inside this tile (-1 where the tap falls outside)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* my = acc + warp * SP_CH * 2 * LY::PLANE;
+    // the item's samples are taken SP_CHUNK at a time
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {
+    const int n = min(SP_CHUNK, end - sb);
+    __syncthreads();
+    // stage the samples: coil values, weights, and the local coordinate of every tap inside
+    // this tile (-1 where the tap falls outside)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int s = ext[beg + i];
+        const int s = ext[sb + i];
         const int64_t un = perm ? perm[s] : s;
 #pragma unroll
         for (int c = 0; c < SP_CH; ++c)
@@ -369,8 +377,6 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* my = acc + warp * SP_CH * 2 * LY::PLANE;
     // Each lane's updates of one sample are independent read-modify-writes of its private
     // copy: all loads are issued before any store, and the next sample's staged data is
     // fetched while the current one is applied.
@@ -448,6 +454,7 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
             __syncwarp();
         }
     }
+    }   // stages
     __syncthreads();
     int P = 1;
 #pragma unroll
@@ -492,10 +499,12 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
 constexpr int SPA_CH = 16;
 constexpr int SPA_THREADS = 256;
 
+// cs = coils per CTA (min(C, SPA_CH)): the accumulator and the staged coil values are sized
+// for the coils actually present, so few-coil plans fit several CTAs per SM
 template <int D>
-static size_t spread_atomic_smem() {
-    return (size_t)SPA_CH * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
-           (size_t)SP_CHUNK * (SPA_CH * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
+static size_t spread_atomic_smem(int cs) {
+    return (size_t)cs * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
+           (size_t)SP_CHUNK * (cs * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
 }
 
 template <int D, typename UT>
@@ -505,9 +514,10 @@ k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const
                 Tiles tl, float2* __restrict__ grid) {
     using LY = SpL<D>;
     extern __shared__ float smem[];
-    float* acc = smem;                                              // [SPA_CH][2][PLANE]
-    float2* su = (float2*)(acc + SPA_CH * 2 * LY::PLANE);           // [SP_CHUNK][SPA_CH]
-    float* sw = (float*)(su + SP_CHUNK * SPA_CH);                   // [SP_CHUNK][D][KW]
+    const int cs = min(geo.C, SPA_CH);                              // coils per CTA (stride)
+    float* acc = smem;                                              // [cs][2][PLANE]
+    float2* su = (float2*)(acc + cs * 2 * LY::PLANE);               // [SP_CHUNK][cs]
+    float* sw = (float*)(su + SP_CHUNK * cs);                       // [SP_CHUNK][D][KW]
     unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D]
     const int4 it = items[blockIdx.x];
     const int tile = it.x, beg = it.y, end = it.z;
@@ -525,12 +535,15 @@ k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const
             e[d] = min(tl.ts[d], geo.g[d] - o[d]);
         }
     }
-    const int n = end - beg;
     for (int i = threadIdx.x; i < cc * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {   // SP_CHUNK samples at a time
+    const int n = min(SP_CHUNK, end - sb);
+    __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int s = ext[beg + i];
+        const int s = ext[sb + i];
         const int64_t un = perm ? perm[s] : s;
-        for (int c = 0; c < cc; ++c) su[i * SPA_CH + c] = ldc<UT>(u, (size_t)(c0 + c) * geo.M + un);
+        for (int c = 0; c < cc; ++c) su[i * cs + c] = ldc<UT>(u, (size_t)(c0 + c) * geo.M + un);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
@@ -548,7 +561,6 @@ k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (D == 2) {
         const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
         for (int i = warp; i < n; i += nw) {
@@ -558,7 +570,7 @@ k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const
             const int lo = la * LY::stride(0) + lb;
             const float w = sw[(i * D) * KW + ta] * sw[(i * D + 1) * KW + tb];
             for (int c = h; c < cc; c += 2) {
-                const float2 uv = su[i * SPA_CH + c];
+                const float2 uv = su[i * cs + c];
                 float* pl = acc + c * 2 * LY::PLANE;
                 atomicAdd(pl + lo, w * uv.x);
                 atomicAdd(pl + LY::PLANE + lo, w * uv.y);
@@ -579,7 +591,7 @@ k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const
                 const int lo = la * LY::stride(0) + lb * LY::stride(1 % D) + lc;
                 const float w = sw[(i * D) * KW + ta] * wbc;
                 for (int c = 0; c < cc; ++c) {
-                    const float2 uv = su[i * SPA_CH + c];
+                    const float2 uv = su[i * cs + c];
                     float* pl = acc + c * 2 * LY::PLANE;
                     atomicAdd(pl + lo, w * uv.x);
                     atomicAdd(pl + LY::PLANE + lo, w * uv.y);
@@ -587,6 +599,7 @@ k_spread_atomic(const int* __restrict__ k0t, const float* __restrict__ wt, const
             }
         }
     }
+    }   // stages
     __syncthreads();
     int P = 1;
 #pragma unroll
@@ -657,10 +670,15 @@ k_spread_warpcoil(const int* __restrict__ k0t, const float* __restrict__ wt, con
             e[d] = min(tl.ts[d], geo.g[d] - o[d]);
         }
     }
-    const int n = end - beg;
     for (int i = threadIdx.x; i < C * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cw0 = warp * SPW_CW;
+    const int ccw = min(SPW_CW, C - cw0);
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {   // SP_CHUNK samples at a time
+    const int n = min(SP_CHUNK, end - sb);
+    __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int s = ext[beg + i];
+        const int s = ext[sb + i];
         const int64_t un = perm ? perm[s] : s;
         for (int c = 0; c < C; ++c) su[i * C + c] = ldc<UT>(u, (size_t)c * geo.M + un);
 #pragma unroll
@@ -680,9 +698,6 @@ k_spread_warpcoil(const int* __restrict__ k0t, const float* __restrict__ wt, con
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cw0 = warp * SPW_CW;
-    const int ccw = min(SPW_CW, C - cw0);
     if (D == 2) {
         const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
         const bool has0 = h < ccw, has1 = h + 2 < ccw;
@@ -734,6 +749,7 @@ k_spread_warpcoil(const int* __restrict__ k0t, const float* __restrict__ wt, con
             }
         }
     }
+    }   // stages
     __syncthreads();
     int P = 1;
 #pragma unroll
@@ -982,7 +998,7 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
                 attr_a[DD - 2][u_t] = true;
             }
             k_spread_atomic<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SPA_CH - 1) / SPA_CH), SPA_THREADS,
-                                      spread_atomic_smem<DD>(), st>>>(
+                                      spread_atomic_smem<DD>(std::min(g.C, SPA_CH)), st>>>(
                 p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
     }
     KP_LAUNCH_CHECK();
@@ -995,37 +1011,62 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
 // Pick the faster spreading variant for this plan's geometry and sample distribution by
 // timing both on the plan's own work items (values do not affect the cost).  Runs once per
 // plan, on the first trajectory.
+// Picks the spreading variant and the samples per work item by timing the adjoint spread
+// on the plan's own trajectory (once per plan, at its first trajectory).  Larger items mean
+// fewer split tiles (fewer global atomics) but fewer, longer CTAs.
 kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (p->spread_tuned) return KP_OK;
-    if (const char* ev = getenv("KPDHG_SPREAD_VARIANT")) {   // tuning override (0, 1, 2)
-        const int v = atoi(ev);
-        if (v >= 0 && v <= 2) { p->spread_variant = v; p->spread_tuned = true; return KP_OK; }
-    }
+    int force_v = -1, force_c = 0;
+    if (const char* ev = getenv("KPDHG_SPREAD_VARIANT")) force_v = atoi(ev);   // tuning overrides
+    if (const char* ev = getenv("KPDHG_SPREAD_CHUNK")) force_c = atoi(ev);
+    if (force_v > 2) force_v = -1;
+    if (force_c < SP_CHUNK || force_c % SP_CHUNK != 0) force_c = 0;
     const Geom& g = p->geo;
+    const int nv = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024 ? 3 : 2;
+    std::vector<int> chunks;
+    if (force_c) chunks.push_back(force_c);
+    else chunks = {256, 1024, 4096};
+    std::vector<int> variants;
+    if (force_v >= 0) variants.push_back(force_v);
+    else for (int v = 0; v < nv; ++v) variants.push_back(v);
+    if (chunks.size() == 1 && variants.size() == 1) {
+        p->spread_variant = variants[0];
+        if (chunks[0] != p->spread_chunk) KP_TRY(build_spread_items(p, chunks[0], st));
+        p->spread_tuned = true;
+        return KP_OK;
+    }
     KP_TRY_CUDA(cudaMemsetAsync(p->d_kt, 0, (size_t)g.C * g.M * sizeof(float2), st));
     cudaEvent_t e0, e1;
     KP_TRY_CUDA(cudaEventCreate(&e0));
     KP_TRY_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_v = 0;
+    int best_v = 0, best_c = p->spread_chunk;
     const bool prof = p->profiling;
     p->profiling = false;
-    const int nv = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024 ? 3 : 2;
-    for (int v = 0; v < nv; ++v) {
-        p->spread_variant = v;
-        KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st));
-        KP_TRY_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < 6; ++r) KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st));
-        KP_TRY_CUDA(cudaEventRecord(e1, st));
-        KP_TRY_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        KP_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_v = v; }
+    kp_status status = KP_OK;
+    for (int c : chunks) {
+        if (c != p->spread_chunk) status = build_spread_items(p, c, st);
+        if (status != KP_OK) break;
+        for (int v : variants) {
+            p->spread_variant = v;
+            status = adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st);
+            if (status != KP_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 4 && status == KP_OK; ++r) status = adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (status != KP_OK || cudaEventSynchronize(e1) != cudaSuccess) { status = status != KP_OK ? status : KP_ECUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_v = v; best_c = c; }
+        }
+        if (status != KP_OK) break;
     }
     p->profiling = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    KP_TRY(status);
     p->spread_variant = best_v;
+    if (best_c != p->spread_chunk) KP_TRY(build_spread_items(p, best_c, st));
     p->spread_tuned = true;
     return KP_OK;
 }

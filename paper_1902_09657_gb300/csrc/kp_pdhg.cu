@@ -304,7 +304,9 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
     // preconditioner
     const float* pu = p_dev;
     if (!pu) {
-        KP_TRY(kp_make_preconditioner(plan, 1, plan->d_puser, stream));
+        // no wait here: entries whose denominator was not positive are left at 0 and
+        // reported through the min-p check below
+        KP_TRY(make_preconditioner_enqueue(plan, 1, plan->d_puser, st));
         pu = plan->d_puser;
     }
     k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(pu, plan->d_ps, plan->d_perm, g.M, g.C);

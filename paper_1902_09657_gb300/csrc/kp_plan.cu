@@ -383,6 +383,50 @@ kp_status plan_destroy_internal(kp_plan p) {
     return KP_OK;
 }
 
+// Spreading work items: each tile's list cut into pieces of at most `chunk` samples (a
+// multiple of the kernels' staging size); tiles cut into several pieces are "split" and
+// accumulate with global atomics into a region cleared before each spread.
+kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st) {
+    const Tiles& tl = p->tiles;
+    p->spread_chunk = chunk;
+    drop_graphs(p);
+    const unsigned tb = nblk(tl.ntiles, 256);
+    k_chunks<<<tb, 256, 0, st>>>(p->d_ext_off, tl.ntiles, chunk, p->d_cnt, p->d_nslots);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_nslots, p->d_slot_off, tl.ntiles);
+    KP_LAUNCH_CHECK();
+    int tot[2];
+    KP_TRY_CUDA(cudaMemcpyAsync(&tot[0], p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaMemcpyAsync(&tot[1], p->d_slot_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int> nsl(tl.ntiles);
+    KP_TRY_CUDA(cudaMemcpyAsync(nsl.data(), p->d_nslots, tl.ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    p->n_items = tot[0];
+    if (p->n_items > p->items_cap) {
+        if (p->d_items) cudaFree(p->d_items);
+        p->d_items = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_items, p->n_items * sizeof(int4)));
+        p->items_cap = p->n_items;
+    }
+    std::vector<int> split;
+    for (int64_t t = 0; t < tl.ntiles; ++t)
+        if (nsl[t] > 0) split.push_back((int)t);
+    p->n_split = (int64_t)split.size();
+    if (p->n_split > p->split_cap) {
+        if (p->d_split) cudaFree(p->d_split);
+        p->d_split = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_split, p->n_split * sizeof(int)));
+        p->split_cap = p->n_split;
+    }
+    if (p->n_split > 0)
+        KP_TRY_CUDA(cudaMemcpyAsync(p->d_split, split.data(), split.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, chunk, p->d_items);
+    KP_LAUNCH_CHECK();
+    KP_TRY_CUDA(cudaStreamSynchronize(st));   // the host split list must outlive its copy
+    p->launches += 4;
+    return KP_OK;
+}
+
 kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale, cudaStream_t st) {
     if (!p || !traj) { set_error("null argument"); return KP_EINVAL; }
     const Geom& g = p->geo;
@@ -426,39 +470,8 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
         return KP_EINVAL;
     }
     p->max_tile = flag[2];
-    // work items for the spreading kernel
+    KP_TRY(build_spread_items(p, p->spread_chunk, st));
     const unsigned tb = nblk(tl.ntiles, 256);
-    k_chunks<<<tb, 256, 0, st>>>(p->d_ext_off, tl.ntiles, p->chunk, p->d_cnt, p->d_nslots);
-    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
-    k_scan_excl<<<1, 1024, 0, st>>>(p->d_nslots, p->d_slot_off, tl.ntiles);
-    KP_LAUNCH_CHECK();
-    int tot[2];
-    KP_TRY_CUDA(cudaMemcpyAsync(&tot[0], p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaMemcpyAsync(&tot[1], p->d_slot_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
-    std::vector<int> nsl(tl.ntiles);
-    KP_TRY_CUDA(cudaMemcpyAsync(nsl.data(), p->d_nslots, tl.ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));
-    p->n_items = tot[0];
-    if (p->n_items > p->items_cap) {
-        if (p->d_items) cudaFree(p->d_items);
-        p->d_items = nullptr;
-        KP_TRY_CUDA(cudaMalloc(&p->d_items, p->n_items * sizeof(int4)));
-        p->items_cap = p->n_items;
-    }
-    std::vector<int> split;
-    for (int64_t t = 0; t < tl.ntiles; ++t)
-        if (nsl[t] > 0) split.push_back((int)t);
-    p->n_split = (int64_t)split.size();
-    if (p->n_split > p->split_cap) {
-        if (p->d_split) cudaFree(p->d_split);
-        p->d_split = nullptr;
-        KP_TRY_CUDA(cudaMalloc(&p->d_split, p->n_split * sizeof(int)));
-        p->split_cap = p->n_split;
-    }
-    if (p->n_split > 0)
-        KP_TRY_CUDA(cudaMemcpy(p->d_split, split.data(), split.size() * sizeof(int), cudaMemcpyHostToDevice));
-    k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, p->chunk, p->d_items);
-    KP_LAUNCH_CHECK();
     // interpolation items (own samples of each tile; d_item_off is free again)
     k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->chunk, p->d_cnt);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
@@ -475,7 +488,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     }
     k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_item_off, tl.ntiles, p->chunk, p->d_iitems);
     KP_LAUNCH_CHECK();
-    p->launches += 15;
+    p->launches += 11;
     p->traj_set = true;
     return autotune_spread(p, st);
 }
@@ -546,13 +559,18 @@ kp_status kp_plan_set_profiling(kp_plan plan, int enable) {
     return KP_OK;
 }
 
+kp_status kp_plan_spread_config(kp_plan plan, int* variant, int* chunk, int64_t* n_items, int64_t* n_split) {
+    if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    if (!plan->traj_set) { set_error("no trajectory set"); return KP_EINVAL; }
+    if (variant) *variant = plan->spread_variant;
+    if (chunk) *chunk = plan->spread_chunk;
+    if (n_items) *n_items = plan->n_items;
+    if (n_split) *n_split = plan->n_split;
+    return KP_OK;
+}
+
 kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_samples) {
     if (!plan) { set_error("null plan"); return KP_EINVAL; }
-    if (max_tile_samples && *max_tile_samples == -1) {   // query of the chosen spreading variant
-        *max_tile_samples = plan->spread_variant;
-        if (ntiles) *ntiles = plan->n_items;
-        return KP_OK;
-    }
     if (ntiles) *ntiles = plan->tiles.ntiles;
     if (max_tile_samples) *max_tile_samples = plan->max_tile;
     return KP_OK;

@@ -215,11 +215,12 @@ __global__ void k_p_out(const float2* __restrict__ den, const int* __restrict__ 
 
 using namespace kp;
 
-extern "C" kp_status kp_make_preconditioner(kp_plan plan, int multichannel, float* p_dev, void* stream) {
+// Enqueues the whole construction on st without waiting; the number of non-positive
+// denominators (entries set to 0) is left in d_flag[7].
+kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st) {
     if (!plan || !p_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || (multichannel && !plan->maps_set)) { set_error("trajectory (and maps) must be set"); return KP_EINVAL; }
     if (plan->unit_maps) { set_error("not available on an internal plan"); return KP_EINVAL; }
-    cudaStream_t st = (cudaStream_t)stream;
     KP_TRY(pre_create(plan, st));
     PrePlan* q = plan->pre;
     kp_plan nu = plan->pre_nufft;
@@ -290,6 +291,12 @@ extern "C" kp_status kp_make_preconditioner(kp_plan plan, int multichannel, floa
         KP_LAUNCH_CHECK();
         plan->launches += 3;
     }
+    return KP_OK;
+}
+
+extern "C" kp_status kp_make_preconditioner(kp_plan plan, int multichannel, float* p_dev, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    KP_TRY(kp::make_preconditioner_enqueue(plan, multichannel, p_dev, st));
     int bad = 0;
     KP_TRY_CUDA(cudaMemcpyAsync(&bad, plan->d_flag + 7, sizeof(int), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));

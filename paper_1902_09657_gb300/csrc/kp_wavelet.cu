@@ -11,7 +11,8 @@
 // applied as the forward kernels write the coefficients, and PDHG's extrapolation
 // xbar = x + theta (x - x_old) is fused into the last inverse level.  Inside a PDHG iteration
 // the level passes run in one persistent cooperative kernel (k_primal_fused, end of file),
-// separated by grid barriers; the standalone level kernels serve kp_wavelet.
+// separated by grid barriers; the standalone level kernels serve kp_wavelet and the batched
+// iteration (several cases at once, where one cooperative grid per case cannot co-reside).
 //
 // Filters: analysis a[k] = sum_n h[n] x[2k+n], d[k] = sum_n g[n] x[2k+n] (indices mod the
 // block length), g[n] = (-1)^n h[7-n]; synthesis is the transpose.

@@ -112,3 +112,30 @@ def test_invalid_params_rejected():
         Plan((32, 32), 2, 100, kernel_width=6)
     with pytest.raises(KpError):
         Plan((30, 32), 2, 100, wavelet_levels=3)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("chunk", [256, 1024])
+def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
+    """Every spreading kernel variant and work-item size (fixed through the tuning overrides)
+    gives the oracle's adjoint, on centre-dense radial trajectories whose central tiles are
+    cut into many items (2D and 3D)."""
+    need_gpu()
+    import synth
+    monkeypatch.setenv("KPDHG_SPREAD_VARIANT", str(variant))
+    monkeypatch.setenv("KPDHG_SPREAD_CHUNK", str(chunk))
+    cases = [((48, 48), 3, synth.radial_golden_angle(n_spokes=150, n_readout=96, kmax=24.0)),
+             ((16, 16, 16), 2, synth.radial_3d_fibonacci(n_spokes=600, n_readout=16, kmax=8.0))]
+    for shape, C, traj in cases:
+        M = traj.shape[0]
+        rng = np.random.default_rng(M)
+        maps = (rng.standard_normal((C,) + shape) + 1j * rng.standard_normal((C,) + shape)).astype(np.complex64)
+        u = (rng.standard_normal((C, M)) + 1j * rng.standard_normal((C, M))).astype(np.complex64)
+        x_ref = onf.nufft_adjoint(u.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+        plan = make_plan(shape, C, M, 1.25)
+        plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+        cfg = plan.spread_config()
+        assert cfg["variant"] == variant and cfg["chunk"] == chunk
+        assert cfg["split_tiles"] > 0
+        xa = plan.sense_adjoint(to_dev(u)).cpu().numpy()
+        assert rel(xa, x_ref) < 1e-5, (shape, cfg)
