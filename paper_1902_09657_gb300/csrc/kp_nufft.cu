@@ -164,8 +164,9 @@ __global__ void k_fwd_pre(const float2* __restrict__ x, const MT* __restrict__ m
 
 // ---------------------------------------------------------------- forward: interpolation
 // One CTA per (tile chunk, coil group): the grid region the tile's samples read
-// ((ts + W - 1)^D points per coil, periodic) is staged in shared memory with coalesced loads,
-// then each thread interpolates one sample for the group's coils from shared memory.
+// ((ts + W - 1)^D points per coil, periodic) is staged in shared memory by bulk asynchronous
+// copies (cp.async.bulk, one or two per grid row, completing on an mbarrier), then each
+// thread interpolates one sample for the group's coils from shared memory.
 constexpr int IP_CH = 4;           // coils per CTA (blockIdx.y selects the group)
 constexpr int IP_THREADS = 256;
 
@@ -178,20 +179,59 @@ struct InterpIO {
     float2* u;           // mode 2: dual variable, sorted
     const float* sched;
     const int* iter;
+    int* flag;           // set to 1 if the staging wait gave up (reported as KP_ETIMEOUT)
 };
 
+// Staged region geometry: R points per axis for the largest tile edge (16 in 2D, 8 in 3D);
+// rows along the last axis are copied RP points long (even, so every copy is a multiple of
+// 16 bytes starting on a 16-byte boundary: the row start is rounded down to an even x).
+template <int D> struct IpL {
+    static constexpr int R = (D == 2 ? 16 : 8) + KW - 1;
+    static constexpr int RP = (R + 2) & ~1;
+    static constexpr int ROWS = D == 2 ? R : R * R;      // rows per coil
+    static constexpr int PER_COIL = ROWS * RP;           // staged points per coil
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared.b64 st, [%0], %1; }"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Waits for phase `parity` of the barrier for about one second at most; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 2000000000LL) return false;
+    return true;
+}
+
 template <int D, int MODE, typename T>
-__global__ void __launch_bounds__(IP_THREADS)
+__global__ void __launch_bounds__(IP_THREADS, D == 3 ? 3 : 4)
 k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const float* __restrict__ wt,
               const float2* __restrict__ grid, Geom geo, Tiles tl, InterpIO io) {
-    extern __shared__ float2 sg[];    // [IP_CH][R^D]
+    using LY = IpL<D>;
+    extern __shared__ __align__(128) float2 sg[];    // [IP_CH][ROWS][RP]
+    __shared__ unsigned long long bar;
     const int4 it = items[blockIdx.x];
     const int tile = it.x, beg = it.y, end = it.z;
     const int c0 = blockIdx.y * IP_CH;
     const int cc = min(IP_CH, geo.C - c0);
-    // staged region: (TS + W - 1)^D points for the largest tile edge TS (16 in 2D, 8 in 3D)
-    constexpr int R = (D == 2 ? 16 : 8) + KW - 1;
-    constexpr int RT = D == 2 ? R * R : R * R * R;
+    constexpr int R = LY::R;
     int o[MAXD];
     {
         int r = tile;
@@ -202,9 +242,9 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
             o[d] = tc * tl.ts[d];
         }
     }
-    // grid row offsets of the staged region, per axis (periodic), computed once per CTA
+    // grid row offsets of the staged region along the slower axes (periodic), computed once
     __shared__ int rowoff[MAXD][R];
-    if (threadIdx.x < D * R) {
+    if (threadIdx.x < (D - 1) * R) {
         const int d = threadIdx.x / R, l = threadIdx.x % R;
         int pp = o[d] + l;
         while (pp >= geo.g[d]) pp -= geo.g[d];
@@ -212,23 +252,41 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
         for (int e = d + 1; e < D; ++e) stride *= geo.g[e];
         rowoff[d][l] = (int)(tunshift(pp, tl.sh[d], geo.g[d]) * stride);
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < cc * RT; idx += blockDim.x) {
-        const int c = idx / RT;
-        const int r = idx - c * RT;
-        int off;
-        if (D == 2) off = rowoff[0][r / R] + rowoff[1 % D][r % R];
-        else off = rowoff[0][r / (R * R)] + rowoff[1 % D][(r / R) % R] + rowoff[D - 1][r % R];
-        sg[idx] = __ldg(grid + (size_t)(c0 + c) * geo.G + off);
+    // first staged x (unshifted), rounded down to even; xo = its parity
+    const int gx = geo.g[D - 1];
+    const int xs = tunshift(o[D - 1] < gx ? o[D - 1] : o[D - 1] - gx, tl.sh[D - 1], gx);
+    const int xo = xs & 1, xlo = xs - xo;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    constexpr int rs0 = D == 2 ? R : R * R, rs1 = D == 2 ? 1 : R;
-    const int Rtot = RT;
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, (unsigned)(cc * LY::PER_COIL * sizeof(float2)));
+    for (int j = threadIdx.x; j < cc * LY::ROWS; j += blockDim.x) {
+        const int c = j / LY::ROWS, row = j - c * LY::ROWS;
+        const int off = D == 2 ? rowoff[0][row] : rowoff[0][row / R] + rowoff[1 % (D - 1)][row % R];
+        const float2* src = grid + (size_t)(c0 + c) * geo.G + off;
+        float2* dst = sg + (size_t)j * LY::RP;
+        // the row is periodic: copy up to the grid edge, then continue from x = 0 (pieces
+        // are even in length because the grid extent and the start are even)
+        for (int pos = 0, x = xlo; pos < LY::RP; x = 0) {
+            const int n = min(LY::RP - pos, gx - x);
+            bulk_g2s(dst + pos, src + x, (unsigned)(n * sizeof(float2)), &bar);
+            pos += n;
+        }
+    }
+    if (!mbar_wait_bounded(&bar, 0)) {
+        if (io.flag) atomicExch(io.flag, 1);
+        mbar_wait_bounded(&bar, 0);      // copies still in flight land in this CTA's memory
+        return;
+    }
+    constexpr int rs0 = D == 2 ? LY::RP : R * LY::RP, rs1 = D == 2 ? 1 : LY::RP;
+    constexpr int Rtot = LY::PER_COIL;
     float sigma = 0.f;
     if (MODE == 2) sigma = io.sched[3 * (*io.iter)];
     for (int s = beg + threadIdx.x; s < end; s += blockDim.x) {
         float w[D][KW];
-        int lb = 0;
+        int lb = xo;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
@@ -286,22 +344,23 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
 }
 
 // ---------------------------------------------------------------- adjoint: spread
-// One CTA per (spreading work item, coil group).  The item's samples (their coil values,
-// first taps and weights) are staged in shared memory by all threads at once; then each
-// warp takes one sample at a time, its lanes covering distinct (tap, coil) pairs, and adds
-// into its own private copy of the tile, so no atomics are needed.  The private copies are
-// summed and the tile is stored (or, for a tile split over several items, added with global
-// atomics into a region cleared beforehand).  Tile coordinates are shifted (Tiles::sh).
-constexpr int SP_CH = 4;           // coils per CTA
-constexpr int SP_THREADS = 128;    // 4 warps, 4 private tile copies
-constexpr int SP_CHUNK = 256;      // samples per work item (== plan chunk)
+// One CTA per (spreading work item, group of CH coils), NW warps.  The item's samples (their
+// coil values, first taps and weights) are staged in shared memory SP_CHUNK at a time by all
+// threads; then each warp takes one sample at a time, its lanes covering distinct (tap, coil)
+// pairs, and adds into its own private copy of the tile, so no atomics are needed.  The
+// private copies are summed and the tile is stored (or, for a tile split over several items,
+// added with global atomics into a region cleared beforehand).  Tile coordinates are shifted
+// (Tiles::sh).  CH and NW trade occupancy (smaller copies, more warps per SM) against work
+// repeated per coil group (staging and tap decoding); the autotuner picks.
+constexpr int SP_CHUNK = 256;      // samples staged at a time (and the interpolation item size)
 
-// Shared-memory layout of one private tile copy, for the largest tile edge (16 in 2D, 8 in
-// 3D).  Strides are padded so that the 32 lanes of a warp (2D: 16 taps x 2 coils; 3D: 32
-// taps) hit 32 different banks.
+// Shared-memory layout of one private tile copy (one coil, re and im planes), for the largest
+// tile edge (16 in 2D, 8 in 3D).  Strides are padded so that the 32 lanes of a warp hit 32
+// different banks.
 template <int D> struct SpL;
 template <> struct SpL<2> {
-    static constexpr int TS = 16, PLANE = 328;        // 2 x PLANE = 16 (mod 32): coil pairs on disjoint banks
+    // lanes (ta, tb, coil parity h): 20 ta + tb + 2 PLANE h covers 32 distinct banks
+    static constexpr int TS = 16, PLANE = 328;
     __device__ static constexpr int stride(int d) { return d == 0 ? 20 : 1; }
 };
 template <> struct SpL<3> {
@@ -311,29 +370,29 @@ template <> struct SpL<3> {
     __device__ static constexpr int stride(int d) { return d == 0 ? 68 : (d == 1 ? 8 : 1); }
 };
 
-template <int D>
+template <int D, int CH, int NW>
 static size_t spread_smem() {
-    return (size_t)(SP_THREADS / 32) * SP_CH * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
-           (size_t)SP_CHUNK * (SP_CH * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
+    return (size_t)NW * CH * 2 * (D == 2 ? SpL<2>::PLANE : SpL<3>::PLANE) * sizeof(float) +
+           (size_t)SP_CHUNK * (CH * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
 }
 
-template <int D, typename UT>
-__global__ void __launch_bounds__(SP_THREADS)
+template <int D, typename UT, int CH, int NW>
+__global__ void __launch_bounds__(NW * 32)
 k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
          const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
          Tiles tl, float2* __restrict__ grid) {
     using LY = SpL<D>;
+    static_assert(D == 3 || CH % 2 == 0 || CH == 1, "2D lanes split coils by parity");
     extern __shared__ float smem[];
-    constexpr int NW = SP_THREADS / 32;
-    float* acc = smem;                                              // [NW][SP_CH][2][PLANE]
-    float2* su = (float2*)(acc + NW * SP_CH * 2 * LY::PLANE);       // [SP_CHUNK][SP_CH]
-    float* sw = (float*)(su + SP_CHUNK * SP_CH);                    // [SP_CHUNK][D][KW]
+    float* acc = smem;                                              // [NW][CH][2][PLANE]
+    float2* su = (float2*)(acc + NW * CH * 2 * LY::PLANE);          // [SP_CHUNK][CH]
+    float* sw = (float*)(su + SP_CHUNK * CH);                       // [SP_CHUNK][D][KW]
     unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D] 4 packed int8 tap coordinates
     const int4 it = items[blockIdx.x];
     const int tile = it.x, beg = it.y, end = it.z;
     const bool split = it.w >= 0;
-    const int c0 = blockIdx.y * SP_CH;
-    const int cc = min(SP_CH, geo.C - c0);
+    const int c0 = blockIdx.y * CH;
+    const int cc = min(CH, geo.C - c0);
     int o[MAXD], e[MAXD];
     {
         int r = tile;
@@ -345,116 +404,103 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
             e[d] = min(tl.ts[d], geo.g[d] - o[d]);
         }
     }
-    for (int i = threadIdx.x; i < NW * SP_CH * 2 * LY::PLANE; i += blockDim.x) acc[i] = 0.f;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* my = acc + warp * SP_CH * 2 * LY::PLANE;
-    // the item's samples are taken SP_CHUNK at a time
-    for (int sb = beg; sb < end; sb += SP_CHUNK) {
-    const int n = min(SP_CHUNK, end - sb);
-    __syncthreads();
-    // stage the samples: coil values, weights, and the local coordinate of every tap inside
-    // this tile (-1 where the tap falls outside)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int s = ext[sb + i];
-        const int64_t un = perm ? perm[s] : s;
-#pragma unroll
-        for (int c = 0; c < SP_CH; ++c)
-            su[i * SP_CH + c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
-            unsigned pk = 0;
-#pragma unroll
-            for (int j = 0; j < KW; ++j) {
-                int pp = p0 + j;
-                if (pp >= geo.g[d]) pp -= geo.g[d];
-                const int l = pp - o[d];
-                const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
-                pk |= byte << (8 * j);
-                sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
-            }
-            sp[i * D + d] = pk;
-        }
+    {
+        float4* a4 = (float4*)acc;
+        for (int i = threadIdx.x; i < NW * CH * 2 * LY::PLANE / 4; i += blockDim.x) a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
-    // Each lane's updates of one sample are independent read-modify-writes of its private
-    // copy: all loads are issued before any store, and the next sample's staged data is
-    // fetched while the current one is applied.
-    if (D == 2) {
-        const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
-        const bool has1 = h + 2 < cc, has0 = h < cc;
-        float* q0 = my + h * 2 * LY::PLANE;
-        float* q1 = my + (h + 2) * 2 * LY::PLANE;
-        unsigned pk0 = 0, pk1 = 0;
-        float wa = 0.f, wb = 0.f;
-        float2 u0 = make_float2(0.f, 0.f), u1 = u0;
-        int i = warp;
-        if (i < n) {
-            pk0 = sp[i * D]; pk1 = sp[i * D + 1];
-            wa = sw[(i * D) * KW + ta]; wb = sw[(i * D + 1) * KW + tb];
-            u0 = su[i * SP_CH + (h & 3)]; u1 = su[i * SP_CH + ((h + 2) & 3)];
-        }
-        for (; i < n; i += NW) {
-            const int la = (int)(signed char)(pk0 >> (8 * ta));
-            const int lb = (int)(signed char)(pk1 >> (8 * tb));
-            const bool ok = la >= 0 && lb >= 0;
-            const int lo = la * LY::stride(0) + lb;
-            const float w = wa * wb;
-            const float2 cu0 = u0, cu1 = u1;
-            const int inx = i + NW;
-            if (inx < n) {
-                pk0 = sp[inx * D]; pk1 = sp[inx * D + 1];
-                wa = sw[(inx * D) * KW + ta]; wb = sw[(inx * D + 1) * KW + tb];
-                u0 = su[inx * SP_CH + (h & 3)]; u1 = su[inx * SP_CH + ((h + 2) & 3)];
-            }
-            if (ok && has0) {
-                float r0 = q0[lo], i0 = q0[LY::PLANE + lo];
-                float r1 = 0.f, i1 = 0.f;
-                if (has1) { r1 = q1[lo]; i1 = q1[LY::PLANE + lo]; }
-                q0[lo] = fmaf(w, cu0.x, r0);
-                q0[LY::PLANE + lo] = fmaf(w, cu0.y, i0);
-                if (has1) {
-                    q1[lo] = fmaf(w, cu1.x, r1);
-                    q1[LY::PLANE + lo] = fmaf(w, cu1.y, i1);
-                }
-            }
-            __syncwarp();
-        }
-    } else {
-        const int tb = (lane >> 2) & 3, tc = lane & 3, ta0 = lane >> 4;   // taps (ta0 + 2k, tb, tc), k = 0, 1
-        for (int i = warp; i < n; i += NW) {
-            const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
-            const int lc = (int)(signed char)(sp[i * D + 2] >> (8 * tc));
-            const float wbc = sw[(i * D + 1) * KW + tb] * sw[(i * D + 2) * KW + tc];
-            const int laA = (int)(signed char)(sp[i * D] >> (8 * ta0));
-            const int laB = (int)(signed char)(sp[i * D] >> (8 * (ta0 + 2)));
-            const bool okA = laA >= 0 && lb >= 0 && lc >= 0, okB = laB >= 0 && lb >= 0 && lc >= 0;
-            const int loA = laA * LY::stride(0) + lb * LY::stride(1 % D) + lc;
-            const int loB = laB * LY::stride(0) + lb * LY::stride(1 % D) + lc;
-            const float wA = sw[(i * D) * KW + ta0] * wbc, wB = sw[(i * D) * KW + ta0 + 2] * wbc;
-            float rA[SP_CH], iA[SP_CH], rB[SP_CH], iB[SP_CH];
-            float2 uv[SP_CH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* my = acc + warp * CH * 2 * LY::PLANE;
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {
+        const int n = min(SP_CHUNK, end - sb);
+        __syncthreads();
+        // stage the samples: coil values, weights, and the local coordinate of every tap
+        // inside this tile (-1 where the tap falls outside)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = ext[sb + i];
+            const int64_t un = perm ? perm[s] : s;
 #pragma unroll
-            for (int c = 0; c < SP_CH; ++c) {
-                uv[c] = su[i * SP_CH + c];
-                if (c < cc) {
+            for (int c = 0; c < CH; ++c)
+                su[i * CH + c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+                unsigned pk = 0;
+#pragma unroll
+                for (int j = 0; j < KW; ++j) {
+                    int pp = p0 + j;
+                    if (pp >= geo.g[d]) pp -= geo.g[d];
+                    const int l = pp - o[d];
+                    const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
+                    pk |= byte << (8 * j);
+                    sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+                }
+                sp[i * D + d] = pk;
+            }
+        }
+        __syncthreads();
+        // Each lane's updates of one sample are independent read-modify-writes of its warp's
+        // private copy: all loads are issued before any store.
+        if (D == 2) {
+            // lanes: taps (ta, tb) x coil parity h; coils h, h + 2, ... (CH = 1: h = 1 idle)
+            constexpr int CL = CH == 1 ? 1 : CH / 2;   // coils per lane
+            const int ta = (lane >> 2) & 3, tb = lane & 3, h = lane >> 4;
+            const bool lane_on = CH > 1 || h == 0;
+            for (int i = warp; i < n; i += NW) {
+                const int la = (int)(signed char)(sp[i * D] >> (8 * ta));
+                const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+                const bool ok = lane_on && la >= 0 && lb >= 0;
+                const int lo = la * LY::stride(0) + lb;
+                const float w = sw[(i * D) * KW + ta] * sw[(i * D + 1) * KW + tb];
+                float rr[CL], ii[CL];
+                float2 uv[CL];
+#pragma unroll
+                for (int k = 0; k < CL; ++k) {
+                    const int c = CH == 1 ? 0 : h + 2 * k;
+                    uv[k] = su[i * CH + c];
+                    if (ok) { float* pl = my + c * 2 * LY::PLANE; rr[k] = pl[lo]; ii[k] = pl[LY::PLANE + lo]; }
+                }
+#pragma unroll
+                for (int k = 0; k < CL; ++k) {
+                    const int c = CH == 1 ? 0 : h + 2 * k;
+                    if (ok) {
+                        float* pl = my + c * 2 * LY::PLANE;
+                        pl[lo] = fmaf(w, uv[k].x, rr[k]);
+                        pl[LY::PLANE + lo] = fmaf(w, uv[k].y, ii[k]);
+                    }
+                }
+                __syncwarp();
+            }
+        } else {
+            const int tb = (lane >> 2) & 3, tc = lane & 3, ta0 = lane >> 4;   // taps (ta0 + 2k, tb, tc), k = 0, 1
+            for (int i = warp; i < n; i += NW) {
+                const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+                const int lc = (int)(signed char)(sp[i * D + 2] >> (8 * tc));
+                const float wbc = sw[(i * D + 1) * KW + tb] * sw[(i * D + 2) * KW + tc];
+                const int laA = (int)(signed char)(sp[i * D] >> (8 * ta0));
+                const int laB = (int)(signed char)(sp[i * D] >> (8 * (ta0 + 2)));
+                const bool okA = laA >= 0 && lb >= 0 && lc >= 0, okB = laB >= 0 && lb >= 0 && lc >= 0;
+                const int loA = laA * LY::stride(0) + lb * LY::stride(1 % D) + lc;
+                const int loB = laB * LY::stride(0) + lb * LY::stride(1 % D) + lc;
+                const float wA = sw[(i * D) * KW + ta0] * wbc, wB = sw[(i * D) * KW + ta0 + 2] * wbc;
+                float rA[CH], iA[CH], rB[CH], iB[CH];
+                float2 uv[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    uv[c] = su[i * CH + c];
                     float* pl = my + c * 2 * LY::PLANE;
                     if (okA) { rA[c] = pl[loA]; iA[c] = pl[LY::PLANE + loA]; }
                     if (okB) { rB[c] = pl[loB]; iB[c] = pl[LY::PLANE + loB]; }
                 }
-            }
 #pragma unroll
-            for (int c = 0; c < SP_CH; ++c) {
-                if (c < cc) {
+                for (int c = 0; c < CH; ++c) {
                     float* pl = my + c * 2 * LY::PLANE;
                     if (okA) { pl[loA] = fmaf(wA, uv[c].x, rA[c]); pl[LY::PLANE + loA] = fmaf(wA, uv[c].y, iA[c]); }
                     if (okB) { pl[loB] = fmaf(wB, uv[c].x, rB[c]); pl[LY::PLANE + loB] = fmaf(wB, uv[c].y, iB[c]); }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
-    }   // stages
     __syncthreads();
     int P = 1;
 #pragma unroll
@@ -478,7 +524,7 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
         float2 v = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            const float* pl = acc + (w * SP_CH + c) * 2 * LY::PLANE;
+            const float* pl = acc + (w * CH + c) * 2 * LY::PLANE;
             v.x += pl[lo];
             v.y += pl[LY::PLANE + lo];
         }
@@ -910,7 +956,7 @@ kp_status fft_forward_only(kp_plan p, cudaStream_t st) {
 template <int MODE>
 static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaStream_t st) {
     const Geom& g = p->geo;
-    const size_t rt = g.D == 2 ? (16 + KW - 1) * (16 + KW - 1) : (8 + KW - 1) * (8 + KW - 1) * (8 + KW - 1);
+    const size_t rt = g.D == 2 ? IpL<2>::PER_COIL : IpL<3>::PER_COIL;
     const size_t smem = (size_t)IP_CH * rt * sizeof(float2);
     const dim3 grid((unsigned)p->n_iitems, (g.C + IP_CH - 1) / IP_CH);
     static bool attr[2][3][3] = {};
@@ -932,6 +978,7 @@ kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, con
     InterpIO io{};
     io.out = out;
     io.perm = perm;
+    io.flag = p->d_flag + 3;
     return launch_interp<0>(p, out_t, io, st);
 }
 
@@ -940,6 +987,7 @@ kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const f
     InterpIO io{};
     io.outs = out_sorted;
     io.ps = ps;
+    io.flag = p->d_flag + 3;
     return launch_interp<1>(p, KP_C64, io, st);
 }
 
@@ -951,6 +999,7 @@ kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st) {
 kp_status interp_dual_only(kp_plan p, cudaStream_t st) {
     InterpIO io{};
     io.ys = p->d_ys;
+    io.flag = p->d_flag + 3;
     io.ps = p->d_ps;
     io.u = p->d_u;
     io.sched = p->d_sched;
@@ -958,11 +1007,25 @@ kp_status interp_dual_only(kp_plan p, cudaStream_t st) {
     return launch_interp<2>(p, p->ys_t, io, st);
 }
 
+// Private-copy spreading with CH coils per CTA and NW warps (variants 0, 3, 4, 5).
+template <int D, typename UT, int CH, int NW>
+static kp_status launch_spread_priv(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
+    static bool attr = false;
+    const size_t sm = spread_smem<D, CH, NW>();
+    if (!attr) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<D, UT, CH, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    const Geom& g = p->geo;
+    k_spread<D, UT, CH, NW><<<dim3((unsigned)p->n_items, (g.C + CH - 1) / CH), NW * 32, sm, st>>>(
+        p->d_k0, p->d_wt, u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2);
+    return KP_OK;
+}
+
 kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st) {
     const Geom& g = p->geo;
     int P = 1;
     for (int d = 0; d < g.D; ++d) P *= p->tiles.ts[d];
-    static bool attr_set[2][3] = {{false}};
     mark(p, PH_SPREAD, st);
     if (p->n_split > 0) {
         KP_DISPATCH_D(g.D, DD, k_zero_split<DD><<<(unsigned)p->n_split, 256, 0, st>>>(p->d_split, g, p->tiles, P,
@@ -971,14 +1034,14 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
         p->launches += 1;
     }
     p->launches += 1;
-    if (p->spread_variant == 0) {
+    if (p->spread_variant == 0 || p->spread_variant >= 3) {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
-            if (!attr_set[DD - 2][u_t]) {
-                KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-                attr_set[DD - 2][u_t] = true;
-            }
-            k_spread<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SP_CH - 1) / SP_CH), SP_THREADS, spread_smem<DD>(), st>>>(
-                p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
+            switch (p->spread_variant) {
+                case 0: KP_TRY((launch_spread_priv<DD, UT, 4, 4>(p, (const UT*)u, perm, st))); break;
+                case 3: KP_TRY((launch_spread_priv<DD, UT, 2, 8>(p, (const UT*)u, perm, st))); break;
+                case 4: KP_TRY((launch_spread_priv<DD, UT, 1, 8>(p, (const UT*)u, perm, st))); break;
+                default: KP_TRY((launch_spread_priv<DD, UT, 2, 4>(p, (const UT*)u, perm, st))); break;
+            }));
     } else if (p->spread_variant == 2) {
         static bool attr_w[2][3] = {{false}};
         const size_t sm = g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C);
@@ -1008,27 +1071,26 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
     return KP_OK;
 }
 
-// Pick the faster spreading variant for this plan's geometry and sample distribution by
-// timing both on the plan's own work items (values do not affect the cost).  Runs once per
-// plan, on the first trajectory.
 // Picks the spreading variant and the samples per work item by timing the adjoint spread
-// on the plan's own trajectory (once per plan, at its first trajectory).  Larger items mean
-// fewer split tiles (fewer global atomics) but fewer, longer CTAs.
+// on the plan's own work items (values do not affect the cost; once per plan, at its first
+// trajectory).  Variants: 0 private copies, 4 coils x 4 warps; 1 shared atomics; 2 warp per
+// 4 coils; 3 private, 2 coils x 8 warps; 4 private, 1 coil x 8 warps; 5 private, 2 coils x 4
+// warps.  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
 kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (p->spread_tuned) return KP_OK;
     int force_v = -1, force_c = 0;
     if (const char* ev = getenv("KPDHG_SPREAD_VARIANT")) force_v = atoi(ev);   // tuning overrides
     if (const char* ev = getenv("KPDHG_SPREAD_CHUNK")) force_c = atoi(ev);
-    if (force_v > 2) force_v = -1;
-    if (force_c < SP_CHUNK || force_c % SP_CHUNK != 0) force_c = 0;
     const Geom& g = p->geo;
-    const int nv = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024 ? 3 : 2;
+    const bool wc_ok = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024;
+    if (force_v > 5 || (force_v == 2 && !wc_ok)) force_v = -1;
+    if (force_c < SP_CHUNK || force_c % SP_CHUNK != 0) force_c = 0;
     std::vector<int> chunks;
     if (force_c) chunks.push_back(force_c);
     else chunks = {256, 1024, 4096};
     std::vector<int> variants;
     if (force_v >= 0) variants.push_back(force_v);
-    else for (int v = 0; v < nv; ++v) variants.push_back(v);
+    else for (int v = 0; v <= 5; ++v) if (v != 2 || wc_ok) variants.push_back(v);
     if (chunks.size() == 1 && variants.size() == 1) {
         p->spread_variant = variants[0];
         if (chunks[0] != p->spread_chunk) KP_TRY(build_spread_items(p, chunks[0], st));

@@ -336,6 +336,7 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_bar, 0, 4 * sizeof(unsigned int), st));   // grid-barrier counter
     // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
     return KP_OK;

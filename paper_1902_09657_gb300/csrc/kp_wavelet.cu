@@ -557,28 +557,31 @@ namespace kp {
 // (about a second of SM clock), after which the kernel records a timeout in *err and carries
 // on (the host reports KP_ETIMEOUT).
 
+// Grid-wide barrier of the persistent kernel: a 64-bit arrival counter that only grows.  Each
+// barrier adds exactly gridDim.x, so at the start of every barrier the counter is a multiple
+// of gridDim.x; a block's arrival returns the old value, from which it knows the count that
+// ends this barrier, and waits until the counter reaches it.  One atomic per block and no
+// reset.  The wait is bounded (about one second of clock64); on timeout the block sets *err
+// and continues, and the solver reports KP_ETIMEOUT (the counter is cleared before each solve).
 struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
+    unsigned long long count;
 };
 
 __device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &b->gen;
-        const unsigned int g = *vgen;
         __threadfence();
-        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*vgen == g) {
-                if (clock64() - t0 > 2000000000LL) {   // about one second at GB300 clocks
-                    atomicExch(err, 1);
-                    break;
-                }
+        unsigned long long old;
+        asm volatile("atom.add.relaxed.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(&b->count) : "memory");
+        const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned long long cur;
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(&b->count) : "memory");
+            if (cur >= target) break;
+            if (clock64() - t0 > 2000000000LL) {   // about one second at GB300 clocks
+                atomicExch(err, 1);
+                break;
             }
         }
         __threadfence();

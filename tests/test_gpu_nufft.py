@@ -114,7 +114,7 @@ def test_invalid_params_rejected():
         Plan((30, 32), 2, 100, wavelet_levels=3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("chunk", [256, 1024])
 def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
     """Every spreading kernel variant and work-item size (fixed through the tuning overrides)
