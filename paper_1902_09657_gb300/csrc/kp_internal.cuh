@@ -291,7 +291,11 @@ kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, con
 kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st);
 kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st);
 // A^H u: u [C][M] (sorted order if perm == nullptr, else user order) -> grid -> x.
-kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st);
+// splits_zeroed: the split tiles' regions of d_grid2 are already zero (the fused primal kernel
+// clears them after its last read of d_grid2, and solve set-up clears them once)
+kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st,
+                          bool splits_zeroed = false);
+kp_status zero_split_only(kp_plan p, cudaStream_t st);
 kp_status grid_to_image(kp_plan p, float2* x, cudaStream_t st);
 kp_status autotune_spread(kp_plan p, cudaStream_t st);
 kp_status adjoint_primal(kp_plan p, int reg, float lambda, cudaStream_t st);

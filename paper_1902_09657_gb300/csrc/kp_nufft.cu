@@ -1022,17 +1022,24 @@ static kp_status launch_spread_priv(kp_plan p, const UT* u, const int* perm, cud
     return KP_OK;
 }
 
-kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st) {
+kp_status zero_split_only(kp_plan p, cudaStream_t st) {
     const Geom& g = p->geo;
     int P = 1;
     for (int d = 0; d < g.D; ++d) P *= p->tiles.ts[d];
-    mark(p, PH_SPREAD, st);
     if (p->n_split > 0) {
         KP_DISPATCH_D(g.D, DD, k_zero_split<DD><<<(unsigned)p->n_split, 256, 0, st>>>(p->d_split, g, p->tiles, P,
                                                                                       p->d_grid2));
         KP_LAUNCH_CHECK();
         p->launches += 1;
     }
+    return KP_OK;
+}
+
+kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st,
+                          bool splits_zeroed) {
+    const Geom& g = p->geo;
+    mark(p, PH_SPREAD, st);
+    if (!splits_zeroed) KP_TRY(zero_split_only(p, st));
     p->launches += 1;
     if (p->spread_variant == 0 || p->spread_variant >= 3) {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,

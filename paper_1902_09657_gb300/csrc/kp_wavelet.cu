@@ -605,6 +605,10 @@ struct PrimalArgs {
     int* iter;
     float lambda;
     int levels;
+    float2* grid2w;        // the same grid, written: split spreading tiles cleared once read
+    const int* split;
+    int n_split;
+    Tiles tiles;
     GridBarrier* bar;
     int* err;
 };
@@ -651,6 +655,37 @@ __device__ __forceinline__ LevelArgs level_args(const PrimalArgs& a, int lev, bo
 
 constexpr int PF_THREADS = 512;
 
+// Clears the split spreading tiles' regions of grid2 (all coils), CTA-strided over tiles, so
+// the next spread can accumulate into them without a separate clearing kernel.
+template <int D>
+__device__ void zero_split_tiles(const PrimalArgs& a) {
+    const Geom& g = a.geo;
+    const Tiles& tl = a.tiles;
+    int P = 1;
+    for (int d = 0; d < D; ++d) P *= tl.ts[d];
+    for (int t = blockIdx.x; t < a.n_split; t += gridDim.x) {
+        int r = a.split[t], o[MAXD], e[MAXD];
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            e[d] = min(tl.ts[d], g.g[d] - o[d]);
+        }
+        for (int i = threadIdx.x; i < g.C * P; i += blockDim.x) {
+            const int c = i / P;
+            int rr = i - c * P, lidx[MAXD];
+            for (int d = D - 1; d >= 0; --d) { lidx[d] = rr % tl.ts[d]; rr /= tl.ts[d]; }
+            bool in = true;
+            int64_t gflat = 0;
+            for (int d = 0; d < D; ++d) {
+                if (lidx[d] >= e[d]) in = false;
+                gflat = gflat * g.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], g.g[d]);
+            }
+            if (in) a.grid2w[(size_t)c * g.G + gflat] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
 template <int D, int T, typename MT, int REG>
 __global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
     extern __shared__ float2 sm[];
@@ -675,6 +710,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
     }
     if (REG == 1) {
         grid_barrier(a.bar, a.err);
+        zero_split_tiles<D>(a);   // grid2 has been read by every block
         for (int lev = 0; lev < a.levels; ++lev) {
             const LevelArgs la = level_args<D, T>(a, lev, true, k);
             for (int t = blockIdx.x; t < la.tiles_total; t += gridDim.x) fwd_level_tile<D, T>(la, t, sm);
@@ -686,7 +722,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
             if (lev > 0) grid_barrier(a.bar, a.err);
         }
     }
-    grid_barrier(a.bar, a.err);   // every block has read the iteration counter
+    grid_barrier(a.bar, a.err);   // every block has read the iteration counter (and grid2)
+    if (REG == 0) zero_split_tiles<D>(a);
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.iter = k + 1;
 }
 
@@ -749,6 +786,10 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st) {
     a.iter = p->d_iter;
     a.lambda = lambda;
     a.levels = p->P.wavelet_levels;
+    a.grid2w = p->d_grid2;
+    a.split = p->d_split;
+    a.n_split = (int)p->n_split;
+    a.tiles = p->tiles;
     a.bar = (GridBarrier*)p->d_bar;
     a.err = p->d_flag + 3;
     mark(p, PH_ADJ, st);
