@@ -209,7 +209,8 @@ struct kp_plan_s {
     int chunk = 256;                 // samples per interpolation work item
     int spread_chunk = 256;          // samples per spreading work item (autotuned, multiple of 256)
     int spread_variant = 0;          // 0/3/4/5: warp-private tiles (coils x warps 4x4, 2x8, 1x8, 2x4);
-                                     // 1: shared atomics, 16 coils per CTA; 2: each warp owns 4 coils
+                                     // 1: shared atomics, 16 coils per CTA; 2: each warp owns 4 coils;
+                                     // 6/7: warp-private interleaved coil pairs, 4 coils x 4 / 8 warps
     bool spread_tuned = false;
     int4* d_iitems = nullptr;        // interpolation work items {tile, begin, end, -1} over d_off ranges
     int64_t n_iitems = 0, iitems_cap = 0;

@@ -538,6 +538,322 @@ k_spread(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __
     }
 }
 
+// Variant with interleaved complex storage: each warp's private tile copy holds, per grid
+// point, the 4 coils of the CTA's group as two float4 (coil pairs), so a tap is one 128-bit
+// load, four FMAs and one 128-bit store for two coils.  Rows are padded to 16 (mod 128) bytes
+// so that the 8 lanes of each quarter-warp (two rows x four consecutive points) fall on
+// distinct banks.  2D lanes: (coil pair, ta, tb); 3D lanes: (ta0, tb, tc), two taps and both
+// coil pairs each.
+template <int D> struct SpV;
+template <> struct SpV<2> {
+    static constexpr int ROW = 33;                 // float4 per row: 16 points x 2 pairs + 1 pad
+    static constexpr int COPY = 16 * ROW;          // float4 per private copy
+    __device__ static int idx(int l0, int l1, int, int k) { return l0 * ROW + l1 * 2 + k; }
+};
+template <> struct SpV<3> {
+    static constexpr int ROW = 17;                 // 8 points x 2 pairs + 1 pad
+    static constexpr int PLANE = 8 * ROW;
+    static constexpr int COPY = 8 * PLANE;
+    __device__ static int idx(int l0, int l1, int l2, int k) { return l0 * PLANE + l1 * ROW + l2 * 2 + k; }
+};
+
+template <int D, int NW>
+static size_t spread_v_smem() {
+    return (size_t)NW * SpV<D>::COPY * sizeof(float4) +
+           (size_t)SP_CHUNK * (4 * sizeof(float2) + D * KW * sizeof(float) + D * sizeof(int));
+}
+
+template <int D, typename UT, int NW>
+__global__ void __launch_bounds__(NW * 32)
+k_spread_v(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+           const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
+           Tiles tl, float2* __restrict__ grid) {
+    using LV = SpV<D>;
+    extern __shared__ __align__(16) float4 smv[];
+    float4* acc = smv;                                              // [NW][COPY]
+    float4* su4 = acc + NW * LV::COPY;                              // [SP_CHUNK][2] coil pairs
+    float* sw = (float*)(su4 + SP_CHUNK * 2);                       // [SP_CHUNK][D][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D]
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z;
+    const bool split = it.w >= 0;
+    const int c0 = blockIdx.y * 4;
+    const int cc = min(4, geo.C - c0);
+    int o[MAXD], e[MAXD];
+    {
+        int r = tile;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            e[d] = min(tl.ts[d], geo.g[d] - o[d]);
+        }
+    }
+    for (int i = threadIdx.x; i < NW * LV::COPY; i += blockDim.x) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* my = acc + warp * LV::COPY;
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {
+        const int n = min(SP_CHUNK, end - sb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = ext[sb + i];
+            const int64_t un = perm ? perm[s] : s;
+            float2 uc[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) uc[c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
+            su4[i * 2] = make_float4(uc[0].x, uc[0].y, uc[1].x, uc[1].y);
+            su4[i * 2 + 1] = make_float4(uc[2].x, uc[2].y, uc[3].x, uc[3].y);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+                unsigned pk = 0;
+#pragma unroll
+                for (int j = 0; j < KW; ++j) {
+                    int pp = p0 + j;
+                    if (pp >= geo.g[d]) pp -= geo.g[d];
+                    const int l = pp - o[d];
+                    const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
+                    pk |= byte << (8 * j);
+                    sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+                }
+                sp[i * D + d] = pk;
+            }
+        }
+        __syncthreads();
+        if (D == 2) {
+            const int k = lane >> 4, ta = (lane >> 2) & 3, tb = lane & 3;
+            for (int i = warp; i < n; i += NW) {
+                const int la = (int)(signed char)(sp[i * D] >> (8 * ta));
+                const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+                if (la >= 0 && lb >= 0) {
+                    const float w = sw[(i * D) * KW + ta] * sw[(i * D + 1) * KW + tb];
+                    const float4 uv = su4[i * 2 + k];
+                    float4* a = my + LV::idx(la, lb, 0, k);
+                    float4 v = *a;
+                    v.x = fmaf(w, uv.x, v.x); v.y = fmaf(w, uv.y, v.y);
+                    v.z = fmaf(w, uv.z, v.z); v.w = fmaf(w, uv.w, v.w);
+                    *a = v;
+                }
+                __syncwarp();
+            }
+        } else {
+            const int ta0 = lane >> 4, tb = (lane >> 2) & 3, tc = lane & 3;   // taps (ta0 + 2m, tb, tc)
+            for (int i = warp; i < n; i += NW) {
+                const int lb = (int)(signed char)(sp[i * D + 1] >> (8 * tb));
+                const int lc = (int)(signed char)(sp[i * D + 2] >> (8 * tc));
+                const int laA = (int)(signed char)(sp[i * D] >> (8 * ta0));
+                const int laB = (int)(signed char)(sp[i * D] >> (8 * (ta0 + 2)));
+                const bool inbc = lb >= 0 && lc >= 0;
+                const bool okA = inbc && laA >= 0, okB = inbc && laB >= 0;
+                if (okA || okB) {
+                    const float wbc = sw[(i * D + 1) * KW + tb] * sw[(i * D + 2) * KW + tc];
+                    const float wA = sw[(i * D) * KW + ta0] * wbc, wB = sw[(i * D) * KW + ta0 + 2] * wbc;
+                    const float4 u0 = su4[i * 2], u1 = su4[i * 2 + 1];
+                    float4* aA = my + LV::idx(okA ? laA : 0, lb, lc, 0);
+                    float4* aB = my + LV::idx(okB ? laB : 0, lb, lc, 0);
+                    float4 vA0, vA1, vB0, vB1;
+                    if (okA) { vA0 = aA[0]; vA1 = aA[1]; }
+                    if (okB) { vB0 = aB[0]; vB1 = aB[1]; }
+                    if (okA) {
+                        vA0.x = fmaf(wA, u0.x, vA0.x); vA0.y = fmaf(wA, u0.y, vA0.y);
+                        vA0.z = fmaf(wA, u0.z, vA0.z); vA0.w = fmaf(wA, u0.w, vA0.w);
+                        vA1.x = fmaf(wA, u1.x, vA1.x); vA1.y = fmaf(wA, u1.y, vA1.y);
+                        vA1.z = fmaf(wA, u1.z, vA1.z); vA1.w = fmaf(wA, u1.w, vA1.w);
+                        aA[0] = vA0; aA[1] = vA1;
+                    }
+                    if (okB) {
+                        vB0.x = fmaf(wB, u0.x, vB0.x); vB0.y = fmaf(wB, u0.y, vB0.y);
+                        vB0.z = fmaf(wB, u0.z, vB0.z); vB0.w = fmaf(wB, u0.w, vB0.w);
+                        vB1.x = fmaf(wB, u1.x, vB1.x); vB1.y = fmaf(wB, u1.y, vB1.y);
+                        vB1.z = fmaf(wB, u1.z, vB1.z); vB1.w = fmaf(wB, u1.w, vB1.w);
+                        aB[0] = vB0; aB[1] = vB1;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    // sum the private copies; one thread per (point, coil pair)
+    int P = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) P *= tl.ts[d];
+    const int npair = (cc + 1) / 2;
+    for (int i = threadIdx.x; i < npair * P; i += blockDim.x) {
+        const int k = i / P;
+        int r = i - k * P;
+        int lidx[MAXD];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
+        bool in = true;
+        int64_t gflat = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (lidx[d] >= e[d]) in = false;
+            gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
+        }
+        if (!in) continue;
+        const int li = D == 2 ? LV::idx(lidx[0], lidx[D - 1], 0, k) : LV::idx(lidx[0], lidx[1 % D], lidx[D - 1], k);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const float4 t = acc[w * LV::COPY + li];
+            v.x += t.x; v.y += t.y; v.z += t.z; v.w += t.w;
+        }
+        const int ca = c0 + 2 * k;
+        float2* d0 = grid + (size_t)ca * geo.G + gflat;
+        float2* d1 = d0 + geo.G;
+        const bool has1 = 2 * k + 1 < cc;
+        if (split) {
+            atomicAdd(&d0->x, v.x);
+            atomicAdd(&d0->y, v.y);
+            if (has1) { atomicAdd(&d1->x, v.z); atomicAdd(&d1->y, v.w); }
+        } else {
+            *d0 = make_float2(v.x, v.y);
+            if (has1) *d1 = make_float2(v.z, v.w);
+        }
+    }
+}
+
+// 3D variant in which warp w owns z-plane w of a single accumulator (8 warps, tile depth at
+// most 8): every warp walks every staged sample and applies only the taps in its own plane
+// (at most one of a sample's four z taps), so no two warps touch the same address and there
+// are no private copies to clear and sum.  CG coils per CTA, stored per grid point as CG/2
+// float4 coil pairs; lanes (ty, tx, h) take one (y, x) tap each and coil pairs h (CG = 4) or
+// 2h, 2h + 1 (CG = 8).  For CG = 8 the pair slot is XOR-swizzled with bit 1 of x so that each
+// quarter-warp (four consecutive x, two h) reads eight distinct 16-byte bank groups.
+template <int CG> struct SpZ {
+    static constexpr int NP = CG / 2;              // float4 per grid point
+    static constexpr int COPY = 512 * NP;
+    __device__ static int idx(int z, int y, int x, int k) {
+        const int slot = CG == 8 ? (k ^ ((x >> 1) & 1)) : k;
+        return ((z * 8 + y) * 8 + x) * NP + slot;
+    }
+};
+
+template <int CG>
+static size_t spread_z_smem() {
+    return (size_t)SpZ<CG>::COPY * sizeof(float4) + (size_t)SP_CHUNK * (CG * sizeof(float2) + 3 * KW * sizeof(float) + 3 * sizeof(int));
+}
+
+template <typename UT, int CG>
+__global__ void __launch_bounds__(256)
+k_spread_z(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+           const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
+           Tiles tl, float2* __restrict__ grid) {
+    constexpr int D = 3, NP = CG / 2;
+    using LZ = SpZ<CG>;
+    extern __shared__ __align__(16) float4 smz[];
+    float4* acc = smz;                                              // [8][8][8][NP]
+    float4* su4 = acc + LZ::COPY;                                   // [SP_CHUNK][NP]
+    float* sw = (float*)(su4 + SP_CHUNK * NP);                      // [SP_CHUNK][3][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][3]
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z;
+    const bool split = it.w >= 0;
+    const int c0 = blockIdx.y * CG;
+    const int cc = min(CG, geo.C - c0);
+    int o[MAXD], e[MAXD];
+    {
+        int r = tile;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            e[d] = min(tl.ts[d], geo.g[d] - o[d]);
+        }
+    }
+    for (int i = threadIdx.x; i < LZ::COPY; i += blockDim.x) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ty = lane >> 3, tx = (lane >> 1) & 3, h = lane & 1;
+    const unsigned wz4 = (unsigned)warp * 0x01010101u;
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {
+        const int n = min(SP_CHUNK, end - sb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = ext[sb + i];
+            const int64_t un = perm ? perm[s] : s;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 ua = 2 * k < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k) * geo.M + un) : make_float2(0.f, 0.f);
+                const float2 ub = 2 * k + 1 < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k + 1) * geo.M + un) : make_float2(0.f, 0.f);
+                su4[i * NP + k] = make_float4(ua.x, ua.y, ub.x, ub.y);
+            }
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
+                unsigned pk = 0;
+#pragma unroll
+                for (int j = 0; j < KW; ++j) {
+                    int pp = p0 + j;
+                    if (pp >= geo.g[d]) pp -= geo.g[d];
+                    const int l = pp - o[d];
+                    const unsigned byte = (l >= 0 && l < e[d]) ? (unsigned)l : 0xFFu;
+                    pk |= byte << (8 * j);
+                    sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+                }
+                sp[i * D + d] = pk;
+            }
+        }
+        __syncthreads();
+        for (int i = 0; i < n; ++i) {
+            const unsigned mz = __vcmpeq4(sp[i * D], wz4);      // which z tap lies in my plane
+            if (mz == 0) continue;                              // warp-uniform
+            const int jz = (__ffs((int)mz) - 1) >> 3;
+            const int ly = (int)(signed char)(sp[i * D + 1] >> (8 * ty));
+            const int lx = (int)(signed char)(sp[i * D + 2] >> (8 * tx));
+            if (ly >= 0 && lx >= 0) {
+                const float w = sw[(i * D) * KW + jz] * sw[(i * D + 1) * KW + ty] * sw[(i * D + 2) * KW + tx];
+#pragma unroll
+                for (int j = 0; j < NP / 2; ++j) {
+                    const int k = (NP / 2) * h + j;
+                    const float4 uv = su4[i * NP + k];
+                    float4* a = acc + LZ::idx(warp, ly, lx, k);
+                    float4 v = *a;
+                    v.x = fmaf(w, uv.x, v.x); v.y = fmaf(w, uv.y, v.y);
+                    v.z = fmaf(w, uv.z, v.z); v.w = fmaf(w, uv.w, v.w);
+                    *a = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    int P = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) P *= tl.ts[d];
+    const int npair = (cc + 1) / 2;
+    for (int i = threadIdx.x; i < npair * P; i += blockDim.x) {
+        const int k = i / P;
+        int r = i - k * P;
+        int lidx[MAXD];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) { lidx[d] = r % tl.ts[d]; r /= tl.ts[d]; }
+        bool in = true;
+        int64_t gflat = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (lidx[d] >= e[d]) in = false;
+            gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
+        }
+        if (!in) continue;
+        const float4 v = acc[LZ::idx(lidx[0], lidx[1], lidx[2], k)];
+        const int ca = c0 + 2 * k;
+        float2* d0 = grid + (size_t)ca * geo.G + gflat;
+        float2* d1 = d0 + geo.G;
+        const bool has1 = 2 * k + 1 < cc;
+        if (split) {
+            atomicAdd(&d0->x, v.x);
+            atomicAdd(&d0->y, v.y);
+            if (has1) { atomicAdd(&d1->x, v.z); atomicAdd(&d1->y, v.w); }
+        } else {
+            *d0 = make_float2(v.x, v.y);
+            if (has1) *d1 = make_float2(v.z, v.w);
+        }
+    }
+}
+
 // Variant with one shared accumulator per CTA and up to SPA_CH coils per CTA (one coil group
 // for C <= 16): the tap geometry of a sample is staged once for all its coils and the lanes
 // add with shared-memory atomics (a warp's lanes cover distinct (tap, coil) addresses; only
@@ -1007,6 +1323,37 @@ kp_status interp_dual_only(kp_plan p, cudaStream_t st) {
     return launch_interp<2>(p, p->ys_t, io, st);
 }
 
+// Interleaved-pair spreading with NW warps (variants 6, 7).
+template <int D, typename UT, int NW>
+static kp_status launch_spread_v(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
+    static bool attr = false;
+    const size_t sm = spread_v_smem<D, NW>();
+    if (!attr) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_v<D, UT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    const Geom& g = p->geo;
+    k_spread_v<D, UT, NW><<<dim3((unsigned)p->n_items, (g.C + 3) / 4), NW * 32, sm, st>>>(
+        p->d_k0, p->d_wt, u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2);
+    return KP_OK;
+}
+
+// Plane-owner spreading, 3D only (variants 8, 9).
+template <int D, typename UT, int CG>
+static kp_status launch_spread_z(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
+    if (D != 3) { set_error("spreading variants 8 and 9 are 3D only"); return KP_EINTERNAL; }
+    static bool attr = false;
+    const size_t sm = spread_z_smem<CG>();
+    if (!attr) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_z<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    const Geom& g = p->geo;
+    k_spread_z<UT, CG><<<dim3((unsigned)p->n_items, (g.C + CG - 1) / CG), 256, sm, st>>>(
+        p->d_k0, p->d_wt, u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2);
+    return KP_OK;
+}
+
 // Private-copy spreading with CH coils per CTA and NW warps (variants 0, 3, 4, 5).
 template <int D, typename UT, int CH, int NW>
 static kp_status launch_spread_priv(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
@@ -1047,6 +1394,10 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
                 case 0: KP_TRY((launch_spread_priv<DD, UT, 4, 4>(p, (const UT*)u, perm, st))); break;
                 case 3: KP_TRY((launch_spread_priv<DD, UT, 2, 8>(p, (const UT*)u, perm, st))); break;
                 case 4: KP_TRY((launch_spread_priv<DD, UT, 1, 8>(p, (const UT*)u, perm, st))); break;
+                case 6: KP_TRY((launch_spread_v<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
+                case 7: KP_TRY((launch_spread_v<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
+                case 8: KP_TRY((launch_spread_z<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
+                case 9: KP_TRY((launch_spread_z<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
                 default: KP_TRY((launch_spread_priv<DD, UT, 2, 4>(p, (const UT*)u, perm, st))); break;
             }));
     } else if (p->spread_variant == 2) {
@@ -1082,7 +1433,8 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
 // on the plan's own work items (values do not affect the cost; once per plan, at its first
 // trajectory).  Variants: 0 private copies, 4 coils x 4 warps; 1 shared atomics; 2 warp per
 // 4 coils; 3 private, 2 coils x 8 warps; 4 private, 1 coil x 8 warps; 5 private, 2 coils x 4
-// warps.  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
+// warps; 6, 7 private interleaved coil pairs, 4 coils x 4 / 8 warps; 8, 9 (3D) z-plane owners,
+// 8 / 4 coils.  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
 kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (p->spread_tuned) return KP_OK;
     int force_v = -1, force_c = 0;
@@ -1090,14 +1442,14 @@ kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (const char* ev = getenv("KPDHG_SPREAD_CHUNK")) force_c = atoi(ev);
     const Geom& g = p->geo;
     const bool wc_ok = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024;
-    if (force_v > 5 || (force_v == 2 && !wc_ok)) force_v = -1;
+    if (force_v > 9 || (force_v == 2 && !wc_ok) || (force_v >= 8 && g.D != 3)) force_v = -1;
     if (force_c < SP_CHUNK || force_c % SP_CHUNK != 0) force_c = 0;
     std::vector<int> chunks;
     if (force_c) chunks.push_back(force_c);
     else chunks = {256, 1024, 4096};
     std::vector<int> variants;
     if (force_v >= 0) variants.push_back(force_v);
-    else for (int v = 0; v <= 5; ++v) if (v != 2 || wc_ok) variants.push_back(v);
+    else for (int v = 0; v <= 9; ++v) if ((v != 2 || wc_ok) && (v < 8 || g.D == 3)) variants.push_back(v);
     if (chunks.size() == 1 && variants.size() == 1) {
         p->spread_variant = variants[0];
         if (chunks[0] != p->spread_chunk) KP_TRY(build_spread_items(p, chunks[0], st));
