@@ -206,14 +206,22 @@ struct kp_plan_s {
     int64_t n_split = 0, split_cap = 0;
     int* d_k0 = nullptr;             // [D][M] wrapped first tap per sorted sample
     float* d_wt = nullptr;           // [D * W][M] Kaiser-Bessel weights per sorted sample
-    int chunk = 256;                 // samples per interpolation work item
+    int chunk = 256;                 // samples per interpolation work item (<= its block size)
     int spread_chunk = 256;          // samples per spreading work item (autotuned, multiple of 256)
     int spread_variant = 0;          // 0/3/4/5: warp-private tiles (coils x warps 4x4, 2x8, 1x8, 2x4);
                                      // 1: shared atomics, 16 coils per CTA; 2: each warp owns 4 coils;
-                                     // 6/7: warp-private interleaved coil pairs, 4 coils x 4 / 8 warps
+                                     // 6/7: warp-private interleaved coil pairs, 4 coils x 4 / 8 warps;
+                                     // 8/9: 3D z-plane owners; 10/11: 3D two-phase (padded tiles + gather)
     bool spread_tuned = false;
     int4* d_iitems = nullptr;        // interpolation work items {tile, begin, end, -1} over d_off ranges
     int64_t n_iitems = 0, iitems_cap = 0;
+    // two-phase 3D spreading (variants 10, 11): own-sample items, one padded-tile slot each
+    int4* d_oitems = nullptr;        // {tile, begin, end, slot} over d_off ranges, at most own_chunk samples
+    int64_t n_oitems = 0, oitems_cap = 0;
+    int* d_tslot = nullptr;          // [ntiles + 1] first slot of each tile
+    float2* d_halo = nullptr;        // [slot][C][(TS + W - 1)^3] padded tile sums
+    size_t halo_cap = 0;             // complex values allocated
+    int own_chunk = 4096;
 
     // operator data
     void* d_maps = nullptr;          // [C][N] in maps_t storage
@@ -310,6 +318,7 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st);
+kp_status build_own_items(kp_plan p, cudaStream_t st);
 kp_status make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st);
 kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);

@@ -275,18 +275,19 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
             pos += n;
         }
     }
-    if (!mbar_wait_bounded(&bar, 0)) {
-        if (io.flag) atomicExch(io.flag, 1);
-        mbar_wait_bounded(&bar, 0);      // copies still in flight land in this CTA's memory
-        return;
-    }
     constexpr int rs0 = D == 2 ? LY::RP : R * LY::RP, rs1 = D == 2 ? 1 : LY::RP;
     constexpr int Rtot = LY::PER_COIL;
+    // While the grid region is in flight: this thread's sample (items hold at most blockDim.x
+    // samples), its tap tables and, for the dual step in 2D, its y, p and u.
+    const int s = beg + (int)threadIdx.x;
+    const bool act = s < end;
+    float w[D][KW];
+    int lb = xo;
+    constexpr bool PRE = MODE == 2 && D == 2;     // 3D keeps registers for the 64 taps
+    float2 yv[PRE ? IP_CH : 1], uv[PRE ? IP_CH : 1];
+    float pv[PRE ? IP_CH : 1];
     float sigma = 0.f;
-    if (MODE == 2) sigma = io.sched[3 * (*io.iter)];
-    for (int s = beg + threadIdx.x; s < end; s += blockDim.x) {
-        float w[D][KW];
-        int lb = xo;
+    if (act) {
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
@@ -294,51 +295,71 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
 #pragma unroll
             for (int j = 0; j < KW; ++j) w[d][j] = wt[(int64_t)(d * KW + j) * geo.M + s];
         }
-        for (int c = 0; c < cc; ++c) {
-            const float2* base = sg + c * Rtot + lb;
-            float2 acc = make_float2(0.f, 0.f);
-            if (D == 2) {
+        if (MODE == 2) sigma = io.sched[3 * (*io.iter)];
+        if (PRE) {
 #pragma unroll
-                for (int a = 0; a < KW; ++a)
+            for (int c = 0; c < IP_CH; ++c) {
+                if (c < cc) {
+                    const size_t os = (size_t)(c0 + c) * geo.M + s;
+                    yv[c] = ldc<T>((const T*)io.ys, os);
+                    pv[c] = io.ps[os];
+                    uv[c] = io.u[os];
+                }
+            }
+        }
+    }
+    if (!mbar_wait_bounded(&bar, 0)) {
+        if (io.flag) atomicExch(io.flag, 1);
+        mbar_wait_bounded(&bar, 0);      // copies still in flight land in this CTA's memory
+        return;
+    }
+    if (!act) return;
 #pragma unroll
-                    for (int b = 0; b < KW; ++b) {
-                        const float ww = w[0][a] * w[D - 1][b];
-                        const float2 v = base[a * rs0 + b];
+    for (int c = 0; c < IP_CH; ++c) {
+        if (c >= cc) break;
+        const float2* base = sg + c * Rtot + lb;
+        float2 acc = make_float2(0.f, 0.f);
+        if (D == 2) {
+#pragma unroll
+            for (int a = 0; a < KW; ++a)
+#pragma unroll
+                for (int b = 0; b < KW; ++b) {
+                    const float ww = w[0][a] * w[D - 1][b];
+                    const float2 v = base[a * rs0 + b];
+                    acc.x = fmaf(ww, v.x, acc.x);
+                    acc.y = fmaf(ww, v.y, acc.y);
+                }
+        } else {
+#pragma unroll
+            for (int a = 0; a < KW; ++a)
+#pragma unroll
+                for (int b = 0; b < KW; ++b) {
+                    const float wab = w[0][a] * w[1 % D][b];
+#pragma unroll
+                    for (int e = 0; e < KW; ++e) {
+                        const float ww = wab * w[D - 1][e];
+                        const float2 v = base[a * rs0 + b * rs1 + e];
                         acc.x = fmaf(ww, v.x, acc.x);
                         acc.y = fmaf(ww, v.y, acc.y);
                     }
-            } else {
-#pragma unroll
-                for (int a = 0; a < KW; ++a)
-#pragma unroll
-                    for (int b = 0; b < KW; ++b) {
-                        const float wab = w[0][a] * w[1 % D][b];
-#pragma unroll
-                        for (int e = 0; e < KW; ++e) {
-                            const float ww = wab * w[D - 1][e];
-                            const float2 v = base[a * rs0 + b * rs1 + e];
-                            acc.x = fmaf(ww, v.x, acc.x);
-                            acc.y = fmaf(ww, v.y, acc.y);
-                        }
-                    }
-            }
-            acc.x *= geo.rsqrtN;
-            acc.y *= geo.rsqrtN;
-            const size_t os = (size_t)(c0 + c) * geo.M + s;
-            if (MODE == 0) {
-                const int64_t oi = io.perm ? io.perm[s] : s;
-                stc<T>((T*)io.out, (size_t)(c0 + c) * geo.M + oi, acc);
-            } else if (MODE == 1) {
-                const float sc = io.ps ? io.ps[os] : 1.f;
-                io.outs[os] = make_float2(acc.x * sc, acc.y * sc);
-            } else {
-                // PDHG dual step (Sec. 4.1): u <- (u + sigma p (A xbar - y)) / (1 + sigma p)
-                const float2 y = ldc<T>((const T*)io.ys, os);
-                const float sp = sigma * io.ps[os];
-                const float inv = 1.f / (1.f + sp);
-                const float2 uo = io.u[os];
-                io.u[os] = make_float2((uo.x + sp * (acc.x - y.x)) * inv, (uo.y + sp * (acc.y - y.y)) * inv);
-            }
+                }
+        }
+        acc.x *= geo.rsqrtN;
+        acc.y *= geo.rsqrtN;
+        const size_t os = (size_t)(c0 + c) * geo.M + s;
+        if (MODE == 0) {
+            const int64_t oi = io.perm ? io.perm[s] : s;
+            stc<T>((T*)io.out, (size_t)(c0 + c) * geo.M + oi, acc);
+        } else if (MODE == 1) {
+            const float sc = io.ps ? io.ps[os] : 1.f;
+            io.outs[os] = make_float2(acc.x * sc, acc.y * sc);
+        } else {
+            // PDHG dual step (Sec. 4.1): u <- (u + sigma p (A xbar - y)) / (1 + sigma p)
+            const float2 y = PRE ? yv[PRE ? c : 0] : ldc<T>((const T*)io.ys, os);
+            const float sp = sigma * (PRE ? pv[PRE ? c : 0] : io.ps[os]);
+            const float inv = 1.f / (1.f + sp);
+            const float2 uo = PRE ? uv[PRE ? c : 0] : io.u[os];
+            io.u[os] = make_float2((uo.x + sp * (acc.x - y.x)) * inv, (uo.y + sp * (acc.y - y.y)) * inv);
         }
     }
 }
@@ -854,6 +875,164 @@ k_spread_z(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* 
     }
 }
 
+// Two-phase 3D spreading (variants 10, 11).  Phase A: one CTA per own-sample item (samples
+// whose first tap lies in the tile, contiguous in sorted order) accumulates every tap of each
+// sample once into a padded tile of (8 + W - 1)^3 points in shared memory (no tap falls
+// outside it, so every lane works), warp w owning the padded z-planes congruent to w mod 8 (a
+// sample's four consecutive z taps meet each residue at most once), and writes the padded
+// tile to its slot.  Phase B: every grid point gathers its tile's slots and, for points within
+// W - 1 of a tile's low edge, the high-side halos of the lower neighbours' slots (periodic),
+// and stores the sum: no atomics, no clearing, and the sum order is fixed.
+constexpr int PT = 8 + KW - 1;                 // padded tile edge
+constexpr int PT3 = PT * PT * PT;
+
+template <int CG> struct SpO {
+    static constexpr int NP = CG / 2;
+    static constexpr int COPY = PT3 * NP;
+    __device__ static int idx(int z, int y, int x, int k) {
+        const int slot = CG == 8 ? (k ^ ((x >> 1) & 1)) : k;
+        return ((z * PT + y) * PT + x) * NP + slot;
+    }
+};
+
+template <int CG>
+static size_t spread_own_smem() {
+    return (size_t)SpO<CG>::COPY * sizeof(float4) + (size_t)SP_CHUNK * (CG * sizeof(float2) + 3 * KW * sizeof(float) + sizeof(int));
+}
+
+template <typename UT, int CG>
+__global__ void __launch_bounds__(256)
+k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+             const int* __restrict__ perm, const int4* __restrict__ items, Geom geo, Tiles tl,
+             float2* __restrict__ halo) {
+    constexpr int D = 3, NP = CG / 2;
+    using LO = SpO<CG>;
+    extern __shared__ __align__(16) float4 smo[];
+    float4* acc = smo;                                              // [PT][PT][PT][NP]
+    float4* su4 = acc + LO::COPY;                                   // [SP_CHUNK][NP]
+    float* sw = (float*)(su4 + SP_CHUNK * NP);                      // [SP_CHUNK][3][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK] local first taps, one byte per axis
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z, slot = it.w;
+    const int c0 = blockIdx.y * CG;
+    const int cc = min(CG, geo.C - c0);
+    int o[MAXD];
+    {
+        int r = tile;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+        }
+    }
+    for (int i = threadIdx.x; i < LO::COPY; i += blockDim.x) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ty = lane >> 3, tx = (lane >> 1) & 3, h = lane & 1;
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {
+        const int n = min(SP_CHUNK, end - sb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = sb + i;
+            const int64_t un = perm ? perm[s] : s;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 ua = 2 * k < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k) * geo.M + un) : make_float2(0.f, 0.f);
+                const float2 ub = 2 * k + 1 < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k + 1) * geo.M + un) : make_float2(0.f, 0.f);
+                su4[i * NP + k] = make_float4(ua.x, ua.y, ub.x, ub.y);
+            }
+            unsigned pk = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int l0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];   // in [0, ts)
+                pk |= (unsigned)l0 << (8 * d);
+#pragma unroll
+                for (int j = 0; j < KW; ++j) sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+            }
+            sp[i] = pk;
+        }
+        __syncthreads();
+        for (int i = 0; i < n; ++i) {
+            const unsigned pk = sp[i];
+            int jz = warp - (int)(pk & 0xFFu);
+            if (jz < 0) jz += 8;
+            if (jz >= KW) continue;                             // warp-uniform
+            const int z = (int)(pk & 0xFFu) + jz;
+            const int y = (int)((pk >> 8) & 0xFFu) + ty;
+            const int x = (int)((pk >> 16) & 0xFFu) + tx;
+            const float w = sw[(i * D) * KW + jz] * sw[(i * D + 1) * KW + ty] * sw[(i * D + 2) * KW + tx];
+#pragma unroll
+            for (int j = 0; j < NP / 2; ++j) {
+                const int k = (NP / 2) * h + j;
+                const float4 uv = su4[i * NP + k];
+                float4* a = acc + LO::idx(z, y, x, k);
+                float4 v = *a;
+                v.x = fmaf(w, uv.x, v.x); v.y = fmaf(w, uv.y, v.y);
+                v.z = fmaf(w, uv.z, v.z); v.w = fmaf(w, uv.w, v.w);
+                *a = v;
+            }
+        }
+    }
+    __syncthreads();
+    // padded tile -> slot, coil-major: halo[(slot * C + c) * PT3 + point]
+    const int npair = (cc + 1) / 2;
+    for (int i = threadIdx.x; i < npair * PT3; i += blockDim.x) {
+        const int k = i / PT3, pt = i - k * PT3;
+        const int z = pt / (PT * PT), y = (pt / PT) % PT, x = pt % PT;
+        const float4 v = acc[LO::idx(z, y, x, k)];
+        float2* d0 = halo + ((size_t)slot * geo.C + c0 + 2 * k) * PT3 + pt;
+        *d0 = make_float2(v.x, v.y);
+        if (2 * k + 1 < cc) d0[PT3] = make_float2(v.z, v.w);
+    }
+}
+
+// Phase B: grid[c][q] = sum over the slots of q's tile and of the lower neighbours whose
+// padded halo covers q (periodic in every axis).
+__global__ void __launch_bounds__(256)
+k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
+              float2* __restrict__ grid) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)geo.C * geo.G) return;
+    const int c = (int)(idx / geo.G);
+    int64_t q = idx - (int64_t)c * geo.G;
+    int t[3], l[3];
+#pragma unroll
+    for (int d = 2; d >= 0; --d) {
+        const int k = (int)(q % geo.g[d]);
+        q /= geo.g[d];
+        const int p = tshift(k, tl.sh[d], geo.g[d]);
+        t[d] = p / tl.ts[d];
+        l[d] = p - t[d] * tl.ts[d];
+    }
+    float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        int tt[3], ll[3];
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if ((m >> (2 - d)) & 1) {
+                if (l[d] >= KW - 1) ok = false;
+                tt[d] = t[d] == 0 ? tl.nt[d] - 1 : t[d] - 1;
+                const int e = min(tl.ts[d], geo.g[d] - tt[d] * tl.ts[d]);
+                ll[d] = l[d] + e;
+            } else {
+                tt[d] = t[d];
+                ll[d] = l[d];
+            }
+        }
+        if (!ok) continue;
+        const int tile = (tt[0] * tl.nt[1] + tt[1]) * tl.nt[2] + tt[2];
+        const int pt = (ll[0] * PT + ll[1]) * PT + ll[2];
+        for (int sl = tslot[tile]; sl < tslot[tile + 1]; ++sl) {
+            const float2 v = halo[((size_t)sl * geo.C + c) * PT3 + pt];
+            sum.x += v.x;
+            sum.y += v.y;
+        }
+    }
+    grid[idx] = sum;
+}
+
 // Variant with one shared accumulator per CTA and up to SPA_CH coils per CTA (one coil group
 // for C <= 16): the tap geometry of a sample is staged once for all its coils and the lanes
 // add with shared-memory atomics (a warp's lanes cover distinct (tap, coil) addresses; only
@@ -1279,6 +1458,7 @@ static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaS
     mark(p, PH_INTERP, st);
     p->launches += 1;
     if (p->n_iitems == 0) return KP_OK;
+    if (p->chunk > IP_THREADS) { set_error("interpolation items larger than the block"); return KP_EINTERNAL; }
     KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(t, T,
         if (!attr[DD - 2][MODE][t]) {
             KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_tile<DD, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
@@ -1338,6 +1518,48 @@ static kp_status launch_spread_v(kp_plan p, const UT* u, const int* perm, cudaSt
     return KP_OK;
 }
 
+// Two-phase spreading, 3D only (variants 10, 11): padded tiles into the slots, then gather.
+template <int D, typename UT, int CG>
+static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
+    const Geom& g = p->geo;
+    if (D != 3 || !p->d_halo || p->halo_cap < (size_t)p->n_oitems * g.C * PT3) {
+        set_error("two-phase spreading needs a 3D plan with its slot storage");
+        return KP_EINTERNAL;
+    }
+    static bool attr = false;
+    const size_t sm = spread_own_smem<CG>();
+    if (!attr) {
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_own<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    if (p->n_oitems > 0)
+        k_spread_own<UT, CG><<<dim3((unsigned)p->n_oitems, (g.C + CG - 1) / CG), 256, sm, st>>>(
+            p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
+    KP_LAUNCH_CHECK();
+    const int64_t tot = (int64_t)g.C * g.G;
+    k_halo_gather<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    p->launches += 1;
+    return KP_OK;
+}
+
+// Allocates the slot storage of the two-phase variants if it fits a budget (a quarter of
+// the free device memory, at most 16 GiB); false when it does not.
+static bool ensure_halo(kp_plan p) {
+    const Geom& g = p->geo;
+    if (g.D != 3 || p->n_oitems == 0) return false;
+    const size_t need = (size_t)p->n_oitems * g.C * PT3;
+    if (p->d_halo && p->halo_cap >= need) return true;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
+    if (need * sizeof(float2) > std::min(fr / 4, (size_t)16 << 30)) return false;
+    if (p->d_halo) cudaFree(p->d_halo);
+    p->d_halo = nullptr;
+    p->halo_cap = 0;
+    if (cudaMalloc(&p->d_halo, need * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); p->d_halo = nullptr; return false; }
+    p->halo_cap = need;
+    return true;
+}
+
 // Plane-owner spreading, 3D only (variants 8, 9).
 template <int D, typename UT, int CG>
 static kp_status launch_spread_z(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
@@ -1386,7 +1608,7 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
                           bool splits_zeroed) {
     const Geom& g = p->geo;
     mark(p, PH_SPREAD, st);
-    if (!splits_zeroed) KP_TRY(zero_split_only(p, st));
+    if (!splits_zeroed && p->spread_variant < 10) KP_TRY(zero_split_only(p, st));   // 10, 11 store every point
     p->launches += 1;
     if (p->spread_variant == 0 || p->spread_variant >= 3) {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
@@ -1398,6 +1620,8 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
                 case 7: KP_TRY((launch_spread_v<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
                 case 8: KP_TRY((launch_spread_z<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
                 case 9: KP_TRY((launch_spread_z<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
+                case 10: KP_TRY((launch_spread_own<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
+                case 11: KP_TRY((launch_spread_own<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
                 default: KP_TRY((launch_spread_priv<DD, UT, 2, 4>(p, (const UT*)u, perm, st))); break;
             }));
     } else if (p->spread_variant == 2) {
@@ -1434,22 +1658,28 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
 // trajectory).  Variants: 0 private copies, 4 coils x 4 warps; 1 shared atomics; 2 warp per
 // 4 coils; 3 private, 2 coils x 8 warps; 4 private, 1 coil x 8 warps; 5 private, 2 coils x 4
 // warps; 6, 7 private interleaved coil pairs, 4 coils x 4 / 8 warps; 8, 9 (3D) z-plane owners,
-// 8 / 4 coils.  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
+// 8 / 4 coils; 10, 11 (3D) two-phase padded tiles + gather, 8 / 4 coils (when their slot
+// storage fits).  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
 kp_status autotune_spread(kp_plan p, cudaStream_t st) {
-    if (p->spread_tuned) return KP_OK;
+    if (p->spread_tuned) {
+        // a new trajectory may need more slots than the two-phase variants hold
+        if (p->spread_variant >= 10 && !ensure_halo(p)) p->spread_variant = 0;
+        return KP_OK;
+    }
     int force_v = -1, force_c = 0;
     if (const char* ev = getenv("KPDHG_SPREAD_VARIANT")) force_v = atoi(ev);   // tuning overrides
     if (const char* ev = getenv("KPDHG_SPREAD_CHUNK")) force_c = atoi(ev);
     const Geom& g = p->geo;
     const bool wc_ok = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024;
-    if (force_v > 9 || (force_v == 2 && !wc_ok) || (force_v >= 8 && g.D != 3)) force_v = -1;
+    const bool own_ok = g.D == 3 && ensure_halo(p);
+    if (force_v > 11 || (force_v == 2 && !wc_ok) || (force_v >= 8 && g.D != 3) || (force_v >= 10 && !own_ok)) force_v = -1;
     if (force_c < SP_CHUNK || force_c % SP_CHUNK != 0) force_c = 0;
     std::vector<int> chunks;
     if (force_c) chunks.push_back(force_c);
     else chunks = {256, 1024, 4096};
     std::vector<int> variants;
     if (force_v >= 0) variants.push_back(force_v);
-    else for (int v = 0; v <= 9; ++v) if ((v != 2 || wc_ok) && (v < 8 || g.D == 3)) variants.push_back(v);
+    else for (int v = 0; v <= 11; ++v) if ((v != 2 || wc_ok) && (v < 8 || g.D == 3) && (v < 10 || own_ok)) variants.push_back(v);
     if (chunks.size() == 1 && variants.size() == 1) {
         p->spread_variant = variants[0];
         if (chunks[0] != p->spread_chunk) KP_TRY(build_spread_items(p, chunks[0], st));
@@ -1469,6 +1699,7 @@ kp_status autotune_spread(kp_plan p, cudaStream_t st) {
         if (c != p->spread_chunk) status = build_spread_items(p, c, st);
         if (status != KP_OK) break;
         for (int v : variants) {
+            if (v >= 10 && c != chunks[0]) continue;   // the two-phase variants ignore the item size
             p->spread_variant = v;
             status = adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st);
             if (status != KP_OK) break;

@@ -173,6 +173,11 @@ __global__ void k_iitems(const int* __restrict__ off, const int* __restrict__ it
     }
 }
 
+__global__ void k_slot_ids(int4* __restrict__ items, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) items[i].w = (int)i;
+}
+
 __global__ void k_items(const int* __restrict__ ext_off, const int* __restrict__ item_off,
                         const int* __restrict__ slot_off, const int* __restrict__ nsl, int64_t ntiles, int chunk,
                         int4* __restrict__ items) {
@@ -372,7 +377,8 @@ kp_status plan_destroy_internal(kp_plan p) {
                     p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
                     p->d_grid2, p->d_gridF, p->d_bar, p->d_tape, p->d_bk,
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
-                    p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter};
+                    p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter,
+                    p->d_oitems, p->d_tslot, p->d_halo};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -423,6 +429,36 @@ kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st) {
     k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, chunk, p->d_items);
     KP_LAUNCH_CHECK();
     KP_TRY_CUDA(cudaStreamSynchronize(st));   // the host split list must outlive its copy
+    p->launches += 4;
+    return KP_OK;
+}
+
+// Own-sample items of the two-phase 3D spreading: each tile's own samples (those whose first
+// tap lies in it) cut into pieces of at most own_chunk; item i writes padded-tile slot i, and
+// d_tslot[t] is the first slot of tile t.  The slot storage itself is allocated on first use.
+kp_status build_own_items(kp_plan p, cudaStream_t st) {
+    const Tiles& tl = p->tiles;
+    const unsigned tb = nblk(tl.ntiles, 256);
+    if (!p->d_tslot) KP_TRY_CUDA(cudaMalloc(&p->d_tslot, (tl.ntiles + 1) * sizeof(int)));
+    k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->own_chunk, p->d_cnt);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_tslot, tl.ntiles);
+    KP_LAUNCH_CHECK();
+    int n = 0;
+    KP_TRY_CUDA(cudaMemcpyAsync(&n, p->d_tslot + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    p->n_oitems = n;
+    if (p->n_oitems > p->oitems_cap) {
+        if (p->d_oitems) cudaFree(p->d_oitems);
+        p->d_oitems = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&p->d_oitems, p->n_oitems * sizeof(int4)));
+        p->oitems_cap = p->n_oitems;
+    }
+    if (p->n_oitems > 0) {
+        k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_tslot, tl.ntiles, p->own_chunk, p->d_oitems);
+        KP_LAUNCH_CHECK();
+        k_slot_ids<<<nblk(p->n_oitems, 256), 256, 0, st>>>(p->d_oitems, p->n_oitems);
+        KP_LAUNCH_CHECK();
+    }
     p->launches += 4;
     return KP_OK;
 }
@@ -489,6 +525,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_item_off, tl.ntiles, p->chunk, p->d_iitems);
     KP_LAUNCH_CHECK();
     p->launches += 11;
+    if (g.D == 3) KP_TRY(build_own_items(p, st));
     p->traj_set = true;
     return autotune_spread(p, st);
 }

@@ -788,7 +788,7 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st) {
     a.levels = p->P.wavelet_levels;
     a.grid2w = p->d_grid2;
     a.split = p->d_split;
-    a.n_split = (int)p->n_split;
+    a.n_split = p->spread_variant >= 10 ? 0 : (int)p->n_split;   // two-phase spreading stores every point
     a.tiles = p->tiles;
     a.bar = (GridBarrier*)p->d_bar;
     a.err = p->d_flag + 3;

@@ -114,12 +114,12 @@ def test_invalid_params_rejected():
         Plan((30, 32), 2, 100, wavelet_levels=3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
 @pytest.mark.parametrize("chunk", [256, 1024])
 def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
     """Every spreading kernel variant and work-item size (fixed through the tuning overrides)
     gives the oracle's adjoint, on centre-dense radial trajectories whose central tiles are
-    cut into many items (2D and 3D; variants 8 and 9 exist in 3D only).  The 3D case has 2
+    cut into many items (2D and 3D; variants 8 to 11 exist in 3D only).  The 3D case has 2
     coils, so coil groups are partly empty."""
     need_gpu()
     import synth
@@ -130,7 +130,7 @@ def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
              ((12, 12, 12), 10, synth.radial_3d_fibonacci(n_spokes=300, n_readout=12, kmax=6.0))]
     for shape, C, traj in cases:
         if variant >= 8 and len(shape) == 2:
-            continue                                  # z-plane owners are 3D kernels
+            continue                                  # z-plane owners and two-phase are 3D kernels
         M = traj.shape[0]
         rng = np.random.default_rng(M)
         maps = (rng.standard_normal((C,) + shape) + 1j * rng.standard_normal((C,) + shape)).astype(np.complex64)
@@ -140,6 +140,6 @@ def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
         plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
         cfg = plan.spread_config()
         assert cfg["variant"] == variant and cfg["chunk"] == chunk
-        assert cfg["split_tiles"] > 0
+        assert cfg["split_tiles"] > 0 or variant >= 10
         xa = plan.sense_adjoint(to_dev(u)).cpu().numpy()
         assert rel(xa, x_ref) < 1e-5, (shape, cfg)
