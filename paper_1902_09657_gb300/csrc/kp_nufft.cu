@@ -1537,6 +1537,7 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
             p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
     KP_LAUNCH_CHECK();
     const int64_t tot = (int64_t)g.C * g.G;
+    mark(p, PH_SPREAD_RED, st);
     k_halo_gather<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
     p->launches += 1;
     return KP_OK;
