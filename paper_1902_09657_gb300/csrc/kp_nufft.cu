@@ -987,50 +987,53 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
 }
 
 // Phase B: grid[c][q] = sum over the slots of q's tile and of the lower neighbours whose
-// padded halo covers q (periodic in every axis).
+// padded halo covers q (periodic in every axis).  Launch: blockIdx.x = (grid row (z, y), block
+// of the fastest axis), threads along the fastest axis, blockIdx.y = coil; all index arithmetic
+// in 32 bits.
+__device__ __forceinline__ void tile_local(int k, int sh, int g, int ts, int& t, int& l) {
+    const int p = tshift(k, sh, g);
+    t = p / ts;
+    l = p - t * ts;
+}
+
 __global__ void __launch_bounds__(256)
 k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
               float2* __restrict__ grid) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)geo.C * geo.G) return;
-    const int c = (int)(idx / geo.G);
-    int64_t q = idx - (int64_t)c * geo.G;
+    const int xb = (geo.g[2] + blockDim.x - 1) / blockDim.x;
+    const int row = blockIdx.x / xb, c = blockIdx.y;
+    const int k2 = (blockIdx.x - row * xb) * blockDim.x + threadIdx.x;
+    if (k2 >= geo.g[2]) return;
+    const int k1 = row % geo.g[1], k0 = row / geo.g[1];
     int t[3], l[3];
+    tile_local(k0, tl.sh[0], geo.g[0], tl.ts[0], t[0], l[0]);
+    tile_local(k1, tl.sh[1], geo.g[1], tl.ts[1], t[1], l[1]);
+    tile_local(k2, tl.sh[2], geo.g[2], tl.ts[2], t[2], l[2]);
+    // per axis: the tile and padded coordinate for "same tile" and "lower neighbour"
+    int tt[3][2], ll[3][2];
 #pragma unroll
-    for (int d = 2; d >= 0; --d) {
-        const int k = (int)(q % geo.g[d]);
-        q /= geo.g[d];
-        const int p = tshift(k, tl.sh[d], geo.g[d]);
-        t[d] = p / tl.ts[d];
-        l[d] = p - t[d] * tl.ts[d];
+    for (int d = 0; d < 3; ++d) {
+        tt[d][0] = t[d];
+        ll[d][0] = l[d];
+        tt[d][1] = t[d] == 0 ? tl.nt[d] - 1 : t[d] - 1;
+        ll[d][1] = l[d] + min(tl.ts[d], geo.g[d] - tt[d][1] * tl.ts[d]);
     }
+    const size_t cstride = (size_t)geo.C * PT3;
+    const float2* hc = halo + (size_t)c * PT3;
     float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        int tt[3], ll[3];
-        bool ok = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if ((m >> (2 - d)) & 1) {
-                if (l[d] >= KW - 1) ok = false;
-                tt[d] = t[d] == 0 ? tl.nt[d] - 1 : t[d] - 1;
-                const int e = min(tl.ts[d], geo.g[d] - tt[d] * tl.ts[d]);
-                ll[d] = l[d] + e;
-            } else {
-                tt[d] = t[d];
-                ll[d] = l[d];
-            }
-        }
-        if (!ok) continue;
-        const int tile = (tt[0] * tl.nt[1] + tt[1]) * tl.nt[2] + tt[2];
-        const int pt = (ll[0] * PT + ll[1]) * PT + ll[2];
-        for (int sl = tslot[tile]; sl < tslot[tile + 1]; ++sl) {
-            const float2 v = halo[((size_t)sl * geo.C + c) * PT3 + pt];
+        const int b0 = (m >> 2) & 1, b1 = (m >> 1) & 1, b2 = m & 1;
+        if ((b0 && l[0] >= KW - 1) || (b1 && l[1] >= KW - 1) || (b2 && l[2] >= KW - 1)) continue;
+        const int tile = (tt[0][b0] * tl.nt[1] + tt[1][b1]) * tl.nt[2] + tt[2][b2];
+        const int pt = (ll[0][b0] * PT + ll[1][b1]) * PT + ll[2][b2];
+        const int s1 = tslot[tile + 1];
+        for (int sl = tslot[tile]; sl < s1; ++sl) {
+            const float2 v = hc[(size_t)sl * cstride + pt];
             sum.x += v.x;
             sum.y += v.y;
         }
     }
-    grid[idx] = sum;
+    grid[(size_t)c * geo.G + (size_t)row * geo.g[2] + k2] = sum;
 }
 
 // Variant with one shared accumulator per CTA and up to SPA_CH coils per CTA (one coil group
@@ -1536,9 +1539,9 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
         k_spread_own<UT, CG><<<dim3((unsigned)p->n_oitems, (g.C + CG - 1) / CG), 256, sm, st>>>(
             p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
     KP_LAUNCH_CHECK();
-    const int64_t tot = (int64_t)g.C * g.G;
     mark(p, PH_SPREAD_RED, st);
-    k_halo_gather<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    const dim3 gg((unsigned)(((g.g[2] + 255) / 256) * g.g[0] * g.g[1]), (unsigned)g.C);
+    k_halo_gather<<<gg, 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
     p->launches += 1;
     return KP_OK;
 }
