@@ -1608,8 +1608,9 @@ kp_status zero_split_only(kp_plan p, cudaStream_t st) {
     return KP_OK;
 }
 
-kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st,
-                          bool splits_zeroed) {
+// The spreading kernels alone (no inverse FFT).
+static kp_status spread_only(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st,
+                             bool splits_zeroed) {
     const Geom& g = p->geo;
     mark(p, PH_SPREAD, st);
     if (!splits_zeroed && p->spread_variant < 10) KP_TRY(zero_split_only(p, st));   // 10, 11 store every point
@@ -1651,13 +1652,19 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
                 p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
     }
     KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* perm, cudaStream_t st,
+                          bool splits_zeroed) {
+    KP_TRY(spread_only(p, u, u_t, perm, st, splits_zeroed));
     mark(p, PH_FFT_INV, st);
     KP_TRY_CUFFT(cufftSetStream(p->fft, st));
     KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
     return KP_OK;
 }
 
-// Picks the spreading variant and the samples per work item by timing the adjoint spread
+// Picks the spreading variant and the samples per work item by timing the spreading kernels
 // on the plan's own work items (values do not affect the cost; once per plan, at its first
 // trajectory).  Variants: 0 private copies, 4 coils x 4 warps; 1 shared atomics; 2 warp per
 // 4 coils; 3 private, 2 coils x 8 warps; 4 private, 1 coil x 8 warps; 5 private, 2 coils x 4
@@ -1694,29 +1701,43 @@ kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     cudaEvent_t e0, e1;
     KP_TRY_CUDA(cudaEventCreate(&e0));
     KP_TRY_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_v = 0, best_c = p->spread_chunk;
+    // The spreading kernels alone are timed (the inverse FFT is the same for every choice),
+    // in two interleaved rounds, keeping each configuration's faster round: one round alone
+    // was noisy enough to pick a variant 20 % slower than the best.
+    std::vector<float> t_min(chunks.size() * variants.size(), 1e30f);
     const bool prof = p->profiling;
     p->profiling = false;
     kp_status status = KP_OK;
-    for (int c : chunks) {
-        if (c != p->spread_chunk) status = build_spread_items(p, c, st);
-        if (status != KP_OK) break;
-        for (int v : variants) {
-            if (v >= 10 && c != chunks[0]) continue;   // the two-phase variants ignore the item size
-            p->spread_variant = v;
-            status = adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st);
-            if (status != KP_OK) break;
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 4 && status == KP_OK; ++r) status = adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st);
-            cudaEventRecord(e1, st);
-            if (status != KP_OK || cudaEventSynchronize(e1) != cudaSuccess) { status = status != KP_OK ? status : KP_ECUDA; break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_v = v; best_c = c; }
+    for (int round = 0; round < 2 && status == KP_OK; ++round) {
+        for (size_t ci = 0; ci < chunks.size() && status == KP_OK; ++ci) {
+            const int c = chunks[ci];
+            if (c != p->spread_chunk) status = build_spread_items(p, c, st);
+            for (size_t vi = 0; vi < variants.size() && status == KP_OK; ++vi) {
+                const int v = variants[vi];
+                if (v >= 10 && ci != 0) continue;   // the two-phase variants ignore the item size
+                p->spread_variant = v;
+                status = spread_only(p, p->d_kt, KP_C64, nullptr, st, true);
+                if (status != KP_OK) break;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 4 && status == KP_OK; ++r) status = spread_only(p, p->d_kt, KP_C64, nullptr, st, true);
+                cudaEventRecord(e1, st);
+                if (status != KP_OK || cudaEventSynchronize(e1) != cudaSuccess) { status = status != KP_OK ? status : KP_ECUDA; break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                float& tm = t_min[ci * variants.size() + vi];
+                tm = std::min(tm, ms);
+            }
         }
-        if (status != KP_OK) break;
     }
+    float best = 1e30f;
+    int best_v = 0, best_c = p->spread_chunk;
+    for (size_t ci = 0; ci < chunks.size(); ++ci)
+        for (size_t vi = 0; vi < variants.size(); ++vi)
+            if (t_min[ci * variants.size() + vi] < best) {
+                best = t_min[ci * variants.size() + vi];
+                best_v = variants[vi];
+                best_c = chunks[ci];
+            }
     p->profiling = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
