@@ -7,6 +7,7 @@
 // tile per CTA and therefore needs no global atomics and no zero-fill of the grid).
 #include "kp_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -389,6 +390,19 @@ kp_status plan_destroy_internal(kp_plan p) {
     return KP_OK;
 }
 
+// Reorders work items longest first (stable), so the CTAs that take longest start in the
+// first wave instead of forming a tail; items are independent, so the order is free.
+static kp_status sort_items_longest_first(int4* d_items, int64_t n, cudaStream_t st) {
+    if (n <= 1) return KP_OK;
+    std::vector<int4> h((size_t)n);
+    KP_TRY_CUDA(cudaMemcpyAsync(h.data(), d_items, n * sizeof(int4), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    std::stable_sort(h.begin(), h.end(), [](const int4& a, const int4& b) { return (a.z - a.y) > (b.z - b.y); });
+    KP_TRY_CUDA(cudaMemcpyAsync(d_items, h.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));   // the host copy must outlive the transfer
+    return KP_OK;
+}
+
 // Spreading work items: each tile's list cut into pieces of at most `chunk` samples (a
 // multiple of the kernels' staging size); tiles cut into several pieces are "split" and
 // accumulate with global atomics into a region cleared before each spread.
@@ -428,6 +442,7 @@ kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st) {
         KP_TRY_CUDA(cudaMemcpyAsync(p->d_split, split.data(), split.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, chunk, p->d_items);
     KP_LAUNCH_CHECK();
+    KP_TRY(sort_items_longest_first(p->d_items, p->n_items, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));   // the host split list must outlive its copy
     p->launches += 4;
     return KP_OK;
@@ -458,6 +473,7 @@ kp_status build_own_items(kp_plan p, cudaStream_t st) {
         KP_LAUNCH_CHECK();
         k_slot_ids<<<nblk(p->n_oitems, 256), 256, 0, st>>>(p->d_oitems, p->n_oitems);
         KP_LAUNCH_CHECK();
+        KP_TRY(sort_items_longest_first(p->d_oitems, p->n_oitems, st));   // slot ids travel with the items
     }
     p->launches += 4;
     return KP_OK;
@@ -524,6 +540,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     }
     k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_item_off, tl.ntiles, p->chunk, p->d_iitems);
     KP_LAUNCH_CHECK();
+    KP_TRY(sort_items_longest_first(p->d_iitems, p->n_iitems, st));
     p->launches += 11;
     if (g.D == 3) KP_TRY(build_own_items(p, st));
     p->traj_set = true;
