@@ -214,6 +214,18 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
     }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the default
+# workload's kernels from one `ncu --set full` capture of `bench.py --steps 2 --warmup 3
+# --no-extras` (the 301st to 303rd matching launches, spreading variant 6 at 256 samples).
+# Entries are valid only for the kernel code they were taken on; set one to None when its
+# kernel changes until it is captured again.
+NCU_TRAFFIC = {
+    "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19913984},
+    "adj_primal": {"kernel": "k_primal_fused<2, 16, float2, 1>", "bytes": 13150464},
+    "interp_dual": {"kernel": "k_interp_tile<2, 2, float2>", "bytes": 36180736},
+}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1902_09657_gb300 import _build
@@ -346,8 +358,11 @@ def gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stre
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = ab[dom] / (own[dom] * 1e-3) / 1e9
+    tr_entry = NCU_TRAFFIC.get(dom) if w.name == WORKLOAD else None
     out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak, "traffic": tr_entry["bytes"] if tr_entry else None,
+                       "traffic_source": ("one ncu capture of " + tr_entry["kernel"] + " on this workload")
+                       if tr_entry else None,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
                        "algorithmic_bytes": int(ab[dom]), "avg_launch_ms": own[dom]}
     # --- time to 1e-3 relative objective (F* = min over a 400-iteration float32 run)
