@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cufft.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -76,6 +77,19 @@ struct Tiles {
 __host__ __device__ __forceinline__ int tshift(int i, int sh, int g) { int p = i + sh; return p >= g ? p - g : p; }
 // grid index of shifted coordinate p (0 <= p < g)
 __host__ __device__ __forceinline__ int tunshift(int p, int sh, int g) { int i = p - sh; return i < 0 ? i + g : i; }
+
+// Once-per-device flag for host-side set-up that the runtime keeps per device, such as
+// cudaFuncSetAttribute (devices 0..63): first() is true the first time it is asked on the
+// current device.
+struct PerDeviceOnce {
+    std::atomic<unsigned long long> done{0};
+    bool first() {
+        int d = 0;
+        cudaGetDevice(&d);
+        const unsigned long long bit = 1ull << (d & 63);
+        return (done.fetch_or(bit) & bit) == 0;
+    }
+};
 
 // ---------------------------------------------------------------- complex storage helpers
 __host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -213,6 +227,7 @@ struct kp_plan_s {
                                      // 6/7: warp-private interleaved coil pairs, 4 coils x 4 / 8 warps;
                                      // 8/9: 3D z-plane owners; 10/11: 3D two-phase (padded tiles + gather)
     bool spread_tuned = false;
+    int cluster_prox = -1;           // 2D l1 prox by one thread-block cluster: -1 unknown, 0 no, 1 yes
     int4* d_iitems = nullptr;        // interpolation work items {tile, begin, end, -1} over d_off ranges
     int64_t n_iitems = 0, iitems_cap = 0;
     // two-phase 3D spreading (variants 10, 11): own-sample items, one padded-tile slot each
@@ -313,6 +328,8 @@ kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st);
 // kp_pdhg.cu
 kp_status wavelet_apply(kp_plan p, const float2* in, float2* out, bool forward, cudaStream_t st);
 kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
+bool cluster_prox_ok(kp_plan p);
+kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st);
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
                       cudaStream_t st);
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);

@@ -1457,16 +1457,14 @@ static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaS
     const size_t rt = g.D == 2 ? IpL<2>::PER_COIL : IpL<3>::PER_COIL;
     const size_t smem = (size_t)IP_CH * rt * sizeof(float2);
     const dim3 grid((unsigned)p->n_iitems, (g.C + IP_CH - 1) / IP_CH);
-    static bool attr[2][3][3] = {};
+    static PerDeviceOnce attr[2][3][3];
     mark(p, PH_INTERP, st);
     p->launches += 1;
     if (p->n_iitems == 0) return KP_OK;
     if (p->chunk > IP_THREADS) { set_error("interpolation items larger than the block"); return KP_EINTERNAL; }
     KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(t, T,
-        if (!attr[DD - 2][MODE][t]) {
+        if (attr[DD - 2][MODE][t].first())
             KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_tile<DD, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            attr[DD - 2][MODE][t] = true;
-        }
         k_interp_tile<DD, MODE, T><<<grid, IP_THREADS, smem, st>>>(p->d_iitems, p->d_k0, p->d_wt, p->d_gridF, g, p->tiles, io)));
     KP_LAUNCH_CHECK();
     return KP_OK;
@@ -1509,12 +1507,9 @@ kp_status interp_dual_only(kp_plan p, cudaStream_t st) {
 // Interleaved-pair spreading with NW warps (variants 6, 7).
 template <int D, typename UT, int NW>
 static kp_status launch_spread_v(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
-    static bool attr = false;
+    static PerDeviceOnce attr;
     const size_t sm = spread_v_smem<D, NW>();
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_v<D, UT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr = true;
-    }
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_v<D, UT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const Geom& g = p->geo;
     k_spread_v<D, UT, NW><<<dim3((unsigned)p->n_items, (g.C + 3) / 4), NW * 32, sm, st>>>(
         p->d_k0, p->d_wt, u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2);
@@ -1529,12 +1524,9 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
         set_error("two-phase spreading needs a 3D plan with its slot storage");
         return KP_EINTERNAL;
     }
-    static bool attr = false;
+    static PerDeviceOnce attr;
     const size_t sm = spread_own_smem<CG>();
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_own<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr = true;
-    }
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_own<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (p->n_oitems > 0)
         k_spread_own<UT, CG><<<dim3((unsigned)p->n_oitems, (g.C + CG - 1) / CG), 256, sm, st>>>(
             p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
@@ -1568,12 +1560,9 @@ static bool ensure_halo(kp_plan p) {
 template <int D, typename UT, int CG>
 static kp_status launch_spread_z(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
     if (D != 3) { set_error("spreading variants 8 and 9 are 3D only"); return KP_EINTERNAL; }
-    static bool attr = false;
+    static PerDeviceOnce attr;
     const size_t sm = spread_z_smem<CG>();
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_z<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr = true;
-    }
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_z<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const Geom& g = p->geo;
     k_spread_z<UT, CG><<<dim3((unsigned)p->n_items, (g.C + CG - 1) / CG), 256, sm, st>>>(
         p->d_k0, p->d_wt, u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2);
@@ -1583,12 +1572,9 @@ static kp_status launch_spread_z(kp_plan p, const UT* u, const int* perm, cudaSt
 // Private-copy spreading with CH coils per CTA and NW warps (variants 0, 3, 4, 5).
 template <int D, typename UT, int CH, int NW>
 static kp_status launch_spread_priv(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
-    static bool attr = false;
+    static PerDeviceOnce attr;
     const size_t sm = spread_smem<D, CH, NW>();
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<D, UT, CH, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr = true;
-    }
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_spread<D, UT, CH, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const Geom& g = p->geo;
     k_spread<D, UT, CH, NW><<<dim3((unsigned)p->n_items, (g.C + CH - 1) / CH), NW * 32, sm, st>>>(
         p->d_k0, p->d_wt, u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2);
@@ -1630,23 +1616,19 @@ static kp_status spread_only(kp_plan p, const void* u, kp_cdtype u_t, const int*
                 default: KP_TRY((launch_spread_priv<DD, UT, 2, 4>(p, (const UT*)u, perm, st))); break;
             }));
     } else if (p->spread_variant == 2) {
-        static bool attr_w[2][3] = {{false}};
+        static PerDeviceOnce attr_w[2][3];
         const size_t sm = g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C);
         const unsigned nthr = 32u * (unsigned)((g.C + SPW_CW - 1) / SPW_CW);
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
-            if (!attr_w[DD - 2][u_t]) {
+            if (attr_w[DD - 2][u_t].first())
                 KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_warpcoil<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-                attr_w[DD - 2][u_t] = true;
-            }
             k_spread_warpcoil<DD, UT><<<(unsigned)p->n_items, nthr, sm, st>>>(
                 p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));
     } else {
-        static bool attr_a[2][3] = {{false}};
+        static PerDeviceOnce attr_a[2][3];
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(u_t, UT,
-            if (!attr_a[DD - 2][u_t]) {
+            if (attr_a[DD - 2][u_t].first())
                 KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_atomic<DD, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-                attr_a[DD - 2][u_t] = true;
-            }
             k_spread_atomic<DD, UT><<<dim3((unsigned)p->n_items, (g.C + SPA_CH - 1) / SPA_CH), SPA_THREADS,
                                       spread_atomic_smem<DD>(std::min(g.C, SPA_CH)), st>>>(
                 p->d_k0, p->d_wt, (const UT*)u, perm, p->d_ext, p->d_items, g, p->tiles, p->d_grid2)));

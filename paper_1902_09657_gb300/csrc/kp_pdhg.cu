@@ -207,7 +207,8 @@ static kp_status issue_iteration(kp_plan p, int reg, float lambda, cudaStream_t 
     KP_TRY(fft_forward_only(p, st));
     KP_TRY(interp_dual_only(p, st));
     KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st, /*splits_zeroed=*/true));
-    KP_TRY(primal_fused(p, reg, lambda, st));
+    if (reg == KP_REG_L1_WAVELET && cluster_prox_ok(p)) KP_TRY(primal_cluster(p, lambda, st));
+    else KP_TRY(primal_fused(p, reg, lambda, st));
     mark(p, PH_OTHER, st);
     return KP_OK;
 }
@@ -339,8 +340,9 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_bar, 0, 4 * sizeof(unsigned int), st));   // grid-barrier counter
     // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
-    // split tiles of the spreading grid start at zero (the fused primal kernel re-clears them)
+    // split tiles of the spreading grid start at zero (the primal step re-clears them)
     KP_TRY(zero_split_only(plan, st));
+    (void)cluster_prox_ok(plan);   // decide the primal path here, outside any graph capture
     return KP_OK;
 }
 

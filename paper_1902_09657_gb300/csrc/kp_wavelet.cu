@@ -18,7 +18,10 @@
 // block length), g[n] = (-1)^n h[7-n]; synthesis is the transpose.
 #include "kp_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <cstdlib>
 
 namespace kp {
 
@@ -339,11 +342,8 @@ static kp_status launch_inv_t(const LevelArgs& a, int nblocks, cudaStream_t st) 
     size_t tot = 1, tot1 = 1;
     for (int d = 0; d < D; ++d) { tot *= 2 * E; tot1 *= (d == D - 1 ? 2 * T : 2 * E); }
     const size_t smem = (tot + tot1) * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level_t<D, T, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level_t<D, T, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     k_dwt_inv_level_t<D, T, MT><<<nblocks, 256, smem, st>>>(a);
     KP_LAUNCH_CHECK();
     return KP_OK;
@@ -371,11 +371,8 @@ static kp_status launch_fwd(const LevelArgs& a, int nblocks, cudaStream_t st) {
     size_t tot = 1, tot1 = 1;
     for (int d = 0; d < D; ++d) { tot *= EI; tot1 *= (d == D - 1 ? 2 * T : EI); }
     const size_t smem = (tot + tot1) * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_fwd_level<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_fwd_level<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     k_dwt_fwd_level<D, T><<<nblocks, 256, smem, st>>>(a);
     KP_LAUNCH_CHECK();
     return KP_OK;
@@ -387,11 +384,8 @@ static kp_status launch_inv(const LevelArgs& a, int nblocks, cudaStream_t st) {
     size_t tot = 1, tot1 = 1;
     for (int d = 0; d < D; ++d) { tot *= 2 * E; tot1 *= (d == D - 1 ? 2 * T : 2 * E); }
     const size_t smem = (tot + tot1) * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     k_dwt_inv_level<D, T><<<nblocks, 256, smem, st>>>(a);
     KP_LAUNCH_CHECK();
     return KP_OK;
@@ -742,16 +736,18 @@ template <int D, int T, typename MT, int REG>
 static kp_status launch_primal(kp_plan p, const PrimalArgs& a, cudaStream_t st) {
     auto kern = k_primal_fused<D, T, MT, REG>;
     const size_t smem = REG == 1 ? primal_smem<D, T>() : 0;
-    static int blocks_cache[4] = {0, 0, 0, 0};
-    int& nblk = blocks_cache[(D - 2) * 2 + REG];
+    static std::atomic<int> blocks_cache[64];   // per device: CTAs of the cooperative grid
+    int dev = 0;
+    KP_TRY_CUDA(cudaGetDevice(&dev));
+    int nblk = blocks_cache[dev & 63].load();
     if (nblk == 0) {
         KP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-        int dev = 0, sms = 0, per = 0;
-        KP_TRY_CUDA(cudaGetDevice(&dev));
+        int sms = 0, per = 0;
         KP_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         KP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, PF_THREADS, smem));
         if (per < 1) { set_error("fused primal kernel does not fit on an SM"); return KP_EINTERNAL; }
         nblk = sms;   // one CTA per SM: the barrier's arrival count stays small
+        blocks_cache[dev & 63].store(nblk);
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)nblk);
@@ -764,6 +760,285 @@ static kp_status launch_primal(kp_plan p, const PrimalArgs& a, cudaStream_t st) 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     KP_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    p->launches += 1;
+    return KP_OK;
+}
+
+
+// ---------------------------------------------------------------- l1 prox by one cluster (2D)
+// The l1-wavelet prox W^H S_t(W z) of a 2D image, with the extrapolation, by one cluster of
+// NC = 16 or 8 CTAs (one per SM, 1024 threads) instead of tiled passes separated by grid-wide barriers.
+// CTA r holds image rows [r R0, (r + 1) R0) (R0 = n0 / NC) in shared memory and transforms
+// them in place in a Mallat layout local to its row block: at level l its block is the top-left
+// (R0 >> l) x (n1 >> l) corner; the x pass (along rows) is local, the y pass reads the rows it
+// needs from the CTAs that own them through distributed shared memory (rows of a level are
+// owned by CTA row / (R0 >> l)), and the CTAs meet at hardware cluster barriers.  Forward
+// levels: x pass into T, cluster barrier, y pass from T into the block (details and, at the
+// last level, the approximation soft-thresholded).  Inverse levels: y pass reading the owners'
+// coefficient rows into T, cluster barrier, x pass into the block, cluster barrier.  The
+// coefficients are the same as those of the tiled transform (same filters, periodic indexing),
+// only stored in a different order, so the prox is the same up to rounding order.
+namespace cgc = cooperative_groups;
+
+constexpr int CP_THREADS = 1024;
+
+__device__ __forceinline__ int cp_wrap(int i, int len) {
+    while (i >= len) i -= len;
+    while (i < 0) i += len;
+    return i;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(CP_THREADS)
+k_wprox_cluster(const float2* __restrict__ z, float2* __restrict__ x, float2* __restrict__ xbar,
+                const float* __restrict__ sched, const int* __restrict__ iter, float lambda, int n0, int n1, int L) {
+    cgc::cluster_group cl = cgc::this_cluster();
+    const int r = (int)cl.block_rank();
+    extern __shared__ __align__(16) float2 smc[];
+    const int R0 = n0 / NC;
+    float2* A = smc;                        // [R0][n1], row stride n1 at every level
+    float2* T0 = A + (size_t)R0 * n1;       // [R0][n1] dense per level (even levels, inverse)
+    float2* T1 = T0 + (size_t)R0 * n1;      // [R0/2][n1/2] dense (odd forward levels)
+    const int k = *iter;
+    const float thr = sched[3 * k + 1] * lambda, theta = sched[3 * k + 2];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const size_t row0 = (size_t)r * R0 * n1;
+    for (int i = tid; i < R0 * n1; i += nt) A[i] = z[row0 + i];
+    __syncthreads();
+    float hh[8], gg[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) { hh[n] = c_wh[n]; gg[n] = c_wg[n]; }
+    for (int lev = 0; lev < L; ++lev) {
+        const int Rl = R0 >> lev, cw = n1 >> lev, nl = n0 >> lev, half = cw / 2, R1 = Rl / 2;
+        float2* T = (lev & 1) ? T1 : T0;
+        // x pass (local): thread per (row, k); a[k] and d[k] from the same 8 inputs
+        for (int o = tid; o < Rl * half; o += nt) {
+            const int i = o / half, kq = o - i * half;
+            const float2* row = A + (size_t)i * n1;
+            int idx = 2 * kq;
+            float2 a = make_float2(0.f, 0.f), d = a;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                const float2 v = row[idx];
+                a.x = fmaf(hh[n], v.x, a.x); a.y = fmaf(hh[n], v.y, a.y);
+                d.x = fmaf(gg[n], v.x, d.x); d.y = fmaf(gg[n], v.y, d.y);
+                if (++idx == cw) idx = 0;
+            }
+            T[(size_t)i * cw + kq] = a;
+            T[(size_t)i * cw + half + kq] = d;
+        }
+        cl.sync();
+        // y pass: thread per (k, column); rows 2k .. 2k + 7 from their owners
+        for (int o = tid; o < R1 * cw; o += nt) {
+            const int kk = o / cw, c = o - kk * cw;
+            int row = cp_wrap(2 * (r * R1 + kk), nl);
+            float2 a = make_float2(0.f, 0.f), d = a;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                const int own = row / Rl;
+                const float2 v = cl.map_shared_rank(T, own)[(size_t)(row - own * Rl) * cw + c];
+                a.x = fmaf(hh[n], v.x, a.x); a.y = fmaf(hh[n], v.y, a.y);
+                d.x = fmaf(gg[n], v.x, d.x); d.y = fmaf(gg[n], v.y, d.y);
+                if (++row == nl) row = 0;
+            }
+            if (c >= half || lev == L - 1) a = soft(a, thr);   // the approximation stays for the next level
+            A[(size_t)kk * n1 + c] = a;
+            A[(size_t)(R1 + kk) * n1 + c] = soft(d, thr);
+        }
+        __syncthreads();
+    }
+    cl.sync();
+    for (int lev = L - 1; lev >= 0; --lev) {
+        const int Rl = R0 >> lev, cw = n1 >> lev, nl = n0 >> lev, half = cw / 2, R1 = Rl / 2, nh = nl / 2;
+        // y pass: thread per (output row pair, column): rows 2m and 2m + 1 from coefficient
+        // rows m - 3 .. m (periodic) of the owners
+        for (int o = tid; o < R1 * cw; o += nt) {
+            const int mm = o / cw, c = o - mm * cw;
+            const int mg = r * R1 + mm;                          // global pair index
+            float2 e = make_float2(0.f, 0.f), od = e;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int kg = cp_wrap(mg - t, nh);
+                const int own = kg / R1, lk = kg - own * R1;
+                const float2* Ar = cl.map_shared_rank(A, own);
+                const float2 av = Ar[(size_t)lk * n1 + c], dv = Ar[(size_t)(R1 + lk) * n1 + c];
+                // x[2 mg] uses n = 2t, x[2 mg + 1] uses n = 2t + 1, both at k = mg - t
+                e.x = fmaf(hh[2 * t], av.x, fmaf(gg[2 * t], dv.x, e.x));
+                e.y = fmaf(hh[2 * t], av.y, fmaf(gg[2 * t], dv.y, e.y));
+                od.x = fmaf(hh[2 * t + 1], av.x, fmaf(gg[2 * t + 1], dv.x, od.x));
+                od.y = fmaf(hh[2 * t + 1], av.y, fmaf(gg[2 * t + 1], dv.y, od.y));
+            }
+            T0[(size_t)(2 * mm) * cw + c] = e;
+            T0[(size_t)(2 * mm + 1) * cw + c] = od;
+        }
+        cl.sync();                                             // every owner's rows have been read
+        // x pass (local): thread per (row, output pair)
+        for (int o = tid; o < Rl * half; o += nt) {
+            const int jj = o / half, mq = o - jj * half;
+            const float2* t = T0 + (size_t)jj * cw;
+            float2 e = make_float2(0.f, 0.f), od = e;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int kq = cp_wrap(mq - u, half);
+                const float2 av = t[kq], dv = t[half + kq];
+                e.x = fmaf(hh[2 * u], av.x, fmaf(gg[2 * u], dv.x, e.x));
+                e.y = fmaf(hh[2 * u], av.y, fmaf(gg[2 * u], dv.y, e.y));
+                od.x = fmaf(hh[2 * u + 1], av.x, fmaf(gg[2 * u + 1], dv.x, od.x));
+                od.y = fmaf(hh[2 * u + 1], av.y, fmaf(gg[2 * u + 1], dv.y, od.y));
+            }
+            A[(size_t)jj * n1 + 2 * mq] = e;
+            A[(size_t)jj * n1 + 2 * mq + 1] = od;
+        }
+        cl.sync();                                             // the next level reads these rows
+    }
+    for (int i = tid; i < R0 * n1; i += nt) {                 // extrapolation (Sec. 4.1)
+        const float2 xn = A[i], xo = x[row0 + i];
+        xbar[row0 + i] = make_float2(xn.x + theta * (xn.x - xo.x), xn.y + theta * (xn.y - xo.y));
+        x[row0 + i] = xn;
+    }
+}
+
+// After the cluster prox: blocks below nb_pre write the next iteration's coil multiply /
+// apodise / pad of xbar into the image region of the forward grid (the zero padding stays from
+// solve set-up); block nb_pre + t clears split spreading tile t of the adjoint grid; block 0
+// advances the iteration counter.  32-bit index arithmetic (2D).
+template <typename MT>
+__global__ void __launch_bounds__(256)
+k_pre_clear(const float2* __restrict__ xbar, const MT* __restrict__ maps, const float* __restrict__ apod, Geom geo,
+            float2* __restrict__ fgrid, int nb_pre, const int* __restrict__ split, Tiles tl, float2* __restrict__ grid2,
+            int* __restrict__ iter) {
+    const int n0 = geo.n[0], n1 = geo.n[1], g0 = geo.g[0], g1 = geo.g[1];
+    if ((int)blockIdx.x < nb_pre) {
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n0 * n1; j += nb_pre * blockDim.x) {
+            const int iy = j / n1, ix = j - iy * n1;
+            const int ny = iy - n0 / 2, nx = ix - n1 / 2;
+            const int gy = ny < 0 ? ny + g0 : ny, gx = nx < 0 ? nx + g1 : nx;
+            const float a = apod[iy] * apod[n0 + ix];
+            float2 v = xbar[j];
+            v.x *= a;
+            v.y *= a;
+            const size_t gi = (size_t)gy * g1 + gx;
+            for (int c = 0; c < geo.C; ++c) {
+                const float2 sv = ldc<MT>(maps, (size_t)c * geo.N + j);
+                fgrid[(size_t)c * geo.G + gi] = cmul(sv, v);
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) *iter += 1;
+        return;
+    }
+    int t = split[blockIdx.x - nb_pre];
+    const int tc1 = t % tl.nt[1], tc0 = t / tl.nt[1];
+    const int o0 = tc0 * tl.ts[0], o1 = tc1 * tl.ts[1];
+    const int e0 = min(tl.ts[0], g0 - o0), e1 = min(tl.ts[1], g1 - o1);
+    for (int i = threadIdx.x; i < geo.C * e0 * e1; i += blockDim.x) {
+        const int c = i / (e0 * e1), p = i - c * e0 * e1;
+        const int l0 = p / e1, l1 = p - l0 * e1;
+        const size_t gflat = (size_t)tunshift(o0 + l0, tl.sh[0], g0) * g1 + tunshift(o1 + l1, tl.sh[1], g1);
+        grid2[(size_t)c * geo.G + gflat] = make_float2(0.f, 0.f);
+    }
+}
+
+static size_t cluster_smem(const Geom& g, int nc) {
+    const size_t R0 = (size_t)g.n[0] / nc, n1 = (size_t)g.n[1];
+    return (2 * R0 * n1 + (R0 / 2) * (n1 / 2)) * sizeof(float2);
+}
+
+template <int NC>
+static cudaLaunchConfig_t cluster_cfg(size_t sm, cudaStream_t st, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(NC);
+    cfg.blockDim = dim3(CP_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = NC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Sets the kernel's attributes on the current device and asks whether one cluster fits.
+template <int NC>
+static bool cluster_fits(size_t sm) {
+    if (cudaFuncSetAttribute(k_wprox_cluster<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        (NC > 8 && cudaFuncSetAttribute(k_wprox_cluster<NC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_cfg<NC>(sm, nullptr, at);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_wprox_cluster<NC>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters >= 1;
+}
+
+// Whether the 2D l1 prox can run as one cluster of 16 (else 8) CTAs: rows split evenly over
+// the CTAs with every level's row block even, shared memory within 200 KB, and the device able
+// to place the cluster.  The choice is made at solve set-up (outside any graph capture).  The
+// environment variable KPDHG_NO_CLUSTER_PROX=1 keeps the cooperative kernel.
+bool cluster_prox_ok(kp_plan p) {
+    if (p->cluster_prox >= 0) return p->cluster_prox > 0;
+    const Geom& g = p->geo;
+    const int L = p->P.wavelet_levels;
+    int chosen = 0;
+    bool allowed = g.D == 2 && L >= 1;
+    if (const char* ev = getenv("KPDHG_NO_CLUSTER_PROX"))
+        if (atoi(ev) != 0) allowed = false;
+    for (int nc : {16, 8}) {
+        if (!allowed || chosen) break;
+        if (g.n[0] % nc != 0 || ((g.n[0] / nc) % (1 << L)) != 0) continue;
+        const size_t sm = cluster_smem(g, nc);
+        if (sm > 200 * 1024) continue;
+        if (nc == 16 ? cluster_fits<16>(sm) : cluster_fits<8>(sm)) chosen = nc;
+    }
+    p->cluster_prox = chosen;
+    return chosen > 0;
+}
+
+// One PDHG primal step for a 2D l1 plan on the cluster path: adjoint combine into z, the
+// cluster prox and extrapolation, then the pre-step, split-tile clearing and counter.
+kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const int nc = p->cluster_prox;
+    KP_TRY(adjoint_primal(p, KP_REG_L1_WAVELET, lambda, st));
+    mark(p, PH_DWT_FWD, st);
+    const size_t sm = cluster_smem(g, nc);
+    cudaLaunchAttribute at[1];
+    if (nc == 16) {
+        static PerDeviceOnce attr;
+        if (attr.first() && !cluster_fits<16>(sm)) { set_error("cluster prox does not fit"); return KP_EINTERNAL; }
+        cudaLaunchConfig_t cfg = cluster_cfg<16>(sm, st, at);
+        KP_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_wprox_cluster<16>, (const float2*)p->d_z, p->d_x, p->d_xbar,
+                                       (const float*)p->d_sched, (const int*)p->d_iter, lambda, g.n[0], g.n[1],
+                                       p->P.wavelet_levels));
+    } else {
+        static PerDeviceOnce attr;
+        if (attr.first() && !cluster_fits<8>(sm)) { set_error("cluster prox does not fit"); return KP_EINTERNAL; }
+        cudaLaunchConfig_t cfg = cluster_cfg<8>(sm, st, at);
+        KP_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_wprox_cluster<8>, (const float2*)p->d_z, p->d_x, p->d_xbar,
+                                       (const float*)p->d_sched, (const int*)p->d_iter, lambda, g.n[0], g.n[1],
+                                       p->P.wavelet_levels));
+    }
+    p->launches += 1;
+    mark(p, PH_FWD_PRE, st);
+    const int nb_pre = 2 * 152;
+    const unsigned nb = (unsigned)(nb_pre + p->n_split);
+    const kp_cdtype mt = p->maps_t;
+    if (mt == KP_C64)
+        k_pre_clear<float2><<<nb, 256, 0, st>>>(p->d_xbar, (const float2*)p->d_maps, p->d_apod, g, p->d_grid, nb_pre,
+                                                p->d_split, p->tiles, p->d_grid2, p->d_iter);
+    else if (mt == KP_C32_BF16)
+        k_pre_clear<__nv_bfloat162><<<nb, 256, 0, st>>>(p->d_xbar, (const __nv_bfloat162*)p->d_maps, p->d_apod, g, p->d_grid,
+                                                        nb_pre, p->d_split, p->tiles, p->d_grid2, p->d_iter);
+    else
+        k_pre_clear<__half2><<<nb, 256, 0, st>>>(p->d_xbar, (const __half2*)p->d_maps, p->d_apod, g, p->d_grid, nb_pre,
+                                                 p->d_split, p->tiles, p->d_grid2, p->d_iter);
+    KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;
 }

@@ -60,6 +60,30 @@ def test_pdhg_iteration_parity_small(reg, lam, iters, levels):
     assert abs(st["lmax"] - L) < 1e-12 * L and abs(st["pmin"] - p.min()) < 1e-6 * p.min()
 
 
+@pytest.mark.parametrize("cluster", ["1", "0"])
+def test_pdhg_l1_primal_paths(cluster, monkeypatch):
+    """2D l1-wavelet PDHG with the prox done by one thread-block cluster (rows spread over its
+    CTAs, distributed shared memory) and with the cooperative fused kernel (tiled levels and
+    grid barriers): both give the oracle's iterates."""
+    need_gpu()
+    if cluster == "0":
+        monkeypatch.setenv("KPDHG_NO_CLUSTER_PROX", "1")
+    w, x, maps, traj = _small_spiral(n=128, C=3, L=6, ns=2048)
+    y = simulate(w, x, maps, traj)
+    A, AH = _ops(maps, traj, 1.25)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    lam = 1e-3 * float(np.abs(AH(y.astype(np.complex128))).max())
+    x_ref, _, _, objs = osv.pdhg(A, AH, y, p, x.shape, "l1_wavelet", lam, 40, L, levels=4, trace=True)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=4)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    xg, tr, _ = plan.pdhg_solve(to_dev(y), to_dev(p.astype(np.float32)), "l1_wavelet", lam, 40, lmax=L, trace=True)
+    assert rel(xg.cpu().numpy(), x_ref) < 1e-5
+    assert abs(tr[-1] - objs[-1]) < 1e-5 * abs(objs[-1])
+    xg2, _, _ = plan.pdhg_solve(to_dev(y), to_dev(p.astype(np.float32)), "l1_wavelet", lam, 40, lmax=L)
+    assert rel(xg2.cpu().numpy(), x_ref) < 1e-5          # graph replay of the same path
+
+
 @pytest.mark.parametrize("name,alpha,iters", [("radial2d_128", 2.0, 30), ("spiral2d_256", 1.25, 8)])
 def test_pdhg_full_chain_workloads(name, alpha, iters):
     """Whole chain on the full-size 2D workloads: GPU builds p (MC) and lambda_max itself."""
