@@ -221,7 +221,6 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
 # kernel changes until it is captured again.
 NCU_TRAFFIC = {
     "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19913984},
-    "adj_primal": {"kernel": "k_primal_fused<2, 16, float2, 1>", "bytes": 13150464},
     "interp_dual": {"kernel": "k_interp_tile<2, 2, float2>", "bytes": 36180736},
 }
 
