@@ -831,15 +831,22 @@ k_wprox_cluster(const float2* __restrict__ z, float2* __restrict__ x, float2* __
         // y pass: thread per (k, column); rows 2k .. 2k + 7 from their owners
         for (int o = tid; o < R1 * cw; o += nt) {
             const int kk = o / cw, c = o - kk * cw;
-            int row = cp_wrap(2 * (r * R1 + kk), nl);
+            // row 2k + n (periodic) lives in CTA own at local row lr; the level's nl rows are
+            // exactly NC blocks of Rl, so (own, lr) step and wrap together
+            const int row = cp_wrap(2 * (r * R1 + kk), nl);
+            int own = row / Rl, lr = row - own * Rl;
+            const float2* Tr = cl.map_shared_rank(T, own);
             float2 a = make_float2(0.f, 0.f), d = a;
 #pragma unroll
             for (int n = 0; n < 8; ++n) {
-                const int own = row / Rl;
-                const float2 v = cl.map_shared_rank(T, own)[(size_t)(row - own * Rl) * cw + c];
+                const float2 v = Tr[(size_t)lr * cw + c];
                 a.x = fmaf(hh[n], v.x, a.x); a.y = fmaf(hh[n], v.y, a.y);
                 d.x = fmaf(gg[n], v.x, d.x); d.y = fmaf(gg[n], v.y, d.y);
-                if (++row == nl) row = 0;
+                if (++lr == Rl) {
+                    lr = 0;
+                    if (++own == NC) own = 0;
+                    Tr = cl.map_shared_rank(T, own);
+                }
             }
             if (c >= half || lev == L - 1) a = soft(a, thr);   // the approximation stays for the next level
             A[(size_t)kk * n1 + c] = a;
@@ -849,18 +856,23 @@ k_wprox_cluster(const float2* __restrict__ z, float2* __restrict__ x, float2* __
     }
     cl.sync();
     for (int lev = L - 1; lev >= 0; --lev) {
-        const int Rl = R0 >> lev, cw = n1 >> lev, nl = n0 >> lev, half = cw / 2, R1 = Rl / 2, nh = nl / 2;
+        const int Rl = R0 >> lev, cw = n1 >> lev, half = cw / 2, R1 = Rl / 2;
         // y pass: thread per (output row pair, column): rows 2m and 2m + 1 from coefficient
         // rows m - 3 .. m (periodic) of the owners
         for (int o = tid; o < R1 * cw; o += nt) {
             const int mm = o / cw, c = o - mm * cw;
-            const int mg = r * R1 + mm;                          // global pair index
+            // coefficient row mg - t (periodic over nh = NC R1 rows) lives in CTA own at local
+            // row lk; stepping down, (own, lk) wrap together
+            int own = r, lk = mm;
+            const float2* Ar = cl.map_shared_rank(A, own);
             float2 e = make_float2(0.f, 0.f), od = e;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                const int kg = cp_wrap(mg - t, nh);
-                const int own = kg / R1, lk = kg - own * R1;
-                const float2* Ar = cl.map_shared_rank(A, own);
+                if (t > 0 && --lk < 0) {
+                    lk = R1 - 1;
+                    if (--own < 0) own = NC - 1;
+                    Ar = cl.map_shared_rank(A, own);
+                }
                 const float2 av = Ar[(size_t)lk * n1 + c], dv = Ar[(size_t)(R1 + lk) * n1 + c];
                 // x[2 mg] uses n = 2t, x[2 mg + 1] uses n = 2t + 1, both at k = mg - t
                 e.x = fmaf(hh[2 * t], av.x, fmaf(gg[2 * t], dv.x, e.x));
