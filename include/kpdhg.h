@@ -257,7 +257,8 @@ kp_status kp_plan_tile_stats(kp_plan plan, int64_t* ntiles, int64_t* max_tile_sa
  * CTA; 3, 4, 5: warp-private copies with 2 coils x 8 warps, 1 coil x 8 warps, 2 coils x 4 warps;
  * 6, 7: warp-private copies of interleaved coil pairs, 4 coils x 4 or 8 warps; 8, 9 (3D): each
  * warp owns one z-plane of a single accumulator, 8 or 4 coils; 10, 11 (3D): two phases, padded
- * tiles of each tile's own samples then a gather over tiles, 8 or 4 coils),
+ * tiles of each tile's own samples then a gather over tiles, 8 or 4 coils; 12 (2D): the same two
+ * phases with warp-private padded tiles of 4 coils),
  * samples per work item, number of work items and of split tiles (tiles cut into several items,
  * accumulated with global atomics).  Any pointer may be NULL.  KP_EINVAL before a trajectory
  * is set.  The environment variables KPDHG_SPREAD_VARIANT and KPDHG_SPREAD_CHUNK, read at that

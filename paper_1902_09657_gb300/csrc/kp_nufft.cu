@@ -1036,6 +1036,127 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
     grid[(size_t)c * geo.G + (size_t)row * geo.g[2] + k2] = sum;
 }
 
+// Two-phase spreading in 2D (variant 12): phase A as in 3D but with warp-private copies of the
+// padded (16 + W - 1)^2 tile (4 coils as two float4 pairs per point), each warp taking its own
+// samples with every lane on a tap (lanes: coil pair, ta, tb); rows padded to 16 (mod 128)
+// bytes so each quarter-warp (two rows x four points) is conflict-free.  Phase B as in 3D.
+constexpr int PT2 = 16 + KW - 1;
+constexpr int PT2SQ = PT2 * PT2;
+constexpr int OW_ROW = 2 * PT2 + 3;            // float4 per padded row (656 bytes)
+constexpr int OW_COPY = PT2 * OW_ROW;
+
+template <int NW>
+static size_t spread_own2_smem() {
+    return (size_t)NW * OW_COPY * sizeof(float4) + (size_t)SP_CHUNK * (2 * sizeof(float4) + 2 * KW * sizeof(float) + sizeof(int));
+}
+
+template <typename UT, int NW>
+__global__ void __launch_bounds__(NW * 32)
+k_spread_own2(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+              const int* __restrict__ perm, const int4* __restrict__ items, Geom geo, Tiles tl,
+              float2* __restrict__ halo) {
+    constexpr int D = 2;
+    extern __shared__ __align__(16) float4 smo2[];
+    float4* acc = smo2;                                             // [NW][PT2][OW_ROW]
+    float4* su4 = acc + NW * OW_COPY;                               // [SP_CHUNK][2]
+    float* sw = (float*)(su4 + SP_CHUNK * 2);                       // [SP_CHUNK][2][KW]
+    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK] local first taps
+    const int4 it = items[blockIdx.x];
+    const int tile = it.x, beg = it.y, end = it.z, slot = it.w;
+    const int c0 = blockIdx.y * 4;
+    const int cc = min(4, geo.C - c0);
+    const int o1 = (tile % tl.nt[1]) * tl.ts[1], o0 = (tile / tl.nt[1]) * tl.ts[0];
+    for (int i = threadIdx.x; i < NW * OW_COPY; i += blockDim.x) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = lane >> 4, ta = (lane >> 2) & 3, tb = lane & 3;
+    float4* my = acc + warp * OW_COPY;
+    for (int sb = beg; sb < end; sb += SP_CHUNK) {
+        const int n = min(SP_CHUNK, end - sb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = sb + i;
+            const int64_t un = perm ? perm[s] : s;
+            float2 uc[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) uc[c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
+            su4[i * 2] = make_float4(uc[0].x, uc[0].y, uc[1].x, uc[1].y);
+            su4[i * 2 + 1] = make_float4(uc[2].x, uc[2].y, uc[3].x, uc[3].y);
+            const int l0 = tshift(k0t[s], tl.sh[0], geo.g[0]) - o0;
+            const int l1 = tshift(k0t[(int64_t)geo.M + s], tl.sh[1], geo.g[1]) - o1;
+            sp[i] = (unsigned)l0 | ((unsigned)l1 << 8);
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+#pragma unroll
+                for (int j = 0; j < KW; ++j) sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+        }
+        __syncthreads();
+        for (int i = warp; i < n; i += NW) {
+            const unsigned pk = sp[i];
+            const int y = (int)(pk & 0xFFu) + ta, x = (int)((pk >> 8) & 0xFFu) + tb;
+            const float w = sw[(i * D) * KW + ta] * sw[(i * D + 1) * KW + tb];
+            const float4 uv = su4[i * 2 + k];
+            float4* a = my + y * OW_ROW + x * 2 + k;
+            float4 v = *a;
+            v.x = fmaf(w, uv.x, v.x); v.y = fmaf(w, uv.y, v.y);
+            v.z = fmaf(w, uv.z, v.z); v.w = fmaf(w, uv.w, v.w);
+            *a = v;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    const int npair = (cc + 1) / 2;
+    for (int i = threadIdx.x; i < npair * PT2SQ; i += blockDim.x) {
+        const int kp = i / PT2SQ, pt = i - kp * PT2SQ;
+        const int y = pt / PT2, x = pt - y * PT2;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const float4 t = acc[w * OW_COPY + y * OW_ROW + x * 2 + kp];
+            v.x += t.x; v.y += t.y; v.z += t.z; v.w += t.w;
+        }
+        float2* d0 = halo + ((size_t)slot * geo.C + c0 + 2 * kp) * PT2SQ + pt;
+        *d0 = make_float2(v.x, v.y);
+        if (2 * kp + 1 < cc) d0[PT2SQ] = make_float2(v.z, v.w);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_halo_gather2(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
+               float2* __restrict__ grid) {
+    const int xb = (geo.g[1] + blockDim.x - 1) / blockDim.x;
+    const int row = blockIdx.x / xb, c = blockIdx.y;
+    const int k1 = (blockIdx.x - row * xb) * blockDim.x + threadIdx.x;
+    if (k1 >= geo.g[1]) return;
+    int t[2], l[2];
+    tile_local(row, tl.sh[0], geo.g[0], tl.ts[0], t[0], l[0]);
+    tile_local(k1, tl.sh[1], geo.g[1], tl.ts[1], t[1], l[1]);
+    int tt[2][2], ll[2][2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        tt[d][0] = t[d];
+        ll[d][0] = l[d];
+        tt[d][1] = t[d] == 0 ? tl.nt[d] - 1 : t[d] - 1;
+        ll[d][1] = l[d] + min(tl.ts[d], geo.g[d] - tt[d][1] * tl.ts[d]);
+    }
+    const size_t cstride = (size_t)geo.C * PT2SQ;
+    const float2* hc = halo + (size_t)c * PT2SQ;
+    float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int b0 = m >> 1, b1 = m & 1;
+        if ((b0 && l[0] >= KW - 1) || (b1 && l[1] >= KW - 1)) continue;
+        const int tile = tt[0][b0] * tl.nt[1] + tt[1][b1];
+        const int pt = ll[0][b0] * PT2 + ll[1][b1];
+        const int s1 = tslot[tile + 1];
+        for (int sl = tslot[tile]; sl < s1; ++sl) {
+            const float2 v = hc[(size_t)sl * cstride + pt];
+            sum.x += v.x;
+            sum.y += v.y;
+        }
+    }
+    grid[(size_t)c * geo.G + (size_t)row * geo.g[1] + k1] = sum;
+}
+
 // Variant with one shared accumulator per CTA and up to SPA_CH coils per CTA (one coil group
 // for C <= 16): the tap geometry of a sample is staged once for all its coils and the lanes
 // add with shared-memory atomics (a warp's lanes cover distinct (tap, coil) addresses; only
@@ -1517,6 +1638,29 @@ static kp_status launch_spread_v(kp_plan p, const UT* u, const int* perm, cudaSt
 }
 
 // Two-phase spreading, 3D only (variants 10, 11): padded tiles into the slots, then gather.
+// Two-phase spreading, 2D (variant 12): padded tiles of 4 coils into the slots, then gather.
+template <typename UT>
+static kp_status launch_spread_own2(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
+    const Geom& g = p->geo;
+    if (g.D != 2 || !p->d_halo || p->halo_cap < (size_t)p->n_oitems * g.C * PT2SQ) {
+        set_error("two-phase spreading needs a 2D plan with its slot storage");
+        return KP_EINTERNAL;
+    }
+    static PerDeviceOnce attr;
+    const size_t sm = spread_own2_smem<4>();
+    if (attr.first())
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_own2<UT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (p->n_oitems > 0)
+        k_spread_own2<UT, 4><<<dim3((unsigned)p->n_oitems, (g.C + 3) / 4), 128, sm, st>>>(
+            p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
+    KP_LAUNCH_CHECK();
+    mark(p, PH_SPREAD_RED, st);
+    const dim3 gg((unsigned)(((g.g[1] + 255) / 256) * g.g[0]), (unsigned)g.C);
+    k_halo_gather2<<<gg, 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    p->launches += 1;
+    return KP_OK;
+}
+
 template <int D, typename UT, int CG>
 static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
     const Geom& g = p->geo;
@@ -1542,8 +1686,8 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
 // the free device memory, at most 16 GiB); false when it does not.
 static bool ensure_halo(kp_plan p) {
     const Geom& g = p->geo;
-    if (g.D != 3 || p->n_oitems == 0) return false;
-    const size_t need = (size_t)p->n_oitems * g.C * PT3;
+    if (p->n_oitems == 0) return false;
+    const size_t need = (size_t)p->n_oitems * g.C * (g.D == 3 ? PT3 : PT2SQ);
     if (p->d_halo && p->halo_cap >= need) return true;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
@@ -1613,6 +1757,7 @@ static kp_status spread_only(kp_plan p, const void* u, kp_cdtype u_t, const int*
                 case 9: KP_TRY((launch_spread_z<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
                 case 10: KP_TRY((launch_spread_own<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
                 case 11: KP_TRY((launch_spread_own<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
+                case 12: KP_TRY((launch_spread_own2<UT>(p, (const UT*)u, perm, st))); break;
                 default: KP_TRY((launch_spread_priv<DD, UT, 2, 4>(p, (const UT*)u, perm, st))); break;
             }));
     } else if (p->spread_variant == 2) {
@@ -1651,8 +1796,8 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
 // trajectory).  Variants: 0 private copies, 4 coils x 4 warps; 1 shared atomics; 2 warp per
 // 4 coils; 3 private, 2 coils x 8 warps; 4 private, 1 coil x 8 warps; 5 private, 2 coils x 4
 // warps; 6, 7 private interleaved coil pairs, 4 coils x 4 / 8 warps; 8, 9 (3D) z-plane owners,
-// 8 / 4 coils; 10, 11 (3D) two-phase padded tiles + gather, 8 / 4 coils (when their slot
-// storage fits).  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
+// 8 / 4 coils; 10, 11 (3D) two-phase padded tiles + gather, 8 / 4 coils, and 12 (2D) two-phase
+// with warp-private padded tiles (when their slot storage fits).  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
 kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (p->spread_tuned) {
         // a new trajectory may need more slots than the two-phase variants hold
@@ -1664,15 +1809,21 @@ kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (const char* ev = getenv("KPDHG_SPREAD_CHUNK")) force_c = atoi(ev);
     const Geom& g = p->geo;
     const bool wc_ok = (g.D == 2 ? spread_warpcoil_smem<2>(g.C) : spread_warpcoil_smem<3>(g.C)) <= 220 * 1024;
-    const bool own_ok = g.D == 3 && ensure_halo(p);
-    if (force_v > 11 || (force_v == 2 && !wc_ok) || (force_v >= 8 && g.D != 3) || (force_v >= 10 && !own_ok)) force_v = -1;
+    const bool own_ok = ensure_halo(p);
+    const auto applies = [&](int v) {
+        if (v == 2) return wc_ok;
+        if (v >= 8 && v <= 11) return g.D == 3 && (v < 10 || own_ok);
+        if (v == 12) return g.D == 2 && own_ok;
+        return v >= 0 && v <= 7;
+    };
+    if (!applies(force_v)) force_v = -1;
     if (force_c < SP_CHUNK || force_c % SP_CHUNK != 0) force_c = 0;
     std::vector<int> chunks;
     if (force_c) chunks.push_back(force_c);
     else chunks = {256, 1024, 4096};
     std::vector<int> variants;
     if (force_v >= 0) variants.push_back(force_v);
-    else for (int v = 0; v <= 11; ++v) if ((v != 2 || wc_ok) && (v < 8 || g.D == 3) && (v < 10 || own_ok)) variants.push_back(v);
+    else for (int v = 0; v <= 12; ++v) if (applies(v)) variants.push_back(v);
     if (chunks.size() == 1 && variants.size() == 1) {
         p->spread_variant = variants[0];
         if (chunks[0] != p->spread_chunk) KP_TRY(build_spread_items(p, chunks[0], st));

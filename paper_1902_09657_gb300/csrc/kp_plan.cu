@@ -454,6 +454,7 @@ kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st) {
 kp_status build_own_items(kp_plan p, cudaStream_t st) {
     const Tiles& tl = p->tiles;
     const unsigned tb = nblk(tl.ntiles, 256);
+    p->own_chunk = p->geo.D == 2 ? 512 : 4096;   // 2D grids have few tiles: shorter items spread the work
     if (!p->d_tslot) KP_TRY_CUDA(cudaMalloc(&p->d_tslot, (tl.ntiles + 1) * sizeof(int)));
     k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->own_chunk, p->d_cnt);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_tslot, tl.ntiles);
@@ -542,7 +543,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     KP_LAUNCH_CHECK();
     KP_TRY(sort_items_longest_first(p->d_iitems, p->n_iitems, st));
     p->launches += 11;
-    if (g.D == 3) KP_TRY(build_own_items(p, st));
+    KP_TRY(build_own_items(p, st));
     p->traj_set = true;
     return autotune_spread(p, st);
 }

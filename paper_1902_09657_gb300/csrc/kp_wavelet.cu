@@ -1039,7 +1039,7 @@ kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st) {
     p->launches += 1;
     mark(p, PH_FWD_PRE, st);
     const int nb_pre = 2 * 152;
-    const unsigned nb = (unsigned)(nb_pre + p->n_split);
+    const unsigned nb = (unsigned)(nb_pre + (p->spread_variant >= 10 ? 0 : p->n_split));   // 10-12 store every point
     const kp_cdtype mt = p->maps_t;
     if (mt == KP_C64)
         k_pre_clear<float2><<<nb, 256, 0, st>>>(p->d_xbar, (const float2*)p->d_maps, p->d_apod, g, p->d_grid, nb_pre,

@@ -114,12 +114,12 @@ def test_invalid_params_rejected():
         Plan((30, 32), 2, 100, wavelet_levels=3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("chunk", [256, 1024])
 def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
     """Every spreading kernel variant and work-item size (fixed through the tuning overrides)
     gives the oracle's adjoint, on centre-dense radial trajectories whose central tiles are
-    cut into many items (2D and 3D; variants 8 to 11 exist in 3D only).  The 3D case has 2
+    cut into many items (2D and 3D; variants 8 to 11 exist in 3D only, 12 in 2D only).  The 3D case has 2
     coils, so coil groups are partly empty."""
     need_gpu()
     import synth
@@ -129,8 +129,8 @@ def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
              ((16, 16, 16), 2, synth.radial_3d_fibonacci(n_spokes=600, n_readout=16, kmax=8.0)),
              ((12, 12, 12), 10, synth.radial_3d_fibonacci(n_spokes=300, n_readout=12, kmax=6.0))]
     for shape, C, traj in cases:
-        if variant >= 8 and len(shape) == 2:
-            continue                                  # z-plane owners and two-phase are 3D kernels
+        if (8 <= variant <= 11 and len(shape) == 2) or (variant == 12 and len(shape) == 3):
+            continue                                  # variants 8-11 are 3D kernels, 12 is 2D
         M = traj.shape[0]
         rng = np.random.default_rng(M)
         maps = (rng.standard_normal((C,) + shape) + 1j * rng.standard_normal((C,) + shape)).astype(np.complex64)
