@@ -216,12 +216,15 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the default
 # workload's kernels from one `ncu --set full` capture of `bench.py --steps 2 --warmup 3
-# --no-extras` (the 301st to 303rd matching launches, spreading variant 6 at 256 samples).
-# Entries are valid only for the kernel code they were taken on; set one to None when its
-# kernel changes until it is captured again.
+# --no-extras` (matching launches 501-505, spreading variant 6 at 256 samples).  Entries are
+# valid only for the kernel code they were taken on; set one to None when its kernel changes
+# until it is captured again.
 NCU_TRAFFIC = {
-    "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19913984},
-    "interp_dual": {"kernel": "k_interp_tile<2, 2, float2>", "bytes": 36180736},
+    "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19909120},
+    "dwt_fwd": {"kernel": "k_wprox_cluster<16>", "bytes": 1074176},
+    "interp_dual": {"kernel": "k_interp_tile<2, 2, float2>", "bytes": 36179712},
+    "adj_primal": {"kernel": "k_adj_primal<2, float2, 1>", "bytes": 13121280},
+    "fwd_pre": {"kernel": "k_pre_clear<float2>", "bytes": 6828288},
 }
 
 
