@@ -220,7 +220,7 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
 # valid only for the kernel code they were taken on; set one to None when its kernel changes
 # until it is captured again.
 NCU_TRAFFIC = {
-    "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19909120},
+    "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19909120, "variant": 6},
     "dwt_fwd": {"kernel": "k_wprox_cluster<16>", "bytes": 1074176},
     "interp_dual": {"kernel": "k_interp_tile<2, 2, float2>", "bytes": 36179712},
     "adj_primal": {"kernel": "k_adj_primal<2, float2, 1>", "bytes": 13121280},
@@ -361,6 +361,11 @@ def gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stre
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = ab[dom] / (own[dom] * 1e-3) / 1e9
     tr_entry = NCU_TRAFFIC.get(dom) if w.name == WORKLOAD else None
+    if dom == "spread":
+        sc = plan.spread_config()
+        out["spread_config"] = sc
+        if tr_entry and tr_entry.get("variant") not in (None, sc["variant"]):
+            tr_entry = None       # captured on another spreading variant than the one timed here
     out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                        "frac": achieved / peak, "traffic": tr_entry["bytes"] if tr_entry else None,
                        "traffic_source": ("one ncu capture of " + tr_entry["kernel"] + " on this workload")

@@ -313,7 +313,9 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
 kp_status build_tap_tables(kp_plan p, cudaStream_t st);
 kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, const int* perm, cudaStream_t st);
 kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st);
-kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st);
+// out = p (A x) in sorted order, divided by sqrt(*n2) when n2 is given (a norm kept on the device)
+kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st,
+                         const double* n2 = nullptr);
 // A^H u: u [C][M] (sorted order if perm == nullptr, else user order) -> grid -> x.
 // splits_zeroed: the split tiles' regions of d_grid2 are already zero (the fused primal kernel
 // clears them after its last read of d_grid2, and solve set-up clears them once)

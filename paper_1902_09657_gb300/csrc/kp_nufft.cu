@@ -180,6 +180,7 @@ struct InterpIO {
     const float* sched;
     const int* iter;
     int* flag;           // set to 1 if the staging wait gave up (reported as KP_ETIMEOUT)
+    const double* n2;    // mode 1: when set, the output is also divided by sqrt(*n2)
 };
 
 // Staged region geometry: R points per axis for the largest tile edge (16 in 2D, 8 in 3D);
@@ -351,7 +352,11 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
             const int64_t oi = io.perm ? io.perm[s] : s;
             stc<T>((T*)io.out, (size_t)(c0 + c) * geo.M + oi, acc);
         } else if (MODE == 1) {
-            const float sc = io.ps ? io.ps[os] : 1.f;
+            float sc = io.ps ? io.ps[os] : 1.f;
+            if (io.n2) {   // float reciprocal square root: fp64 division here costs more than the taps
+                const float q = (float)*io.n2;
+                sc *= q > 0.f ? rsqrtf(q) : 0.f;
+            }
             io.outs[os] = make_float2(acc.x * sc, acc.y * sc);
         } else {
             // PDHG dual step (Sec. 4.1): u <- (u + sigma p (A xbar - y)) / (1 + sigma p)
@@ -1600,11 +1605,13 @@ kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, con
     return launch_interp<0>(p, out_t, io, st);
 }
 
-kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st) {
+kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const float* ps, cudaStream_t st,
+                         const double* n2) {
     KP_TRY(fwd_grid(p, x, st));
     InterpIO io{};
     io.outs = out_sorted;
     io.ps = ps;
+    io.n2 = n2;
     io.flag = p->d_flag + 3;
     return launch_interp<1>(p, KP_C64, io, st);
 }

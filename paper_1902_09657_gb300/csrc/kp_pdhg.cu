@@ -121,18 +121,39 @@ __global__ void k_pmin(const float* __restrict__ p, int64_t n, int* __restrict__
     if (nb) atomicAdd(bad, nb);
 }
 
-// v <- w / ||w||; lmax <- ||w|| (power method step, ||v_prev|| = 1)
-__global__ void k_normalize(const float2* __restrict__ w, float2* __restrict__ v, int64_t n,
-                            const double* __restrict__ n2, double* __restrict__ lmax_out) {
-    const double nrm = sqrt(*n2);
-    const float inv = nrm > 0 ? (float)(1.0 / nrm) : 0.f;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && lmax_out) *lmax_out = nrm;
-    if (i < n) {
-        float2 a = w[i];
-        v[i] = make_float2(a.x * inv, a.y * inv);
+// ||x||^2 added into *out and, in the same launch, the split spreading tiles of grid2 cleared
+// for the next spread (the previous kernel was the last to read grid2).
+template <int D>
+__global__ void k_norm2_clear(const float2* __restrict__ x, int64_t n, double* __restrict__ out,
+                              const int* __restrict__ split, int n_split, Geom geo, Tiles tl, float2* __restrict__ grid2) {
+    double s = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float2 v = x[i];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    block_sum_to<int>(s, out);
+    for (int t = blockIdx.x; t < n_split; t += gridDim.x) {    // one split tile per block pass
+        int r = split[t], o[MAXD], e[MAXD], P = 1;
+        for (int d = D - 1; d >= 0; --d) {
+            const int tc = r % tl.nt[d];
+            r /= tl.nt[d];
+            o[d] = tc * tl.ts[d];
+            e[d] = min(tl.ts[d], geo.g[d] - o[d]);
+        }
+        for (int d = 0; d < D; ++d) P *= e[d];
+        for (int i = threadIdx.x; i < geo.C * P; i += blockDim.x) {
+            const int c = i / P;
+            int rr = i - c * P, lidx[MAXD];
+            for (int d = D - 1; d >= 0; --d) { lidx[d] = rr % e[d]; rr /= e[d]; }
+            int64_t gflat = 0;
+            for (int d = 0; d < D; ++d) gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
+            grid2[(size_t)c * geo.G + gflat] = make_float2(0.f, 0.f);
+        }
     }
 }
+
+__global__ void k_store_sqrt(const double* __restrict__ n2, double* __restrict__ out) { *out = sqrt(*n2); }
 
 // Step sizes (Sec. 4.1): sigma_0 = 1, tau_0 = 1/L, theta_k = 1/(1 + 2 sigma_k pmin),
 // sigma_{k+1} = theta_k sigma_k, tau_{k+1} = tau_k / theta_k; float64 recursion.
@@ -181,22 +202,34 @@ static kp_status reduce_norm2(kp_plan p, const float2* x, int64_t n, double* out
 }
 
 // Power method on A^H P A (Sec. 6: 30 iterations) using the sorted p in d_ps (or none).
-// Start vector in d_z (unnormalised); result L in d_schedd[0].
+// Start vector in d_z (unnormalised); result L in d_schedd[0].  Each iteration applies
+// A^H P A to w / ||w|| without forming it: the forward pre-step reads w and the interpolation
+// divides by ||w||, taken from the device (the same vector up to rounding order); the norm
+// kernel also clears the split spreading tiles for the next spread.  L = ||w|| of the last
+// iteration, w = A^H P A v with v of unit norm.
 static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cudaStream_t st) {
     const Geom& g = p->geo;
+    const int n_split = p->spread_variant >= 10 ? 0 : (int)p->n_split;   // 10-12 store every point
+    const unsigned nb = (unsigned)std::min<int64_t>(nblk(g.N, 256), 1216);
+    KP_TRY(zero_split_only(p, st));
     KP_TRY(reduce_norm2(p, p->d_z, g.N, p->d_red, st));
-    k_normalize<<<nblk(g.N, 256), 256, 0, st>>>(p->d_z, p->d_z, g.N, p->d_red, nullptr);
-    KP_LAUNCH_CHECK();
-    p->launches += 1;
+    const float2* w = p->d_z;
     for (int it = 0; it < iters; ++it) {
-        KP_TRY(forward_scaled(p, p->d_z, p->d_kt, ps_sorted, st));
-        KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st));
+        KP_TRY(forward_scaled(p, w, p->d_kt, ps_sorted, st, p->d_red));
+        KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st, /*splits_zeroed=*/true));
         KP_TRY(grid_to_image(p, p->d_w, st));
-        KP_TRY(reduce_norm2(p, p->d_w, g.N, p->d_red, st));
-        k_normalize<<<nblk(g.N, 256), 256, 0, st>>>(p->d_w, p->d_z, g.N, p->d_red, p->d_schedd);
+        KP_TRY_CUDA(cudaMemsetAsync(p->d_red, 0, sizeof(double), st));
+        if (g.D == 2)
+            k_norm2_clear<2><<<nb, 256, 0, st>>>(p->d_w, g.N, p->d_red, p->d_split, n_split, g, p->tiles, p->d_grid2);
+        else
+            k_norm2_clear<3><<<nb, 256, 0, st>>>(p->d_w, g.N, p->d_red, p->d_split, n_split, g, p->tiles, p->d_grid2);
         KP_LAUNCH_CHECK();
         p->launches += 1;
+        w = p->d_w;
     }
+    k_store_sqrt<<<1, 1, 0, st>>>(p->d_red, p->d_schedd);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
     return KP_OK;
 }
 
