@@ -91,6 +91,26 @@ struct PerDeviceOnce {
     }
 };
 
+// Per-device dynamic shared memory limit of one kernel whose requirement depends on the plan
+// (devices 0..63): ensure() raises the limit to at least `bytes` and never lowers it, so that
+// plans of different sizes can share the kernel in any order.
+struct SmemLimit {
+    std::atomic<int> cur[64] = {};
+    template <typename F>
+    cudaError_t ensure(F* fn, size_t bytes) {
+        int d = 0;
+        cudaError_t e = cudaGetDevice(&d);
+        if (e != cudaSuccess) return e;
+        std::atomic<int>& c = cur[d & 63];
+        int have = c.load();
+        if ((int)bytes <= have) return cudaSuccess;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        while (have < (int)bytes && !c.compare_exchange_weak(have, (int)bytes)) {}
+        return cudaSuccess;
+    }
+};
+
 // ---------------------------------------------------------------- complex storage helpers
 __host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __host__ __device__ inline float2 cmulc(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); } // conj(a)*b

@@ -973,8 +973,14 @@ static cudaLaunchConfig_t cluster_cfg(size_t sm, cudaStream_t st, cudaLaunchAttr
 
 // Sets the kernel's attributes on the current device and asks whether one cluster fits.
 template <int NC>
+static SmemLimit& cluster_limit() {
+    static SmemLimit lim;
+    return lim;
+}
+
+template <int NC>
 static bool cluster_fits(size_t sm) {
-    if (cudaFuncSetAttribute(k_wprox_cluster<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+    if (cluster_limit<NC>().ensure(k_wprox_cluster<NC>, sm) != cudaSuccess ||
         (NC > 8 && cudaFuncSetAttribute(k_wprox_cluster<NC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
         cudaGetLastError();
         return false;
@@ -1022,15 +1028,13 @@ kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st) {
     const size_t sm = cluster_smem(g, nc);
     cudaLaunchAttribute at[1];
     if (nc == 16) {
-        static PerDeviceOnce attr;
-        if (attr.first() && !cluster_fits<16>(sm)) { set_error("cluster prox does not fit"); return KP_EINTERNAL; }
+        KP_TRY_CUDA(cluster_limit<16>().ensure(k_wprox_cluster<16>, sm));
         cudaLaunchConfig_t cfg = cluster_cfg<16>(sm, st, at);
         KP_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_wprox_cluster<16>, (const float2*)p->d_z, p->d_x, p->d_xbar,
                                        (const float*)p->d_sched, (const int*)p->d_iter, lambda, g.n[0], g.n[1],
                                        p->P.wavelet_levels));
     } else {
-        static PerDeviceOnce attr;
-        if (attr.first() && !cluster_fits<8>(sm)) { set_error("cluster prox does not fit"); return KP_EINTERNAL; }
+        KP_TRY_CUDA(cluster_limit<8>().ensure(k_wprox_cluster<8>, sm));
         cudaLaunchConfig_t cfg = cluster_cfg<8>(sm, st, at);
         KP_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_wprox_cluster<8>, (const float2*)p->d_z, p->d_x, p->d_xbar,
                                        (const float*)p->d_sched, (const int*)p->d_iter, lambda, g.n[0], g.n[1],

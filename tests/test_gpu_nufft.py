@@ -143,3 +143,30 @@ def test_spread_variants_and_item_sizes(variant, chunk, monkeypatch):
         assert cfg["split_tiles"] > 0 or variant >= 10
         xa = plan.sense_adjoint(to_dev(u)).cpu().numpy()
         assert rel(xa, x_ref) < 1e-5, (shape, cfg)
+
+
+# Image sizes whose 1.25x grids (rounded up to even) have the prime factors 2, 3, 5, 7 and 13
+# on either axis, with ragged tiles.
+GRID_CASES = [
+    (32, 32),       # 40 x 40
+    (48, 40),       # 60 x 50
+    (56, 44),       # 70 x 56
+    (100, 40),      # 126 x 50
+    (20, 100),      # 26 x 126
+]
+
+
+@pytest.mark.parametrize("shape", GRID_CASES)
+def test_forward_adjoint_grid_sizes(shape):
+    """Forward and adjoint against the oracle on grids of mixed-radix and prime-factor sizes."""
+    need_gpu()
+    C, M = 3, 2500
+    x, maps, traj = random_problem(shape, C, M, 11, edge=True)
+    u = (np.random.default_rng(12).standard_normal((C, M))
+         + 1j * np.random.default_rng(13).standard_normal((C, M))).astype(np.complex64)
+    y_ref = onf.nufft_forward(x.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+    x_ref = onf.nufft_adjoint(u.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+    plan = make_plan(shape, C, M, 1.25)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    assert rel(plan.sense_forward(to_dev(x)).cpu().numpy(), y_ref) < 1e-5
+    assert rel(plan.sense_adjoint(to_dev(u)).cpu().numpy(), x_ref) < 1e-5

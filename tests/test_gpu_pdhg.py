@@ -84,6 +84,26 @@ def test_pdhg_l1_primal_paths(cluster, monkeypatch):
     assert rel(xg2.cpu().numpy(), x_ref) < 1e-5          # graph replay of the same path
 
 
+def test_cluster_prox_plans_of_different_sizes():
+    """Two 2D l1 plans on the 16-CTA cluster prox with different shared-memory needs (128^2 with
+    3 levels: 18 KB; 64^2 with 2 levels: 5 KB), solved in turn: the larger plan's second solve
+    (after the smaller plan's) still launches and repeats its first result."""
+    need_gpu()
+    runs = []
+    for n, lev in ((128, 3), (64, 2)):
+        w, x, maps, traj = _small_spiral(n=n, C=2, L=4, ns=1024)
+        y = simulate(w, x, maps, traj)
+        plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=lev)
+        plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+        lam = 1e-3 * float(plan.sense_adjoint(to_dev(y)).abs().max())
+        runs.append((plan, to_dev(y), lam))
+    xa1 = runs[0][0].pdhg_solve(runs[0][1], None, "l1_wavelet", runs[0][2], 10)[0].cpu().numpy()
+    xb = runs[1][0].pdhg_solve(runs[1][1], None, "l1_wavelet", runs[1][2], 10)[0].cpu().numpy()
+    xa2 = runs[0][0].pdhg_solve(runs[0][1], None, "l1_wavelet", runs[0][2], 10)[0].cpu().numpy()
+    assert np.isfinite(xb).all()
+    assert rel(xa2, xa1) < 1e-5
+
+
 @pytest.mark.parametrize("name,alpha,iters", [("radial2d_128", 2.0, 30), ("spiral2d_256", 1.25, 8)])
 def test_pdhg_full_chain_workloads(name, alpha, iters):
     """Whole chain on the full-size 2D workloads: GPU builds p (MC) and lambda_max itself."""
