@@ -10,28 +10,33 @@
 // one FFT: |Q_dc|^2[m] = |Q_cd|^2[-m].  Single channel (Eq. sc_precond): C = 1, s = 1.
 #include "kp_internal.cuh"
 
+#include <algorithm>
 #include <vector>
 
 namespace kp {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Device memory the construction may use for a batch of 2N-grid spectra.
+constexpr size_t PRE_BATCH_BYTES = (size_t)256 << 20;
+
 struct PrePlan {
     int D = 0;
     int nb[MAXD] = {1, 1, 1};
     int64_t Nb = 0;
     int C = 0;            // coils of the owning plan
-    int B = 0;            // pairs per FFT batch
+    int B = 0;            // pairs per FFT batch (all pairs when they fit in the budget below)
+    int Cb = 0;           // coils per batch of the r_c -> v_c steps
     double* d_R = nullptr;      // [C][Nb]
     float2* d_q = nullptr;      // [B][Nb]
-    float2* d_r = nullptr;      // [Nb]
+    float2* d_r = nullptr;      // [Cb][Nb]
     float2* d_h = nullptr;      // [Nb]
-    float2* d_v = nullptr;      // [Nb]
+    float2* d_v = nullptr;      // [Cb][Nb]
     double* d_norm = nullptr;   // [C]
     int2* d_pairs = nullptr;    // [C(C+1)/2]
     int npairs = 0;
-    cufftHandle fft_pairs = 0, fft_one = 0;
-    bool ok_pairs = false, ok_one = false;
+    cufftHandle fft_pairs = 0, fft_one = 0, fft_coils = 0;
+    bool ok_pairs = false, ok_one = false, ok_coils = false;
     int traj_version = -1;
 };
 
@@ -41,6 +46,7 @@ void pre_destroy(kp_plan p) {
     if (!q) return;
     if (q->ok_pairs) cufftDestroy(q->fft_pairs);
     if (q->ok_one) cufftDestroy(q->fft_one);
+    if (q->ok_coils) cufftDestroy(q->fft_coils);
     void* bufs[] = {q->d_R, q->d_q, q->d_r, q->d_h, q->d_v, q->d_norm, q->d_pairs};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -59,13 +65,18 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     q->Nb = 1;
     for (int d = 0; d < g.D; ++d) { q->nb[d] = 2 * g.n[d]; q->Nb *= q->nb[d]; }
     q->npairs = g.C * (g.C + 1) / 2;
+    // every pair spectrum at once when they fit in PRE_BATCH_BYTES (one FFT batch, R written
+    // once per coil), else batches of 16 (2D) or 2 (3D) accumulated into R
+    const size_t grid_bytes = (size_t)q->Nb * sizeof(float2);
     const int bmax = g.D == 2 ? 16 : 2;
-    q->B = q->npairs < bmax ? q->npairs : bmax;
+    if ((size_t)q->npairs * grid_bytes <= PRE_BATCH_BYTES) q->B = q->npairs;
+    else q->B = q->npairs < bmax ? q->npairs : bmax;
+    q->Cb = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.C, PRE_BATCH_BYTES / (2 * grid_bytes)));
     KP_TRY_CUDA(cudaMalloc(&q->d_R, (size_t)g.C * q->Nb * sizeof(double)));
     KP_TRY_CUDA(cudaMalloc(&q->d_q, (size_t)q->B * q->Nb * sizeof(float2)));
-    KP_TRY_CUDA(cudaMalloc(&q->d_r, (size_t)q->Nb * sizeof(float2)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_r, (size_t)q->Cb * q->Nb * sizeof(float2)));
     KP_TRY_CUDA(cudaMalloc(&q->d_h, (size_t)q->Nb * sizeof(float2)));
-    KP_TRY_CUDA(cudaMalloc(&q->d_v, (size_t)q->Nb * sizeof(float2)));
+    KP_TRY_CUDA(cudaMalloc(&q->d_v, (size_t)q->Cb * q->Nb * sizeof(float2)));
     KP_TRY_CUDA(cudaMalloc(&q->d_norm, (size_t)g.C * sizeof(double)));
     std::vector<int2> pairs;
     for (int c = 0; c < g.C; ++c)
@@ -77,6 +88,8 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     q->ok_pairs = true;
     KP_TRY_CUFFT(cufftPlanMany(&q->fft_one, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, 1));
     q->ok_one = true;
+    KP_TRY_CUFFT(cufftPlanMany(&q->fft_coils, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, q->Cb));
+    q->ok_coils = true;
     // NUFFT on the 2N image with unit maps and one coil
     kp_params prm = p->P;
     prm.ncoils = 1;
@@ -146,16 +159,50 @@ __global__ void k_accum_R(const float2* __restrict__ Q, const int2* __restrict__
     }
 }
 
-__global__ void k_R_to_c(const double* __restrict__ R, int64_t Nb, float2* __restrict__ out) {
+// With every pair's spectrum in Q (pair (c, d), c <= d, at index c C - c (c - 1) / 2 + d - c):
+// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, written once (float64).
+__global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0, int nb1, int nb2, int64_t Nb,
+                            double* __restrict__ R) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < Nb) out[m] = make_float2((float)(R[m] / (double)Nb), 0.f);
+    if (m >= Nb) return;
+    const int nb[3] = {nb0, nb1, nb2};
+    int64_t r = m, mneg = 0, stride = 1;
+    for (int d = D - 1; d >= 0; --d) {
+        int i = (int)(r % nb[d]);
+        r /= nb[d];
+        int in = i == 0 ? 0 : nb[d] - i;
+        mneg += in * stride;
+        stride *= nb[d];
+    }
+    for (int c = 0; c < C; ++c) {
+        double acc = 0.0;
+        for (int d = 0; d < c; ++d) {
+            const float2 b = Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg];
+            acc += (double)b.x * b.x + (double)b.y * b.y;
+        }
+        const size_t p0 = (size_t)(c * C - c * (c - 1) / 2);
+        for (int d = c; d < C; ++d) {
+            const float2 a = Q[(p0 + d - c) * Nb + m];
+            acc += (double)a.x * a.x + (double)a.y * a.y;
+        }
+        R[(size_t)c * Nb + m] = acc;
+    }
+}
+
+// r_c = R_c / Nb for the coils c0 .. c0 + nc - 1 (grid c - c0 of out).
+__global__ void k_R_to_c(const double* __restrict__ R, int64_t Nb, int nc, float2* __restrict__ out) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < Nb * nc) out[m] = make_float2((float)(R[m] / (double)Nb), 0.f);
 }
 
 // v[j] = r[(j - n) mod 2n] * h[j] on the centred 2N image (lag k_d = j_d - n_d).
+// (blockIdx.y selects the coil of a batch: r and v advance by Nb per coil)
 __global__ void k_rh(const float2* __restrict__ r, const float2* __restrict__ h, int D, int nb0, int nb1, int nb2,
                      int64_t Nb, float2* __restrict__ v) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Nb) return;
+    r += (size_t)blockIdx.y * Nb;
+    v += (size_t)blockIdx.y * Nb;
     const int nb[3] = {nb0, nb1, nb2};
     int64_t rr = j, ri = 0, stride = 1;
     for (int d = D - 1; d >= 0; --d) {
@@ -246,30 +293,37 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
     KP_LAUNCH_CHECK();
     plan->launches += 1;
     // R_c = sum_d |FFT(q_cd)|^2
-    KP_TRY_CUDA(cudaMemsetAsync(q->d_R, 0, (size_t)C * q->Nb * sizeof(double), st));
     KP_TRY_CUFFT(cufftSetStream(q->fft_pairs, st));
     KP_TRY_CUFFT(cufftSetStream(q->fft_one, st));
+    KP_TRY_CUFFT(cufftSetStream(q->fft_coils, st));
     const int npairs = mc ? q->npairs : 1;
+    const bool all_at_once = mc && npairs == q->B && npairs > 1;
+    if (!all_at_once) KP_TRY_CUDA(cudaMemsetAsync(q->d_R, 0, (size_t)C * q->Nb * sizeof(double), st));
     for (int p0 = 0; p0 < npairs; p0 += q->B) {
         const int nv = npairs - p0 < q->B ? npairs - p0 : q->B;
+        const int nwrite = nv == 1 ? 1 : q->B;      // a lone pair goes through the batch-1 plan
         switch (mc ? plan->maps_t : KP_C64) {
             case KP_C64:
                 k_make_q<float2><<<nblk(q->Nb, 256), 256, 0, st>>>(mc ? (const float2*)plan->d_maps : nullptr, q->d_pairs, p0, nv, g,
-                                                                   g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->B, q->d_q);
+                                                                   g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, nwrite, q->d_q);
                 break;
             case KP_C32_BF16:
                 k_make_q<__nv_bfloat162><<<nblk(q->Nb, 256), 256, 0, st>>>((const __nv_bfloat162*)plan->d_maps, q->d_pairs, p0, nv, g,
-                                                                           g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->B, q->d_q);
+                                                                           g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, nwrite, q->d_q);
                 break;
             default:
                 k_make_q<__half2><<<nblk(q->Nb, 256), 256, 0, st>>>((const __half2*)plan->d_maps, q->d_pairs, p0, nv, g,
-                                                                    g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->B, q->d_q);
+                                                                    g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, nwrite, q->d_q);
                 break;
         }
         KP_LAUNCH_CHECK();
-        KP_TRY_CUFFT(cufftExecC2C(q->fft_pairs, (cufftComplex*)q->d_q, (cufftComplex*)q->d_q, CUFFT_FORWARD));
-        k_accum_R<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_q, q->d_pairs, p0, nv, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb,
-                                                    q->d_R, !mc);
+        KP_TRY_CUFFT(cufftExecC2C(nwrite == 1 ? q->fft_one : q->fft_pairs, (cufftComplex*)q->d_q, (cufftComplex*)q->d_q,
+                                  CUFFT_FORWARD));
+        if (all_at_once)
+            k_accum_all<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_q, C, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_R);
+        else
+            k_accum_R<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_q, q->d_pairs, p0, nv, g.D, q->nb[0], q->nb[1], q->nb[2],
+                                                        q->Nb, q->d_R, !mc);
         KP_LAUNCH_CHECK();
         plan->launches += 2;
     }
@@ -279,17 +333,24 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
     KP_TRY(adjoint_to_grid(nu, nu->d_kt, KP_C64, nullptr, st));
     KP_TRY(grid_to_image(nu, q->d_h, st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag + 7, 0, sizeof(int), st));
-    for (int c = 0; c < C; ++c) {
-        k_R_to_c<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_R + (size_t)c * q->Nb, q->Nb, q->d_r);
+    // per batch of Cb coils: r_c = IFFT(R_c) / Nb, v_c = r_c * h; then per coil the forward
+    // NUFFT of v_c and p_c
+    for (int c0 = 0; c0 < C; c0 += q->Cb) {
+        const int nc = C - c0 < q->Cb ? C - c0 : q->Cb;
+        k_R_to_c<<<nblk(q->Nb * nc, 256), 256, 0, st>>>(q->d_R + (size_t)c0 * q->Nb, q->Nb, nc, q->d_r);
         KP_LAUNCH_CHECK();
-        KP_TRY_CUFFT(cufftExecC2C(q->fft_one, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r, CUFFT_INVERSE));
-        k_rh<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_r, q->d_h, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v);
+        KP_TRY_CUFFT(cufftExecC2C(nc == 1 ? q->fft_one : q->fft_coils, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r,
+                                  CUFFT_INVERSE));
+        k_rh<<<dim3(nblk(q->Nb, 256), nc), 256, 0, st>>>(q->d_r, q->d_h, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v);
         KP_LAUNCH_CHECK();
-        KP_TRY(forward_to(nu, q->d_v, nu->d_kt, KP_C64, nullptr, st));
-        k_p_out<<<nblk(g.M, 256), 256, 0, st>>>(nu->d_kt, nu->d_perm, g.M, q->d_norm, c, mc ? c : 0, mc ? 1 : g.C, g.D,
-                                                p_dev, plan->d_flag + 7);
-        KP_LAUNCH_CHECK();
-        plan->launches += 3;
+        plan->launches += 2;
+        for (int c = c0; c < c0 + nc; ++c) {
+            KP_TRY(forward_to(nu, q->d_v + (size_t)(c - c0) * q->Nb, nu->d_kt, KP_C64, nullptr, st));
+            k_p_out<<<nblk(g.M, 256), 256, 0, st>>>(nu->d_kt, nu->d_perm, g.M, q->d_norm, c, mc ? c : 0, mc ? 1 : g.C, g.D,
+                                                    p_dev, plan->d_flag + 7);
+            KP_LAUNCH_CHECK();
+            plan->launches += 1;
+        }
     }
     return KP_OK;
 }
