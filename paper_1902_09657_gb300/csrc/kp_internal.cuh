@@ -236,6 +236,11 @@ struct kp_plan_s {
     int* d_item_off = nullptr;       // [ntiles + 1]
     int* d_slot_off = nullptr;       // [ntiles + 1] first partial slot of each split tile
     int* d_nslots = nullptr;         // [ntiles + 1] partial slots per tile (0 = not split)
+    int* d_sflag = nullptr;          // [ntiles + 1] 1 for a split tile
+    int* d_spos = nullptr;           // [ntiles + 1] position of each split tile in d_split
+    int* d_iitem_off = nullptr;      // [ntiles + 1] first interpolation item of each tile
+    int* d_counts = nullptr;         // [8] flags and item counts for the host
+    int4* d_sort_tmp = nullptr;      // [8192] scratch of the item sort
     int* d_split = nullptr;          // tiles whose list spans several work items
     int64_t n_split = 0, split_cap = 0;
     int* d_k0 = nullptr;             // [D][M] wrapped first tap per sorted sample
@@ -357,7 +362,6 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st);
-kp_status build_own_items(kp_plan p, cudaStream_t st);
 kp_status make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st);
 kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);

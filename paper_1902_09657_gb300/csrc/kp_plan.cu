@@ -193,6 +193,68 @@ __global__ void k_items(const int* __restrict__ ext_off, const int* __restrict__
     }
 }
 
+// Split tiles (tiles with partial slots) in tile order: f[t] = 1 for a split tile; the exclusive
+// scan of f gives each its position in the list.
+__global__ void k_split_flags(const int* __restrict__ nsl, int64_t ntiles, int* __restrict__ f) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) f[t] = nsl[t] > 0 ? 1 : 0;
+}
+
+__global__ void k_split_list(const int* __restrict__ nsl, const int* __restrict__ pos, int64_t ntiles,
+                             int* __restrict__ split) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles && nsl[t] > 0) split[pos[t]] = (int)t;
+}
+
+// Everything the host needs after binning, in one array for one copy: the four trajectory
+// flags, then the numbers of spreading items, split tiles, interpolation items and own items.
+__global__ void k_gather_counts(const int* __restrict__ flag, const int* __restrict__ n_items,
+                                const int* __restrict__ n_split, const int* __restrict__ n_iitems,
+                                const int* __restrict__ n_oitems, int* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) out[i] = flag[i];
+        out[4] = *n_items;
+        out[5] = *n_split;
+        out[6] = *n_iitems;
+        out[7] = *n_oitems;
+    }
+}
+
+// Longest-first order of at most SORT_MAX work items (length z - y descending; equal lengths
+// keep their index order, as a stable sort would): one CTA sorts the keys
+// (2^18 - 1 - length) * 2^13 + index bitonically in shared memory, then out[i] = in[index of
+// the i-th key].
+constexpr int SORT_MAX = 8192;
+__global__ void __launch_bounds__(1024) k_sort_items(const int4* __restrict__ in, int n, int4* __restrict__ out) {
+    __shared__ unsigned key[SORT_MAX];
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        if (i < n) {
+            const int len = max(0, min(in[i].z - in[i].y, (1 << 18) - 1));
+            key[i] = ((unsigned)((1 << 18) - 1 - len) << 13) | (unsigned)i;
+        } else {
+            key[i] = 0xFFFFFFFFu;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned a = key[i], b = key[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        key[i] = b;
+                        key[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = in[key[i] & 0x1FFFu];
+}
+
 template <typename T>
 __global__ void k_copy_maps(const T* __restrict__ in, T* __restrict__ out, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,6 +409,11 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
         KP_A(p->d_wl1, (N >> D) + 1);
     }
     KP_A(p->d_red, 16);
+    KP_A(p->d_sflag, tl.ntiles + 1);
+    KP_A(p->d_spos, tl.ntiles + 1);
+    KP_A(p->d_iitem_off, tl.ntiles + 1);
+    KP_A(p->d_tslot, tl.ntiles + 1);
+    KP_A(p->d_counts, 8);
     KP_A(p->d_schedd, 8);
     KP_A(p->d_iter, 4);
 #undef KP_A
@@ -379,7 +446,8 @@ kp_status plan_destroy_internal(kp_plan p) {
                     p->d_grid2, p->d_gridF, p->d_bar, p->d_tape, p->d_bk,
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
                     p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter,
-                    p->d_oitems, p->d_tslot, p->d_halo};
+                    p->d_oitems, p->d_tslot, p->d_halo, p->d_sflag, p->d_spos, p->d_iitem_off, p->d_counts,
+                    p->d_sort_tmp};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -392,8 +460,16 @@ kp_status plan_destroy_internal(kp_plan p) {
 
 // Reorders work items longest first (stable), so the CTAs that take longest start in the
 // first wave instead of forming a tail; items are independent, so the order is free.
-static kp_status sort_items_longest_first(int4* d_items, int64_t n, cudaStream_t st) {
+static kp_status sort_items_longest_first(kp_plan p, int4* d_items, int64_t n, cudaStream_t st) {
     if (n <= 1) return KP_OK;
+    if (n <= SORT_MAX) {
+        if (!p->d_sort_tmp) KP_TRY_CUDA(cudaMalloc(&p->d_sort_tmp, SORT_MAX * sizeof(int4)));
+        k_sort_items<<<1, 1024, 0, st>>>(d_items, (int)n, p->d_sort_tmp);
+        KP_LAUNCH_CHECK();
+        KP_TRY_CUDA(cudaMemcpyAsync(d_items, p->d_sort_tmp, n * sizeof(int4), cudaMemcpyDeviceToDevice, st));
+        p->launches += 1;
+        return KP_OK;
+    }
     std::vector<int4> h((size_t)n);
     KP_TRY_CUDA(cudaMemcpyAsync(h.data(), d_items, n * sizeof(int4), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));
@@ -405,63 +481,82 @@ static kp_status sort_items_longest_first(int4* d_items, int64_t n, cudaStream_t
 
 // Spreading work items: each tile's list cut into pieces of at most `chunk` samples (a
 // multiple of the kernels' staging size); tiles cut into several pieces are "split" and
-// accumulate with global atomics into a region cleared before each spread.
-kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st) {
+// accumulate with global atomics into a region cleared before each spread.  The counts are
+// enqueued first (d_item_off[ntiles] items, d_spos[ntiles] split tiles); the items are built
+// once the host knows them.
+static void spread_items_counts(kp_plan p, int chunk, cudaStream_t st) {
     const Tiles& tl = p->tiles;
-    p->spread_chunk = chunk;
-    drop_graphs(p);
     const unsigned tb = nblk(tl.ntiles, 256);
     k_chunks<<<tb, 256, 0, st>>>(p->d_ext_off, tl.ntiles, chunk, p->d_cnt, p->d_nslots);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_nslots, p->d_slot_off, tl.ntiles);
-    KP_LAUNCH_CHECK();
-    int tot[2];
-    KP_TRY_CUDA(cudaMemcpyAsync(&tot[0], p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaMemcpyAsync(&tot[1], p->d_slot_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
-    std::vector<int> nsl(tl.ntiles);
-    KP_TRY_CUDA(cudaMemcpyAsync(nsl.data(), p->d_nslots, tl.ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));
-    p->n_items = tot[0];
+    k_split_flags<<<tb, 256, 0, st>>>(p->d_nslots, tl.ntiles, p->d_sflag);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_sflag, p->d_spos, tl.ntiles);
+    p->launches += 5;
+}
+
+static kp_status spread_items_finish(kp_plan p, int chunk, int64_t n_items, int64_t n_split, cudaStream_t st) {
+    const Tiles& tl = p->tiles;
+    const unsigned tb = nblk(tl.ntiles, 256);
+    p->spread_chunk = chunk;
+    p->n_items = n_items;
     if (p->n_items > p->items_cap) {
         if (p->d_items) cudaFree(p->d_items);
         p->d_items = nullptr;
         KP_TRY_CUDA(cudaMalloc(&p->d_items, p->n_items * sizeof(int4)));
         p->items_cap = p->n_items;
     }
-    std::vector<int> split;
-    for (int64_t t = 0; t < tl.ntiles; ++t)
-        if (nsl[t] > 0) split.push_back((int)t);
-    p->n_split = (int64_t)split.size();
+    p->n_split = n_split;
     if (p->n_split > p->split_cap) {
         if (p->d_split) cudaFree(p->d_split);
         p->d_split = nullptr;
         KP_TRY_CUDA(cudaMalloc(&p->d_split, p->n_split * sizeof(int)));
         p->split_cap = p->n_split;
     }
-    if (p->n_split > 0)
-        KP_TRY_CUDA(cudaMemcpyAsync(p->d_split, split.data(), split.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (p->n_split > 0) k_split_list<<<tb, 256, 0, st>>>(p->d_nslots, p->d_spos, tl.ntiles, p->d_split);
     k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, chunk, p->d_items);
     KP_LAUNCH_CHECK();
-    KP_TRY(sort_items_longest_first(p->d_items, p->n_items, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));   // the host split list must outlive its copy
-    p->launches += 4;
+    p->launches += 2;
+    return sort_items_longest_first(p, p->d_items, p->n_items, st);
+}
+
+// The four trajectory flags and the item counts into d_counts, read with one copy.
+static kp_status read_counts(kp_plan p, const int* n_iitems, const int* n_oitems, int out[8], cudaStream_t st) {
+    const int64_t nt = p->tiles.ntiles;
+    k_gather_counts<<<1, 32, 0, st>>>(p->d_flag, p->d_item_off + nt, p->d_spos + nt, n_iitems, n_oitems, p->d_counts);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    KP_TRY_CUDA(cudaMemcpyAsync(out, p->d_counts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
     return KP_OK;
 }
 
-// Own-sample items of the two-phase 3D spreading: each tile's own samples (those whose first
-// tap lies in it) cut into pieces of at most own_chunk; item i writes padded-tile slot i, and
-// d_tslot[t] is the first slot of tile t.  The slot storage itself is allocated on first use.
-kp_status build_own_items(kp_plan p, cudaStream_t st) {
+// Rebuilds the spreading items for another chunk size (the autotuner's candidates).
+kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st) {
+    drop_graphs(p);
+    spread_items_counts(p, chunk, st);
+    KP_LAUNCH_CHECK();
+    int cnt[8];
+    KP_TRY(read_counts(p, p->d_item_off + p->tiles.ntiles, p->d_item_off + p->tiles.ntiles, cnt, st));
+    return spread_items_finish(p, chunk, cnt[4], cnt[5], st);
+}
+
+// Own-sample items of the two-phase spreading: each tile's own samples (those whose first tap
+// lies in it) cut into pieces of at most own_chunk; item i writes padded-tile slot i, and
+// d_tslot[t] is the first slot of tile t (d_tslot[ntiles] items).  The slot storage itself is
+// allocated on first use.
+static void own_items_counts(kp_plan p, cudaStream_t st) {
     const Tiles& tl = p->tiles;
     const unsigned tb = nblk(tl.ntiles, 256);
     p->own_chunk = p->geo.D == 2 ? 512 : 4096;   // 2D grids have few tiles: shorter items spread the work
-    if (!p->d_tslot) KP_TRY_CUDA(cudaMalloc(&p->d_tslot, (tl.ntiles + 1) * sizeof(int)));
     k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->own_chunk, p->d_cnt);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_tslot, tl.ntiles);
-    KP_LAUNCH_CHECK();
-    int n = 0;
-    KP_TRY_CUDA(cudaMemcpyAsync(&n, p->d_tslot + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    p->launches += 2;
+}
+
+static kp_status own_items_finish(kp_plan p, int64_t n, cudaStream_t st) {
+    const Tiles& tl = p->tiles;
+    const unsigned tb = nblk(tl.ntiles, 256);
     p->n_oitems = n;
     if (p->n_oitems > p->oitems_cap) {
         if (p->d_oitems) cudaFree(p->d_oitems);
@@ -474,9 +569,9 @@ kp_status build_own_items(kp_plan p, cudaStream_t st) {
         KP_LAUNCH_CHECK();
         k_slot_ids<<<nblk(p->n_oitems, 256), 256, 0, st>>>(p->d_oitems, p->n_oitems);
         KP_LAUNCH_CHECK();
-        KP_TRY(sort_items_longest_first(p->d_oitems, p->n_oitems, st));   // slot ids travel with the items
+        p->launches += 2;
+        KP_TRY(sort_items_longest_first(p, p->d_oitems, p->n_oitems, st));   // slot ids travel with the items
     }
-    p->launches += 4;
     return KP_OK;
 }
 
@@ -514,36 +609,38 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     if (g.D == 2) k_ext<2, true><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
     else k_ext<3, true><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
     KP_LAUNCH_CHECK();
-    int flag[4];
-    KP_TRY_CUDA(cudaMemcpyAsync(flag, p->d_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));
-    if (flag[0] != 0) {
-        set_error(std::to_string(flag[0]) + " trajectory coordinates outside [-N/2, N/2] or not finite");
+    // every count the host needs (flags, spreading, interpolation and own items), one copy
+    spread_items_counts(p, p->spread_chunk, st);
+    const unsigned tb = nblk(tl.ntiles, 256);
+    k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->chunk, p->d_cnt);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_iitem_off, tl.ntiles);
+    KP_LAUNCH_CHECK();
+    own_items_counts(p, st);
+    KP_LAUNCH_CHECK();
+    p->launches += 11;
+    if (!p->d_tslot) { set_error("plan without slot table"); return KP_EINTERNAL; }
+    int cnt[8];
+    KP_TRY(read_counts(p, p->d_iitem_off + tl.ntiles, p->d_tslot + tl.ntiles, cnt, st));
+    if (cnt[0] != 0) {
+        set_error(std::to_string(cnt[0]) + " trajectory coordinates outside [-N/2, N/2] or not finite");
         p->traj_set = false;
         return KP_EINVAL;
     }
-    p->max_tile = flag[2];
-    KP_TRY(build_spread_items(p, p->spread_chunk, st));
-    const unsigned tb = nblk(tl.ntiles, 256);
-    // interpolation items (own samples of each tile; d_item_off is free again)
-    k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->chunk, p->d_cnt);
-    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_item_off, tl.ntiles);
-    KP_LAUNCH_CHECK();
-    int nii = 0;
-    KP_TRY_CUDA(cudaMemcpyAsync(&nii, p->d_item_off + tl.ntiles, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));
-    p->n_iitems = nii;
+    p->max_tile = cnt[2];
+    KP_TRY(spread_items_finish(p, p->spread_chunk, cnt[4], cnt[5], st));
+    // interpolation items (own samples of each tile, pieces of at most chunk)
+    p->n_iitems = cnt[6];
     if (p->n_iitems > p->iitems_cap) {
         if (p->d_iitems) cudaFree(p->d_iitems);
         p->d_iitems = nullptr;
         KP_TRY_CUDA(cudaMalloc(&p->d_iitems, p->n_iitems * sizeof(int4)));
         p->iitems_cap = p->n_iitems;
     }
-    k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_item_off, tl.ntiles, p->chunk, p->d_iitems);
+    k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_iitem_off, tl.ntiles, p->chunk, p->d_iitems);
     KP_LAUNCH_CHECK();
-    KP_TRY(sort_items_longest_first(p->d_iitems, p->n_iitems, st));
-    p->launches += 11;
-    KP_TRY(build_own_items(p, st));
+    p->launches += 1;
+    KP_TRY(sort_items_longest_first(p, p->d_iitems, p->n_iitems, st));
+    KP_TRY(own_items_finish(p, cnt[7], st));
     p->traj_set = true;
     return autotune_spread(p, st);
 }
