@@ -1,6 +1,6 @@
 // l2-optimised diagonal k-space preconditioner (Sec. 5, App. A), fast route of Sec. 5.1:
 //
-//   q_cd = s_c s_d^*  zero-padded to the 2N grid  -> FFT -> R_c = sum_d |Q_cd|^2 (float64)
+//   q_cd = s_c s_d^*  zero-padded to the 2N grid  -> FFT -> R_c = sum_d |Q_cd|^2
 //   r_c  = IFFT(R_c) / (2^D N)                      (autocorrelation sum, lags in [-N_d, N_d))
 //   h    = N^{-1/2} sum_j e^{+i 2 pi f_j k/N}        (type-1 NUFFT of ones at 2 f_j on the 2N image)
 //   p_c[i] = ||s_c||^2 sqrt(N) / Re(sum_k r_c[k] h[k] e^{-i 2 pi f_i k / N})   (type-2 NUFFT at 2 f_i)
@@ -160,11 +160,15 @@ __global__ void k_accum_R(const float2* __restrict__ Q, const int2* __restrict__
 }
 
 // With every pair's spectrum in Q (pair (c, d), c <= d, at index c C - c (c - 1) / 2 + d - c):
-// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, written once (float64).
+// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, written once.  One thread per
+// (m, c), c = blockIdx.y.  The C positive terms are summed in float32 (relative error below
+// C 2^-24; R is rounded to float32 for its inverse FFT right after): float64 arithmetic runs
+// at a small fraction of the float32 rate on this GPU and made the sum the slowest step.
 __global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0, int nb1, int nb2, int64_t Nb,
                             double* __restrict__ R) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Nb) return;
+    const int c = blockIdx.y;
     const int nb[3] = {nb0, nb1, nb2};
     int64_t r = m, mneg = 0, stride = 1;
     for (int d = D - 1; d >= 0; --d) {
@@ -174,19 +178,17 @@ __global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0,
         mneg += in * stride;
         stride *= nb[d];
     }
-    for (int c = 0; c < C; ++c) {
-        double acc = 0.0;
-        for (int d = 0; d < c; ++d) {
-            const float2 b = Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg];
-            acc += (double)b.x * b.x + (double)b.y * b.y;
-        }
-        const size_t p0 = (size_t)(c * C - c * (c - 1) / 2);
-        for (int d = c; d < C; ++d) {
-            const float2 a = Q[(p0 + d - c) * Nb + m];
-            acc += (double)a.x * a.x + (double)a.y * a.y;
-        }
-        R[(size_t)c * Nb + m] = acc;
+    float acc = 0.f;
+    for (int d = 0; d < c; ++d) {
+        const float2 b = Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg];
+        acc += fmaf(b.x, b.x, b.y * b.y);
     }
+    const size_t p0 = (size_t)(c * C - c * (c - 1) / 2);
+    for (int d = c; d < C; ++d) {
+        const float2 a = Q[(p0 + d - c) * Nb + m];
+        acc += fmaf(a.x, a.x, a.y * a.y);
+    }
+    R[(size_t)c * Nb + m] = (double)acc;
 }
 
 // r_c = R_c / Nb for the coils c0 .. c0 + nc - 1 (grid c - c0 of out).
@@ -320,7 +322,8 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
         KP_TRY_CUFFT(cufftExecC2C(nwrite == 1 ? q->fft_one : q->fft_pairs, (cufftComplex*)q->d_q, (cufftComplex*)q->d_q,
                                   CUFFT_FORWARD));
         if (all_at_once)
-            k_accum_all<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_q, C, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_R);
+            k_accum_all<<<dim3(nblk(q->Nb, 256), C), 256, 0, st>>>(q->d_q, C, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb,
+                                                                   q->d_R);
         else
             k_accum_R<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_q, q->d_pairs, p0, nv, g.D, q->nb[0], q->nb[1], q->nb[2],
                                                         q->Nb, q->d_R, !mc);
