@@ -18,6 +18,21 @@ an independent l1 optimum.
 Parity: pinned by tests/test_oracle_solvers.py (power method against numpy.linalg.eigvalsh,
 PDHG l2 against the CG solution and the KKT relations u* = A x* - y and
 -A^H u* = lambda x*, PDHG l1 fixed point and agreement with FISTA, sigma*tau invariant).
+
+PDHG for g(x) = h(G x) (Sec. 4.2, total variation h = lambda ||.||_1, G the finite-difference
+operator), iteration k:
+    u <- (I + sigma P)^{-1} (u + sigma P (A xbar - y))
+    v <- prox_{sigma h*}(v + sigma G xbar)
+    x_new <- x - tau (A^H u + G^H v)
+    xbar <- x_new + theta (x_new - x)
+with the fixed steps theta = 1, sigma = 1, tau = 1/(lambda_max(P A A^H) + lambda_max(G G^H)).
+Readings: G is the periodic forward difference along every axis, (G x)_k[j] = x[j + e_k] - x[j],
+so lambda_max(G G^H) = 4 d for even sizes (bound for odd ones); h is the anisotropic complex
+l1 norm lambda sum_k sum_j |(G x)_k[j]|; the paper's prox_{tau h} in the v step is read as
+prox_{sigma h*}, the projection onto {|v_i| <= lambda} (v is the dual variable of h); v_0 = 0.
+Pinned by tests/test_oracle_tv.py (G^H against the adjoint identity, the spectrum of G^H G
+against its closed form, the projection against the Moreau identity with the complex soft
+threshold, the KKT conditions of the TV problem at convergence, lambda = 0 against least squares).
 """
 from __future__ import annotations
 
@@ -28,7 +43,8 @@ import numpy as np
 from . import wavelet as wv
 
 __all__ = ["power_method", "pdhg_schedule", "objective", "pdhg", "cg_l2", "fista_l1",
-           "prox_l2", "make_prox"]
+           "prox_l2", "make_prox", "grad_fd", "grad_fd_adjoint", "proj_linf_ball", "tv_norm",
+           "objective_tv", "pdhg_tv"]
 
 
 def power_method(A, AH, p, x_shape, iters=30, v0=None):
@@ -139,3 +155,59 @@ def fista_l1(A, AH, y, lam, x_shape, levels, iters=2000, L=None):
         z = x_new + ((t - 1) / t_new) * (x_new - x)
         x, t = x_new, t_new
     return x
+
+
+def grad_fd(x):
+    """G x: periodic forward differences, (G x)_k[j] = x[j + e_k] - x[j]; shape (d,) + x.shape."""
+    x = np.asarray(x)
+    return np.stack([np.roll(x, -1, axis=k) - x for k in range(x.ndim)])
+
+
+def grad_fd_adjoint(v):
+    """G^H v = sum_k (v_k[j - e_k] - v_k[j])."""
+    v = np.asarray(v)
+    return sum(np.roll(v[k], 1, axis=k) - v[k] for k in range(v.shape[0]))
+
+
+def proj_linf_ball(z, lam):
+    """prox of sigma h* for h = lam ||.||_1 on complex entries: the projection onto |z_i| <= lam."""
+    z = np.asarray(z, dtype=np.complex128)
+    mag = np.abs(z)
+    out = z.copy()
+    big = mag > lam
+    out[big] = z[big] * (lam / mag[big])
+    return out
+
+
+def tv_norm(x):
+    """sum_k sum_j |(G x)_k[j]| (anisotropic, complex magnitude)."""
+    return float(np.sum(np.abs(grad_fd(x))))
+
+
+def objective_tv(A, x, y, lam):
+    """F(x) = 1/2 ||A x - y||^2 + lambda ||G x||_1."""
+    r = A(x) - y
+    return 0.5 * float(np.vdot(r, r).real) + lam * tv_norm(x)
+
+
+def pdhg_tv(A, AH, y, p, x_shape, lam, iters, L, trace=False):
+    """PDHG with the TV regulariser (Sec. 4.2).  Returns (x, u, v, xbar, objective trace or None)."""
+    y = np.asarray(y, dtype=np.complex128)
+    p = np.broadcast_to(np.asarray(p, dtype=np.float64), y.shape)
+    d = len(x_shape)
+    sig, theta = 1.0, 1.0
+    tau = 1.0 / (L + 4.0 * d)
+    x = np.zeros(x_shape, dtype=np.complex128)
+    xbar = x.copy()
+    u = np.zeros_like(y)
+    v = np.zeros((d,) + tuple(x_shape), dtype=np.complex128)
+    objs = [] if trace else None
+    for _ in range(iters):
+        u = (u + sig * p * (A(xbar) - y)) / (1.0 + sig * p)
+        v = proj_linf_ball(v + sig * grad_fd(xbar), lam)
+        x_new = x - tau * (AH(u) + grad_fd_adjoint(v))
+        xbar = x_new + theta * (x_new - x)
+        x = x_new
+        if trace:
+            objs.append(objective_tv(A, x, y, lam))
+    return x, u, v, xbar, objs
