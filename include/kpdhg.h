@@ -61,8 +61,10 @@ typedef enum {
 
 typedef enum {
     KP_REG_L2 = 0,           /* g(x) = lambda ||x||^2 / 2                       (Sec. 2) */
-    KP_REG_L1_WAVELET = 1    /* g(x) = lambda ||W x||_1, W periodised orthonormal
+    KP_REG_L1_WAVELET = 1,   /* g(x) = lambda ||W x||_1, W periodised orthonormal
                                 8-tap Daubechies, `wavelet_levels` levels       (Sec. 2, 6) */
+    KP_REG_TV = 2            /* g(x) = lambda ||G x||_1, G periodic forward differences
+                                along every axis, |.| of each complex difference (Sec. 4.2) */
 } kp_reg;
 
 typedef struct {
@@ -154,6 +156,10 @@ kp_status kp_max_eig(kp_plan plan, const float* p_dev, const void* v0_dev, int i
  * preconditioner first.  lmax <= 0 runs 30 power iterations from the all-ones image.
  * x_dev: complex64 [N] output.  obj_trace: host double[iters] receiving F(x_k) after each
  * iteration, or NULL (tracing adds a forward NUFFT per iteration).  stats: host or NULL.
+ * KP_REG_TV follows Sec. 4.2 instead: a second dual variable v [ndim][N],
+ *   v <- projection of v + sigma G xbar onto {|v_i| <= lambda},
+ *   x <- x - tau (A^H u + G^H v),  xbar <- 2 x - x_old,
+ * with sigma = 1, theta = 1 and tau = 1/(lmax + 4 ndim) at every iteration, v_0 = 0.
  * The iteration is replayed from a CUDA graph captured once per plan and regulariser.
  * Synchronous.  Errors: KP_EINVAL (iters < 0, lambda < 0, wavelet levels 0 for l1,
  * non-positive p or lmax found on the device), KP_ENONFINITE, KP_EDIVERGED. */

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "libkpdhg.so")
 
 KP_OK, KP_EINVAL, KP_ENOMEM, KP_ECUDA, KP_ECUFFT, KP_EDIVERGED, KP_ENONFINITE, KP_ETIMEOUT, KP_EINTERNAL = range(9)
 KP_C64, KP_C32_BF16, KP_C32_FP16 = 0, 1, 2
-KP_REG_L2, KP_REG_L1_WAVELET = 0, 1
+KP_REG_L2, KP_REG_L1_WAVELET, KP_REG_TV = 0, 1, 2
 
 
 class KpParams(ctypes.Structure):

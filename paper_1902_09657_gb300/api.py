@@ -14,7 +14,7 @@ import torch
 
 from . import _lib as L
 
-_REG = {"l2": L.KP_REG_L2, "l1_wavelet": L.KP_REG_L1_WAVELET}
+_REG = {"l2": L.KP_REG_L2, "l1_wavelet": L.KP_REG_L1_WAVELET, "tv": L.KP_REG_TV}
 
 
 def _stream(device):
@@ -228,8 +228,9 @@ class Plan:
         return out
 
     def pdhg_solve(self, y, p=None, reg="l2", lam=0.0, iters=30, lmax=0.0, trace=False, out=None):
-        """Preconditioned PDHG.  y may live on the host (it is then copied in, and x copied
-        back to the host).  Returns (x, objective trace or None, stats dict)."""
+        """Preconditioned PDHG; reg is "l2", "l1_wavelet" (Sec. 4.1) or "tv" (Sec. 4.2).  y may
+        live on the host (it is then copied in, and x copied back to the host).  Returns
+        (x, objective trace or None, stats dict)."""
         host = not y.is_cuda
         yd = y.to(self.device, non_blocking=True) if host else y
         yd = self._dev(yd, "y")

@@ -88,6 +88,7 @@ kp_status kp_batch_solve(kp_batch b, const void* const* y_devs, const kp_cdtype*
     for (int i = 0; i < n; ++i) {
         kp_plan p = b->plans[i];
         if (!p->traj_set || !p->maps_set) { set_error("every plan needs a trajectory and maps"); return KP_EINVAL; }
+        if (regs[i] != KP_REG_L2 && regs[i] != KP_REG_L1_WAVELET && regs[i] != KP_REG_TV) { set_error("bad regulariser"); return KP_EINVAL; }
         if (regs[i] == KP_REG_L1_WAVELET && p->P.wavelet_levels < 1) { set_error("l1-wavelet case without levels"); return KP_EINVAL; }
     }
     // per-case set-up (preconditioner, power method, schedule, zero iterates), each case on its
@@ -96,7 +97,7 @@ kp_status kp_batch_solve(kp_batch b, const void* const* y_devs, const kp_cdtype*
     for (int i = 0; i < n; ++i) {
         KP_TRY_CUDA(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
         KP_TRY(solve_setup(b->plans[i], y_devs[i], y_types[i], p_devs ? p_devs[i] : nullptr, 0.0, std::max(iters, 1),
-                           b->streams[i]));
+                           b->streams[i], (int)regs[i]));
         KP_TRY_CUDA(cudaEventRecord(b->joins[i], b->streams[i]));
         KP_TRY_CUDA(cudaStreamWaitEvent(st, b->joins[i], 0));
     }

@@ -240,6 +240,7 @@ struct kp_plan_s {
     int* d_spos = nullptr;           // [ntiles + 1] position of each split tile in d_split
     int* d_iitem_off = nullptr;      // [ntiles + 1] first interpolation item of each tile
     int* d_counts = nullptr;         // [8] flags and item counts for the host
+    float2* d_v = nullptr;           // [D][N] TV dual variable (allocated at the first TV solve)
     int4* d_sort_tmp = nullptr;      // [8192] scratch of the item sort
     int* d_split = nullptr;          // tiles whose list spans several work items
     int64_t n_split = 0, split_cap = 0;
@@ -304,7 +305,7 @@ struct kp_plan_s {
     float tape_lambda = 0.f;
     float2* d_bk = nullptr;          // [2][C][M] reverse-sweep k-space work (g_r, g_y)
 
-    kp::Graph graphs[2];
+    kp::Graph graphs[3];             // per regulariser
     // profiling: when on, PDHG runs without the graph and records an event at each phase
     bool profiling = false;
     cudaEvent_t* ev = nullptr;
@@ -350,6 +351,8 @@ kp_status zero_split_only(kp_plan p, cudaStream_t st);
 kp_status grid_to_image(kp_plan p, float2* x, cudaStream_t st);
 kp_status autotune_spread(kp_plan p, cudaStream_t st);
 kp_status adjoint_primal(kp_plan p, int reg, float lambda, cudaStream_t st);
+kp_status tv_sumabs(kp_plan p, const float2* x, double* out, cudaStream_t st);
+kp_status ensure_tv_dual(kp_plan p);
 kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st);
 
 // kp_pdhg.cu
@@ -358,7 +361,7 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
 bool cluster_prox_ok(kp_plan p);
 kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st);
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st);
+                      cudaStream_t st, int reg = 0);
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st);

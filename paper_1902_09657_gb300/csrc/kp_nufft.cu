@@ -1491,12 +1491,58 @@ __global__ void k_adj_image(const float2* __restrict__ grid, const MT* __restric
     x[j] = adj_pixel<D, MT>(grid, maps, apod, geo, j);
 }
 
-// Primal step (Sec. 4.1): z = x - tau A^H u; l2 prox z/(1 + tau lambda) and extrapolation
-// fused (REG == 0); for the wavelet prox (REG == 1) z is written for the DWT.
+// Image coordinates of pixel j and the strides of its axes (slowest axis first).
+template <int D>
+__device__ __forceinline__ void pix_coords(int64_t j, const Geom& geo, int* jj, int64_t* stride) {
+    int64_t r = j, s = 1;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) {
+        jj[d] = (int)(r % geo.n[d]);
+        r /= geo.n[d];
+        stride[d] = s;
+        s *= geo.n[d];
+    }
+}
+
+// TV dual step (Sec. 4.2): v_k[j] <- projection of v_k[j] + sigma (xbar[j + e_k] - xbar[j])
+// onto |v| <= lambda (periodic forward differences).  Each thread owns v at its pixel and only
+// reads xbar, so the update is in place.
+template <int D>
+__global__ void k_tv_dual(const float2* __restrict__ xbar, float2* __restrict__ v, Geom geo,
+                          const float* __restrict__ sched, const int* __restrict__ iter, float lambda) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= geo.N) return;
+    const float sigma = sched[3 * (*iter)];
+    int jj[D];
+    int64_t stride[D];
+    pix_coords<D>(j, geo, jj, stride);
+    const float2 xc = xbar[j];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const int64_t jn = jj[k] + 1 < geo.n[k] ? j + stride[k] : j - (int64_t)(geo.n[k] - 1) * stride[k];
+        const float2 xn = xbar[jn];
+        float2 z = v[(size_t)k * geo.N + j];
+        z.x += sigma * (xn.x - xc.x);
+        z.y += sigma * (xn.y - xc.y);
+        const float m = sqrtf(z.x * z.x + z.y * z.y);
+        if (m > lambda) {
+            const float sc = lambda / m;
+            z.x *= sc;
+            z.y *= sc;
+        }
+        v[(size_t)k * geo.N + j] = z;
+    }
+}
+
+// Primal step: z = x - tau A^H u; l2 prox z/(1 + tau lambda) and extrapolation fused
+// (REG == 0, Sec. 4.1); for the wavelet prox (REG == 1) z is written for the DWT; for TV
+// (REG == 2, Sec. 4.2) x <- z - tau G^H v, G^H v = sum_k (v_k[j - e_k] - v_k[j]), and the
+// extrapolation.
 template <int D, typename MT, int REG>
 __global__ void k_adj_primal(const float2* __restrict__ grid, const MT* __restrict__ maps, const float* __restrict__ apod,
                              Geom geo, float2* __restrict__ x, float2* __restrict__ xbar, float2* __restrict__ z,
-                             const float* __restrict__ sched, const int* __restrict__ iter, float lambda) {
+                             const float* __restrict__ sched, const int* __restrict__ iter, float lambda,
+                             const float2* __restrict__ v) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= geo.N) return;
     const int k = *iter;
@@ -1507,6 +1553,21 @@ __global__ void k_adj_primal(const float2* __restrict__ grid, const MT* __restri
     if (REG == 0) {
         float sc = 1.f / (1.f + tau * lambda);
         float2 xn = make_float2(zz.x * sc, zz.y * sc);
+        xbar[j] = make_float2(xn.x + theta * (xn.x - xo.x), xn.y + theta * (xn.y - xo.y));
+        x[j] = xn;
+    } else if (REG == 2) {
+        int jj[D];
+        int64_t stride[D];
+        pix_coords<D>(j, geo, jj, stride);
+        float2 gh = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int64_t jm = jj[a] > 0 ? j - stride[a] : j + (int64_t)(geo.n[a] - 1) * stride[a];
+            const float2 vm = v[(size_t)a * geo.N + jm], vc = v[(size_t)a * geo.N + j];
+            gh.x += vm.x - vc.x;
+            gh.y += vm.y - vc.y;
+        }
+        const float2 xn = make_float2(zz.x - tau * gh.x, zz.y - tau * gh.y);
         xbar[j] = make_float2(xn.x + theta * (xn.x - xo.x), xn.y + theta * (xn.y - xo.y));
         x[j] = xn;
     } else {
@@ -1908,12 +1969,63 @@ kp_status adjoint_primal(kp_plan p, int reg, float lambda, cudaStream_t st) {
     if (reg == KP_REG_L2) {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
             k_adj_primal<DD, MT, 0><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid2, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
-                                                                   p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda)));
+                                                                   p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda,
+                                                                   nullptr)));
+    } else if (reg == KP_REG_TV) {
+        // dual step on v from the current xbar, then the primal step reading the new v
+        if (!p->d_v) { set_error("TV dual variable not allocated"); return KP_EINTERNAL; }
+        p->launches += 1;
+        KP_DISPATCH_D(g.D, DD,
+            k_tv_dual<DD><<<nblk(g.N, 256), 256, 0, st>>>(p->d_xbar, p->d_v, g, p->d_sched, p->d_iter, lambda));
+        KP_LAUNCH_CHECK();
+        KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
+            k_adj_primal<DD, MT, 2><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid2, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
+                                                                   p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda,
+                                                                   p->d_v)));
     } else {
         KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
             k_adj_primal<DD, MT, 1><<<nblk(g.N, 256), 256, 0, st>>>(p->d_grid2, (const MT*)p->d_maps, p->d_apod, g, p->d_x,
-                                                                   p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda)));
+                                                                   p->d_xbar, p->d_z, p->d_sched, p->d_iter, lambda,
+                                                                   nullptr)));
     }
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+// sum_k sum_j |x[j + e_k] - x[j]| (float64) added into *out.
+template <int D>
+__global__ void k_tv_sumabs(const float2* __restrict__ x, Geom geo, double* __restrict__ out) {
+    __shared__ double ws[32];
+    double s = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < geo.N; j += (int64_t)gridDim.x * blockDim.x) {
+        int jj[D];
+        int64_t stride[D];
+        pix_coords<D>(j, geo, jj, stride);
+        const float2 xc = x[j];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int64_t jn = jj[k] + 1 < geo.n[k] ? j + stride[k] : j - (int64_t)(geo.n[k] - 1) * stride[k];
+            const float2 xn = x[jn];
+            const double dx = (double)xn.x - xc.x, dy = (double)xn.y - xc.y;
+            s += sqrt(dx * dx + dy * dy);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) atomicAdd(out, s);
+    }
+}
+
+kp_status tv_sumabs(kp_plan p, const float2* x, double* out, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const unsigned b = (unsigned)std::min<int64_t>(nblk(g.N, 256), 1216);
+    p->launches += 1;
+    KP_DISPATCH_D(g.D, DD, k_tv_sumabs<DD><<<b, 256, 0, st>>>(x, g, out));
     KP_LAUNCH_CHECK();
     return KP_OK;
 }

@@ -158,8 +158,10 @@ __global__ void k_store_sqrt(const double* __restrict__ n2, double* __restrict__
 // Step sizes (Sec. 4.1): sigma_0 = 1, tau_0 = 1/L, theta_k = 1/(1 + 2 sigma_k pmin),
 // sigma_{k+1} = theta_k sigma_k, tau_{k+1} = tau_k / theta_k; float64 recursion.
 // schedd: [0] L, [1] pmin (written here from minbits), [2] sigma_last, [3] tau_last.
+// tv_d > 0: the fixed steps of Sec. 4.2 for TV in tv_d dimensions, sigma = theta = 1 and
+// tau = 1/(L + lambda_max(G G^H)) with lambda_max(G G^H) = 4 tv_d.
 __global__ void k_schedule(double* __restrict__ schedd, const int* __restrict__ minbits, int iters,
-                           float* __restrict__ sched, int* __restrict__ flag) {
+                           float* __restrict__ sched, int* __restrict__ flag, int tv_d) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double L = schedd[0];
     const double pmin = minbits ? (double)__int_as_float(*minbits) : schedd[1];
@@ -167,6 +169,17 @@ __global__ void k_schedule(double* __restrict__ schedd, const int* __restrict__ 
     if (!(L > 0) || !isfinite(L) || !(pmin > 0) || !isfinite(pmin)) {
         flag[0] = 1;
         for (int k = 0; k < iters; ++k) { sched[3 * k] = 0.f; sched[3 * k + 1] = 0.f; sched[3 * k + 2] = 0.f; }
+        return;
+    }
+    if (tv_d > 0) {
+        const double tau = 1.0 / (L + 4.0 * tv_d);
+        for (int k = 0; k < iters; ++k) {
+            sched[3 * k] = 1.f;
+            sched[3 * k + 1] = (float)tau;
+            sched[3 * k + 2] = 1.f;
+        }
+        schedd[2] = 1.0;
+        schedd[3] = tau;
         return;
     }
     double sig = 1.0, tau = 1.0 / L;
@@ -239,6 +252,17 @@ static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cuda
 static kp_status issue_iteration(kp_plan p, int reg, float lambda, cudaStream_t st) {
     KP_TRY(fft_forward_only(p, st));
     KP_TRY(interp_dual_only(p, st));
+    if (reg == KP_REG_TV) {
+        // Sec. 4.2: spreading (it clears its split tiles itself), v and x steps, next pre-step
+        KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st, /*splits_zeroed=*/false));
+        KP_TRY(adjoint_primal(p, KP_REG_TV, lambda, st));
+        KP_TRY(pre_only(p, p->d_xbar, st));
+        k_advance<<<1, 1, 0, st>>>(p->d_iter);
+        KP_LAUNCH_CHECK();
+        p->launches += 1;
+        mark(p, PH_OTHER, st);
+        return KP_OK;
+    }
     KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st, /*splits_zeroed=*/true));
     if (reg == KP_REG_L1_WAVELET && cluster_prox_ok(p)) KP_TRY(primal_cluster(p, lambda, st));
     else KP_TRY(primal_fused(p, reg, lambda, st));
@@ -298,6 +322,8 @@ static kp_status objective(kp_plan p, int reg, float lambda, double* F, cudaStre
     const unsigned bn = (unsigned)std::min<int64_t>(nblk(g.N, 256), 1216);
     if (reg == KP_REG_L2) {
         k_norm2<<<bn, 256, 0, st>>>(p->d_x, g.N, p->d_red + 2);
+    } else if (reg == KP_REG_TV) {
+        KP_TRY(tv_sumabs(p, p->d_x, p->d_red + 2, st));
     } else {
         KP_TRY(wavelet_apply(p, p->d_x, p->d_w, true, st));
         k_sumabs<<<bn, 256, 0, st>>>(p->d_w, g.N, p->d_red + 2);
@@ -321,11 +347,19 @@ static kp_status ensure_sched(kp_plan p, int iters) {
     return KP_OK;
 }
 
+// The TV dual variable v [D][N], allocated at the plan's first TV solve.
+kp_status ensure_tv_dual(kp_plan p) {
+    if (p->d_v) return KP_OK;
+    KP_TRY_CUDA(cudaMalloc(&p->d_v, (size_t)p->geo.D * p->geo.N * sizeof(float2)));
+    drop_graphs(p);
+    return KP_OK;
+}
+
 // Everything a PDHG run needs before its first iteration (Sec. 4.1): measurements and
 // preconditioner in sorted order, min p, lambda_max (given, or 30 power iterations), the
 // step-size schedule, zero initial iterates and the forward grid of xbar_0 = 0.
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st) {
+                      cudaStream_t st, int reg) {
     const Geom& g = plan->geo;
     void* stream = (void*)st;
     KP_TRY(ensure_sched(plan, std::max(iters, 1)));
@@ -362,13 +396,18 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
         plan->launches += 1;
         KP_TRY(power_method(plan, plan->d_ps, 30, st));
     }
-    k_schedule<<<1, 1, 0, st>>>(plan->d_schedd, plan->d_flag + 4, std::max(iters, 1), plan->d_sched, plan->d_flag + 6);
+    k_schedule<<<1, 1, 0, st>>>(plan->d_schedd, plan->d_flag + 4, std::max(iters, 1), plan->d_sched, plan->d_flag + 6,
+                                reg == KP_REG_TV ? g.D : 0);
     KP_LAUNCH_CHECK();
     plan->launches += 1;
     // x0 = xbar0 = 0, u0 = 0
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_x, 0, g.N * sizeof(float2), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
+    if (reg == KP_REG_TV) {
+        KP_TRY(ensure_tv_dual(plan));
+        KP_TRY_CUDA(cudaMemsetAsync(plan->d_v, 0, (size_t)g.D * g.N * sizeof(float2), st));   // v_0 = 0
+    }
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_bar, 0, 4 * sizeof(unsigned int), st));   // grid-barrier counter
     // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
@@ -388,7 +427,7 @@ kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream
     KP_TRY(fft_forward_only(p, st));
     KP_TRY(interp_dual_only(p, st));
     KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st));
-    KP_TRY(adjoint_primal(p, reg, lambda, st));
+    KP_TRY(adjoint_primal(p, reg, lambda, st));   // TV: dual step on v, then the primal step
     if (reg == KP_REG_L1_WAVELET) KP_TRY(wavelet_prox_levels(p, lambda, st));
     else KP_TRY(pre_only(p, p->d_xbar, st));
     k_advance<<<1, 1, 0, st>>>(p->d_iter);
@@ -450,12 +489,12 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
     if (!(lambda >= 0.f) || !std::isfinite(lambda)) { set_error("lambda must be finite and >= 0"); return KP_EINVAL; }
-    if (reg != KP_REG_L2 && reg != KP_REG_L1_WAVELET) { set_error("bad regulariser"); return KP_EINVAL; }
+    if (reg != KP_REG_L2 && reg != KP_REG_L1_WAVELET && reg != KP_REG_TV) { set_error("bad regulariser"); return KP_EINVAL; }
     if (reg == KP_REG_L1_WAVELET && plan->P.wavelet_levels < 1) { set_error("l1-wavelet needs wavelet_levels >= 1"); return KP_EINVAL; }
     if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
     const Geom& g = plan->geo;
-    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st));
+    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st, (int)reg));
     kp_status status = KP_OK;
     double F0 = 0, F = NAN;
     double phase_ms[PH_N] = {0};

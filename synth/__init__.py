@@ -149,7 +149,7 @@ class Workload:
     ncoils: int
     oversamp: float
     width: int
-    reg: str                 # "l2" or "l1_wavelet"
+    reg: str                 # "l2", "l1_wavelet" or "tv"
     lam_rel: float           # l2: lambda itself; l1: lambda / max|A^H y|
     iters: int
     wavelet_levels: int

@@ -147,3 +147,17 @@ def test_batch_uneven_workload_cases():
     for i in range(len(cases)):
         xg, _, _ = plans[i].pdhg_solve(yd[i], None, regs[i], lams[i], 20)
         assert rel(xs[i].cpu().numpy(), xg.cpu().numpy()) < 2e-6, i
+
+
+def test_batch_tv_case():
+    """A TV case (Sec. 4.2) next to an l2 case in one batch: each equals its single-plan solve."""
+    need_gpu()
+    from paper_1902_09657_gb300.api import Batch
+    cases = [(0, 64, 4, "spiral", 6, "tv", 0), (1, 48, 3, "radial", 40, "l2", 0)]
+    plans, ys, ps, Ls, lams, oin = _setup(cases)
+    regs = [c[5] for c in cases]
+    yd = [to_dev(y) for y in ys]
+    xs = Batch(plans).solve(yd, None, regs, lams, 20)
+    for i in range(len(cases)):
+        xg, _, _ = plans[i].pdhg_solve(yd[i], None, regs[i], lams[i], 20)
+        assert rel(xs[i].cpu().numpy(), xg.cpu().numpy()) < 2e-6, i

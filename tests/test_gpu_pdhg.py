@@ -84,6 +84,31 @@ def test_pdhg_l1_primal_paths(cluster, monkeypatch):
     assert rel(xg2.cpu().numpy(), x_ref) < 1e-5          # graph replay of the same path
 
 
+def test_pdhg_tv_matches_oracle():
+    """TV-regularised PDHG (Sec. 4.2): the GPU iterates and objective trace equal the oracle's
+    (sigma = theta = 1, tau = 1/(L + 4 d), projected dual v), and a graph replay repeats them."""
+    need_gpu()
+    w, x, maps, traj = _small_spiral(n=64, C=3, L=8, ns=1024)
+    y = simulate(w, x, maps, traj)
+    A, AH = _ops(maps, traj, 1.25)
+    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    lam = 1e-3 * float(np.abs(AH(y.astype(np.complex128))).max())
+    x_ref, _, v_ref, _, objs = osv.pdhg_tv(A, AH, y, p, x.shape, lam, 40, L, trace=True)
+    assert np.abs(v_ref).max() > 0.99 * lam          # the dual projection is active
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0])
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    pd = to_dev(p.astype(np.float32))
+    xg, tr, st = plan.pdhg_solve(to_dev(y), pd, "tv", lam, 40, lmax=L, trace=True)
+    assert rel(xg.cpu().numpy(), x_ref) < 1e-5
+    assert abs(tr[-1] - objs[-1]) < 1e-5 * abs(objs[-1])
+    assert abs(st["tau_last"] - 1.0 / (L + 8.0)) < 1e-9 and st["sigma_last"] == 1.0
+    xg2, _, _ = plan.pdhg_solve(to_dev(y), pd, "tv", lam, 40, lmax=L)
+    assert rel(xg2.cpu().numpy(), x_ref) < 1e-5          # graph replay, v restarted from 0
+    xl2, _, _ = plan.pdhg_solve(to_dev(y), pd, "l2", lam, 5, lmax=L)   # the other graphs still work
+    assert np.isfinite(xl2.cpu().numpy()).all()
+
+
 def test_cluster_prox_plans_of_different_sizes():
     """Two 2D l1 plans on the 16-CTA cluster prox with different shared-memory needs (128^2 with
     3 levels: 18 KB; 64^2 with 2 levels: 5 KB), solved in turn: the larger plan's second solve
