@@ -33,6 +33,14 @@ prox_{sigma h*}, the projection onto {|v_i| <= lambda} (v is the dual variable o
 Pinned by tests/test_oracle_tv.py (G^H against the adjoint identity, the spectrum of G^H G
 against its closed form, the projection against the Moreau identity with the complex soft
 threshold, the KKT conditions of the TV problem at convergence, lambda = 0 against least squares).
+
+l2 through the dual (appendix on the connection to Trzasko et al.): for g = lambda ||x||^2 / 2
+the dual optimum w solves (A A^H + lambda I) w = lambda y and x = A^H w / lambda.  Reading: the
+paper preconditions this system by the diagonal P without naming a solver; here it is conjugate
+gradients with P as the preconditioner (M^{-1} = P: the Hermitian positive definite system is
+solved, P shapes the iterates), from w = 0.  In the sign convention of Sec. 4.1 (u = A x - y at
+the fixed point) w = -u.  Pinned by tests/test_oracle_dual_l2.py (dense solve of the dual system,
+the primal ridge solution through the push-through identity, PDHG's dual fixed point u = -w).
 """
 from __future__ import annotations
 
@@ -44,7 +52,7 @@ from . import wavelet as wv
 
 __all__ = ["power_method", "pdhg_schedule", "objective", "pdhg", "cg_l2", "fista_l1",
            "prox_l2", "make_prox", "grad_fd", "grad_fd_adjoint", "proj_linf_ball", "tv_norm",
-           "objective_tv", "pdhg_tv"]
+           "objective_tv", "pdhg_tv", "dual_l2_pcg"]
 
 
 def power_method(A, AH, p, x_shape, iters=30, v0=None):
@@ -211,3 +219,32 @@ def pdhg_tv(A, AH, y, p, x_shape, lam, iters, L, trace=False):
         if trace:
             objs.append(objective_tv(A, x, y, lam))
     return x, u, v, xbar, objs
+
+
+def dual_l2_pcg(A, AH, y, p, lam, iters, tol=0.0):
+    """(A A^H + lam I) w = lam y by conjugate gradients preconditioned by the diagonal p, from
+    w = 0; x = A^H w / lam.  Stops after `iters` iterations or when ||r|| <= tol ||lam y||.
+    Returns (x, w, residual norms ||lam y - (A A^H + lam I) w|| per iteration, first at w = 0)."""
+    y = np.asarray(y, dtype=np.complex128)
+    p = np.broadcast_to(np.asarray(p, dtype=np.float64), y.shape)
+    w = np.zeros_like(y)
+    r = lam * y
+    z = p * r
+    d = z.copy()
+    rz = float(np.vdot(r, z).real)
+    res = [float(np.linalg.norm(r))]
+    for _ in range(iters):
+        if rz == 0.0:
+            break
+        q = A(AH(d)) + lam * d
+        alpha = rz / float(np.vdot(d, q).real)
+        w = w + alpha * d
+        r = r - alpha * q
+        res.append(float(np.linalg.norm(r)))
+        if tol > 0 and res[-1] <= tol * res[0]:
+            break
+        z = p * r
+        rz_new = float(np.vdot(r, z).real)
+        d = z + (rz_new / rz) * d
+        rz = rz_new
+    return AH(w) / lam, w, res
