@@ -167,6 +167,19 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
                         kp_reg reg, float lambda, int iters, double lmax, void* x_dev,
                         double* obj_trace, kp_stats* stats, void* stream);
 
+/* l2-regularised reconstruction through the dual (appendix on the connection to Trzasko
+ * et al.): (A A^H + lambda I) w = lambda y by `iters` conjugate-gradient iterations with the
+ * diagonal p as preconditioner, from w = 0, then x = A^H w / lambda, the minimiser of
+ * 1/2 ||A x - y||^2 + lambda/2 ||x||^2 (w = -u for the dual u of kp_pdhg_solve with KP_REG_L2).
+ * y_dev: complex64 [C][M].  p_dev: float32 [C][M] (every entry positive), or NULL for none.
+ * x_dev: complex64 [N] output.  res_trace: host double[iters + 1] receiving
+ * ||lambda y - (A A^H + lambda I) w|| before the first and after each iteration, or NULL.
+ * Uses the plan's PDHG work buffers.  Synchronous.  Errors: KP_EINVAL (lambda <= 0,
+ * iters < 0, no trajectory or maps, a p entry not positive), KP_ENONFINITE (a residual not
+ * finite). */
+kp_status kp_dual_l2_solve(kp_plan plan, const void* y_dev, const float* p_dev, float lambda, int iters,
+                           void* x_dev, double* res_trace, void* stream);
+
 /* Trajectory gradient through y = A x (differentiable reconstruction; Sec. 6 operator with the
  * Kaiser-Bessel derivative phi'): gtraj[i][d] = Re sum_c conj(gy_c[i]) d y_c[i] / d f_{i,d},
  * taps held fixed (y jumps where a coordinate crosses a grid line, at the window edge).

@@ -64,6 +64,8 @@ _SIGS = {
     "kp_unrolled_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int, ctypes.c_double, _vp, _vp]),
     "kp_unrolled_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
     "kp_plan_tile_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "kp_dual_l2_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int, _vp,
+                                        ctypes.POINTER(ctypes.c_double), _vp]),
     "kp_plan_spread_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "kp_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),

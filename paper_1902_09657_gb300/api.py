@@ -227,6 +227,20 @@ class Plan:
                 "kp_wavelet")
         return out
 
+    def dual_l2_solve(self, y, p=None, lam=1.0, iters=50):
+        """l2 reconstruction through the dual: (A A^H + lam I) w = lam y by conjugate gradients
+        with p (complex64 y [C, M]; float32 p [C, M] or None) as preconditioner, x = A^H w / lam.
+        Returns (x, residual norms before and after each iteration)."""
+        yd = self._dev(y, "y")
+        if yd.dtype != torch.complex64 or tuple(yd.shape) != (self.ncoils, self.nsamples):
+            raise ValueError("y must be complex64 [C, M]")
+        pd = self._dev(p, "p") if p is not None else None
+        x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
+        tr = (ctypes.c_double * (int(iters) + 1))()
+        L.check(self.lib.kp_dual_l2_solve(self._h, _ptr(yd), _ptr(pd) if pd is not None else None, float(lam),
+                                          int(iters), _ptr(x), tr, _stream(self.device)), "kp_dual_l2_solve")
+        return x, list(tr)
+
     def pdhg_solve(self, y, p=None, reg="l2", lam=0.0, iters=30, lmax=0.0, trace=False, out=None):
         """Preconditioned PDHG; reg is "l2", "l1_wavelet" (Sec. 4.1) or "tv" (Sec. 4.2).  y may
         live on the host (it is then copied in, and x copied back to the host).  Returns

@@ -241,6 +241,10 @@ struct kp_plan_s {
     int* d_iitem_off = nullptr;      // [ntiles + 1] first interpolation item of each tile
     int* d_counts = nullptr;         // [8] flags and item counts for the host
     float2* d_v = nullptr;           // [D][N] TV dual variable (allocated at the first TV solve)
+    float2* d_cg_r = nullptr;        // [C][M] residual of the dual conjugate gradients
+    float2* d_cg_d = nullptr;        // [C][M] their search direction
+    double* d_cg_trace = nullptr;    // residual norms of the last dual solve
+    int64_t cg_cap = 0, cg_trace_cap = 0;
     int4* d_sort_tmp = nullptr;      // [8192] scratch of the item sort
     int* d_split = nullptr;          // tiles whose list spans several work items
     int64_t n_split = 0, split_cap = 0;

@@ -436,11 +436,201 @@ kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream
     return KP_OK;
 }
 
+// ---------------------------------------------------------------- l2 through the dual
+// (A A^H + lambda I) w = lambda y by conjugate gradients with the diagonal p as preconditioner
+// (appendix on the connection to Trzasko et al.), in the plan's sorted sample order, with the
+// scalars on the device so that no iteration waits for the host; x = A^H w / lambda.
+// s[0] = <r, p r>, s[1] = <d, q>, s[2] = the next <r, p r>, s[3] = ||r||^2, s[4] = alpha,
+// s[5] = beta.
+
+// w = 0, r = lambda y, d = p r; s[0] += <r, p r>, s[3] += ||r||^2
+__global__ void k_cg_init(const float2* __restrict__ ys, const float* __restrict__ ps, int64_t n, float lambda,
+                          float2* __restrict__ w, float2* __restrict__ r, float2* __restrict__ d,
+                          double* __restrict__ s) {
+    double a = 0, b = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 y = ys[i];
+        const float pi = ps ? ps[i] : 1.f;
+        const float2 ri = make_float2(lambda * y.x, lambda * y.y);
+        w[i] = make_float2(0.f, 0.f);
+        r[i] = ri;
+        d[i] = make_float2(pi * ri.x, pi * ri.y);
+        const double m2 = (double)ri.x * ri.x + (double)ri.y * ri.y;
+        a += pi * m2;
+        b += m2;
+    }
+    block_sum_to<int>(a, s);
+    __syncthreads();
+    block_sum_to<int>(b, s + 3);
+}
+
+// q <- q + lambda d (q = A A^H d on entry); s[1] += Re <d, q>
+__global__ void k_cg_dq(float2* __restrict__ q, const float2* __restrict__ d, int64_t n, float lambda,
+                        double* __restrict__ s) {
+    double a = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 di = d[i];
+        float2 qi = q[i];
+        qi.x += lambda * di.x;
+        qi.y += lambda * di.y;
+        q[i] = qi;
+        a += (double)di.x * qi.x + (double)di.y * qi.y;
+    }
+    block_sum_to<int>(a, s + 1);
+}
+
+// mode 0: alpha = s[0] / s[1]; mode 1: beta = s[2] / s[0], trace[k] = ||r||, s[0] = s[2] and
+// the accumulators cleared; mode 2 (start): trace[k] = ||r||, s[3] cleared.  A zero
+// denominator (the residual vanished) gives a zero step.
+__global__ void k_cg_scalars(double* __restrict__ s, int mode, double* __restrict__ trace, int k,
+                             int* __restrict__ bad) {
+    if (mode == 0) {
+        s[4] = s[1] > 0 ? s[0] / s[1] : 0.0;
+        return;
+    }
+    trace[k] = sqrt(s[3]);
+    if (!isfinite(s[3])) *bad = 1;
+    if (mode == 2) {
+        s[3] = 0.0;
+        return;
+    }
+    s[5] = s[0] > 0 ? s[2] / s[0] : 0.0;
+    s[0] = s[2];
+    s[1] = 0.0;
+    s[2] = 0.0;
+    s[3] = 0.0;
+}
+
+// w += alpha d, r -= alpha q; s[2] += <r, p r>, s[3] += ||r||^2
+__global__ void k_cg_step(float2* __restrict__ w, float2* __restrict__ r, const float2* __restrict__ d,
+                          const float2* __restrict__ q, const float* __restrict__ ps, int64_t n,
+                          double* __restrict__ s) {
+    const float alpha = (float)s[4];
+    double a = 0, b = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 di = d[i], qi = q[i];
+        float2 wi = w[i], ri = r[i];
+        wi.x += alpha * di.x;
+        wi.y += alpha * di.y;
+        ri.x -= alpha * qi.x;
+        ri.y -= alpha * qi.y;
+        w[i] = wi;
+        r[i] = ri;
+        const double m2 = (double)ri.x * ri.x + (double)ri.y * ri.y;
+        a += (ps ? ps[i] : 1.f) * m2;
+        b += m2;
+    }
+    block_sum_to<int>(a, s + 2);
+    __syncthreads();
+    block_sum_to<int>(b, s + 3);
+}
+
+// d = p r + beta d
+__global__ void k_cg_dir(float2* __restrict__ d, const float2* __restrict__ r, const float* __restrict__ ps, int64_t n,
+                         const double* __restrict__ s) {
+    const float beta = (float)s[5];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float pi = ps ? ps[i] : 1.f;
+        const float2 ri = r[i], di = d[i];
+        d[i] = make_float2(pi * ri.x + beta * di.x, pi * ri.y + beta * di.y);
+    }
+}
+
+__global__ void k_scale_copy(const float2* __restrict__ in, float2* __restrict__ out, int64_t n, float a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2(a * in[i].x, a * in[i].y);
+}
+
+static kp_status dual_l2(kp_plan p, const float2* y_dev, const float* p_dev, float lambda, int iters, float2* x_dev,
+                         double* res_trace, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const int64_t n = (int64_t)g.C * g.M;
+    if (n > p->cg_cap) {
+        if (p->d_cg_r) cudaFree(p->d_cg_r);
+        if (p->d_cg_d) cudaFree(p->d_cg_d);
+        p->d_cg_r = p->d_cg_d = nullptr;
+        p->cg_cap = 0;
+        KP_TRY_CUDA(cudaMalloc(&p->d_cg_r, n * sizeof(float2)));
+        KP_TRY_CUDA(cudaMalloc(&p->d_cg_d, n * sizeof(float2)));
+        p->cg_cap = n;
+    }
+    if (iters + 1 > p->cg_trace_cap) {
+        if (p->d_cg_trace) cudaFree(p->d_cg_trace);
+        p->d_cg_trace = nullptr;
+        p->cg_trace_cap = 0;
+        KP_TRY_CUDA(cudaMalloc(&p->d_cg_trace, (size_t)(iters + 1) * sizeof(double)));
+        p->cg_trace_cap = iters + 1;
+    }
+    // measurements and preconditioner into sorted order; min p and its sign check
+    k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>(y_dev, (float2*)p->d_ys, p->d_perm, g.M, g.C);
+    KP_LAUNCH_CHECK();
+    const float* ps = nullptr;
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag, 0, 8 * sizeof(int), st));
+    if (p_dev) {
+        k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(p_dev, p->d_ps, p->d_perm, g.M, g.C);
+        static const int init = 0x7f7fffff;
+        KP_TRY_CUDA(cudaMemcpyAsync(p->d_flag + 4, &init, sizeof(int), cudaMemcpyHostToDevice, st));
+        k_pmin<<<(unsigned)std::min<int64_t>(nblk(n, 256), 1216), 256, 0, st>>>(p->d_ps, n, p->d_flag + 4, p->d_flag + 5);
+        KP_LAUNCH_CHECK();
+        ps = p->d_ps;
+        p->launches += 2;
+    }
+    p->launches += 1;
+    float2* w = p->d_u;
+    float2* r = p->d_cg_r;
+    float2* d = p->d_cg_d;
+    float2* q = p->d_kt;
+    double* s = p->d_red + 8;     // 6 scalars (d_red holds 16)
+    int* bad = p->d_flag + 6;
+    const unsigned nb = (unsigned)std::min<int64_t>(nblk(n, 256), 1216);
+    KP_TRY_CUDA(cudaMemsetAsync(s, 0, 6 * sizeof(double), st));
+    k_cg_init<<<nb, 256, 0, st>>>((const float2*)p->d_ys, ps, n, lambda, w, r, d, s);
+    k_cg_scalars<<<1, 1, 0, st>>>(s, 2, p->d_cg_trace, 0, bad);   // trace[0] = ||lambda y||
+    KP_LAUNCH_CHECK();
+    p->launches += 2;
+    for (int k = 0; k < iters; ++k) {
+        KP_TRY(adjoint_to_grid(p, d, KP_C64, nullptr, st));              // A^H d (sorted order in)
+        KP_TRY(grid_to_image(p, p->d_w, st));
+        KP_TRY(forward_to(p, p->d_w, q, KP_C64, nullptr, st));            // A A^H d (sorted order out)
+        k_cg_dq<<<nb, 256, 0, st>>>(q, d, n, lambda, s);
+        k_cg_scalars<<<1, 1, 0, st>>>(s, 0, p->d_cg_trace, k + 1, bad);
+        k_cg_step<<<nb, 256, 0, st>>>(w, r, d, q, ps, n, s);
+        k_cg_scalars<<<1, 1, 0, st>>>(s, 1, p->d_cg_trace, k + 1, bad);
+        k_cg_dir<<<nb, 256, 0, st>>>(d, r, ps, n, s);
+        KP_LAUNCH_CHECK();
+        p->launches += 5;
+    }
+    // x = A^H w / lambda
+    KP_TRY(adjoint_to_grid(p, w, KP_C64, nullptr, st));
+    KP_TRY(grid_to_image(p, p->d_w, st));
+    k_scale_copy<<<nblk(g.N, 256), 256, 0, st>>>(p->d_w, x_dev, g.N, 1.f / lambda);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    int flags[8];
+    KP_TRY_CUDA(cudaMemcpyAsync(flags, p->d_flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (res_trace)
+        KP_TRY_CUDA(cudaMemcpyAsync(res_trace, p->d_cg_trace, (size_t)(iters + 1) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (flags[5] != 0) { set_error(std::to_string(flags[5]) + " preconditioner entries are not positive and finite"); return KP_EINVAL; }
+    if (flags[6] != 0) { set_error("a residual of the dual conjugate gradients is not finite"); return KP_ENONFINITE; }
+    return KP_OK;
+}
+
 }  // namespace kp
 
 using namespace kp;
 
 extern "C" {
+
+kp_status kp_dual_l2_solve(kp_plan plan, const void* y_dev, const float* p_dev, float lambda, int iters, void* x_dev,
+                           double* res_trace, void* stream) {
+    if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
+    if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
+    if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
+    if (!(lambda > 0.f) || !std::isfinite(lambda)) { set_error("lambda must be finite and > 0"); return KP_EINVAL; }
+    return dual_l2(plan, (const float2*)y_dev, p_dev, lambda, iters, (float2*)x_dev, res_trace, (cudaStream_t)stream);
+}
 
 kp_status kp_wavelet(kp_plan plan, const void* in_dev, void* out_dev, int forward, void* stream) {
     if (!plan || !in_dev || !out_dev) { set_error("null argument"); return KP_EINVAL; }

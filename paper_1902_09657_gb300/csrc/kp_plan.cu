@@ -447,7 +447,7 @@ kp_status plan_destroy_internal(kp_plan p) {
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
                     p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter,
                     p->d_oitems, p->d_tslot, p->d_halo, p->d_sflag, p->d_spos, p->d_iitem_off, p->d_counts,
-                    p->d_sort_tmp, p->d_v};
+                    p->d_sort_tmp, p->d_v, p->d_cg_r, p->d_cg_d, p->d_cg_trace};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
