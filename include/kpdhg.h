@@ -249,7 +249,8 @@ kp_status kp_sense_adjoint_noalloc(const kp_params* params, const float* traj_de
 typedef struct kp_batch_s* kp_batch;
 kp_status kp_batch_create(kp_batch* out, kp_plan* plans, int ncases);
 
-/* Runs `iters` iterations of Sec. 4.1 on every case of the batch.  Arrays of length ncases:
+/* Runs `iters` PDHG iterations (Sec. 4.1; Sec. 4.2 for KP_REG_TV cases) on every case of the
+ * batch.  Arrays of length ncases:
  * y_devs[i] ([C_i][M_i] of type y_types[i]), p_devs[i] (float32 [C_i][M_i], or NULL entries /
  * a NULL array for the multi-channel preconditioner), regs[i], lambdas[i], x_devs[i]
  * (complex64 [N_i] output).  Start, step sizes and power method follow kp_pdhg_solve per case.
@@ -257,8 +258,8 @@ kp_status kp_batch_create(kp_batch* out, kp_plan* plans, int ncases);
  * first call and again when regs, lambdas or y types change) in which every case runs on its
  * own forked stream, so the cases overlap on the GPU; the graph is replayed `iters` times on
  * `stream`.  Each case's result equals that case's kp_pdhg_solve up to float32 rounding order.
- * Synchronous.  Errors: KP_EINVAL (iters < 0, l1 case without wavelet levels, non-positive p
- * or lambda_max of some case), KP_ECUDA, KP_ECUFFT. */
+ * Synchronous.  Errors: KP_EINVAL (iters < 0, an unknown regulariser, l1 case without wavelet
+ * levels, non-positive p or lambda_max of some case), KP_ECUDA, KP_ECUFFT. */
 kp_status kp_batch_solve(kp_batch batch, const void* const* y_devs, const kp_cdtype* y_types,
                          const float* const* p_devs, const kp_reg* regs, const float* lambdas, int iters,
                          void* const* x_devs, void* stream);
