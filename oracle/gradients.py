@@ -59,15 +59,14 @@ def _grid_spectrum(x, maps, oversamp, W):
     return np.fft.fftn(grid, axes=tuple(range(1, d + 1))).reshape(maps.shape[0], -1), gshape
 
 
-def nufft_forward_dtraj(x, maps, traj, oversamp=1.25, W=4, exact_coords=False):
+def nufft_forward_dtraj(x, maps, traj, oversamp=1.25, W=4):
     """d y_c[i] / d f_{i,d} for the NUFFT forward: complex array [C, M, D]."""
     img_shape = x.shape
     D = len(img_shape)
     N = int(np.prod(img_shape))
     Xhat, gshape = _grid_spectrum(x, maps, oversamp, W)
-    t32 = nf.grid_coords(traj, img_shape, gshape, exact_coords)
-    k0 = nf.first_tap(t32, W)
-    t = t32.astype(np.float64)
+    t = nf.grid_coords(traj, img_shape, gshape)
+    k0 = nf.first_tap(t, W)
     M = t.shape[0]
     w, dw, idx = [], [], []
     for d in range(D):
@@ -89,22 +88,22 @@ def nufft_forward_dtraj(x, maps, traj, oversamp=1.25, W=4, exact_coords=False):
     return out / math.sqrt(N)
 
 
-def traj_grad_forward(x, maps, traj, gy, oversamp=1.25, W=4, exact_coords=False):
+def traj_grad_forward(x, maps, traj, gy, oversamp=1.25, W=4):
     """dL/df through y = A x given g_y: [M, D] real."""
-    Dy = nufft_forward_dtraj(x, maps, traj, oversamp, W, exact_coords)
+    Dy = nufft_forward_dtraj(x, maps, traj, oversamp, W)
     return np.real(np.sum(np.conj(gy)[:, :, None] * Dy, axis=0))
 
 
-def traj_grad_adjoint(u, maps, traj, gx, oversamp=1.25, W=4, exact_coords=False):
+def traj_grad_adjoint(u, maps, traj, gx, oversamp=1.25, W=4):
     """dL/df through x = A^H u given g_x: [M, D] real."""
-    return traj_grad_forward(gx, maps, traj, u, oversamp, W, exact_coords)
+    return traj_grad_forward(gx, maps, traj, u, oversamp, W)
 
 
-def unrolled_pdhg_l2(y, maps, traj, p, lam, iters, L, oversamp=1.25, W=4, exact_coords=False):
+def unrolled_pdhg_l2(y, maps, traj, p, lam, iters, L, oversamp=1.25, W=4):
     """Forward of the unrolled l2 PDHG; returns (x_K, tape of per-iteration iterates)."""
     m = maps.astype(np.complex128)
-    A = lambda v: nf.nufft_forward(v, m, traj, oversamp, W, exact_coords)
-    AH = lambda u: nf.nufft_adjoint(u, m, traj, oversamp, W, exact_coords)
+    A = lambda v: nf.nufft_forward(v, m, traj, oversamp, W)
+    AH = lambda u: nf.nufft_adjoint(u, m, traj, oversamp, W)
     y = np.asarray(y, dtype=np.complex128)
     p = np.broadcast_to(np.asarray(p, dtype=np.float64), y.shape)
     x = np.zeros(maps.shape[1:], dtype=np.complex128)
@@ -122,13 +121,12 @@ def unrolled_pdhg_l2(y, maps, traj, p, lam, iters, L, oversamp=1.25, W=4, exact_
     return x, dict(tape=tape, sched=sched)
 
 
-def unrolled_pdhg_l2_grad(gx_K, y, maps, traj, p, lam, iters, L, tape, oversamp=1.25, W=4, want_traj=True,
-                          exact_coords=False):
+def unrolled_pdhg_l2_grad(gx_K, y, maps, traj, p, lam, iters, L, tape, oversamp=1.25, W=4, want_traj=True):
     """Reverse-mode sweep: gradients of a real loss w.r.t. y (complex, [C, M]), lambda (real)
     and the trajectory ([M, D]) given g = dL/dx_K."""
     m = maps.astype(np.complex128)
-    A = lambda v: nf.nufft_forward(v, m, traj, oversamp, W, exact_coords)
-    AH = lambda u: nf.nufft_adjoint(u, m, traj, oversamp, W, exact_coords)
+    A = lambda v: nf.nufft_forward(v, m, traj, oversamp, W)
+    AH = lambda u: nf.nufft_adjoint(u, m, traj, oversamp, W)
     y = np.asarray(y, dtype=np.complex128)
     p = np.broadcast_to(np.asarray(p, dtype=np.float64), y.shape)
     sched = tape["sched"]
@@ -151,12 +149,12 @@ def unrolled_pdhg_l2_grad(gx_K, y, maps, traj, p, lam, iters, L, tape, oversamp=
         gx_k = gx_k + gv
         gu_next = gu - tau * A(gv)                  # total gradient w.r.t. u_{k+1}
         if want_traj:
-            gf += -tau * traj_grad_adjoint(st["u_new"], maps, traj, gv, oversamp, W, exact_coords)
+            gf += -tau * traj_grad_adjoint(st["u_new"], maps, traj, gv, oversamp, W)
         gu = alpha * gu_next
         gr = beta * gu_next
         gxb = AH(gr)
         gy = gy - gr
         if want_traj:
-            gf += traj_grad_forward(st["xbar"], maps, traj, gr, oversamp, W, exact_coords)
+            gf += traj_grad_forward(st["xbar"], maps, traj, gr, oversamp, W)
         gx = gx_k
     return gy, glam, gf

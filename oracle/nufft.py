@@ -7,7 +7,7 @@ Model (Sec. 2, Eq. model_i, extended to d dimensions with a centred index):
 
 NUFFT (Sec. 6: "following Beatty et al.", oversampling 1.25, kernel width 4):
 grid size G_d = ceil(alpha N_d) rounded up to even, grid coordinate
-t_{i,d} = f_{i,d} * (G_d/N_d) (evaluated in float32), Kaiser-Bessel kernel
+t_{i,d} = f_{i,d} * (G_d/N_d) (float64), Kaiser-Bessel kernel
 
     phi_d(u) = I0(beta_d sqrt(1 - (2u/W)^2)) for |u| <= W/2, else 0,
     beta_d = pi sqrt((W/a_d)^2 (a_d - 1/2)^2 - 0.8),  a_d = G_d/N_d   (Beatty 2005),
@@ -18,9 +18,8 @@ apodisation by its continuous Fourier transform
 
 (sin form when the radicand is negative), zero padding with pixel n_d stored at
 grid index n_d mod G_d, a forward DFT of size G, and W^d-tap interpolation with
-taps k_d = ceil(t_d - W/2) + j, j = 0..W-1, evaluated as ceil(t_d) - W/2 + j (exact for
-even W, no rounding; t_d itself is the float32 value the GPU uses), read at index
-k_d mod G_d.  Every tap then has |t_d - k_d| <= W/2.
+taps k_d = ceil(t_d - W/2) + j, j = 0..W-1, evaluated as ceil(t_d) - W/2 + j (the same
+integer for even W, with no rounding of t_d - W/2), read at index k_d mod G_d.  Every tap then has |t_d - k_d| <= W/2.
 The adjoint is the exact transpose, step by step in reverse order.
 
 Parity: pinned by tests/test_oracle_nufft.py (brute-force NUDFT on tiny inputs,
@@ -79,22 +78,16 @@ def kb_apod(n, G, W, beta):
     return out
 
 
-def grid_coords(traj, img_shape, gshape, exact=False):
-    """t_{i,d} = f_{i,d} * (G_d / N_d), computed in float32 as the GPU does (exact=True: float64,
-    used only by finite-difference checks, whose steps float32 coordinates cannot resolve)."""
-    if exact:
-        traj = np.asarray(traj, dtype=np.float64)
-        return traj * np.array([g / n for g, n in zip(gshape, img_shape)])[None, :]
-    traj = np.asarray(traj, dtype=np.float32)
-    scale = np.array([np.float32(g) / np.float32(n) for g, n in zip(gshape, img_shape)],
-                     dtype=np.float32)
-    return traj * scale[None, :]
+def grid_coords(traj, img_shape, gshape):
+    """t_{i,d} = f_{i,d} * (G_d / N_d) in float64 (the operator as the paper defines it)."""
+    traj = np.asarray(traj, dtype=np.float64)
+    return traj * np.array([g / n for g, n in zip(gshape, img_shape)])[None, :]
 
 
 def first_tap(t, W):
     """k0 = ceil(t) - W/2 for even W: the same integer as ceil(t - W/2) in exact arithmetic,
-    computed without rounding (t - W/2 in float32 can round onto an integer when |t| < W/2,
-    which would push the first tap just outside the window)."""
+    computed without rounding (t - W/2 in floating point can round onto an integer when |t| is
+    tiny, which would push the first tap just outside the window)."""
     t = np.asarray(t)
     return np.ceil(t).astype(np.int64) - W // 2
 
@@ -152,11 +145,10 @@ def nudft_adjoint(y, maps, traj):
 class _Taps:
     """Per-sample interpolation taps: flat grid indices [T, M] and weights [T, M]."""
 
-    def __init__(self, traj, img_shape, gshape, W, exact=False):
+    def __init__(self, traj, img_shape, gshape, W):
         d = len(img_shape)
-        t32 = grid_coords(traj, img_shape, gshape, exact)
-        k0 = first_tap(t32, W)
-        t = t32.astype(np.float64)
+        t = grid_coords(traj, img_shape, gshape)
+        k0 = first_tap(t, W)
         per_dim_idx, per_dim_w = [], []
         for dd in range(d):
             beta = kb_beta(W, gshape[dd] / img_shape[dd])
@@ -195,7 +187,7 @@ def _pad_index(img_shape, gshape):
     return np.ix_(*[np.mod(_centred(n), g) for n, g in zip(img_shape, gshape)])
 
 
-def nufft_forward(x, maps, traj, oversamp=1.25, W=4, exact_coords=False):
+def nufft_forward(x, maps, traj, oversamp=1.25, W=4):
     """NUFFT approximation of A x: coil multiply, apodise, pad, DFT, interpolate. [C, M]."""
     img_shape = x.shape
     d = len(img_shape)
@@ -206,14 +198,14 @@ def nufft_forward(x, maps, traj, oversamp=1.25, W=4, exact_coords=False):
     grid = np.zeros((C,) + gshape, dtype=np.complex128)
     grid[(slice(None),) + _pad_index(img_shape, gshape)] = img
     Xhat = np.fft.fftn(grid, axes=tuple(range(1, d + 1))).reshape(C, -1)
-    taps = _Taps(traj, img_shape, gshape, W, exact_coords)
+    taps = _Taps(traj, img_shape, gshape, W)
     y = np.zeros((C, taps.w.shape[1]), dtype=np.complex128)
     for j in range(taps.w.shape[0]):
         y += taps.w[j][None, :] * Xhat[:, taps.flat[j]]
     return y / math.sqrt(N)
 
 
-def nufft_adjoint(y, maps, traj, oversamp=1.25, W=4, exact_coords=False):
+def nufft_adjoint(y, maps, traj, oversamp=1.25, W=4):
     """Exact transpose of nufft_forward: spread, inverse DFT (unnormalised), crop, apodise, coil combine."""
     img_shape = maps.shape[1:]
     d = len(img_shape)
@@ -221,7 +213,7 @@ def nufft_adjoint(y, maps, traj, oversamp=1.25, W=4, exact_coords=False):
     N = int(np.prod(img_shape))
     G = int(np.prod(gshape))
     C = maps.shape[0]
-    taps = _Taps(traj, img_shape, gshape, W, exact_coords)
+    taps = _Taps(traj, img_shape, gshape, W)
     flat = taps.flat.ravel()
     grid = np.empty((C, G), dtype=np.complex128)
     for c in range(C):

@@ -119,7 +119,7 @@ def psf_h(traj, img_shape, oversamp=1.25, W=4, exact=False):
     M = traj.shape[0]
     if exact:
         return nf.nudft_adjoint(np.ones((1, M)), _ones_maps(big), 2.0 * traj) * math.sqrt(2 ** len(img_shape))
-    traj2 = (2.0 * np.asarray(traj, dtype=np.float32)).astype(np.float32)
+    traj2 = 2.0 * traj
     hb = nf.nufft_adjoint(np.ones((1, M)), _ones_maps(big), traj2, oversamp, W)
     # adjoint on the 2N image carries (2^d N)^{-1/2}; h carries N^{-1/2}
     return hb * math.sqrt(np.prod(big) / N)
@@ -132,16 +132,16 @@ def mc_precond_fast(maps, traj, oversamp=1.25, W=4, exact=False):
     C = maps.shape[0]
     N = int(np.prod(img_shape))
     big = tuple(2 * n for n in img_shape)
-    traj = np.asarray(traj, dtype=np.float32)
+    traj = np.asarray(traj, dtype=np.float64)
     r = autocorrelation_sum(maps)
     h = psf_h(traj, img_shape, oversamp, W, exact=exact)
-    traj2 = (2.0 * traj).astype(np.float32)
+    traj2 = 2.0 * traj
     ones = _ones_maps(big)
     p = np.empty((C, traj.shape[0]))
     for c in range(C):
         v = r[c] * h
         if exact:
-            s = nf.nudft_forward(v, ones, traj2.astype(np.float64))[0]
+            s = nf.nudft_forward(v, ones, traj2)[0]
         else:
             s = nf.nufft_forward(v, ones, traj2, oversamp, W)[0]
         s = s * math.sqrt(np.prod(big))

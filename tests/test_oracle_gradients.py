@@ -39,14 +39,14 @@ def test_kb_derivative_matches_fd():
 def test_forward_traj_derivative_fd():
     x, maps, traj = _problem()
     h = 1e-4
-    D = og.nufft_forward_dtraj(x, maps, traj, exact_coords=True)
+    D = og.nufft_forward_dtraj(x, maps, traj)
     ok = _safe(traj, x.shape, h)
     assert ok.sum() > 40
     for d in range(2):
         tp, tm = traj.copy(), traj.copy()
         tp[:, d] += h
         tm[:, d] -= h
-        fd = (nf.nufft_forward(x, maps, tp, 1.25, 4, True) - nf.nufft_forward(x, maps, tm, 1.25, 4, True)) / (2 * h)
+        fd = (nf.nufft_forward(x, maps, tp, 1.25, 4) - nf.nufft_forward(x, maps, tm, 1.25, 4)) / (2 * h)
         err = np.abs(D[:, ok, d] - fd[:, ok]).max() / np.abs(fd[:, ok]).max()
         assert err < 1e-5
 
@@ -58,8 +58,8 @@ def test_adjoint_traj_gradient_fd():
     gx = rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)
     h = 1e-4
     ok = _safe(traj, x.shape, h)
-    G = og.traj_grad_adjoint(u, maps, traj, gx, exact_coords=True)
-    Lf = lambda tr: float(np.real(np.vdot(gx, nf.nufft_adjoint(u, maps, tr, 1.25, 4, True))))
+    G = og.traj_grad_adjoint(u, maps, traj, gx)
+    Lf = lambda tr: float(np.real(np.vdot(gx, nf.nufft_adjoint(u, maps, tr, 1.25, 4))))
     for i in np.nonzero(ok)[0][:12]:
         for d in range(2):
             tp, tm = traj.copy(), traj.copy()
@@ -113,11 +113,9 @@ def test_unrolled_grad_lambda_and_traj_fd(unrolled):
     u = unrolled
     rng = np.random.default_rng(4)
     c = rng.standard_normal(u["shape"]) + 1j * rng.standard_normal(u["shape"])
-    run = lambda lam, tr: _loss(og.unrolled_pdhg_l2(u["y"], u["maps"], tr, u["p"], lam, u["iters"], u["L"],
-                                                    exact_coords=True)[0], c)
-    xK, tape = og.unrolled_pdhg_l2(u["y"], u["maps"], u["traj"], u["p"], u["lam"], u["iters"], u["L"], exact_coords=True)
-    _, glam, gf = og.unrolled_pdhg_l2_grad(c, u["y"], u["maps"], u["traj"], u["p"], u["lam"], u["iters"], u["L"], tape,
-                                           exact_coords=True)
+    run = lambda lam, tr: _loss(og.unrolled_pdhg_l2(u["y"], u["maps"], tr, u["p"], lam, u["iters"], u["L"])[0], c)
+    xK, tape = og.unrolled_pdhg_l2(u["y"], u["maps"], u["traj"], u["p"], u["lam"], u["iters"], u["L"])
+    _, glam, gf = og.unrolled_pdhg_l2_grad(c, u["y"], u["maps"], u["traj"], u["p"], u["lam"], u["iters"], u["L"], tape)
     h = 1e-6
     fd = (run(u["lam"] + h, u["traj"]) - run(u["lam"] - h, u["traj"])) / (2 * h)
     assert abs(glam - fd) < 1e-6 * abs(fd)
