@@ -109,7 +109,8 @@ kp_status kp_plan_create(kp_plan* out, const kp_params* params, void* stream);
 kp_status kp_plan_destroy(kp_plan plan);
 
 /* Set the trajectory (Sec. 2: sampling points f_i): converts to grid coordinates
- * t = f G/N (float32), sorts samples by grid tile (counting sort) and builds the
+ * t = f G/N (formed in float64; kept as the first tap and a float32 offset), sorts samples
+ * by grid tile (counting sort) and builds the
  * per-tile lists used by the spreading kernel.  traj_dev: float32 [M][ndim].
  * Synchronous (it checks the coordinate range).  Errors: KP_EINVAL if any coordinate is
  * outside [-N_d/2, N_d/2] or not finite. */
@@ -136,6 +137,8 @@ kp_status kp_sense_adjoint(kp_plan plan, const void* y_dev, kp_cdtype y_t, void*
  *   |sum_n s_c s_d^* e^{-i 2 pi (f_i - f_j) n/N}|^2;
  * multichannel = 0: Eq. sc_precond with the 1/N^2 prefactor of the general form
  *   (C = 1, s = 1), the same value written for every coil.
+ * FFTs and gridding in float32; the denominator sums (R_c = sum_d |Q_cd|^2 and the taps of the
+ * last type-2 interpolation) accumulate in float64.
  * p_dev: float32 [C][M], sample order of the trajectory.  Synchronous.
  * Errors: KP_ENONFINITE if a denominator came out non-positive (NUFFT error). */
 kp_status kp_make_preconditioner(kp_plan plan, int multichannel, float* p_dev, void* stream);
@@ -231,11 +234,12 @@ kp_status kp_plan_launch_count(kp_plan plan, int64_t* count);
  * Work space is one fixed 4 MiB device array built into the library (2^19 complex64 values,
  * held on every GPU that loads the library until exit); problems needing more than
  * C x (G + G / g_last x n_last) values are rejected with KP_EINVAL (G = prod g_d, g_d the
- * oversampled grid).  Its device address is looked up on the first call on each device,
- * with that device current; make that first call before any stream capture.  The grid is
+ * oversampled grid).  Its device address is looked up on every call, on the current device;
+ * the first call on a device also loads the library's device code there, so make that first
+ * call before any stream capture.  The grid is
  * cleared at the start of every call; calls that overlap on the GPU share the array and race,
  * so issue them one at a time.  The inverse DFT is evaluated directly (no cuFFT plan), so the
- * result matches kp_sense_adjoint to float32 rounding.  Samples with a coordinate outside
+ * result matches kp_sense_adjoint to float32 rounding (float64 grid coordinates, like the plan).  Samples with a coordinate outside
  * [-N_d/2, N_d/2] or not finite are skipped (this path cannot report them without a
  * synchronisation; kp_plan_set_trajectory validates a trajectory).  Asynchronous. */
 kp_status kp_sense_adjoint_noalloc(const kp_params* params, const float* traj_dev, const void* maps_dev,

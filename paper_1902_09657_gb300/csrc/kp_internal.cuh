@@ -73,6 +73,18 @@ struct Tiles {
     int64_t ntiles;
 };
 
+// Grid coordinate of a sample along one axis, t = f s g / n (s = 1, or 2 on the preconditioner's
+// 2N grid), evaluated in float64 as one correctly rounded quotient (f s g is exact in float64),
+// so the taps and weights are those of the operator in exact arithmetic up to float32 storage
+// of the offset.  Returns the first Kaiser-Bessel tap k0 = ceil(t) - W/2 (not wrapped) and sets
+// *u0 = t - ceil(t) in (-1, 0]; tap j of the sample sits at distance t - (k0 + j) = u0 + W/2 - j.
+__host__ __device__ __forceinline__ int grid_tap(float f, float s, int n, int g, float* u0) {
+    const double t = ((double)f * (double)s * (double)g) / (double)n;
+    const double c = ceil(t);
+    *u0 = (float)(t - c);
+    return (int)c - KW / 2;
+}
+
 // shifted tile coordinate of grid index i (0 <= i < g)
 __host__ __device__ __forceinline__ int tshift(int i, int sh, int g) { int p = i + sh; return p >= g ? p - g : p; }
 // grid index of shifted coordinate p (0 <= p < g)
@@ -221,7 +233,7 @@ struct kp_plan_s {
     uint64_t graph_gen = 0;          // bumped whenever captured graphs become stale
 
     // trajectory (sorted by tile)
-    float* d_t = nullptr;            // [D][M] grid coordinates t = f * g/n, sorted order
+    float* d_t = nullptr;            // [D][M] offsets u0 = t - ceil(t) of the grid coordinates t = f g/n, sorted order
     int* d_perm = nullptr;           // sorted position -> original sample index
     int* d_key = nullptr;            // [M] tile key per original sample (scratch)
     int* d_cnt = nullptr;            // [ntiles + 1]
@@ -248,7 +260,7 @@ struct kp_plan_s {
     int4* d_sort_tmp = nullptr;      // [8192] scratch of the item sort
     int* d_split = nullptr;          // tiles whose list spans several work items
     int64_t n_split = 0, split_cap = 0;
-    int* d_k0 = nullptr;             // [D][M] wrapped first tap per sorted sample
+    int* d_k0 = nullptr;             // [D][M] wrapped first tap ceil(t) - W/2 per sorted sample
     float* d_wt = nullptr;           // [D * W][M] Kaiser-Bessel weights per sorted sample
     int chunk = 256;                 // samples per interpolation work item (<= its block size)
     int spread_chunk = 256;          // samples per spreading work item (autotuned, multiple of 256)

@@ -9,7 +9,7 @@
 //
 // What it computes: the same operator as kp_sense_adjoint (Kaiser-Bessel spreading onto the
 // oversampled grid, unnormalised inverse DFT, crop, 1/Phi apodisation, conj(s_c) coil
-// combine, N^{-1/2}), with the same float32 grid coordinates and taps.  Because it may not
+// combine, N^{-1/2}), with the same float64 grid coordinates and taps.  Because it may not
 // create a cuFFT plan, the inverse DFT is evaluated directly, one axis at a time, only at
 // the N_d output pixels of each axis; spreading uses global atomics straight into the
 // scratch grid.  The results agree with kp_sense_adjoint to float32 rounding (summation
@@ -17,14 +17,14 @@
 //
 // Scratch: one file-scope device array of KP_NOALLOC_SCRATCH_ELEMS complex64 values (4 MiB),
 // present on every GPU that loads this library until the process exits.  Its device address
-// is looked up once per device (cudaGetSymbolAddress) on the first call made with that device
-// current.  Every call shares the array: the spreading grid is cleared at the start of each
+// is looked up (cudaGetSymbolAddress) on every call, with the caller's device current; the
+// first call on a device also loads the device code there, so make it before any stream
+// capture.  Every call shares the array: the spreading grid is cleared at the start of each
 // call, and calls that overlap on the GPU (different streams, or different host threads)
 // race on it and must not be issued.
 #include "kp_internal.cuh"
 
 #include <cmath>
-#include <mutex>
 
 #define KP_NOALLOC_SCRATCH_ELEMS (1 << 19)
 
@@ -55,7 +55,7 @@ __global__ void k_zero(float2* __restrict__ p, int64_t n) {
         p[i] = make_float2(0.f, 0.f);
 }
 
-// One thread per sample (caller's order): taps k = ceil(t) - 2 + j, t = f * (g/n) in float32.
+// One thread per sample (caller's order): taps k = ceil(t) - 2 + j, t = f g / n formed in float64.
 __global__ void k_spread_atomic(const float* __restrict__ traj, const float2* __restrict__ y, Dims dm,
                                 float2* __restrict__ grid) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,13 +66,11 @@ __global__ void k_spread_atomic(const float* __restrict__ traj, const float2* __
         const float f = traj[i * dm.D + d];
         const float half = 0.5f * (float)dm.n[d];
         if (!(f >= -half && f <= half)) return;   // out of range or not finite: sample skipped
-        const float sc = (float)dm.g[d] / (float)dm.n[d];
-        const float t = f * sc;
-        const int k0 = (int)ceilf(t) - KW / 2;
+        float u0;
+        const int k0 = grid_tap(f, 1.f, dm.n[d], dm.g[d], &u0);
         for (int j = 0; j < KW; ++j) {
-            const int k = k0 + j;
-            w[d][j] = kb4(t - (float)k, dm.beta[d]);
-            idx[d][j] = wrapi(k, dm.g[d]);
+            w[d][j] = kb4(u0 + (float)(KW / 2 - j), dm.beta[d]);
+            idx[d][j] = wrapi(k0 + j, dm.g[d]);
         }
     }
     const int taps = dm.D == 2 ? KW * KW : KW * KW * KW;
@@ -163,24 +161,18 @@ __global__ void k_combine(const float2* __restrict__ img, const float2* __restri
     x[j] = make_float2(acc.x * sc, acc.y * sc);
 }
 
-static std::mutex g_mu;
-static float2* g_addr[64] = {nullptr};
-
+// Device address of the scratch array on the current device, looked up on every call: the
+// lookup allocates nothing, and a cached address would go stale after cudaDeviceReset or a
+// re-created primary context.  The first lookup on a device also loads this library's device
+// code there, which is why the first call should not be made during a stream capture.
 static kp_status scratch_address(float2** out) {
-    int dev = 0;
-    KP_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) { set_error("device index out of range"); return KP_EINVAL; }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-            return KP_ECUDA;
-        }
-        g_addr[dev] = (float2*)p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        return KP_ECUDA;
     }
-    *out = g_addr[dev];
+    *out = (float2*)p;
     return KP_OK;
 }
 

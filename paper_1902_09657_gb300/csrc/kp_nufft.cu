@@ -13,8 +13,9 @@
 // The Kaiser-Bessel weights and first taps of every sample are tabulated once per
 // trajectory (sorted order, structure of arrays), so no Bessel function is evaluated
 // inside the iteration.
-// The grid coordinates t = f g/n are float32; the first tap is k0 = ceil(t) - W/2, which equals
-// ceil(t - W/2) exactly and involves no rounding, so |t - k| <= W/2 for every tap.
+// The grid coordinates t = f g/n are formed in float64 at binning (grid_tap); the first tap is
+// k0 = ceil(t) - W/2, which equals ceil(t - W/2) exactly, so |t - k| <= W/2 for every tap, and
+// the weights come from the float32 offset t - ceil(t).
 #include "kp_internal.cuh"
 
 #include <cstdlib>
@@ -59,26 +60,24 @@ __device__ __forceinline__ void make_taps(const int* __restrict__ k0t, const flo
     }
 }
 
-// Tap tables of the sorted samples: wrapped first tap k0 = ceil(t) - W/2 (mod g) and the
-// Kaiser-Bessel weights phi(t - k) of the W taps per axis.
+// Kaiser-Bessel weights of the sorted samples: phi(t - k) for the W taps per axis, from the
+// offset u0 = t - ceil(t) written by the binning (t - (k0 + j) = u0 + W/2 - j).
 template <int D>
-__global__ void k_tap_tables(const float* __restrict__ t, Geom geo, int* __restrict__ k0t, float* __restrict__ wt) {
+__global__ void k_tap_tables(const float* __restrict__ u0t, Geom geo, float* __restrict__ wt) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= geo.M) return;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const float td = t[(int64_t)d * geo.M + s];
-        const int k0 = (int)ceilf(td) - KW / 2;
-        k0t[(int64_t)d * geo.M + s] = wrapg(k0, geo.g[d]);
+        const float u0 = u0t[(int64_t)d * geo.M + s];
 #pragma unroll
-        for (int j = 0; j < KW; ++j) wt[(int64_t)(d * KW + j) * geo.M + s] = kbw(td - (float)(k0 + j), geo.beta[d]);
+        for (int j = 0; j < KW; ++j) wt[(int64_t)(d * KW + j) * geo.M + s] = kbw(u0 + (float)(KW / 2 - j), geo.beta[d]);
     }
 }
 
 kp_status build_tap_tables(kp_plan p, cudaStream_t st) {
     const Geom& g = p->geo;
-    if (g.D == 2) k_tap_tables<2><<<nblk(g.M, 256), 256, 0, st>>>(p->d_t, g, p->d_k0, p->d_wt);
-    else k_tap_tables<3><<<nblk(g.M, 256), 256, 0, st>>>(p->d_t, g, p->d_k0, p->d_wt);
+    if (g.D == 2) k_tap_tables<2><<<nblk(g.M, 256), 256, 0, st>>>(p->d_t, g, p->d_wt);
+    else k_tap_tables<3><<<nblk(g.M, 256), 256, 0, st>>>(p->d_t, g, p->d_wt);
     KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;

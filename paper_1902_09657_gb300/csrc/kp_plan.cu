@@ -1,7 +1,8 @@
 // Plan life cycle, trajectory binning (counting sort by grid tile) and coil maps.
 //
 // The trajectory step converts each sample to grid coordinates t_d = f_d * (g_d / n_d)
-// (float32, Sec. 6 NUFFT with oversampling g/n), sorts samples by the grid tile that
+// (float64, Sec. 6 NUFFT with oversampling g/n; kept as the first tap and a float32 offset),
+// sorts samples by the grid tile that
 // holds their first Kaiser-Bessel tap, and builds, per tile, the list of samples whose
 // W^D footprint touches that tile (used by the spreading kernel, which owns one output
 // tile per CTA and therefore needs no global atomics and no zero-fill of the grid).
@@ -62,12 +63,11 @@ __global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geo
     int k0w[D];
     bool bad = false;
     for (int d = 0; d < D; ++d) {
-        float f = traj[i * D + d] * traj_scale;
+        float f = traj[i * D + d];
         float half = 0.5f * (float)geo.n[d];
-        if (!(f >= -half && f <= half)) bad = true;   // also catches NaN
-        float sc = (float)geo.g[d] / (float)geo.n[d];
-        float t = bad ? 0.f : f * sc;
-        int k0 = (int)ceilf(t) - KW / 2;
+        if (!(f * traj_scale >= -half && f * traj_scale <= half)) bad = true;   // also catches NaN
+        float u0;
+        int k0 = grid_tap(bad ? 0.f : f, traj_scale, geo.n[d], geo.g[d], &u0);
         k0w[d] = tshift(wrap(k0, geo.g[d]), tl.sh[d], geo.g[d]);
     }
     if (bad) atomicAdd(flag, 1);
@@ -76,33 +76,36 @@ __global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geo
     atomicAdd(&cnt[kk], 1);
 }
 
-// Pass 2: scatter sample i to its slot in the sorted order.
+// Pass 2: scatter sample i to its slot in the sorted order, with its wrapped first tap
+// k0t[d][pos] and its float32 offset u0[d][pos] = t - ceil(t) (grid_tap).
 template <int D>
 __global__ void k_traj_scatter(const float* __restrict__ traj, float traj_scale, Geom geo,
                                const int* __restrict__ key, const int* __restrict__ off,
-                               int* __restrict__ fill, int* __restrict__ perm, float* __restrict__ t) {
+                               int* __restrict__ fill, int* __restrict__ perm, float* __restrict__ u0t,
+                               int* __restrict__ k0t) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= geo.M) return;
     int kk = key[i];
     int pos = off[kk] + atomicAdd(&fill[kk], 1);
     perm[pos] = (int)i;
     for (int d = 0; d < D; ++d) {
-        float f = traj[i * D + d] * traj_scale;
+        float f = traj[i * D + d];
         float half = 0.5f * (float)geo.n[d];
-        if (!(f >= -half && f <= half)) f = 0.f;
-        float sc = (float)geo.g[d] / (float)geo.n[d];
-        t[(int64_t)d * geo.M + pos] = f * sc;
+        if (!(f * traj_scale >= -half && f * traj_scale <= half)) f = 0.f;
+        float u0;
+        const int k0 = grid_tap(f, traj_scale, geo.n[d], geo.g[d], &u0);
+        u0t[(int64_t)d * geo.M + pos] = u0;
+        k0t[(int64_t)d * geo.M + pos] = wrap(k0, geo.g[d]);
     }
 }
 
 // Tiles touched by the footprint of sorted sample s, per axis (1 or 2 each).
 template <int D>
-__device__ __forceinline__ void footprint_tiles(const float* __restrict__ t, int64_t s, const Geom& geo,
+__device__ __forceinline__ void footprint_tiles(const int* __restrict__ k0t, int64_t s, const Geom& geo,
                                                 const Tiles& tl, int lo[D], int hi[D]) {
     for (int d = 0; d < D; ++d) {
-        float td = t[(int64_t)d * geo.M + s];
-        int k0 = (int)ceilf(td) - KW / 2;
-        int a = tshift(wrap(k0, geo.g[d]), tl.sh[d], geo.g[d]);
+        const int k0 = k0t[(int64_t)d * geo.M + s];
+        int a = tshift(k0, tl.sh[d], geo.g[d]);
         int b = tshift(wrap(k0 + KW - 1, geo.g[d]), tl.sh[d], geo.g[d]);
         lo[d] = a / tl.ts[d];
         hi[d] = b / tl.ts[d];
@@ -110,12 +113,12 @@ __device__ __forceinline__ void footprint_tiles(const float* __restrict__ t, int
 }
 
 template <int D, bool FILL>
-__global__ void k_ext(const float* __restrict__ t, Geom geo, Tiles tl, int* __restrict__ cnt,
+__global__ void k_ext(const int* __restrict__ k0t, Geom geo, Tiles tl, int* __restrict__ cnt,
                       const int* __restrict__ off, int* __restrict__ ext) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= geo.M) return;
     int lo[D], hi[D];
-    footprint_tiles<D>(t, s, geo, tl, lo, hi);
+    footprint_tiles<D>(k0t, s, geo, tl, lo, hi);
     for (int m = 0; m < (1 << D); ++m) {
         int64_t key = 0;
         bool dup = false;
@@ -594,20 +597,20 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_off, tl.ntiles);
     KP_LAUNCH_CHECK();
     KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    if (g.D == 2) k_traj_scatter<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t);
-    else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t);
+    if (g.D == 2) k_traj_scatter<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t, p->d_k0);
+    else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t, p->d_k0);
     KP_LAUNCH_CHECK();
     KP_TRY(build_tap_tables(p, st));
     // spreading lists
     KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    if (g.D == 2) k_ext<2, false><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, nullptr, nullptr);
-    else k_ext<3, false><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, nullptr, nullptr);
+    if (g.D == 2) k_ext<2, false><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, nullptr, nullptr);
+    else k_ext<3, false><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, nullptr, nullptr);
     KP_LAUNCH_CHECK();
     k_max_count<<<64, 256, 0, st>>>(p->d_cnt, tl.ntiles, p->d_flag + 2);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_ext_off, tl.ntiles);
     KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    if (g.D == 2) k_ext<2, true><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
-    else k_ext<3, true><<<nblk(g.M, T), T, 0, st>>>(p->d_t, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
+    if (g.D == 2) k_ext<2, true><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
+    else k_ext<3, true><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
     KP_LAUNCH_CHECK();
     // every count the host needs (flags, spreading, interpolation and own items), one copy
     spread_items_counts(p, p->spread_chunk, st);

@@ -5,6 +5,8 @@
 //   h    = N^{-1/2} sum_j e^{+i 2 pi f_j k/N}        (type-1 NUFFT of ones at 2 f_j on the 2N image)
 //   p_c[i] = ||s_c||^2 sqrt(N) / Re(sum_k r_c[k] h[k] e^{-i 2 pi f_i k / N})   (type-2 NUFFT at 2 f_i)
 //
+// FFTs and gridding run in float32; the denominator sums (R_c over coil pairs, and the
+// interpolation taps of the last type-2 step, real part only) accumulate in float64.
 // With the 2N-image NUFFT carrying (2^D N)^{-1/2} in both directions, the last line is
 // p_c[i] = ||s_c||^2 / (2^D Re(fwd_2N(r_c * adj_2N(1))[i])).  Pairs (c, d) and (d, c) share
 // one FFT: |Q_dc|^2[m] = |Q_cd|^2[-m].  Single channel (Eq. sc_precond): C = 1, s = 1.
@@ -160,10 +162,8 @@ __global__ void k_accum_R(const float2* __restrict__ Q, const int2* __restrict__
 }
 
 // With every pair's spectrum in Q (pair (c, d), c <= d, at index c C - c (c - 1) / 2 + d - c):
-// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, written once.  One thread per
-// (m, c), c = blockIdx.y.  The C positive terms are summed in float32 (relative error below
-// C 2^-24; R is rounded to float32 for its inverse FFT right after): float64 arithmetic runs
-// at a small fraction of the float32 rate on this GPU and made the sum the slowest step.
+// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, summed in float64 and written
+// once.  One thread per (m, c), c = blockIdx.y.
 __global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0, int nb1, int nb2, int64_t Nb,
                             double* __restrict__ R) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,17 +178,19 @@ __global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0,
         mneg += in * stride;
         stride *= nb[d];
     }
-    float acc = 0.f;
+    double acc = 0.0;
     for (int d = 0; d < c; ++d) {
         const float2 b = Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg];
-        acc += fmaf(b.x, b.x, b.y * b.y);
+        acc = fma((double)b.x, (double)b.x, acc);
+        acc = fma((double)b.y, (double)b.y, acc);
     }
     const size_t p0 = (size_t)(c * C - c * (c - 1) / 2);
     for (int d = c; d < C; ++d) {
         const float2 a = Q[(p0 + d - c) * Nb + m];
-        acc += fmaf(a.x, a.x, a.y * a.y);
+        acc = fma((double)a.x, (double)a.x, acc);
+        acc = fma((double)a.y, (double)a.y, acc);
     }
-    R[(size_t)c * Nb + m] = (double)acc;
+    R[(size_t)c * Nb + m] = acc;
 }
 
 // r_c = R_c / Nb for the coils c0 .. c0 + nc - 1 (grid c - c0 of out).
@@ -243,12 +245,52 @@ __global__ void k_set_norm(double* out, int C, double v) {
     if (c < C) out[c] = v;
 }
 
-// p[c][i] = ||s_c||^2 / (2^D Re(den[s])) with den in the 2N plan's sorted order.
-__global__ void k_p_out(const float2* __restrict__ den, const int* __restrict__ perm, int64_t M, const double* __restrict__ norm,
-                        int cnorm, int c_first, int c_count, int D, float* __restrict__ p, int* __restrict__ bad) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    const double dv = (double)den[s].x * (double)(1 << D);
+// Final step of the fast route: for each sorted sample s of the 2N plan, the denominator
+// den = (2^D N)^{-1/2} Re sum_taps phi(t - k) Vhat[k mod g] (type-2 interpolation of the 2N
+// plan's forward grid spectrum Vhat = FFT(pad(v_c / Phi))), the taps' products and their sum
+// taken in float64, and p[c][perm[s]] = ||s_c||^2 / (2^D den) for the coils c_first ..
+// c_first + c_count - 1.  A denominator that is not positive (interpolation error) gives p = 0
+// and is counted in *bad.
+template <int D>
+__global__ void k_den_p(const float2* __restrict__ Vhat, const int* __restrict__ k0t, const float* __restrict__ wt,
+                        const int* __restrict__ perm, Geom g2, const double* __restrict__ norm, int cnorm,
+                        int c_first, int c_count, float* __restrict__ p, int* __restrict__ bad) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g2.M) return;
+    int64_t off[D][KW];
+    double w[D][KW];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        int64_t stride = 1;
+        for (int e = d + 1; e < D; ++e) stride *= g2.g[e];
+        const int k0 = k0t[(int64_t)d * g2.M + s];
+#pragma unroll
+        for (int j = 0; j < KW; ++j) {
+            int ix = k0 + j;
+            if (ix >= g2.g[d]) ix -= g2.g[d];
+            off[d][j] = ix * stride;
+            w[d][j] = (double)wt[(int64_t)(d * KW + j) * g2.M + s];
+        }
+    }
+    double acc = 0.0;
+    if (D == 2) {
+#pragma unroll
+        for (int a = 0; a < KW; ++a)
+#pragma unroll
+            for (int b = 0; b < KW; ++b)
+                acc = fma(w[0][a] * w[D - 1][b], (double)Vhat[off[0][a] + off[D - 1][b]].x, acc);
+    } else {
+#pragma unroll
+        for (int a = 0; a < KW; ++a)
+#pragma unroll
+            for (int b = 0; b < KW; ++b) {
+                const double wab = w[0][a] * w[1 % D][b];
+#pragma unroll
+                for (int e = 0; e < KW; ++e)
+                    acc = fma(wab * w[D - 1][e], (double)Vhat[off[0][a] + off[1 % D][b] + off[D - 1][e]].x, acc);
+            }
+    }
+    const double dv = acc * (double)(1 << D) / sqrt((double)g2.N);
     const int64_t i = perm[s];
     float val;
     if (dv > 0 && isfinite(dv)) {
@@ -257,7 +299,7 @@ __global__ void k_p_out(const float2* __restrict__ den, const int* __restrict__ 
         val = 0.f;
         atomicAdd(bad, 1);
     }
-    for (int c = c_first; c < c_first + c_count; ++c) p[(size_t)c * M + i] = val;
+    for (int c = c_first; c < c_first + c_count; ++c) p[(size_t)c * g2.M + i] = val;
 }
 
 }  // namespace kp
@@ -348,9 +390,13 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
         KP_LAUNCH_CHECK();
         plan->launches += 2;
         for (int c = c0; c < c0 + nc; ++c) {
-            KP_TRY(forward_to(nu, q->d_v + (size_t)(c - c0) * q->Nb, nu->d_kt, KP_C64, nullptr, st));
-            k_p_out<<<nblk(g.M, 256), 256, 0, st>>>(nu->d_kt, nu->d_perm, g.M, q->d_norm, c, mc ? c : 0, mc ? 1 : g.C, g.D,
-                                                    p_dev, plan->d_flag + 7);
+            KP_TRY(forward_grid_only(nu, q->d_v + (size_t)(c - c0) * q->Nb, st));
+            if (g.D == 2)
+                k_den_p<2><<<nblk(g.M, 256), 256, 0, st>>>(nu->d_gridF, nu->d_k0, nu->d_wt, nu->d_perm, nu->geo, q->d_norm,
+                                                           c, mc ? c : 0, mc ? 1 : g.C, p_dev, plan->d_flag + 7);
+            else
+                k_den_p<3><<<nblk(g.M, 256), 256, 0, st>>>(nu->d_gridF, nu->d_k0, nu->d_wt, nu->d_perm, nu->geo, q->d_norm,
+                                                           c, mc ? c : 0, mc ? 1 : g.C, p_dev, plan->d_flag + 7);
             KP_LAUNCH_CHECK();
             plan->launches += 1;
         }

@@ -44,22 +44,22 @@ __device__ __forceinline__ int wrapk(int k, int g) { return k < 0 ? k + g : (k >
 
 // out[perm[s]][d] (+)= coeff * (g_d/n_d) N^{-1/2} sum_c Re(conj(a_c) sum_taps dphi_d prod phi Xhat_c[k])
 template <int D>
-__global__ void k_traj_grad(const float* __restrict__ t, const float2* __restrict__ grid, const float2* __restrict__ a,
-                            const int* __restrict__ aperm, Geom geo, const int* __restrict__ perm, float coeff,
-                            int accumulate, float* __restrict__ out) {
+__global__ void k_traj_grad(const float* __restrict__ u0t, const int* __restrict__ k0t, const float2* __restrict__ grid,
+                            const float2* __restrict__ a, const int* __restrict__ aperm, Geom geo,
+                            const int* __restrict__ perm, float coeff, int accumulate, float* __restrict__ out) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= geo.M) return;
     float w[D][KW], dw[D][KW];
     int off[D][KW];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const float td = t[(int64_t)d * geo.M + s];
-        const int k0 = (int)ceilf(td) - KW / 2;
+        const float u0 = u0t[(int64_t)d * geo.M + s];      // t - ceil(t)
+        const int k0 = k0t[(int64_t)d * geo.M + s];        // ceil(t) - W/2, wrapped
         int stride = 1;
         for (int e = d + 1; e < D; ++e) stride *= geo.g[e];
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
-            const float u = td - (float)(k0 + j);
+            const float u = u0 + (float)(KW / 2 - j);
             w[d][j] = kb_w(u, geo.beta[d]);
             dw[d][j] = kb_dw(u, geo.beta[d]);
             off[d][j] = wrapk(k0 + j, geo.g[d]) * stride;
@@ -110,8 +110,8 @@ __global__ void k_traj_grad(const float* __restrict__ t, const float2* __restric
 static kp_status traj_grad(kp_plan p, const float2* a, const int* aperm, float coeff, bool accumulate, float* out,
                            cudaStream_t st) {
     const Geom& g = p->geo;
-    if (g.D == 2) k_traj_grad<2><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_gridF, a, aperm, g, p->d_perm, coeff, accumulate, out);
-    else k_traj_grad<3><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_gridF, a, aperm, g, p->d_perm, coeff, accumulate, out);
+    if (g.D == 2) k_traj_grad<2><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_k0, p->d_gridF, a, aperm, g, p->d_perm, coeff, accumulate, out);
+    else k_traj_grad<3><<<nblk(g.M, 128), 128, 0, st>>>(p->d_t, p->d_k0, p->d_gridF, a, aperm, g, p->d_perm, coeff, accumulate, out);
     KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;

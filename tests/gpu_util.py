@@ -4,7 +4,9 @@ Inputs come from ``synth`` (shared seeded generators); expected values come only
 ``oracle`` (float64 CPU).  The CUDA path is reached through ``paper_1902_09657_gb300.api``
 (ctypes over the C ABI).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -22,10 +24,31 @@ def need_gpu():
     _build.build()
 
 
-def rel(a, b):
+MEASURED = []
+
+
+def rel(a, b, what=""):
+    """Relative l2 error ||a - b|| / ||b||; every value is kept with the test that measured it and
+    written to $KPDHG_PARITY_LOG (JSON lines) when that variable is set."""
     a = np.asarray(a, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128)
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    e = float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    MEASURED.append((test, what, e))
+    path = os.environ.get("KPDHG_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": test, "what": what, "rel_err": e}) + "\n")
+    return e
+
+
+def rounded(t):
+    """Values of a half-storage tensor [..., 2] (or complex64) as complex128 on the host: the
+    exact inputs the GPU computed with, for arithmetic parity against the oracle."""
+    if t.dtype == torch.complex64:
+        return t.cpu().numpy().astype(np.complex128)
+    f = t.float().cpu().numpy().astype(np.float64)
+    return f[..., 0] + 1j * f[..., 1]
 
 
 def random_problem(shape, C, M, seed, edge=False):

@@ -2,9 +2,9 @@
 of the SENSE pair; gradients of the unrolled l2 PDHG w.r.t. y, lambda and the trajectory),
 through the C ABI and the torch.autograd wrappers.
 
-Tolerances: 1e-4 relative l2 for y-gradients and lambda (float32 reverse sweep over ten
-iterations); 2e-3 for trajectory gradients, which sum Kaiser-Bessel derivative terms of both
-signs (cancellation amplifies float32 rounding)."""
+Tolerances: 1e-5 relative l2 for x and the y-gradients, 1e-4 for lambda and the trajectory
+gradients, which sum Kaiser-Bessel derivative terms of both signs over the window (the
+cancellation amplifies float32 rounding)."""
 import numpy as np
 import pytest
 
@@ -29,15 +29,15 @@ def test_sense_traj_gradients():
     plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
     gf = plan.sense_forward_traj_grad(to_dev(x), to_dev(gy)).cpu().numpy()
     ga = plan.sense_adjoint_traj_grad(to_dev(gy), to_dev(gx)).cpu().numpy()
-    assert rel(gf, ref_f) < 2e-3
-    assert rel(ga, ref_a) < 2e-3
+    assert rel(gf, ref_f, "forward traj grad") < 1e-4
+    assert rel(ga, ref_a, "adjoint traj grad") < 1e-4
     # through torch.autograd
     from paper_1902_09657_gb300.autograd import sense_forward, sense_adjoint
     xt = to_dev(x).requires_grad_(True)
     tt = to_dev(traj).requires_grad_(True)
     y = sense_forward(xt, tt, plan)
     (y.conj() * to_dev(gy)).real.sum().backward()
-    assert rel(tt.grad.cpu().numpy(), ref_f) < 2e-3
+    assert rel(tt.grad.cpu().numpy(), ref_f, "autograd traj grad") < 1e-4
     ref_gx = onf.nufft_adjoint(gy.astype(np.complex128), maps.astype(np.complex128), traj)
     assert rel(xt.grad.cpu().numpy(), ref_gx) < 1e-5
 
@@ -72,9 +72,9 @@ def test_unrolled_gradients_match_oracle():
     xg = unrolled_pdhg(yt, lt, tt, plan, to_dev(p.astype(np.float32)), K, Lmax)
     assert rel(xg.detach().cpu().numpy(), xK) < 1e-5
     (xg.conj() * to_dev(c)).real.sum().backward()
-    assert rel(yt.grad.cpu().numpy(), gy_ref) < 1e-4
+    assert rel(yt.grad.cpu().numpy(), gy_ref, "dL/dy") < 1e-5
     assert abs(float(lt.grad) - gl_ref) < 1e-4 * abs(gl_ref)
-    assert rel(tt.grad.cpu().numpy(), gt_ref) < 2e-3
+    assert rel(tt.grad.cpu().numpy(), gt_ref, "dL/dtraj") < 1e-4
 
 
 def test_unrolled_full_size_adjointness():

@@ -5,7 +5,7 @@ Solver parity is checked two ways: (a) the oracle's p and lambda_max are passed 
 sides, so only the iteration is compared (tolerance 1e-5 relative l2 on x after the
 workload's iteration count); (b) the GPU computes p and lambda_max itself (MC
 preconditioner, 30 power iterations from the all-ones image) and the whole chain is compared
-(tolerance 1e-4: the preconditioner's own 1e-4 bound carries through the step sizes)."""
+at the same 1e-5 after the workload's full iteration count."""
 import numpy as np
 import pytest
 
@@ -129,9 +129,10 @@ def test_cluster_prox_plans_of_different_sizes():
     assert rel(xa2, xa1) < 1e-5
 
 
-@pytest.mark.parametrize("name,alpha,iters", [("radial2d_128", 2.0, 30), ("spiral2d_256", 1.25, 8)])
+@pytest.mark.parametrize("name,alpha,iters", [("radial2d_128", 2.0, 30), ("spiral2d_256", 1.25, 100)])
 def test_pdhg_full_chain_workloads(name, alpha, iters):
-    """Whole chain on the full-size 2D workloads: GPU builds p (MC) and lambda_max itself."""
+    """Whole chain on the full-size 2D workloads with their iteration counts (30 and 100): the
+    GPU builds p (MC) and lambda_max itself; the oracle runs the same chain in float64."""
     need_gpu()
     w, x, maps, traj = workload_problem(name)
     y = simulate(w, x, maps, traj)
@@ -141,12 +142,13 @@ def test_pdhg_full_chain_workloads(name, alpha, iters):
     lam = w.lam_rel
     if w.reg == "l1_wavelet":
         lam = lam * float(np.abs(AH(y.astype(np.complex128))).max())
-    x_ref, _, _, _ = osv.pdhg(A, AH, y, p, x.shape, w.reg, lam, iters, L, levels=w.wavelet_levels)
+    x_ref, _, _, objs = osv.pdhg(A, AH, y, p, x.shape, w.reg, lam, iters, L, levels=w.wavelet_levels, trace=True)
     plan = make_plan(x.shape, maps.shape[0], traj.shape[0], alpha, w.wavelet_levels)
     plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
-    xg, _, st = plan.pdhg_solve(to_dev(y), None, w.reg, lam, iters)
-    assert abs(st["lmax"] - L) < 1e-4 * L
-    assert rel(xg.cpu().numpy(), x_ref) < 1e-4
+    xg, tr, st = plan.pdhg_solve(to_dev(y), None, w.reg, lam, iters, trace=True)
+    assert abs(st["lmax"] - L) < 1e-5 * L
+    assert rel(xg.cpu().numpy(), x_ref, f"x after {iters} iterations") < 1e-5
+    assert abs(tr[-1] - objs[-1]) < 1e-5 * abs(objs[-1])
 
 
 def test_pdhg_host_buffers_roundtrip():
@@ -201,30 +203,60 @@ def test_pdhg_3d_parity(reg, lam):
     plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
     plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
     pg = plan.make_preconditioner(True).cpu().numpy()
-    assert rel(pg, p) < 1e-4
+    assert rel(pg, p, "precond") < 1e-5
     xg, _, st = plan.pdhg_solve(to_dev(y), to_dev(p.astype(np.float32)), reg, lam, 20, lmax=L)
-    assert rel(xg.cpu().numpy(), x_ref) < 1e-5
+    assert rel(xg.cpu().numpy(), x_ref, "x") < 1e-5
 
 
-@pytest.mark.parametrize("ystore,mstore,tol", [("bf16", "fp16", 2e-3), ("fp16", "bf16", 2e-3), ("bf16", "bf16", 3e-3)])
-def test_pdhg_half_storage(ystore, mstore, tol):
-    """Mixed precision: measurements and coil maps stored in 16-bit floats, float32 arithmetic,
-    against the float64 oracle on the unrounded inputs (spec tolerance 2e-3; bf16 maps
-    and data together carry twice the rounding and get 3e-3)."""
-    need_gpu()
+def _half_case(x, maps, traj, y, ystore, mstore, iters, levels, lam_rel):
+    """GPU l1-wavelet PDHG on 16-bit stored y and maps, and the oracle on (a) the stored values
+    and (b) the unrounded inputs, each with its own preconditioner and lambda_max."""
     from paper_1902_09657_gb300.api import to_storage
+    from tests.gpu_util import rounded
+    md = to_storage(to_dev(maps), mstore)
+    yd = to_storage(to_dev(y), ystore)
+    out = {}
+    for key, m_o, y_o in (("stored", rounded(md).reshape(maps.shape), rounded(yd).reshape(y.shape)),
+                          ("unrounded", maps.astype(np.complex128), y.astype(np.complex128))):
+        A, AH = _ops(m_o, traj, 1.25)
+        p = opc.mc_precond_fast(m_o, traj, 1.25, 4)
+        L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+        lam = lam_rel * float(np.abs(AH(y_o)).max())
+        out[key] = (osv.pdhg(A, AH, y_o, p, x.shape, "l1_wavelet", lam, iters, L, levels=levels)[0], p, L, lam)
+    _, p, L, lam = out["stored"]
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=levels)
+    plan.set_trajectory(to_dev(traj)).set_maps(md)
+    xg, _, _ = plan.pdhg_solve(yd, to_dev(p.astype(np.float32)), "l1_wavelet", lam, iters, lmax=L)
+    return xg.cpu().numpy(), out["stored"][0], out["unrounded"][0]
+
+
+@pytest.mark.parametrize("ystore,mstore", [("bf16", "fp16"), ("fp16", "bf16"), ("bf16", "c64"), ("c64", "fp16"),
+                                           ("bf16", "bf16")])
+def test_pdhg_half_storage(ystore, mstore):
+    """Mixed precision (2D spiral, 30 iterations): measurements and coil maps stored in 16-bit
+    floats, float32 arithmetic.  On the stored values the GPU iterates equal the oracle's to
+    1e-5; against the oracle on the unrounded inputs the reconstruction is within 2e-3 whenever
+    at most one of the two is bf16 (bf16 maps with bf16 data carry two 8-bit roundings and are
+    held to the first check only)."""
+    need_gpu()
     w, x, maps, traj = _small_spiral()
     y = simulate(w, x, maps, traj)
-    A, AH = _ops(maps, traj, 1.25)
-    p = opc.mc_precond_fast(maps.astype(np.complex128), traj, 1.25, 4)
-    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
-    lam = 1e-3 * float(np.abs(AH(y.astype(np.complex128))).max())
-    x_ref, _, _, _ = osv.pdhg(A, AH, y, p, x.shape, "l1_wavelet", lam, 30, L, levels=3)
-    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=3)
-    plan.set_trajectory(to_dev(traj)).set_maps(to_storage(to_dev(maps), mstore))
-    xg, _, _ = plan.pdhg_solve(to_storage(to_dev(y), ystore), to_dev(p.astype(np.float32)), "l1_wavelet", lam, 30,
-                               lmax=L)
-    assert rel(xg.cpu().numpy(), x_ref) < tol
+    xg, x_st, x_unr = _half_case(x, maps, traj, y, ystore, mstore, 30, 3, 1e-3)
+    assert rel(xg, x_st, "x, stored inputs") < 1e-5
+    e = rel(xg, x_unr, "x storage error")
+    if not (ystore == "bf16" and mstore == "bf16"):
+        assert e < 2e-3
+
+
+def test_pdhg_3d_fp16_maps():
+    """The 3D workload's precision form on a small 3D case (16^3 x 3 coils): coil maps in fp16,
+    float32 arithmetic, l1-wavelet PDHG: 1e-5 on the stored maps, 2e-3 against unrounded maps."""
+    need_gpu()
+    w, x, maps, traj = _small_3d()
+    y = simulate(w, x, maps, traj)
+    xg, x_st, x_unr = _half_case(x, maps, traj, y, "c64", "fp16", 20, 2, 1e-3)
+    assert rel(xg, x_st, "x, stored maps") < 1e-5
+    assert rel(xg, x_unr, "x storage error") < 2e-3
 
 
 def test_ute3d_full_size_properties():

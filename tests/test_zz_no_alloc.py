@@ -1,4 +1,5 @@
-"""The allocation-free adjoint (kp_sense_adjoint_noalloc) against the plan-based kp_sense_adjoint.
+"""The allocation-free adjoint (kp_sense_adjoint_noalloc) against the plan-based kp_sense_adjoint
+and against the float64 oracle's adjoint.
 
 The allocation-free entry point exists for callers that reserve all device memory up front
 and cannot let a library allocate in the middle of a reconstruction.  It keeps its work space
@@ -11,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import nufft as onf
 from tests.gpu_util import need_gpu, rel, random_problem, to_dev, make_plan
 
 pytestmark = pytest.mark.gpu
@@ -55,7 +57,10 @@ def test_noalloc_adjoint_matches_plan_adjoint_twice(shape, C, M):
         x_d = torch.empty(shape, dtype=torch.complex64, device="cuda")
         assert _noalloc(prm, traj_d, maps_d, y_d, x_d) == _lib.KP_OK
         torch.cuda.synchronize()
-        assert rel(x_d.cpu().numpy(), ref) < 1e-5
+        got = x_d.cpu().numpy()
+        assert rel(got, ref, f"call {call} vs plan adjoint") < 1e-5
+        x_ref = onf.nufft_adjoint(y.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+        assert rel(got, x_ref, f"call {call} vs oracle") < 1e-5
 
 
 def test_noalloc_rejects_oversize_problem():
