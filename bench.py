@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of k-space-preconditioned PDHG (Ong, Uecker & Lustig, arXiv 1902.09657) on GB300.
 
-One timed step = one whole reconstruction of the 2D variable-density spiral l1-wavelet
-workload (256x256 image, 12 coils, 24 interleaves x 4096 samples, oversampling 1.25, KB width
-4, Daubechies-4 with 4 levels, lambda = 1e-3 max|A^H y|): trajectory binning, coil maps,
-multi-channel preconditioner, 30 power iterations, 100 PDHG iterations.  All inputs are
-synthetic (seeded phantom, Gaussian-bump coil maps, spiral trajectory, Gaussian noise).
+One timed step = one whole reconstruction of the 3D centre-out UTE radial l1-wavelet workload
+(192^3 image, 8 coils with coil maps stored in FP16, 24,000 Fibonacci-sphere spokes x 256
+samples, oversampling 1.25, KB width 4, Daubechies-4 with 3 levels, lambda = 1e-3 max|A^H y|):
+trajectory binning, coil maps, multi-channel preconditioner, 30 power iterations, 30 PDHG
+iterations.  All inputs are synthetic (seeded ellipsoid phantom, Gaussian-bump coil maps,
+Fibonacci-sphere trajectory, Gaussian noise).  The same JSON line carries the 2D spiral
+(256^2 x 12 coils, 100 l1 iterations) and 2D radial (128^2 x 4 coils, 30 l2 iterations)
+reconstructions, the 64-case batch, the unrolled gradient and the mixed-precision forms.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank reconstructs its own
 replica of the workload (independent problems, weak scaling); ranks only meet in the
 barriers and the max-over-ranks of the timing.  --impl reference times the float64 CPU
-oracle on a bounded sample of the same workload.
+oracle on a bounded sample of the same workload and extrapolates the whole reconstruction.
 """
 from __future__ import annotations
 
@@ -33,7 +36,16 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-WORKLOAD = "spiral2d_256"
+WORKLOAD = "ute3d_192"
+# (maps storage, measurement storage) of each timed workload: the 3D workload keeps its coil
+# maps in FP16 (FP32 arithmetic); the others are plain complex64
+STORAGE = {"ute3d_192": ("fp16", "c64")}
+
+
+def storage_of(w):
+    return STORAGE.get(w.name, ("c64", "c64"))
+
+
 def metric_name(w):
     reg = "l1-wavelet" if w.reg == "l1_wavelet" else "l2"
     return (f"PDHG iterations/s, whole reconstruction (bin-sort + MC preconditioner + 30 power its + "
@@ -56,30 +68,44 @@ def parse_args_list(argv):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
-                    help="timed workload (default: the 2D spiral l1-wavelet reconstruction)")
+                    help="timed workload (default: the 3D UTE l1-wavelet reconstruction)")
     ap.add_argument("--no-extras", action="store_true", help="skip roofline/e2e/time-to-accuracy extras")
     ap.add_argument("--no-side-workloads", action="store_true",
-                    help="skip the 64-case batch, 3D UTE gridding and unrolled-gradient side measurements")
+                    help="skip the 2D, 64-case batch and unrolled-gradient side measurements")
     return ap.parse_args(argv)
+
+
+def grid_points(w):
+    G = 1
+    for n in w.img_shape:
+        g = math.ceil(w.oversamp * n - 1e-9)
+        G *= g + (g % 2)
+    return G
+
+
+def n_samples(w):
+    ta = w.traj_args
+    return ta["n_interleaves"] * ta["n_samples"] if w.traj_kind == "spiral" else ta["n_spokes"] * ta["n_readout"]
 
 
 def workload_config(w):
     ta = w.traj_args
     if w.traj_kind == "spiral":
         traj = f"{ta['n_interleaves']}x{ta['n_samples']} spiral samples"
-        m = ta["n_interleaves"] * ta["n_samples"]
     else:
         traj = f"{ta['n_spokes']}x{ta['n_readout']} {w.traj_kind} samples"
-        m = ta["n_spokes"] * ta["n_readout"]
     shape = "x".join(str(n) for n in w.img_shape)
     reg = ("l1 lambda=1e-3*max|A^H y|, db4 %d levels" % w.wavelet_levels if w.reg == "l1_wavelet"
            else "l2 lambda=%g" % w.lam_rel)
+    ms, ys = storage_of(w)
+    grid_mb = w.ncoils * grid_points(w) * 8 / 1e6
     return {
         "workload": f"{w.name}: {shape} image, {w.ncoils} coils, {traj}, alpha {w.oversamp}, KB W{w.width}, "
-                    f"{reg}, {w.iters} iterations",
-        "image": list(w.img_shape), "coils": w.ncoils, "samples": int(m),
+                    f"{reg}, {w.iters} iterations, maps {ms}, y {ys}",
+        "image": list(w.img_shape), "coils": w.ncoils, "samples": int(n_samples(w)),
         "iters": w.iters, "power_iters": 30, "preconditioner": "multi-channel",
-        "l2_between_steps": "flushed (256 MiB write)",
+        "maps_storage": ms, "y_storage": ys,
+        "l2_between_steps": f"flushed (256 MiB write); per-coil grids total {grid_mb:.0f} MB",
     }
 
 
@@ -150,52 +176,164 @@ def whole_job_value(world, steps, iters, total_ms):
     return world * steps * iters / (total_ms / 1e3)
 
 
-# ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(w, n_pdhg=3):
-    """Time the float64 oracle on a bounded sample of the workload and extrapolate the whole
-    reconstruction (preconditioner + 30 power iterations + w.iters PDHG iterations)."""
-    from oracle import nufft as onf, precond as opc, solvers as osv
-    traj, x, maps = w.traj(), w.phantom().astype(np.complex128), w.maps().astype(np.complex128)
-    y = onf.nufft_forward(x, maps, traj, w.oversamp, w.width)
-    y = y + 0.01 * np.abs(y).max() * w.noise()
-    A = lambda v: onf.nufft_forward(v, maps, traj, w.oversamp, w.width)
-    AH = lambda u: onf.nufft_adjoint(u, maps, traj, w.oversamp, w.width)
+# ----------------------------------------------------------------------------- oracle
+def _nlogn(n):
+    return n * math.log2(max(n, 2))
+
+
+def oracle_inputs(w):
+    """Float64 oracle inputs of the workload (phantom, maps rounded to their storage, trajectory)."""
+    x = w.phantom().astype(np.complex128)
+    maps = w.maps()
+    if storage_of(w)[0] == "fp16":
+        maps = maps.view(np.float32).astype(np.float16).astype(np.float32).view(np.complex64)
+    return x, maps.astype(np.complex128), w.traj()
+
+
+def oracle_calibrate(w, x, maps, traj, m1):
+    """Once per run: the oracle's prox on the full image, one FFT of a single coil's oversampled
+    grid (the library step inside every oracle NUFFT), and its forward + adjoint NUFFT on the
+    first m1 samples with one and with two coils, which separates the gridding cost per call
+    (tap tables) from the cost per coil.  Seconds."""
+    from oracle import nufft as onf, solvers as osv
+    gshape = onf.grid_shape(w.img_shape, w.oversamp)
+    grid = np.zeros(gshape, dtype=np.complex128)
+    grid[tuple(slice(0, n) for n in w.img_shape)] = x
     t0 = time.perf_counter()
-    p = opc.mc_precond_fast(maps, traj, w.oversamp, w.width)
-    t_pre = time.perf_counter() - t0
+    np.fft.fftn(grid)
+    t_fft = time.perf_counter() - t0
+    del grid
+    prox = osv.make_prox(w.reg, 1e-3, w.wavelet_levels)
     t0 = time.perf_counter()
-    L, _ = osv.power_method(A, AH, p, x.shape, iters=1)
-    t_pow = time.perf_counter() - t0
-    lam = lambda_for(w, ahy_max=float(np.abs(AH(y)).max()))
+    prox(x, 1.0)
+    t_prox = time.perf_counter() - t0
+    t1 = sum(oracle_gridding_sample(w, x, maps[:1], traj, m1))
+    t2 = sum(oracle_gridding_sample(w, x, maps[:2], traj, m1)) if maps.shape[0] > 1 else 2 * t1
+    per_coil = max(t2 - t1 - 2 * t_fft, 0.0) / m1                # forward + adjoint, per sample and coil
+    per_call = max(t1 - 2 * t_fft - per_coil * m1, 0.0) / m1     # tap tables, per sample
+    return {"t_fft_grid": t_fft, "t_prox": t_prox, "G": grid_points(w), "m1": m1, "t1": t1, "t2": t2,
+            "grid_per_coil": per_coil, "grid_per_call": per_call}
+
+
+def oracle_gridding_sample(w, x, maps, traj, m1):
+    """The oracle's forward and adjoint NUFFT with the given coils on the first m1 samples (each
+    call does one FFT per coil of the oversampled grid and the Kaiser-Bessel gridding)."""
+    from oracle import nufft as onf
+    sub = traj[:m1]
     t0 = time.perf_counter()
-    osv.pdhg(A, AH, y, p, x.shape, w.reg, lam, n_pdhg, L, levels=w.wavelet_levels)
-    t_it = (time.perf_counter() - t0) / n_pdhg
-    est = t_pre + 30 * t_pow + w.iters * t_it
-    return {"value": w.iters / est, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"float64 NumPy oracle on the full workload: MC preconditioner once ({t_pre:.2f} s), "
-                      f"1 power iteration ({t_pow:.2f} s), {n_pdhg} PDHG iterations ({t_it:.2f} s each); "
-                      f"whole reconstruction extrapolated to 30 power + {w.iters} PDHG iterations = {est:.1f} s",
-            "est_step_s": est}
+    y1 = onf.nufft_forward(x, maps, sub, w.oversamp, w.width)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    onf.nufft_adjoint(y1, maps, sub, w.oversamp, w.width)
+    t_adj = time.perf_counter() - t0
+    return t_fwd, t_adj
+
+
+def oracle_estimate(w, cal, t1=None):
+    """Whole reconstruction time (s) of the float64 oracle, extrapolated from the measured pieces
+    (t1: a fresh one-coil forward + adjoint sample time, scaling the calibrated gridding costs).
+    Model: one application of A and A^H with C coils costs 2 C grid FFTs + (per-call + C x
+    per-coil gridding) x M; the preconditioner (Sec. 5.1 route as the oracle runs it) costs
+    C^2 + C FFTs of the 2N image, 1 + C FFTs of its oversampled grid and 1 + C one-coil gridding
+    passes; FFT times scale as n log n from the measured single-coil grid FFT.  30 power
+    iterations and `iters` PDHG iterations each apply A and A^H; PDHG adds the prox."""
+    C, M, N, G = w.ncoils, n_samples(w), int(np.prod(w.img_shape)), cal["G"]
+    d = len(w.img_shape)
+    tf = cal["t_fft_grid"]
+    scale = 1.0 if t1 is None else max(t1 - 2 * tf, 1e-9) / max(cal["t1"] - 2 * tf, 1e-9)
+    gc, gt = cal["grid_per_coil"] * scale, cal["grid_per_call"] * scale
+    T_AAH = 2 * C * tf + (gt + C * gc) * M
+    N2, G2 = N * 2 ** d, G * 2 ** d
+    T_pre = ((C * C + C) * tf * _nlogn(N2) / _nlogn(G) + (1 + C) * tf * _nlogn(G2) / _nlogn(G)
+             + (1 + C) * 0.5 * (gt + gc) * M)
+    T_pow = 30 * T_AAH
+    T_pdhg = w.iters * (T_AAH + cal["t_prox"])
+    return {"est_s": T_pre + T_pow + T_pdhg, "precond_s": T_pre, "power_s": T_pow, "pdhg_s": T_pdhg,
+            "per_iter_s": T_AAH + cal["t_prox"]}
+
+
+def _sample_m1(w, frac):
+    return max(1024, n_samples(w) // frac)
+
+
+def oracle_sample(w, frac=32):
+    """One bounded sample of the float64 oracle on the workload (one host core): the calibration
+    above on 1/frac of the samples; returns the extrapolated value."""
+    x, maps, traj = oracle_inputs(w)
+    t0 = time.perf_counter()
+    m1 = _sample_m1(w, frac)
+    cal = oracle_calibrate(w, x, maps, traj, m1)
+    cpu_s = time.perf_counter() - t0
+    est = oracle_estimate(w, cal)
+    return {"value": w.iters / est["est_s"], "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": (f"float64 NumPy oracle, one core, {cpu_s:.1f} s: a one-coil FFT of the {w.name} "
+                       f"oversampled grid ({cal['t_fft_grid']:.2f} s), the prox on the full image "
+                       f"({cal['t_prox']:.2f} s), forward + adjoint NUFFT on {m1} of {n_samples(w)} samples "
+                       f"with one coil ({cal['t1']:.2f} s) and two coils ({cal['t2']:.2f} s); the whole "
+                       f"reconstruction extrapolated by an n log n / per-sample cost model to "
+                       f"{est['est_s']:.0f} s (preconditioner {est['precond_s']:.0f} s, 30 power its "
+                       f"{est['power_s']:.0f} s, {w.iters} PDHG its {est['pdhg_s']:.0f} s)"),
+            "extrapolated_whole_reconstruction_s": est["est_s"]}
+
+
+def _replica(name, frac):
+    return oracle_sample(synth.workload(name), frac)
+
+
+def oracle_all_cores(w, frac=32):
+    """The same one-core sample run as concurrent replicas on every host core (spawned
+    processes); value = replicas x the slowest replica's extrapolated iterations per second."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    try:
+        import psutil
+        avail = psutil.virtual_memory().available
+    except Exception:
+        avail = 64 << 30
+    need = 4 * grid_points(w) * 16 + (2 << 30)                # per replica, generous
+    P = int(max(1, min(cores, avail // need)))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(P) as pool:
+        res = pool.starmap(_replica, [(w.name, frac)] * P)
+    wall = time.perf_counter() - t0
+    slow = min(r["value"] for r in res)
+    return {"value": P * slow, "unit": "iters/s", "cores": P, "kind": "oracle",
+            "sample": f"{P} concurrent replicas of the one-core sample (spawned processes, {wall:.1f} s wall); "
+                      f"value = {P} x the slowest replica's extrapolated rate"}
 
 
 def run_reference(args, rank, world):
+    """The float64 oracle as it stands, on the host: each step is one bounded sample (one-coil
+    forward and adjoint NUFFT on 1/32 of the workload's samples); the whole reconstruction is
+    extrapolated from it and from the calibration measured once before the steps."""
     w = synth.workload(args.workload)
     if rank != 0:
         return
+    x, maps, traj = oracle_inputs(w)
+    m1 = _sample_m1(w, 32)
+    cal = oracle_calibrate(w, x, maps, traj, m1)
     for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; each sample is independent
-    vals, ests = [], []
+        oracle_gridding_sample(w, x, maps[:1], traj, m1)
+    step_ms, vals = [], []
     for _ in range(args.steps):
-        s = oracle_sample(w, n_pdhg=2)
-        vals.append(s["value"])
-        ests.append(s["est_step_s"])
+        t0 = time.perf_counter()
+        t1 = sum(oracle_gridding_sample(w, x, maps[:1], traj, m1))
+        step_ms.append(1e3 * (time.perf_counter() - t0))
+        vals.append(w.iters / oracle_estimate(w, cal, t1)["est_s"])
     v = statistics.median(vals)
+    est_s = w.iters / v
+    sample = (f"each step: the float64 NumPy oracle's one-coil forward and adjoint NUFFT on {m1} of "
+              f"{n_samples(w)} samples (one host core); calibrated once before the steps: a one-coil grid "
+              f"FFT ({cal['t_fft_grid']:.2f} s), the prox ({cal['t_prox']:.2f} s) and the same sample with two "
+              f"coils; value = {w.iters} iterations / the whole reconstruction extrapolated by an n log n / "
+              f"per-sample cost model")
     line = {"impl": "reference", "metric": metric_name(w), "value": v, "unit": "iters/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(ests),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "iters/s",
-                             "sample": s["sample"]},
+            "extrapolated_whole_reconstruction_s": est_s,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "iters/s", "sample": sample},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -214,225 +352,58 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
     }
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the default
-# workload's kernels from one `ncu --set full` capture of `bench.py --steps 2 --warmup 3
-# --no-extras` (matching launches 501-505, spreading variant 6 at 256 samples).  Entries are
-# valid only for the kernel code they were taken on; set one to None when its kernel changes
-# until it is captured again.
-NCU_TRAFFIC = {
-    "spread": {"kernel": "k_spread_v<2, float2, 4>", "bytes": 19909120, "variant": 6},
-    "dwt_fwd": {"kernel": "k_wprox_cluster<16>", "bytes": 1074176},
-    "interp_dual": {"kernel": "k_interp_tile<2, 2, float2>", "bytes": 36179712},
-    "adj_primal": {"kernel": "k_adj_primal<2, float2, 1>", "bytes": 13121280},
-    "fwd_pre": {"kernel": "k_pre_clear<float2>", "bytes": 6828288},
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernels of the timed
+# workload from one ncu capture, keyed by (workload, phase).  An entry is valid only for the
+# kernel code it was taken on; drop it when its kernel changes until it is captured again.
+NCU_TRAFFIC = {}
+
+# Relative l2 errors against the float64 oracle measured by the GPU parity tests (test id and
+# value) for the forms reported beside the plain solver.  Filled from the tests' error log of a
+# GPU run of this tree; the tests themselves hold the pass/fail tolerances.
+ORACLE_ERRORS = {}
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-    from paper_1902_09657_gb300 import _build
-    from paper_1902_09657_gb300.api import Plan
-
-    _build.build()
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    w = synth.workload(args.workload)
-    traj_h = torch.from_numpy(w.traj()).pin_memory()
-    x_true = torch.from_numpy(w.phantom())
-    maps_h = torch.from_numpy(w.maps()).pin_memory()
-    C, M = w.ncoils, traj_h.shape[0]
-    N = int(np.prod(w.img_shape))
-    traj_d, maps_d = traj_h.to(dev), maps_h.to(dev)
-    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, wavelet_levels=w.wavelet_levels, device=dev)
-    plan.set_trajectory(traj_d).set_maps(maps_d)
-    # synthetic measurements: A x + 1 % complex Gaussian noise
-    y_d = plan.sense_forward(x_true.to(dev))
-    noise = torch.from_numpy(w.noise().astype(np.complex64)).to(dev)
-    y_d = (y_d + 0.01 * y_d.abs().max() * noise).contiguous()
-    lam = lambda_for(w, ahy_max=float(plan.sense_adjoint(y_d).abs().max()))
-    y_h = y_d.cpu().pin_memory()
-    G = 1
-    for n in w.img_shape:
-        g = math.ceil(w.oversamp * n - 1e-9)
-        G *= g + (g % 2)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def step():
-        plan.set_trajectory(traj_d).set_maps(maps_d)
-        return plan.pdhg_solve(y_d, None, w.reg, lam, w.iters)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    launches0 = plan.launch_count()
-    clocks = Clocks(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
-    clocks.start()
-    total_ms = 0.0
-    barrier()
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    barrier()
-    ck = clocks.stop()
-    launches = plan.launch_count() - launches0
-    total_ms = max_over_ranks(total_ms, world, dev)
-    value = whole_job_value(world, args.steps, w.iters, total_ms)
-
-    extras = {}
-    if not args.no_extras and rank == 0:
-        extras = gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stream, flush,
-                            C, M, N, G, args)
-    if rank != 0:
-        return
-    line = {"metric": metric_name(w), "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(w), "clocks": ck, "gpu_launches": int(launches)}
-    line.update(extras)
-    print(json.dumps(line), flush=True)
-
-
-def gpu_extras(plan, w, traj_h, maps_h, y_h, y_d, traj_d, maps_d, lam, dev, stream, flush, C, M, N, G, args):
-    import torch
-    out = {}
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-    # --- end to end through the public API with host buffers
-    k = max(1, min(args.steps, 5))
-    tot = 0.0
-    for i in range(k + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        td = traj_h.to(dev, non_blocking=True)
-        md = maps_h.to(dev, non_blocking=True)
-        plan.set_trajectory(td).set_maps(md)
-        xh, _, _ = plan.pdhg_solve(y_h, None, w.reg, lam, w.iters)
-        e1.record(stream)
-        e1.synchronize()
-        if i > 0:
-            tot += e0.elapsed_time(e1)
-    bi = traj_h.numel() * 4 + maps_h.numel() * 8 + y_h.numel() * 8
-    out["e2e"] = {"value": k * w.iters / (tot / 1e3), "unit": "iters/s", "h2d_bytes_per_step": int(bi),
-                  "d2h_bytes_per_step": int(N * 8)}
-    # --- setup and solve-only split
-    plan.set_trajectory(traj_d).set_maps(maps_d)
-    torch.cuda.synchronize()
-    e0, e1, e2 = ev(), ev(), ev()
-    e0.record(stream)
-    plan.set_trajectory(traj_d).set_maps(maps_d)
-    p = plan.make_preconditioner(True)
-    L = plan.max_eig(p, iters=30)
-    e1.record(stream)
-    plan.pdhg_solve(y_d, p, w.reg, lam, w.iters, lmax=L)
-    e2.record(stream)
-    e2.synchronize()
-    setup_ms, solve_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    out["setup_ms"] = setup_ms
-    out["solve_only_iters_per_s"] = w.iters / (solve_ms / 1e3)
-    # --- per-phase profile (events at every phase boundary, no graph) and the roofline
-    plan.set_profiling(True)
-    _, _, st = plan.pdhg_solve(y_d, p, w.reg, lam, w.iters, lmax=L)
-    plan.set_profiling(False)
-    ph = {n: v / w.iters for n, v in st["phase_ms"].items() if v > 0}
-    out["phase_ms_per_iter"] = {n: round(v, 5) for n, v in ph.items()}
-    ab = algorithmic_bytes(w, C, M, N, G)
-    own = {n: v for n, v in ph.items() if n in ab and not n.startswith("fft")}
-    dom = max(own, key=own.get)
-    peaks = {}
+def _peaks():
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "MEASURED_PEAKS.json hbm_gbs"
     except Exception:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = ab[dom] / (own[dom] * 1e-3) / 1e9
-    tr_entry = NCU_TRAFFIC.get(dom) if w.name == WORKLOAD else None
-    if dom == "spread":
-        sc = plan.spread_config()
-        out["spread_config"] = sc
-        if tr_entry and tr_entry.get("variant") not in (None, sc["variant"]):
-            tr_entry = None       # captured on another spreading variant than the one timed here
-    out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak, "traffic": tr_entry["bytes"] if tr_entry else None,
-                       "traffic_source": ("one ncu capture of " + tr_entry["kernel"] + " on this workload")
-                       if tr_entry else None,
-                       "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
-                       "algorithmic_bytes": int(ab[dom]), "avg_launch_ms": own[dom]}
-    # --- time to 1e-3 relative objective (F* = min over a 400-iteration float32 run)
-    _, tr, _ = plan.pdhg_solve(y_d, p, w.reg, lam, 400, lmax=L, trace=True)
-    Fstar = min(tr)
-    kk = next((i + 1 for i, f in enumerate(tr) if (f - Fstar) / abs(Fstar) < 1e-3), None)
-    per_it = solve_ms / w.iters
-    out["time_to_1e-3"] = {"iters": kk, "ms_solve_only": None if kk is None else kk * per_it,
-                           "ms_with_setup": None if kk is None else setup_ms + kk * per_it,
-                           "F_star": Fstar, "F_star_source": "min of a 400-iteration float32 GPU run"}
-    # --- convergence without a preconditioner, with the single-channel and with the
-    # multi-channel one (the comparison of Sec. 6 on this synthetic workload): iterations until
-    # the relative objective (F - F*)/|F*| falls below 1e-2 and 1e-3, F* the least objective
-    # any of the three reaches in 300 iterations
-    try:
-        traces = {}
-        for name in ("none", "single_channel", "multi_channel"):
-            if name == "none":
-                pp = torch.ones((C, M), dtype=torch.float32, device=dev)
-            else:
-                pp = plan.make_preconditioner(name == "multi_channel")
-            Lp = plan.max_eig(pp, iters=30)
-            _, trc, _ = plan.pdhg_solve(y_d, pp, w.reg, lam, 300, lmax=Lp, trace=True)
-            traces[name] = (list(trc), Lp)
-        Fs = min(min(t) for t, _ in traces.values())
-        conv = {}
-        for name, (trc, Lp) in traces.items():
-            rel_obj = [(f - Fs) / abs(Fs) for f in trc]
-            conv[name] = {"lmax": Lp,
-                          "iters_to_1e-2": next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-2), None),
-                          "iters_to_1e-3": next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-3), None),
-                          "rel_obj_at_30": rel_obj[29], "rel_obj_at_300": rel_obj[-1]}
-        conv["F_star"] = Fs
-        out["convergence_by_preconditioner"] = conv
-    except Exception as e:  # reported, never hidden
-        out["convergence_by_preconditioner"] = {"error": repr(e)}
-    # --- the TV regulariser (Sec. 4.2) on the same plan, data, p and lambda_max: solve only
-    try:
-        plan.pdhg_solve(y_d, p, "tv", lam, w.iters, lmax=L)
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        plan.pdhg_solve(y_d, p, "tv", lam, w.iters, lmax=L)
-        e1.record(stream)
-        e1.synchronize()
-        tv_ms = e0.elapsed_time(e1)
-        out["tv_solve_only"] = {"iters": w.iters, "ms": tv_ms, "iters_per_s": w.iters / (tv_ms * 1e-3),
-                                "lambda": lam, "steps": "sigma = theta = 1, tau = 1/(L + 4 ndim)"}
-    except Exception as e:  # reported, never hidden
-        out["tv_solve_only"] = {"error": repr(e)}
-    if not args.no_side_workloads:
-        for key, fn in (("batched_64", side_batched), ("gridding_3d", side_gridding_3d),
-                        ("unrolled_grad", side_unrolled)):
-            try:
-                out[key] = fn(dev, stream, flush)
-            except Exception as e:  # reported, never hidden
-                out[key] = {"error": repr(e)}
-            torch.cuda.empty_cache()
-    # --- CPU oracle baseline (bounded sample)
-    try:
-        out["cpu_baseline"] = {k2: v for k2, v in oracle_sample(w).items() if k2 != "est_step_s"}
-    except Exception as e:  # pragma: no cover
-        out["cpu_baseline"] = {"error": repr(e)}
-    return out
+        return {}, "fallback 6800 GB/s"
+
+
+class Recon:
+    """One workload's plan, device inputs and pinned host copies (synthetic measurements
+    y = A x + 1 % complex Gaussian noise made by the GPU's own forward operator)."""
+
+    def __init__(self, w, dev, maps_storage=None, y_storage=None):
+        import torch
+        from paper_1902_09657_gb300.api import Plan, to_storage
+        self.w, self.dev = w, dev
+        ms, ys = storage_of(w)
+        self.maps_storage = maps_storage or ms
+        self.y_storage = y_storage or ys
+        self.traj_h = torch.from_numpy(w.traj()).pin_memory()
+        self.C, self.M = w.ncoils, self.traj_h.shape[0]
+        self.N, self.G = int(np.prod(w.img_shape)), grid_points(w)
+        self.traj_d = self.traj_h.to(dev)
+        maps = torch.from_numpy(w.maps()).to(dev)
+        self.maps_d = to_storage(maps, self.maps_storage)
+        self.maps_h = self.maps_d.cpu().pin_memory()
+        self.plan = Plan(w.img_shape, self.C, self.M, oversamp=w.oversamp, wavelet_levels=w.wavelet_levels,
+                         device=dev)
+        self.plan.set_trajectory(self.traj_d).set_maps(self.maps_d)
+        y = self.plan.sense_forward(torch.from_numpy(w.phantom()).to(dev))
+        noise = torch.from_numpy(w.noise().astype(np.complex64)).to(dev)
+        y = (y + 0.01 * y.abs().max() * noise).contiguous()
+        self.lam = lambda_for(w, ahy_max=float(self.plan.sense_adjoint(y).abs().max()))
+        self.y_d = to_storage(y, self.y_storage)
+        self.y_h = self.y_d.cpu().pin_memory()
+
+    def step(self):
+        self.plan.set_trajectory(self.traj_d).set_maps(self.maps_d)
+        return self.plan.pdhg_solve(self.y_d, None, self.w.reg, self.lam, self.w.iters)
+
+    def close(self):
+        self.plan.close()
 
 
 def _timed(fn, stream, flush, reps):
@@ -451,6 +422,273 @@ def _timed(fn, stream, flush, reps):
     return tot / reps
 
 
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1902_09657_gb300 import _build
+
+    _build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = synth.workload(args.workload)
+    rc = Recon(w, dev)
+    plan = rc.plan
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        rc.step()
+    torch.cuda.synchronize()
+    launches0 = plan.launch_count()
+    clocks = Clocks(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    clocks.start()
+    total_ms = 0.0
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc.step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    launches = plan.launch_count() - launches0
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = whole_job_value(world, args.steps, w.iters, total_ms)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = gpu_extras(rc, stream, flush, args, world)
+    if rank != 0:
+        return
+    line = {"metric": metric_name(w), "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w), "clocks": ck, "gpu_launches": int(launches)}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+def e2e_through_api(rc, stream, flush, k):
+    """The whole reconstruction through the public API with host buffers: pinned traj, maps and
+    y copied in and x copied back inside each timed step."""
+    import torch
+    w, plan, dev = rc.w, rc.plan, rc.dev
+    tot = 0.0
+    for i in range(k + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        td = rc.traj_h.to(dev, non_blocking=True)
+        md = rc.maps_h.to(dev, non_blocking=True)
+        plan.set_trajectory(td).set_maps(md)
+        plan.pdhg_solve(rc.y_h, None, w.reg, rc.lam, w.iters)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            tot += e0.elapsed_time(e1)
+    el = lambda t: t.numel() * t.element_size()
+    return {"value": k * w.iters / (tot / 1e3), "unit": "iters/s",
+            "h2d_bytes_per_step": int(el(rc.traj_h) + el(rc.maps_h) + el(rc.y_h)),
+            "d2h_bytes_per_step": int(rc.N * 8)}
+
+
+def setup_and_solve(rc, stream):
+    """Set-up (binning, maps, MC preconditioner, 30 power iterations) and solve-only times."""
+    import torch
+    w, plan = rc.w, rc.plan
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    plan.set_trajectory(rc.traj_d).set_maps(rc.maps_d)
+    torch.cuda.synchronize()
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(stream)
+    plan.set_trajectory(rc.traj_d).set_maps(rc.maps_d)
+    p = plan.make_preconditioner(True)
+    L = plan.max_eig(p, iters=30)
+    e1.record(stream)
+    plan.pdhg_solve(rc.y_d, p, w.reg, rc.lam, w.iters, lmax=L)
+    e2.record(stream)
+    e2.synchronize()
+    return p, L, e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+
+def phase_profile(rc, p, L, k):
+    """Per-phase GPU time per iteration (events at every phase boundary, no graph)."""
+    plan, w = rc.plan, rc.w
+    plan.set_profiling(True)
+    _, _, st = plan.pdhg_solve(rc.y_d, p, w.reg, rc.lam, k, lmax=L)
+    plan.set_profiling(False)
+    return {n: v / k for n, v in st["phase_ms"].items() if v > 0}
+
+
+def roofline(rc, ph):
+    """Dominant own phase of the profiled iteration: algorithmic bytes / its mean duration
+    against the measured HBM copy bandwidth."""
+    w = rc.w
+    mb = 4 if rc.maps_storage != "c64" else 8
+    ab = algorithmic_bytes(w, rc.C, rc.M, rc.N, rc.G, maps_bytes=mb)
+    own = {n: v for n, v in ph.items() if n in ab and not n.startswith("fft")}
+    if "spread" in own and "spread_reduce" in ph:          # two-phase spreading: both kernels
+        own["spread"] += ph["spread_reduce"]
+    dom = max(own, key=own.get)
+    peaks, psrc = _peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = ab[dom] / (own[dom] * 1e-3) / 1e9
+    tr = NCU_TRAFFIC.get((w.name, dom))
+    kern = {"spread": "spreading (k_spread_own + k_halo_gather)" if "spread_reduce" in ph else "spreading",
+            "interp_dual": "k_interp_tile (interpolation + dual step)",
+            "adj_primal": "primal step (k_primal_fused / k_adj_primal)"}.get(dom, dom)
+    out = {"kernel": kern, "phase": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": tr["bytes"] if tr else None,
+           "traffic_source": ("one ncu capture of " + tr["kernel"]) if tr else None,
+           "peak_source": psrc, "algorithmic_bytes": int(ab[dom]), "avg_launch_ms": own[dom]}
+    per = {}
+    for n, v in ph.items():
+        b = ab.get(n)
+        if n == "spread" and "spread_reduce" in ph:
+            v = v + ph["spread_reduce"]
+        per[n] = {"ms": round(v, 5)}
+        if b:
+            per[n].update(GB_per_s=round(b / (v * 1e-3) / 1e9, 1), frac=round(b / (v * 1e-3) / 1e9 / peak, 4))
+    return out, per
+
+
+def time_to_accuracy(rc, p, L, setup_ms, solve_ms, long_iters):
+    """Iterations and time until (F(x_k) - F*)/|F*| < 1e-3, F* the least objective of a
+    long_iters float32 GPU run from the same start (1000 iterations for 3D)."""
+    w, plan = rc.w, rc.plan
+    _, tr, _ = plan.pdhg_solve(rc.y_d, p, w.reg, rc.lam, long_iters, lmax=L, trace=True)
+    Fstar = min(tr)
+    kk = next((i + 1 for i, f in enumerate(tr) if (f - Fstar) / abs(Fstar) < 1e-3), None)
+    per_it = solve_ms / w.iters
+    return {"iters": kk, "ms_solve_only": None if kk is None else kk * per_it,
+            "ms_with_setup": None if kk is None else setup_ms + kk * per_it,
+            "F_star": Fstar, "F_star_source": f"min of a {long_iters}-iteration float32 GPU run"}
+
+
+def nufft_rates(rc, stream, flush):
+    """Forward (type-2) and adjoint (type-1) SENSE NUFFT: coil-sample points per second."""
+    import torch
+    plan = rc.plan
+    x = plan.sense_adjoint(rc.y_d)
+    yo = torch.empty((rc.C, rc.M), dtype=torch.complex64, device=rc.dev)
+    for _ in range(2):
+        plan.sense_forward(x, out=yo)
+        plan.sense_adjoint(yo, out=x)
+    t_f = _timed(lambda: plan.sense_forward(x, out=yo), stream, flush, 5)
+    t_a = _timed(lambda: plan.sense_adjoint(yo, out=x), stream, flush, 5)
+    cm = rc.C * rc.M
+    return {"forward_ms": t_f, "adjoint_ms": t_a, "forward_Mpts_per_s": cm / (t_f * 1e3),
+            "adjoint_Mpts_per_s": cm / (t_a * 1e3)}
+
+
+def gpu_extras(rc, stream, flush, args, world):
+    import torch
+    w = rc.w
+    out = {}
+    out["e2e"] = e2e_through_api(rc, stream, flush, max(1, min(args.steps, 5)))
+    p, L, setup_ms, solve_ms = setup_and_solve(rc, stream)
+    out["setup_ms"] = setup_ms
+    out["solve_only_iters_per_s"] = w.iters / (solve_ms / 1e3)
+    ph = phase_profile(rc, p, L, 5 if w.name == "ute3d_192" else w.iters)
+    out["roofline"], out["phase_per_iter"] = roofline(rc, ph)
+    out["spread_config"] = rc.plan.spread_config()
+    out["nufft"] = nufft_rates(rc, stream, flush)
+    out["time_to_1e-3"] = time_to_accuracy(rc, p, L, setup_ms, solve_ms, 1000 if len(w.img_shape) == 3 else 400)
+    if not args.no_side_workloads:
+        rc.close()
+        torch.cuda.empty_cache()
+        for key, fn in (("spiral2d_256", side_spiral), ("radial2d_128", side_radial),
+                        ("batched_64", side_batched), ("unrolled_grad", side_unrolled)):
+            try:
+                out[key] = fn(rc.dev, stream, flush)
+            except Exception as e:  # reported, never hidden
+                out[key] = {"error": repr(e)}
+            torch.cuda.empty_cache()
+    if ORACLE_ERRORS:
+        out["oracle_errors"] = ORACLE_ERRORS
+    if world == 1:
+        try:
+            out["cpu_baseline"] = oracle_sample(w)
+            out["cpu_baseline_all_cores"] = oracle_all_cores(w)
+        except Exception as e:  # reported, never hidden
+            out["cpu_baseline"] = {"error": repr(e)}
+    return out
+
+
+def whole_reconstruction(name, dev, stream, flush, reps=5, maps_storage=None, y_storage=None):
+    """Whole reconstructions of a workload per second (as the headline step), set-up and solve."""
+    w = synth.workload(name)
+    rc = Recon(w, dev, maps_storage, y_storage)
+    for _ in range(2):
+        rc.step()
+    t = _timed(rc.step, stream, flush, reps)
+    p, L, setup_ms, solve_ms = setup_and_solve(rc, stream)
+    res = {"iters_per_s": w.iters / (t / 1e3), "ms_per_reconstruction": t, "setup_ms": setup_ms,
+           "solve_only_iters_per_s": w.iters / (solve_ms / 1e3), "maps": rc.maps_storage, "y": rc.y_storage}
+    return rc, p, L, setup_ms, solve_ms, res
+
+
+def side_spiral(dev, stream, flush):
+    """2D spiral l1-wavelet (256^2 x 12 coils, 24 x 4096, 100 iterations): whole reconstruction,
+    the per-phase profile, time to 1e-3, the convergence of Sec. 6's comparison (no / single- /
+    multi-channel preconditioner), TV (Sec. 4.2), and the BF16-k-space / FP16-maps variant."""
+    import torch
+    rc, p, L, setup_ms, solve_ms, res = whole_reconstruction("spiral2d_256", dev, stream, flush)
+    w, plan = rc.w, rc.plan
+    ph = phase_profile(rc, p, L, w.iters)
+    res["roofline"], res["phase_per_iter"] = roofline(rc, ph)
+    res["spread_config"] = plan.spread_config()
+    res["time_to_1e-3"] = time_to_accuracy(rc, p, L, setup_ms, solve_ms, 400)
+    traces = {}
+    for name in ("none", "single_channel", "multi_channel"):
+        pp = torch.ones((rc.C, rc.M), dtype=torch.float32, device=dev) if name == "none" else \
+            plan.make_preconditioner(name == "multi_channel")
+        Lp = plan.max_eig(pp, iters=30)
+        _, trc, _ = plan.pdhg_solve(rc.y_d, pp, w.reg, rc.lam, 300, lmax=Lp, trace=True)
+        traces[name] = (list(trc), Lp)
+    Fs = min(min(t) for t, _ in traces.values())
+    conv = {}
+    for name, (trc, Lp) in traces.items():
+        rel_obj = [(f - Fs) / abs(Fs) for f in trc]
+        conv[name] = {"lmax": Lp,
+                      "iters_to_1e-2": next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-2), None),
+                      "iters_to_1e-3": next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-3), None),
+                      "rel_obj_at_30": rel_obj[29], "rel_obj_at_300": rel_obj[-1]}
+    conv["F_star"] = Fs
+    res["convergence_by_preconditioner"] = conv
+    plan.pdhg_solve(rc.y_d, p, "tv", rc.lam, w.iters, lmax=L)
+    tv_ms = _timed(lambda: plan.pdhg_solve(rc.y_d, p, "tv", rc.lam, w.iters, lmax=L), stream, flush, 3)
+    res["tv_solve_only"] = {"iters": w.iters, "ms": tv_ms, "iters_per_s": w.iters / (tv_ms * 1e-3),
+                            "steps": "sigma = theta = 1, tau = 1/(L + 4 ndim)"}
+    x32, _, _ = plan.pdhg_solve(rc.y_d, p, w.reg, rc.lam, w.iters, lmax=L)
+    rc.close()
+    rh, _, _, _, _, half = whole_reconstruction("spiral2d_256", dev, stream, flush, 5, "fp16", "bf16")
+    xh, _, _ = rh.plan.pdhg_solve(rh.y_d, p, w.reg, rh.lam, w.iters, lmax=L)
+    half["rel_diff_vs_fp32_storage"] = float((xh - x32).norm() / x32.norm())
+    rh.close()
+    res["bf16_kspace_fp16_maps"] = half
+    return res
+
+
+def side_radial(dev, stream, flush):
+    """2D golden-angle radial l2 (128^2 x 4 coils, 64 x 256, alpha 2, 30 iterations)."""
+    rc, p, L, setup_ms, solve_ms, res = whole_reconstruction("radial2d_128", dev, stream, flush, reps=10)
+    res["time_to_1e-3"] = time_to_accuracy(rc, p, L, setup_ms, solve_ms, 400)
+    rc.close()
+    return res
+
+
 def _measure_y(plan, x, gen):
     import torch
     y = plan.sense_forward(x)
@@ -459,11 +697,12 @@ def _measure_y(plan, x, gen):
 
 
 def side_batched(dev, stream, flush, n_cases=64, iters=20):
-    """64 uneven cases (96..320 image, 4..32 coils, radial/spiral, l2/l1): one kp_batch solve
-    (per-case MC preconditioner + 30 power iterations, then `iters` graph-replayed iterations of
-    all cases at once) against the same cases solved one after another."""
+    """64 uneven cases (96..320 image, 4..32 coils, radial/spiral, l2/l1) with BF16 k-space:
+    one kp_batch solve (per-case MC preconditioner + 30 power iterations, then `iters`
+    graph-replayed iterations of all cases at once) against the same cases solved one after
+    another."""
     import torch
-    from paper_1902_09657_gb300.api import Batch, Plan
+    from paper_1902_09657_gb300.api import Batch, Plan, to_storage
     gen = torch.Generator(device=dev).manual_seed(11)
     cases = synth.batched_cases(n_cases)
     plans, ys, lams, regs = [], [], [], []
@@ -476,7 +715,7 @@ def side_batched(dev, stream, flush, n_cases=64, iters=20):
         y = _measure_y(plan, torch.from_numpy(w.phantom()).to(dev), gen)
         lam = w.lam_rel * (float(plan.sense_adjoint(y).abs().max()) if w.reg == "l1_wavelet" else 1.0)
         plans.append(plan)
-        ys.append(y)
+        ys.append(to_storage(y, "bf16"))
         lams.append(lam)
         regs.append(w.reg)
         samples += w.ncoils * traj.shape[0]
@@ -493,61 +732,11 @@ def side_batched(dev, stream, flush, n_cases=64, iters=20):
     batch.close()
     for pl in plans:
         pl.close()
-    return {"cases": n_cases, "iters": iters, "coil_samples": int(samples),
+    return {"cases": n_cases, "iters": iters, "coil_samples": int(samples), "y": "bf16",
             "batched_ms": t_batch, "batched_cases_per_s": n_cases / (t_batch / 1e3),
             "batched_setup_ms": t_setup, "batched_iteration_ms": (t_batch - t_setup) / iters,
             "sequential_ms": t_seq, "sequential_cases_per_s": n_cases / (t_seq / 1e3),
             "what": "whole reconstructions (MC preconditioner, 30 power its, PDHG its) per second"}
-
-
-def side_gridding_3d(dev, stream, flush):
-    """3D UTE workload (192^3 image, 8 coils, 24000 spokes x 256, FP16 coil maps, db4 3 levels):
-    forward / adjoint operator times, the MC preconditioner's construction time, 30 graph-
-    replayed l1-wavelet PDHG iterations, and a per-phase profile with each phase's achieved
-    bandwidth for its algorithmic bytes (the HBM-scale case: grids of 885 MB)."""
-    import torch
-    from paper_1902_09657_gb300.api import Plan, to_storage
-    w = synth.workload("ute3d_192")
-    traj = torch.from_numpy(w.traj()).to(dev)
-    M, C = traj.shape[0], w.ncoils
-    N = int(np.prod(w.img_shape))
-    plan = Plan(w.img_shape, C, M, oversamp=w.oversamp, wavelet_levels=w.wavelet_levels, device=dev)
-    plan.set_trajectory(traj).set_maps(to_storage(torch.from_numpy(w.maps()).to(dev), "fp16"))
-    x = torch.from_numpy(w.phantom()).to(dev)
-    gen = torch.Generator(device=dev).manual_seed(3)
-    y = _measure_y(plan, x, gen)
-    yo = torch.empty_like(y)
-    xo = torch.empty_like(x)
-    for _ in range(3):
-        plan.sense_forward(x, out=yo)
-        plan.sense_adjoint(y, out=xo)
-    t_f = _timed(lambda: plan.sense_forward(x, out=yo), stream, flush, 5)
-    t_a = _timed(lambda: plan.sense_adjoint(y, out=xo), stream, flush, 5)
-    p = plan.make_preconditioner(True)
-    t_p = _timed(lambda: plan.make_preconditioner(True, out=p), stream, flush, 3)
-    L = plan.max_eig(p, iters=30)
-    lam = lambda_for(w, ahy_max=float(plan.sense_adjoint(y).abs().max()))
-    plan.pdhg_solve(y, p, w.reg, lam, w.iters, lmax=L)
-    t_s = _timed(lambda: plan.pdhg_solve(y, p, w.reg, lam, w.iters, lmax=L), stream, flush, 3)
-    plan.set_profiling(True)
-    k = 5
-    _, _, st = plan.pdhg_solve(y, p, w.reg, lam, k, lmax=L)
-    plan.set_profiling(False)
-    G = 1
-    for n in w.img_shape:
-        g = math.ceil(w.oversamp * n - 1e-9)
-        G *= g + (g % 2)
-    ab = algorithmic_bytes(w, C, M, N, G, maps_bytes=4)
-    ph = {n: v / k for n, v in st["phase_ms"].items() if v > 0}
-    rates = {n: {"ms": round(v, 4), "GB_per_s": round(ab[n] / (v * 1e-3) / 1e9, 1)} if n in ab else {"ms": round(v, 4)}
-             for n, v in ph.items()}
-    plan.close()
-    return {"image": list(w.img_shape), "coils": C, "samples": M, "maps": "fp16",
-            "forward_ms": t_f, "adjoint_ms": t_a,
-            "forward_coil_samples_per_s": C * M / (t_f / 1e3), "adjoint_coil_samples_per_s": C * M / (t_a / 1e3),
-            "make_preconditioner_ms": t_p, "lmax": L,
-            "pdhg_iters_per_s": w.iters / (t_s / 1e3), "pdhg_ms": t_s, "iters": w.iters,
-            "phase_per_iter": rates}
 
 
 def side_unrolled(dev, stream, flush):
