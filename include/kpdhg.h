@@ -165,10 +165,40 @@ kp_status kp_max_eig(kp_plan plan, const float* p_dev, const void* v0_dev, int i
  * with sigma = 1, theta = 1 and tau = 1/(lmax + 4 ndim) at every iteration, v_0 = 0.
  * The iteration is replayed from a CUDA graph captured once per plan and regulariser.
  * Synchronous.  Errors: KP_EINVAL (iters < 0, lambda < 0, wavelet levels 0 for l1,
- * non-positive p or lmax found on the device), KP_ENONFINITE, KP_EDIVERGED. */
+ * non-positive p or lmax found on the device), KP_ENONFINITE (the returned x holds a NaN or
+ * Inf, checked on the device after every solve, or a non-finite objective in the trace),
+ * KP_EDIVERGED (traced objective above 1e3 x its first value), KP_ETIMEOUT (a bounded device
+ * wait gave up: see kp_plan_set_wait_limit). */
 kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev,
                         kp_reg reg, float lambda, int iters, double lmax, void* x_dev,
                         double* obj_trace, kp_stats* stats, void* stream);
+
+/* State of a PDHG run (Sec. 4.1) between iterations, for checkpoints and warm starts: the
+ * iterates x_k, xbar_k and the dual variable u_k, and the number k of iterations already taken
+ * (the step sizes sigma_k, tau_k, theta_k follow from k, lambda_max and min p).  All pointers
+ * are device buffers owned by the caller: x and xbar complex64 [N]; u complex64 [C][M] in the
+ * trajectory's sample order; v complex64 [ndim][N], the dual variable of Sec. 4.2, used with
+ * KP_REG_TV only (NULL otherwise). */
+typedef struct {
+    void* x;
+    void* xbar;
+    void* u;
+    void* v;
+    int k;
+} kp_pdhg_state;
+
+/* kp_pdhg_solve with a state in and out.  start: NULL runs from x_0 = xbar_0 = 0, u_0 = 0
+ * (v_0 = 0), k = 0 like kp_pdhg_solve; otherwise the run continues from that state, so
+ * `a` iterations followed by `b` iterations resumed from the returned state equal a + b
+ * iterations in one call (same y, p, lambda and lambda_max; pass the lambda_max the first call
+ * used, found in kp_stats.lmax).  end: receives the state after the last iteration; end->x is
+ * required (the reconstruction), the other pointers may be NULL (not written); end->k is set.
+ * start and end may point at the same buffers.  Synchronous.  Errors as kp_pdhg_solve, and
+ * KP_EINVAL for start->k < 0, a NULL start->x, start->xbar or start->u, or a NULL start->v with
+ * KP_REG_TV. */
+kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg,
+                           float lambda, int iters, double lmax, const kp_pdhg_state* start, kp_pdhg_state* end,
+                           double* obj_trace, kp_stats* stats, void* stream);
 
 /* l2-regularised reconstruction through the dual (appendix on the connection to Trzasko
  * et al.): (A A^H + lambda I) w = lambda y by `iters` conjugate-gradient iterations with the
@@ -220,6 +250,20 @@ kp_status kp_wavelet(kp_plan plan, const void* in_dev, void* out_dev, int forwar
  * directly (no CUDA graph), records a CUDA event at every phase boundary on the caller's
  * stream, and returns the per-phase GPU time in kp_stats.phase_ms. */
 kp_status kp_plan_set_profiling(kp_plan plan, int enable);
+
+/* Limit, in SM clock cycles, of every bounded wait inside this plan's kernels (the bulk-copy
+ * staging of the interpolation, the grid barriers of the persistent primal kernel); the default
+ * 2e9 is about a second.  A wait that reaches it gives up: the kernel records the timeout,
+ * still lets its own copies in flight land (waiting up to the default limit for them), and
+ * finishes; results of that launch are then invalid and the next synchronous call on the plan
+ * (kp_pdhg_solve, kp_plan_sync, ...) returns KP_ETIMEOUT.  cycles >= 0.  Captured iteration
+ * graphs are dropped (they hold the limit). */
+kp_status kp_plan_set_wait_limit(kp_plan plan, long long cycles);
+
+/* Waits for the stream and reports device-side conditions recorded by the plan's asynchronous
+ * calls since the last check (kp_sense_forward, kp_sense_adjoint, kp_wavelet): KP_ETIMEOUT if a
+ * bounded wait gave up.  The recorded condition is cleared.  Synchronous. */
+kp_status kp_plan_sync(kp_plan plan, void* stream);
 
 /* Number of this library's own kernel launches issued through this plan so far (kernels
  * inside replayed CUDA graphs included; cuFFT's kernels not included). */

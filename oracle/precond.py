@@ -18,9 +18,22 @@ Sec. 5 and App. A: p = argmin_p ||diag(p) A A^H - I||_F^2, solved row by row as
 Parity: pinned by tests/test_oracle_precond.py (dense brute force, the Dirichlet closed
 form, p = 1 for Cartesian sampling, SC == MC with C = 1 and s = 1, the triangle
 autocorrelation of an all-ones image, the argmin property, and fast vs brute force).
+
+l2-optimised circulant preconditioner (App. B, the comparison system of Sec. 6):
+P = argmin over circulant P of ||A^H A - P||_F^2, P[m, n] = c[(m - n) mod N] (modulo per axis),
+solved diagonal by diagonal: c[k] = 1/N sum over the pairs (m, n) with (m - n) mod N = k of
+(A^H A)[m, n].  With r[k] = N^{-1/2} sum_c sum_{m - n = k} s_c^*[m] s_c[n] and the point-spread
+function h of Sec. 5.1, every pair with m - n = d contributes r[d] h[d] / N in total, so
+c[k] = 1/N sum over the lags d = k - s N (s in {0, 1} per axis) of r[d] h[d].  Reading: the
+appendix prints c[k] = r[k] h[k] + r[k - N] h[k - N] without the 1/N that its own averaging over
+the N entries of a circulant diagonal produces; the argmin is used here (a uniform scale, which
+preconditioned CG does not see).  Pinned by tests/test_oracle_circulant.py (the dense argmin,
+its normal equations, the identity for fully sampled Cartesian k-space with one unit coil,
+Hermitian symmetry, and PCG reaching the CG optimum).
 """
 from __future__ import annotations
 
+import itertools
 import math
 
 import numpy as np
@@ -30,7 +43,8 @@ from . import nufft as nf
 __all__ = [
     "precond_bruteforce", "sc_precond_dirichlet", "mc_precond_direct",
     "autocorrelation_sum", "psf_h", "mc_precond_fast", "sc_precond_fast",
-    "precond_objective",
+    "precond_objective", "circulant_kernel_bruteforce", "coil_autocorrelation", "circulant_kernel",
+    "circulant_eigenvalues", "circulant_objective",
 ]
 
 
@@ -153,3 +167,69 @@ def mc_precond_fast(maps, traj, oversamp=1.25, W=4, exact=False):
 def sc_precond_fast(traj, img_shape, oversamp=1.25, W=4, exact=False):
     """Single-channel preconditioner: the fast route with C = 1 and s = 1 (Fig. 2 caption). [M]."""
     return mc_precond_fast(_ones_maps(img_shape), traj, oversamp, W, exact=exact)[0]
+
+
+def _lag_index(img_shape):
+    """Flat image index -> multi-index, for the brute-force diagonal sums."""
+    return np.stack(np.unravel_index(np.arange(int(np.prod(img_shape))), img_shape), axis=-1)
+
+
+def circulant_kernel_bruteforce(A, img_shape):
+    """App. B argmin from a dense A: c[k] = 1/N sum over (m, n) with (m - n) mod N = k (per axis)
+    of (A^H A)[m, n].  Returned with index k_d in [0, N_d) (array position k)."""
+    H = A.conj().T @ A
+    N = int(np.prod(img_shape))
+    idx = _lag_index(img_shape)
+    c = np.zeros(img_shape, dtype=np.complex128)
+    lag = np.mod(idx[:, None, :] - idx[None, :, :], np.array(img_shape))
+    np.add.at(c, tuple(lag[..., d].ravel() for d in range(len(img_shape))), H.ravel())
+    return c / N
+
+
+def circulant_objective(c, A, img_shape):
+    """||A^H A - P||_F^2 for the circulant P[m, n] = c[(m - n) mod N]."""
+    H = A.conj().T @ A
+    idx = _lag_index(img_shape)
+    lag = np.mod(idx[:, None, :] - idx[None, :, :], np.array(img_shape))
+    P = c[tuple(lag[..., d] for d in range(len(img_shape)))]
+    return float(np.sum(np.abs(H - P) ** 2))
+
+
+def coil_autocorrelation(maps):
+    """r[k] = N^{-1/2} sum_c sum_{m - n = k} s_c^*[m] s_c[n] for lags k_d in [-N_d, N_d), by FFT on
+    the zero-padded 2N grid; returned centred (array position k_d + N_d holds lag k_d)."""
+    img_shape = maps.shape[1:]
+    d = len(img_shape)
+    N = int(np.prod(img_shape))
+    big = tuple(2 * n for n in img_shape)
+    R = np.zeros(big)
+    for c in range(maps.shape[0]):
+        q = np.zeros(big, dtype=np.complex128)
+        q[tuple(slice(0, n) for n in img_shape)] = maps[c]
+        R += np.abs(np.fft.fftn(q)) ** 2
+    # IFFT of |S|^2 is sum_n s[n + k] s^*[n]; the conjugate-mirrored lag gives sum_n s^*[n + k] s[n]
+    rho = np.fft.ifftn(R)
+    r = np.conj(rho)
+    return np.fft.fftshift(r) / math.sqrt(N)
+
+
+def circulant_kernel(maps, traj, oversamp=1.25, W=4, exact=False):
+    """App. B through r and h: c[k] = 1/N sum over s in {0, 1}^d of r[k - s N] h[k - s N], k_d in
+    [0, N_d); h as in Sec. 5.1 (exact=True: the direct sum; else the type-1 NUFFT of ones)."""
+    img_shape = maps.shape[1:]
+    N = int(np.prod(img_shape))
+    r = coil_autocorrelation(maps.astype(np.complex128))
+    h = psf_h(traj, img_shape, oversamp, W, exact=exact)
+    rh = r * h                                        # centred: position k + N_d holds lag k
+    c = np.zeros(img_shape, dtype=np.complex128)
+    for shift in itertools.product((0, 1), repeat=len(img_shape)):
+        # lag k - s N for k in [0, N): position k - s N + N = k + (1 - s) N
+        sl = tuple(slice((1 - s) * n, (1 - s) * n + n) for s, n in zip(shift, img_shape))
+        c += rh[sl]
+    return c / N
+
+
+def circulant_eigenvalues(c):
+    """Eigenvalues of the (multi-level) circulant P[m, n] = c[(m - n) mod N]: the DFT of c, real
+    for the Hermitian P that A^H A gives."""
+    return np.fft.fftn(c)

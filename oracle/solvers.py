@@ -50,7 +50,8 @@ import numpy as np
 
 from . import wavelet as wv
 
-__all__ = ["power_method", "pdhg_schedule", "objective", "pdhg", "cg_l2", "fista_l1",
+__all__ = ["power_method", "pdhg_schedule", "objective", "pdhg", "cg_l2", "pcg_l2_circulant", "fista",
+           "fista_l1",
            "prox_l2", "make_prox", "grad_fd", "grad_fd_adjoint", "proj_linf_ball", "tv_norm",
            "objective_tv", "pdhg_tv", "dual_l2_pcg"]
 
@@ -147,6 +148,53 @@ def cg_l2(A, AH, y, lam, x_shape, iters=500, tol=1e-13):
         d = r + (rr_new / rr) * d
         rr = rr_new
     return x
+
+
+def pcg_l2_circulant(A, AH, y, lam, x_shape, eigs, iters, trace=False):
+    """Conjugate gradients on (A^H A + lam I) x = A^H y preconditioned by M = P + lam I, P the
+    App. B circulant with eigenvalues `eigs` (M^{-1} v = IDFT((DFT v) / (eigs + lam))), from x = 0.
+    eigs=None runs plain CG.  Returns (x, objective trace F(x_k) after each iteration or None)."""
+    b = AH(np.asarray(y, dtype=np.complex128))
+    minv = (lambda v: v) if eigs is None else (lambda v: np.fft.ifftn(np.fft.fftn(v) / (np.real(eigs) + lam)))
+    x = np.zeros(x_shape, dtype=np.complex128)
+    r = b.copy()
+    z = minv(r)
+    d = z.copy()
+    rz = float(np.vdot(r, z).real)
+    objs = [] if trace else None
+    for _ in range(iters):
+        q = AH(A(d)) + lam * d
+        a = rz / float(np.vdot(d, q).real)
+        x = x + a * d
+        r = r - a * q
+        z = minv(r)
+        rz_new = float(np.vdot(r, z).real)
+        d = z + (rz_new / rz) * d
+        rz = rz_new
+        if trace:
+            objs.append(objective(A, x, y, "l2", lam))
+    return x, objs
+
+
+def fista(A, AH, y, reg, lam, x_shape, L, iters, levels=0, trace=False):
+    """FISTA (Beck & Teboulle) on 1/2 ||A x - y||^2 + g(x) with step 1/L, L >= lambda_max(A^H A):
+    x_{k+1} = prox_{g/L}(z_k - A^H (A z_k - y) / L), t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,
+    z_{k+1} = x_{k+1} + (t_k - 1)/t_{k+1} (x_{k+1} - x_k), x_0 = z_0 = 0, t_0 = 1.
+    Returns (x, objective trace or None)."""
+    prox = make_prox(reg, lam, levels)
+    y = np.asarray(y, dtype=np.complex128)
+    x = np.zeros(x_shape, dtype=np.complex128)
+    z = x.copy()
+    t = 1.0
+    objs = [] if trace else None
+    for _ in range(iters):
+        x_new = prox(z - AH(A(z) - y) / L, 1.0 / L)
+        t_new = (1 + math.sqrt(1 + 4 * t * t)) / 2
+        z = x_new + ((t - 1) / t_new) * (x_new - x)
+        x, t = x_new, t_new
+        if trace:
+            objs.append(objective(A, x, y, reg, lam, levels))
+    return x, objs
 
 
 def fista_l1(A, AH, y, lam, x_shape, levels, iters=2000, L=None):

@@ -36,6 +36,16 @@ class KpStats(ctypes.Structure):
     ]
 
 
+class KpState(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_void_p),
+        ("xbar", ctypes.c_void_p),
+        ("u", ctypes.c_void_p),
+        ("v", ctypes.c_void_p),
+        ("k", ctypes.c_int),
+    ]
+
+
 PHASES = ["fwd_pre", "fft_fwd", "interp_dual", "spread", "spread_reduce", "fft_inv", "adj_primal",
           "dwt_fwd", "soft", "dwt_inv", "extrap", "counter"]
 
@@ -55,6 +65,11 @@ _SIGS = {
     "kp_pdhg_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                      ctypes.c_double, _vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(KpStats), _vp]),
+    "kp_pdhg_solve_ex": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(KpState), ctypes.POINTER(KpState),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(KpStats), _vp]),
+    "kp_plan_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "kp_plan_sync": (ctypes.c_int, [_vp, _vp]),
     "kp_wavelet": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "kp_plan_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "kp_plan_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),

@@ -103,6 +103,7 @@ class Plan:
         if t.dtype != torch.float32 or tuple(t.shape) != (self.nsamples, self.ndim):
             raise ValueError("traj must be float32 [M, ndim]")
         L.check(self.lib.kp_plan_set_trajectory(self._h, _ptr(t), _stream(self.device)), "kp_plan_set_trajectory")
+        self.trajectory = t.detach().clone()
         return self
 
     def set_maps(self, maps):
@@ -198,7 +199,9 @@ class Plan:
         return out
 
     def unrolled_forward(self, y, p=None, lam=0.0, iters=10, lmax=0.0):
-        """Unrolled l2 PDHG keeping per-iteration checkpoints; returns x_K."""
+        """Unrolled l2 PDHG keeping per-iteration checkpoints; returns x_K.  The checkpoints of
+        an earlier call are replaced (tape_id counts the calls)."""
+        self.tape_id = getattr(self, "tape_id", 0) + 1
         x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
         p = self._dev(p, "p") if p is not None else None
         y = self._dev(y, "y")
@@ -241,10 +244,13 @@ class Plan:
                                           int(iters), _ptr(x), tr, _stream(self.device)), "kp_dual_l2_solve")
         return x, list(tr)
 
-    def pdhg_solve(self, y, p=None, reg="l2", lam=0.0, iters=30, lmax=0.0, trace=False, out=None):
+    def pdhg_solve(self, y, p=None, reg="l2", lam=0.0, iters=30, lmax=0.0, trace=False, out=None, state=None,
+                   return_state=False):
         """Preconditioned PDHG; reg is "l2", "l1_wavelet" (Sec. 4.1) or "tv" (Sec. 4.2).  y may
-        live on the host (it is then copied in, and x copied back to the host).  Returns
-        (x, objective trace or None, stats dict)."""
+        live on the host (it is then copied in, and x copied back to the host).  state: None to
+        start from zero, or a dict (x, xbar, u, v, k) returned by an earlier call with
+        return_state=True, to continue that run (kp_pdhg_solve_ex).  Returns (x, objective trace
+        or None, stats dict), plus the state dict after the last iteration when return_state."""
         host = not y.is_cuda
         yd = y.to(self.device, non_blocking=True) if host else y
         yd = self._dev(yd, "y")
@@ -255,16 +261,45 @@ class Plan:
         x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device) if out is None or host else out
         tr = (ctypes.c_double * max(int(iters), 1))() if trace else None
         st = L.KpStats()
-        status = self.lib.kp_pdhg_solve(self._h, _ptr(yd), _ctype_of(yd), _ptr(pd) if pd is not None else None,
-                                        _REG[reg], float(lam), int(iters), float(lmax), _ptr(x),
-                                        tr, ctypes.byref(st), _stream(self.device))
-        L.check(status, "kp_pdhg_solve")
+        start = None
+        if state is not None:
+            sx, sxb, su = (self._dev(state[k], k) for k in ("x", "xbar", "u"))
+            sv = self._dev(state["v"], "v") if state.get("v") is not None else None
+            start = L.KpState(sx.data_ptr(), sxb.data_ptr(), su.data_ptr(), sv.data_ptr() if sv is not None else None,
+                              int(state["k"]))
+        new_state = None
+        if return_state:
+            new_state = {"x": x, "xbar": torch.empty_like(x),
+                         "u": torch.empty((self.ncoils, self.nsamples), dtype=torch.complex64, device=self.device),
+                         "v": torch.empty((self.ndim,) + self.img_shape, dtype=torch.complex64, device=self.device)
+                         if reg == "tv" else None}
+        end = L.KpState(x.data_ptr(), new_state["xbar"].data_ptr() if new_state else None,
+                        new_state["u"].data_ptr() if new_state else None,
+                        new_state["v"].data_ptr() if new_state and new_state["v"] is not None else None, 0)
+        status = self.lib.kp_pdhg_solve_ex(self._h, _ptr(yd), _ctype_of(yd), _ptr(pd) if pd is not None else None,
+                                           _REG[reg], float(lam), int(iters), float(lmax),
+                                           ctypes.byref(start) if start is not None else None, ctypes.byref(end),
+                                           tr, ctypes.byref(st), _stream(self.device))
+        L.check(status, "kp_pdhg_solve_ex")
         if host:
             x = x.to("cpu")
         stats = dict(iters=st.iters, lmax=st.lmax, pmin=st.pmin, sigma_last=st.sigma_last,
                      tau_last=st.tau_last, final_obj=st.final_obj,
                      phase_ms={n: st.phase_ms[i] for i, n in enumerate(L.PHASES)})
-        return x, (list(tr)[: int(iters)] if trace else None), stats
+        out_t = (x, (list(tr)[: int(iters)] if trace else None), stats)
+        if return_state:
+            new_state["k"] = end.k
+            return out_t + (new_state,)
+        return out_t
+
+    def set_wait_limit(self, cycles):
+        """Limit (SM clock cycles) of every bounded device wait of this plan's kernels."""
+        L.check(self.lib.kp_plan_set_wait_limit(self._h, int(cycles)), "kp_plan_set_wait_limit")
+        return self
+
+    def sync(self):
+        """Wait for the plan's stream work and report recorded device-side timeouts."""
+        L.check(self.lib.kp_plan_sync(self._h, _stream(self.device)), "kp_plan_sync")
 
 
 class Batch:

@@ -207,6 +207,21 @@ __device__ __forceinline__ void pre_pixel(float2* __restrict__ grid, const MT* _
 // ---------------------------------------------------------------- plan
 struct PrePlan;   // preconditioner workspace (kp_precond.cu)
 
+// Device status words of a plan (d_flag[i]).
+enum {
+    KP_FLAG_TRAJ_BAD = 0,      // trajectory coordinates outside [-N/2, N/2] or not finite (count)
+    KP_FLAG_MAX_TILE = 1,      // most own samples of a tile
+    KP_FLAG_MAX_EXT = 2,       // longest spreading list of a tile
+    KP_FLAG_TIMEOUT = 3,       // a bounded device wait gave up (bulk-copy staging or a grid barrier)
+    KP_FLAG_PMIN = 4,          // min p as float bits
+    KP_FLAG_P_BAD = 5,         // preconditioner entries not positive and finite (count)
+    KP_FLAG_SCHED_BAD = 6,     // lambda_max or min p not positive and finite
+    KP_FLAG_PRE_BAD = 7,       // non-positive preconditioner denominators (count)
+    KP_FLAG_NONFINITE = 8,     // a solve's result holds a NaN or Inf
+    KP_NFLAGS = 16
+};
+constexpr long long KP_DRAIN_CYCLES = 2000000000LL;   // wait for copies still in flight after a timeout
+
 // Phases of one PDHG iteration, for event-based profiling (kp_plan_set_profiling).
 enum Phase { PH_FWD_PRE = 0, PH_FFT_FWD, PH_INTERP, PH_SPREAD, PH_SPREAD_RED, PH_FFT_INV, PH_ADJ, PH_DWT_FWD,
              PH_SOFT, PH_DWT_INV, PH_EXTRAP, PH_OTHER, PH_N };
@@ -235,12 +250,18 @@ struct kp_plan_s {
     // trajectory (sorted by tile)
     float* d_t = nullptr;            // [D][M] offsets u0 = t - ceil(t) of the grid coordinates t = f g/n, sorted order
     int* d_perm = nullptr;           // sorted position -> original sample index
-    int* d_key = nullptr;            // [M] tile key per original sample (scratch)
+    int* d_key = nullptr;            // [M] cell key per original sample (scratch)
+    int* d_ccnt = nullptr;           // [ncells + 1] samples per first-tap cell (then fill counters)
+    int* d_coff = nullptr;           // [ncells + 1] exclusive scan of d_ccnt: first sorted position per cell
+    int* d_scan_part = nullptr;      // [ncells / SCAN_B + 2] block sums of the multi-block scan
+    int* d_scan_poff = nullptr;      // [ncells / SCAN_B + 2] their exclusive scan
+    int64_t ncells = 0;              // ntiles x cells_per_tile
+    int cells_per_tile = 0;          // prod ts_d
     int* d_cnt = nullptr;            // [ntiles + 1]
     int* d_off = nullptr;            // [ntiles + 1] exclusive scan of tile counts
     int* d_ext_off = nullptr;        // [ntiles + 1] spreading lists: offsets
     int* d_ext = nullptr;            // [M * 2^D] spreading lists: sorted sample positions
-    int* d_flag = nullptr;           // [4] device status words
+    int* d_flag = nullptr;           // [16] device status words (KP_FLAG_* below)
     int64_t max_tile = 0;
     // spreading work items: {tile, begin, end, partial slot or -1}
     int4* d_items = nullptr;
@@ -331,6 +352,7 @@ struct kp_plan_s {
     kp::PrePlan* pre = nullptr;
     kp_plan_s* pre_nufft = nullptr;  // NUFFT plan on the 2N image (preconditioner)
     cudaStream_t cap_stream = nullptr;
+    long long wait_cycles = 2000000000LL;   // limit of every bounded device wait (SM clock cycles)
 };
 
 namespace kp {
@@ -377,7 +399,7 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
 bool cluster_prox_ok(kp_plan p);
 kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st);
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st, int reg = 0);
+                      cudaStream_t st, int reg = 0, const kp_pdhg_state* start = nullptr);
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st);

@@ -180,6 +180,7 @@ struct InterpIO {
     const int* iter;
     int* flag;           // set to 1 if the staging wait gave up (reported as KP_ETIMEOUT)
     const double* n2;    // mode 1: when set, the output is also divided by sqrt(*n2)
+    long long wait;      // limit of the staging wait (SM clock cycles)
 };
 
 // Staged region geometry: R points per axis for the largest tile edge (16 in 2D, 8 in 3D);
@@ -212,11 +213,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// Waits for phase `parity` of the barrier for about one second at most; false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.test_wait.parity.shared.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of the barrier for at most `limit` SM clock cycles; false if it gave
+// up.  A limit of 0 does not wait at all: a phase not yet complete gives up at once.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, long long limit) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if (limit <= 0) return false;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -308,9 +318,9 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
             }
         }
     }
-    if (!mbar_wait_bounded(&bar, 0)) {
+    if (!mbar_wait_bounded(&bar, 0, io.wait)) {
         if (io.flag) atomicExch(io.flag, 1);
-        mbar_wait_bounded(&bar, 0);      // copies still in flight land in this CTA's memory
+        mbar_wait_bounded(&bar, 0, KP_DRAIN_CYCLES);      // copies still in flight land in this CTA's memory
         return;
     }
     if (!act) return;
@@ -880,46 +890,45 @@ k_spread_z(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* 
 }
 
 // Two-phase 3D spreading (variants 10, 11).  Phase A: one CTA per own-sample item (samples
-// whose first tap lies in the tile, contiguous in sorted order) accumulates every tap of each
-// sample once into a padded tile of (8 + W - 1)^3 points in shared memory (no tap falls
-// outside it, so every lane works), warp w owning the padded z-planes congruent to w mod 8 (a
-// sample's four consecutive z taps meet each residue at most once), and writes the padded
-// tile to its slot.  Phase B: every grid point gathers its tile's slots and, for points within
-// W - 1 of a tile's low edge, the high-side halos of the lower neighbours' slots (periodic),
-// and stores the sum: no atomics, no clearing, and the sum order is fixed.
+// whose first tap lies in the tile, contiguous in sorted order, which within a tile is ordered
+// by that first tap) accumulates every tap of each sample once into a padded tile of
+// (8 + W - 1)^3 points in shared memory (no tap falls outside it) and writes the padded tile
+// to its slot.  The CTA has 2 NP warps for NP coil pairs: warp w owns coil pair w mod NP and the
+// padded z-planes of parity w / NP, so for each sample every warp updates its two planes x
+// 16 (y, x) taps of its pair, one tap per lane, and no two warps ever write the same word.
+// Consecutive samples with the same first tap have the same footprint: a lane sums their
+// contributions in registers and updates shared memory once per run.  Phase B: one CTA per tile
+// stores every grid point as the sum of its tile's slots and, for points within W - 1 of a low
+// face, of the lower neighbours' halos (periodic): no atomics, no clearing, fixed sum order.
 constexpr int PT = 8 + KW - 1;                 // padded tile edge
 constexpr int PT3 = PT * PT * PT;
+constexpr int OT_RS = 12;                      // float4 per padded row: x padded to 12 so that a quarter-warp's
+constexpr int OT_PS = PT * OT_RS;              // lanes (4 consecutive x, 2 rows) hit 8 different bank groups
+constexpr int OT_PAIR = PT * OT_PS;            // float4 per coil pair
+constexpr int OT_CHUNK = 128;                  // samples staged at a time
 
-template <int CG> struct SpO {
-    static constexpr int NP = CG / 2;
-    static constexpr int COPY = PT3 * NP;
-    __device__ static int idx(int z, int y, int x, int k) {
-        const int slot = CG == 8 ? (k ^ ((x >> 1) & 1)) : k;
-        return ((z * PT + y) * PT + x) * NP + slot;
-    }
-};
-
-template <int CG>
+template <int NP>
 static size_t spread_own_smem() {
-    return (size_t)SpO<CG>::COPY * sizeof(float4) + (size_t)SP_CHUNK * (CG * sizeof(float2) + 3 * KW * sizeof(float) + sizeof(int));
+    return (size_t)NP * OT_PAIR * sizeof(float4) +
+           (size_t)OT_CHUNK * (NP * sizeof(float4) + (KW + KW * KW) * sizeof(float) + sizeof(int));
 }
 
-template <typename UT, int CG>
-__global__ void __launch_bounds__(256)
+template <typename UT, int NP>
+__global__ void __launch_bounds__(NP * 64)
 k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
              const int* __restrict__ perm, const int4* __restrict__ items, Geom geo, Tiles tl,
              float2* __restrict__ halo) {
-    constexpr int D = 3, NP = CG / 2;
-    using LO = SpO<CG>;
+    constexpr int D = 3, NT = NP * 64;
     extern __shared__ __align__(16) float4 smo[];
-    float4* acc = smo;                                              // [PT][PT][PT][NP]
-    float4* su4 = acc + LO::COPY;                                   // [SP_CHUNK][NP]
-    float* sw = (float*)(su4 + SP_CHUNK * NP);                      // [SP_CHUNK][3][KW]
-    unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK] local first taps, one byte per axis
+    float4* acc = smo;                                              // [NP][PT][PT][OT_RS]
+    float4* su = acc + NP * OT_PAIR;                                // [OT_CHUNK][NP] coil pairs
+    float* swz = (float*)(su + OT_CHUNK * NP);                      // [OT_CHUNK][KW] z weights
+    float* swyx = swz + OT_CHUNK * KW;                              // [OT_CHUNK][KW * KW] y x weight products
+    int* sb = (int*)(swyx + OT_CHUNK * KW * KW);                    // [OT_CHUNK] (padded offset << 1) | z0 parity
     const int4 it = items[blockIdx.x];
     const int tile = it.x, beg = it.y, end = it.z, slot = it.w;
-    const int c0 = blockIdx.y * CG;
-    const int cc = min(CG, geo.C - c0);
+    const int c0 = blockIdx.y * 2 * NP;
+    const int cc = min(2 * NP, geo.C - c0);
     int o[MAXD];
     {
         int r = tile;
@@ -930,114 +939,144 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
             o[d] = tc * tl.ts[d];
         }
     }
-    for (int i = threadIdx.x; i < LO::COPY; i += blockDim.x) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < NP * OT_PAIR; i += NT) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ty = lane >> 3, tx = (lane >> 1) & 3, h = lane & 1;
-    for (int sb = beg; sb < end; sb += SP_CHUNK) {
-        const int n = min(SP_CHUNK, end - sb);
+    const int pair = warp % NP, par = warp / NP;
+    const int jsel = lane >> 4, yx = lane & 15;
+    // this lane's tap relative to the sample's first tap: z offset jzb + 2 jsel (jzb from parity), y = yx >> 2, x = yx & 3
+    float4* const mine = acc + pair * OT_PAIR + 2 * jsel * OT_PS + (yx >> 2) * OT_RS + (yx & 3);
+    const bool live = 2 * pair < cc;
+    for (int s0 = beg; s0 < end; s0 += OT_CHUNK) {
+        const int n = min(OT_CHUNK, end - s0);
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int s = sb + i;
+        for (int i = threadIdx.x; i < n; i += NT) {
+            const int s = s0 + i;
             const int64_t un = perm ? perm[s] : s;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const float2 ua = 2 * k < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k) * geo.M + un) : make_float2(0.f, 0.f);
                 const float2 ub = 2 * k + 1 < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k + 1) * geo.M + un) : make_float2(0.f, 0.f);
-                su4[i * NP + k] = make_float4(ua.x, ua.y, ub.x, ub.y);
+                su[i * NP + k] = make_float4(ua.x, ua.y, ub.x, ub.y);
             }
-            unsigned pk = 0;
+            int l[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int l0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];   // in [0, ts)
-                pk |= (unsigned)l0 << (8 * d);
+            for (int d = 0; d < D; ++d) l[d] = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];   // in [0, ts)
+            sb[i] = ((l[0] * OT_PS + l[1] * OT_RS + l[2]) << 1) | (l[0] & 1);
+            float wy[KW], wx[KW];
 #pragma unroll
-                for (int j = 0; j < KW; ++j) sw[(i * D + d) * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
+            for (int j = 0; j < KW; ++j) {
+                swz[i * KW + j] = wt[(int64_t)j * geo.M + s];
+                wy[j] = wt[(int64_t)(KW + j) * geo.M + s];
+                wx[j] = wt[(int64_t)(2 * KW + j) * geo.M + s];
             }
-            sp[i] = pk;
+#pragma unroll
+            for (int a = 0; a < KW; ++a)
+#pragma unroll
+                for (int b = 0; b < KW; ++b) swyx[i * KW * KW + a * KW + b] = wy[a] * wx[b];
         }
         __syncthreads();
-        for (int i = 0; i < n; ++i) {
-            const unsigned pk = sp[i];
-            int jz = warp - (int)(pk & 0xFFu);
-            if (jz < 0) jz += 8;
-            if (jz >= KW) continue;                             // warp-uniform
-            const int z = (int)(pk & 0xFFu) + jz;
-            const int y = (int)((pk >> 8) & 0xFFu) + ty;
-            const int x = (int)((pk >> 16) & 0xFFu) + tx;
-            const float w = sw[(i * D) * KW + jz] * sw[(i * D + 1) * KW + ty] * sw[(i * D + 2) * KW + tx];
-#pragma unroll
-            for (int j = 0; j < NP / 2; ++j) {
-                const int k = (NP / 2) * h + j;
-                const float4 uv = su4[i * NP + k];
-                float4* a = acc + LO::idx(z, y, x, k);
-                float4 v = *a;
-                v.x = fmaf(w, uv.x, v.x); v.y = fmaf(w, uv.y, v.y);
-                v.z = fmaf(w, uv.z, v.z); v.w = fmaf(w, uv.w, v.w);
-                *a = v;
+        if (live) {
+            int run = -1;                                            // current run's key (sb value), warp-uniform
+            float4* dst = nullptr;
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < n; ++i) {
+                const int b = sb[i];
+                const int jzb = (par ^ b) & 1;                       // planes z0 + jz of this warp's parity: jz = jzb, jzb + 2
+                if (b != run) {
+                    if (dst) {
+                        float4 v = *dst;
+                        v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
+                        *dst = v;
+                    }
+                    run = b;
+                    dst = mine + (b >> 1) + jzb * OT_PS;
+                    r = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                const float w = swz[i * KW + jzb + 2 * jsel] * swyx[i * KW * KW + yx];
+                const float4 uv = su[i * NP + pair];
+                r.x = fmaf(w, uv.x, r.x); r.y = fmaf(w, uv.y, r.y);
+                r.z = fmaf(w, uv.z, r.z); r.w = fmaf(w, uv.w, r.w);
+            }
+            if (dst) {
+                float4 v = *dst;
+                v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
+                *dst = v;
             }
         }
     }
     __syncthreads();
     // padded tile -> slot, coil-major: halo[(slot * C + c) * PT3 + point]
     const int npair = (cc + 1) / 2;
-    for (int i = threadIdx.x; i < npair * PT3; i += blockDim.x) {
+    for (int i = threadIdx.x; i < npair * PT3; i += NT) {
         const int k = i / PT3, pt = i - k * PT3;
         const int z = pt / (PT * PT), y = (pt / PT) % PT, x = pt % PT;
-        const float4 v = acc[LO::idx(z, y, x, k)];
+        const float4 v = acc[k * OT_PAIR + z * OT_PS + y * OT_RS + x];
         float2* d0 = halo + ((size_t)slot * geo.C + c0 + 2 * k) * PT3 + pt;
         *d0 = make_float2(v.x, v.y);
         if (2 * k + 1 < cc) d0[PT3] = make_float2(v.z, v.w);
     }
 }
 
-// Phase B: grid[c][q] = sum over the slots of q's tile and of the lower neighbours whose
-// padded halo covers q (periodic in every axis).  Launch: blockIdx.x = (grid row (z, y), block
-// of the fastest axis), threads along the fastest axis, blockIdx.y = coil; all index arithmetic
-// in 32 bits.
+// Phase B: one CTA per tile (empty tiles included, so every grid point is stored once).  For the
+// tile and its 7 lower neighbours (periodic) the CTA first looks up their slot ranges and the
+// padded offset at which the neighbour's halo meets this tile; then each thread takes (coil,
+// point) pairs of the tile and sums the slots that cover the point.
+__global__ void __launch_bounds__(256)
+k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
+              float2* __restrict__ grid) {
+    __shared__ int nb_beg[8], nb_end[8], nb_off[8], org[3], ext[3];
+    const int tile = blockIdx.x;
+    if (threadIdx.x < 8) {
+        const int m = threadIdx.x;
+        const int nt0 = tl.nt[0], nt1 = tl.nt[1], nt2 = tl.nt[2];
+        const int ts0 = tl.ts[0], ts1 = tl.ts[1], ts2 = tl.ts[2];
+        const int t2 = tile % nt2, t1 = (tile / nt2) % nt1, t0 = tile / (nt2 * nt1);
+        const int b0 = (m >> 2) & 1, b1 = (m >> 1) & 1, b2 = m & 1;
+        const int n0 = b0 ? (t0 == 0 ? nt0 - 1 : t0 - 1) : t0;
+        const int n1 = b1 ? (t1 == 0 ? nt1 - 1 : t1 - 1) : t1;
+        const int n2 = b2 ? (t2 == 0 ? nt2 - 1 : t2 - 1) : t2;
+        const int nb = (n0 * nt1 + n1) * nt2 + n2;
+        nb_beg[m] = tslot[nb];
+        nb_end[m] = tslot[nb + 1];
+        nb_off[m] = (b0 ? min(ts0, geo.g[0] - n0 * ts0) * PT * PT : 0) + (b1 ? min(ts1, geo.g[1] - n1 * ts1) * PT : 0) +
+                    (b2 ? min(ts2, geo.g[2] - n2 * ts2) : 0);
+        if (m == 0) {
+            org[0] = t0 * ts0; org[1] = t1 * ts1; org[2] = t2 * ts2;
+            ext[0] = min(ts0, geo.g[0] - org[0]); ext[1] = min(ts1, geo.g[1] - org[1]); ext[2] = min(ts2, geo.g[2] - org[2]);
+        }
+    }
+    __syncthreads();
+    const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
+    const size_t cstride = (size_t)geo.C * PT3;
+    const int total = geo.C * 512;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int c = i >> 9, lz = (i >> 6) & 7, ly = (i >> 3) & 7, lx = i & 7;
+        if (lz >= e0 || ly >= e1 || lx >= e2) continue;
+        const int pt = (lz * PT + ly) * PT + lx;
+        const int low = (lz < KW - 1 ? 4 : 0) | (ly < KW - 1 ? 2 : 0) | (lx < KW - 1 ? 1 : 0);
+        const float2* hc = halo + (size_t)c * PT3 + pt;
+        float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            if (m & ~low) continue;
+            const int e = nb_end[m], o = nb_off[m];
+            for (int sl = nb_beg[m]; sl < e; ++sl) {
+                const float2 v = hc[(size_t)sl * cstride + o];
+                sum.x += v.x;
+                sum.y += v.y;
+            }
+        }
+        const int gz = tunshift(org[0] + lz, tl.sh[0], geo.g[0]);
+        const int gy = tunshift(org[1] + ly, tl.sh[1], geo.g[1]);
+        const int gx = tunshift(org[2] + lx, tl.sh[2], geo.g[2]);
+        grid[(size_t)c * geo.G + ((size_t)gz * geo.g[1] + gy) * geo.g[2] + gx] = sum;
+    }
+}
+
 __device__ __forceinline__ void tile_local(int k, int sh, int g, int ts, int& t, int& l) {
     const int p = tshift(k, sh, g);
     t = p / ts;
     l = p - t * ts;
-}
-
-__global__ void __launch_bounds__(256)
-k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
-              float2* __restrict__ grid) {
-    const int xb = (geo.g[2] + blockDim.x - 1) / blockDim.x;
-    const int row = blockIdx.x / xb, c = blockIdx.y;
-    const int k2 = (blockIdx.x - row * xb) * blockDim.x + threadIdx.x;
-    if (k2 >= geo.g[2]) return;
-    const int k1 = row % geo.g[1], k0 = row / geo.g[1];
-    int t[3], l[3];
-    tile_local(k0, tl.sh[0], geo.g[0], tl.ts[0], t[0], l[0]);
-    tile_local(k1, tl.sh[1], geo.g[1], tl.ts[1], t[1], l[1]);
-    tile_local(k2, tl.sh[2], geo.g[2], tl.ts[2], t[2], l[2]);
-    // per axis: the tile and padded coordinate for "same tile" and "lower neighbour"
-    int tt[3][2], ll[3][2];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        tt[d][0] = t[d];
-        ll[d][0] = l[d];
-        tt[d][1] = t[d] == 0 ? tl.nt[d] - 1 : t[d] - 1;
-        ll[d][1] = l[d] + min(tl.ts[d], geo.g[d] - tt[d][1] * tl.ts[d]);
-    }
-    const size_t cstride = (size_t)geo.C * PT3;
-    const float2* hc = halo + (size_t)c * PT3;
-    float2 sum = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int b0 = (m >> 2) & 1, b1 = (m >> 1) & 1, b2 = m & 1;
-        if ((b0 && l[0] >= KW - 1) || (b1 && l[1] >= KW - 1) || (b2 && l[2] >= KW - 1)) continue;
-        const int tile = (tt[0][b0] * tl.nt[1] + tt[1][b1]) * tl.nt[2] + tt[2][b2];
-        const int pt = (ll[0][b0] * PT + ll[1][b1]) * PT + ll[2][b2];
-        const int s1 = tslot[tile + 1];
-        for (int sl = tslot[tile]; sl < s1; ++sl) {
-            const float2 v = hc[(size_t)sl * cstride + pt];
-            sum.x += v.x;
-            sum.y += v.y;
-        }
-    }
-    grid[(size_t)c * geo.G + (size_t)row * geo.g[2] + k2] = sum;
 }
 
 // Two-phase spreading in 2D (variant 12): phase A as in 3D but with warp-private copies of the
@@ -1661,7 +1700,8 @@ kp_status forward_to(kp_plan p, const float2* x, void* out, kp_cdtype out_t, con
     InterpIO io{};
     io.out = out;
     io.perm = perm;
-    io.flag = p->d_flag + 3;
+    io.flag = p->d_flag + KP_FLAG_TIMEOUT;
+    io.wait = p->wait_cycles;
     return launch_interp<0>(p, out_t, io, st);
 }
 
@@ -1672,7 +1712,8 @@ kp_status forward_scaled(kp_plan p, const float2* x, float2* out_sorted, const f
     io.outs = out_sorted;
     io.ps = ps;
     io.n2 = n2;
-    io.flag = p->d_flag + 3;
+    io.flag = p->d_flag + KP_FLAG_TIMEOUT;
+    io.wait = p->wait_cycles;
     return launch_interp<1>(p, KP_C64, io, st);
 }
 
@@ -1684,7 +1725,8 @@ kp_status forward_dual(kp_plan p, const float2* xbar, cudaStream_t st) {
 kp_status interp_dual_only(kp_plan p, cudaStream_t st) {
     InterpIO io{};
     io.ys = p->d_ys;
-    io.flag = p->d_flag + 3;
+    io.flag = p->d_flag + KP_FLAG_TIMEOUT;
+    io.wait = p->wait_cycles;
     io.ps = p->d_ps;
     io.u = p->d_u;
     io.sched = p->d_sched;
@@ -1728,23 +1770,24 @@ static kp_status launch_spread_own2(kp_plan p, const UT* u, const int* perm, cud
     return KP_OK;
 }
 
-template <int D, typename UT, int CG>
+template <int D, typename UT, int NP>
 static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
     const Geom& g = p->geo;
-    if (D != 3 || !p->d_halo || p->halo_cap < (size_t)p->n_oitems * g.C * PT3) {
-        set_error("two-phase spreading needs a 3D plan with its slot storage");
+    if (D != 3 || !p->d_halo || p->halo_cap < (size_t)p->n_oitems * g.C * PT3 || p->tiles.ts[0] > 8 ||
+        p->tiles.ts[1] > 8 || p->tiles.ts[2] > 8) {
+        set_error("two-phase spreading needs a 3D plan with tiles of at most 8 and its slot storage");
         return KP_EINTERNAL;
     }
     static PerDeviceOnce attr;
-    const size_t sm = spread_own_smem<CG>();
-    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_own<UT, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t sm = spread_own_smem<NP>();
+    if (attr.first()) KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_own<UT, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (p->n_oitems > 0)
-        k_spread_own<UT, CG><<<dim3((unsigned)p->n_oitems, (g.C + CG - 1) / CG), 256, sm, st>>>(
+        k_spread_own<UT, NP><<<dim3((unsigned)p->n_oitems, (g.C + 2 * NP - 1) / (2 * NP)), NP * 64, sm, st>>>(
             p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
     KP_LAUNCH_CHECK();
     mark(p, PH_SPREAD_RED, st);
-    const dim3 gg((unsigned)(((g.g[2] + 255) / 256) * g.g[0] * g.g[1]), (unsigned)g.C);
-    k_halo_gather<<<gg, 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    k_halo_gather<<<(unsigned)p->tiles.ntiles, 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;
 }
@@ -1822,8 +1865,8 @@ static kp_status spread_only(kp_plan p, const void* u, kp_cdtype u_t, const int*
                 case 7: KP_TRY((launch_spread_v<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
                 case 8: KP_TRY((launch_spread_z<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
                 case 9: KP_TRY((launch_spread_z<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
-                case 10: KP_TRY((launch_spread_own<DD, UT, 8>(p, (const UT*)u, perm, st))); break;
-                case 11: KP_TRY((launch_spread_own<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
+                case 10: KP_TRY((launch_spread_own<DD, UT, 4>(p, (const UT*)u, perm, st))); break;
+                case 11: KP_TRY((launch_spread_own<DD, UT, 2>(p, (const UT*)u, perm, st))); break;
                 case 12: KP_TRY((launch_spread_own2<UT>(p, (const UT*)u, perm, st))); break;
                 default: KP_TRY((launch_spread_priv<DD, UT, 2, 4>(p, (const UT*)u, perm, st))); break;
             }));

@@ -197,6 +197,27 @@ __global__ void k_schedule(double* __restrict__ schedd, const int* __restrict__ 
 
 __global__ void k_advance(int* iter) { *iter += 1; }
 
+// out[c][perm[s]] = in[c][s]: a sorted-order k-space array back to the trajectory's order
+__global__ void k_unpermute_c64(const float2* __restrict__ in, float2* __restrict__ out, const int* __restrict__ perm,
+                                int64_t M, int C) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const int64_t o = perm[s];
+    for (int c = 0; c < C; ++c) out[(size_t)c * M + o] = in[(size_t)c * M + s];
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+// flag = 1 if any of the n complex values is a NaN or an Inf
+__global__ void k_nonfinite(const float2* __restrict__ x, int64_t n, int* __restrict__ flag) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = x[i];
+        bad |= !isfinite(v.x) || !isfinite(v.y);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
 template <typename T>
 __global__ void k_permute(const T* __restrict__ in, T* __restrict__ out, const int* __restrict__ perm, int64_t M, int C) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,11 +378,14 @@ kp_status ensure_tv_dual(kp_plan p) {
 
 // Everything a PDHG run needs before its first iteration (Sec. 4.1): measurements and
 // preconditioner in sorted order, min p, lambda_max (given, or 30 power iterations), the
-// step-size schedule, zero initial iterates and the forward grid of xbar_0 = 0.
+// step-size schedule, the initial iterates (zero, or a caller's state whose dual variable is
+// brought into sorted order) and the forward grid of xbar.
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st, int reg) {
+                      cudaStream_t st, int reg, const kp_pdhg_state* start) {
     const Geom& g = plan->geo;
     void* stream = (void*)st;
+    const int k0 = start ? start->k : 0;
+    iters += k0;                       // the schedule runs from iteration 0; the run starts at k0
     KP_TRY(ensure_sched(plan, std::max(iters, 1)));
     // measurements into sorted order
     plan->ys_t = y_t;
@@ -379,7 +403,7 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
     }
     k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(pu, plan->d_ps, plan->d_perm, g.M, g.C);
     KP_LAUNCH_CHECK();
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag, 0, 8 * sizeof(int), st));
+    KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag, 0, KP_NFLAGS * sizeof(int), st));
     {
         static const int init = 0x7f7fffff;
         KP_TRY_CUDA(cudaMemcpyAsync(plan->d_flag + 4, &init, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -400,18 +424,31 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
                                 reg == KP_REG_TV ? g.D : 0);
     KP_LAUNCH_CHECK();
     plan->launches += 1;
-    // x0 = xbar0 = 0, u0 = 0
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_x, 0, g.N * sizeof(float2), st));
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
+    if (!start) {
+        // x0 = xbar0 = 0, u0 = 0
+        KP_TRY_CUDA(cudaMemsetAsync(plan->d_x, 0, g.N * sizeof(float2), st));
+        KP_TRY_CUDA(cudaMemsetAsync(plan->d_xbar, 0, g.N * sizeof(float2), st));
+        KP_TRY_CUDA(cudaMemsetAsync(plan->d_u, 0, (size_t)g.C * g.M * sizeof(float2), st));
+    } else {
+        // a caller's state: x_k, xbar_k, u_k (user sample order -> sorted)
+        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_x, start->x, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_xbar, start->xbar, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>((const float2*)start->u, plan->d_u, plan->d_perm, g.M, g.C);
+        KP_LAUNCH_CHECK();
+        plan->launches += 1;
+    }
     if (reg == KP_REG_TV) {
         KP_TRY(ensure_tv_dual(plan));
-        KP_TRY_CUDA(cudaMemsetAsync(plan->d_v, 0, (size_t)g.D * g.N * sizeof(float2), st));   // v_0 = 0
+        if (start) KP_TRY_CUDA(cudaMemcpyAsync(plan->d_v, start->v, (size_t)g.D * g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        else KP_TRY_CUDA(cudaMemsetAsync(plan->d_v, 0, (size_t)g.D * g.N * sizeof(float2), st));   // v_0 = 0
     }
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_iter, 0, sizeof(int), st));
+    k_set_int<<<1, 1, 0, st>>>(plan->d_iter, k0);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
     KP_TRY_CUDA(cudaMemsetAsync(plan->d_bar, 0, 4 * sizeof(unsigned int), st));   // grid-barrier counter
-    // forward grid of xbar_0 = 0 (the fused primal kernel writes the next one each iteration)
-    KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
+    // forward grid of xbar (the primal step writes the next one each iteration)
+    if (!start) KP_TRY_CUDA(cudaMemsetAsync(plan->d_grid, 0, (size_t)g.C * g.G * sizeof(float2), st));
+    else KP_TRY(pre_only(plan, plan->d_xbar, st));
     // split tiles of the spreading grid start at zero (the primal step re-clears them)
     KP_TRY(zero_split_only(plan, st));
     (void)cluster_prox_ok(plan);   // decide the primal path here, outside any graph capture
@@ -565,7 +602,7 @@ static kp_status dual_l2(kp_plan p, const float2* y_dev, const float* p_dev, flo
     k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>(y_dev, (float2*)p->d_ys, p->d_perm, g.M, g.C);
     KP_LAUNCH_CHECK();
     const float* ps = nullptr;
-    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag, 0, 8 * sizeof(int), st));
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag, 0, KP_NFLAGS * sizeof(int), st));
     if (p_dev) {
         k_permute<float><<<nblk(g.M, 256), 256, 0, st>>>(p_dev, p->d_ps, p->d_perm, g.M, g.C);
         static const int init = 0x7f7fffff;
@@ -606,8 +643,8 @@ static kp_status dual_l2(kp_plan p, const float2* y_dev, const float* p_dev, flo
     k_scale_copy<<<nblk(g.N, 256), 256, 0, st>>>(p->d_w, x_dev, g.N, 1.f / lambda);
     KP_LAUNCH_CHECK();
     p->launches += 1;
-    int flags[8];
-    KP_TRY_CUDA(cudaMemcpyAsync(flags, p->d_flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int flags[KP_NFLAGS];
+    KP_TRY_CUDA(cudaMemcpyAsync(flags, p->d_flag, KP_NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
     if (res_trace)
         KP_TRY_CUDA(cudaMemcpyAsync(res_trace, p->d_cg_trace, (size_t)(iters + 1) * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
@@ -673,18 +710,24 @@ static kp_status ensure_events(kp_plan p, int n) {
     return KP_OK;
 }
 
-kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg, float lambda,
-                        int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats, void* stream) {
-    if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
+kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg,
+                           float lambda, int iters, double lmax, const kp_pdhg_state* start, kp_pdhg_state* end,
+                           double* obj_trace, kp_stats* stats, void* stream) {
+    if (!plan || !y_dev || !end || !end->x) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
     if (!(lambda >= 0.f) || !std::isfinite(lambda)) { set_error("lambda must be finite and >= 0"); return KP_EINVAL; }
     if (reg != KP_REG_L2 && reg != KP_REG_L1_WAVELET && reg != KP_REG_TV) { set_error("bad regulariser"); return KP_EINVAL; }
     if (reg == KP_REG_L1_WAVELET && plan->P.wavelet_levels < 1) { set_error("l1-wavelet needs wavelet_levels >= 1"); return KP_EINVAL; }
     if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
+    if (start && (start->k < 0 || !start->x || !start->xbar || !start->u || (reg == KP_REG_TV && !start->v))) {
+        set_error("a start state needs k >= 0 and x, xbar, u (and v for TV)");
+        return KP_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const Geom& g = plan->geo;
-    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st, (int)reg));
+    const int k0 = start ? start->k : 0;
+    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st, (int)reg, start));
     kp_status status = KP_OK;
     double F0 = 0, F = NAN;
     double phase_ms[PH_N] = {0};
@@ -719,12 +762,26 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
             }
         }
     }
-    KP_TRY_CUDA(cudaMemcpyAsync(x_dev, plan->d_x, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    int flags[8];
+    // the result, checked on the device, and the rest of the state
+    k_nonfinite<<<(unsigned)std::min<int64_t>(nblk(g.N, 256), 1216), 256, 0, st>>>(plan->d_x, g.N,
+                                                                                   plan->d_flag + KP_FLAG_NONFINITE);
+    KP_LAUNCH_CHECK();
+    plan->launches += 1;
+    KP_TRY_CUDA(cudaMemcpyAsync(end->x, plan->d_x, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (end->xbar) KP_TRY_CUDA(cudaMemcpyAsync(end->xbar, plan->d_xbar, g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (end->u) {
+        k_unpermute_c64<<<nblk(g.M, 256), 256, 0, st>>>(plan->d_u, (float2*)end->u, plan->d_perm, g.M, g.C);
+        KP_LAUNCH_CHECK();
+        plan->launches += 1;
+    }
+    if (end->v && reg == KP_REG_TV)
+        KP_TRY_CUDA(cudaMemcpyAsync(end->v, plan->d_v, (size_t)g.D * g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    int flags[KP_NFLAGS];
     double sd[4];
-    KP_TRY_CUDA(cudaMemcpyAsync(flags, plan->d_flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaMemcpyAsync(flags, plan->d_flag, KP_NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaMemcpyAsync(sd, plan->d_schedd, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));
+    end->k = k0 + iters;
     if (stats) {
         stats->iters = iters;
         stats->lmax = sd[0];
@@ -734,10 +791,23 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
         stats->final_obj = obj_trace ? F : NAN;
         for (int i = 0; i < KP_NPHASES && i < PH_N; ++i) stats->phase_ms[i] = phase_ms[i];
     }
-    if (flags[5] != 0) { set_error(std::to_string(flags[5]) + " preconditioner entries are not positive and finite"); return KP_EINVAL; }
-    if (flags[6] != 0) { set_error("lambda_max or min p is not positive and finite"); return KP_EINVAL; }
-    if (flags[3] != 0) { set_error("a grid barrier of the fused primal kernel timed out"); return KP_ETIMEOUT; }
+    if (flags[KP_FLAG_P_BAD] != 0) { set_error(std::to_string(flags[KP_FLAG_P_BAD]) + " preconditioner entries are not positive and finite"); return KP_EINVAL; }
+    if (flags[KP_FLAG_SCHED_BAD] != 0) { set_error("lambda_max or min p is not positive and finite"); return KP_EINVAL; }
+    if (flags[KP_FLAG_TIMEOUT] != 0) {
+        set_error("a bounded device wait (bulk-copy staging of the interpolation or a grid barrier of the primal kernel) gave up");
+        return KP_ETIMEOUT;
+    }
+    if (status == KP_OK && flags[KP_FLAG_NONFINITE] != 0) { set_error("the reconstruction holds a NaN or an Inf"); return KP_ENONFINITE; }
+    if (status == KP_ENONFINITE) set_error("the objective is not finite");
+    if (status == KP_EDIVERGED) set_error("the objective grew above 1e3 times its first value");
     return status;
+}
+
+kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg, float lambda,
+                        int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats, void* stream) {
+    if (!x_dev) { set_error("null argument"); return KP_EINVAL; }
+    kp_pdhg_state end{x_dev, nullptr, nullptr, nullptr, 0};
+    return kp_pdhg_solve_ex(plan, y_dev, y_t, p_dev, reg, lambda, iters, lmax, nullptr, &end, obj_trace, stats, stream);
 }
 
 }  // extern "C"

@@ -46,6 +46,63 @@ __global__ void k_scan_excl(const int* __restrict__ in, int* __restrict__ out, i
     if (threadIdx.x == T - 1) out[n] = (int)part[T - 1];
 }
 
+// Exclusive scan of n ints over many CTAs: k_scan_part sums each block of SCAN_B elements,
+// the block sums are scanned by k_scan_excl, and k_scan_fin scans each block from its offset.
+// out[n] = total.
+constexpr int SCAN_T = 256, SCAN_PER = 8, SCAN_B = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+    __shared__ int ws[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < SCAN_T / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < SCAN_T / 32) ws[lane] = t;
+    }
+    __syncthreads();
+    const int before = w ? ws[w - 1] : 0;
+    *total = ws[SCAN_T / 32 - 1];
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_part(const int* __restrict__ in, int64_t n, int* __restrict__ part) {
+    const int64_t b0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_PER;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) s += b0 + k < n ? in[b0 + k] : 0;
+    int tot;
+    (void)block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_fin(const int* __restrict__ in, int64_t n, const int* __restrict__ part_off,
+                                                     int* __restrict__ out) {
+    const int64_t b0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_PER;
+    int v[SCAN_PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) { v[k] = b0 + k < n ? in[b0 + k] : 0; s += v[k]; }
+    int tot;
+    int run = block_excl_scan(s, &tot) + part_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        if (b0 + k < n) out[b0 + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part_off[gridDim.x];
+}
+
 // Tile index of one sample from its first taps k0 (already wrapped into [0, g)).
 template <int D>
 __device__ __forceinline__ int64_t tile_of(const int* k0w, const Tiles& tl) {
@@ -54,26 +111,39 @@ __device__ __forceinline__ int64_t tile_of(const int* k0w, const Tiles& tl) {
     return key;   // k0w already shifted
 }
 
-// Pass 1: validate, convert to grid coordinates, key by tile, histogram.
+// Pass 1: validate, convert to grid coordinates, key by the first tap's grid cell in tile-major
+// order (tile index x cells per tile + the cell's local index, slowest axis first), histogram.
 template <int D>
-__global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geom geo, Tiles tl,
+__global__ void k_traj_key(const float* __restrict__ traj, float traj_scale, Geom geo, Tiles tl, int cells_per_tile,
                            int* __restrict__ key, int* __restrict__ cnt, int* __restrict__ flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= geo.M) return;
-    int k0w[D];
+    int64_t tile = 0, cell = 0;
     bool bad = false;
     for (int d = 0; d < D; ++d) {
         float f = traj[i * D + d];
         float half = 0.5f * (float)geo.n[d];
         if (!(f * traj_scale >= -half && f * traj_scale <= half)) bad = true;   // also catches NaN
         float u0;
-        int k0 = grid_tap(bad ? 0.f : f, traj_scale, geo.n[d], geo.g[d], &u0);
-        k0w[d] = tshift(wrap(k0, geo.g[d]), tl.sh[d], geo.g[d]);
+        const int k0 = grid_tap(bad ? 0.f : f, traj_scale, geo.n[d], geo.g[d], &u0);
+        const int pd = tshift(wrap(k0, geo.g[d]), tl.sh[d], geo.g[d]);
+        const int td = pd / tl.ts[d];
+        tile = tile * tl.nt[d] + td;
+        cell = cell * tl.ts[d] + (pd - td * tl.ts[d]);
     }
     if (bad) atomicAdd(flag, 1);
-    int64_t kk = tile_of<D>(k0w, tl);
+    const int64_t kk = tile * cells_per_tile + cell;
     key[i] = (int)kk;
     atomicAdd(&cnt[kk], 1);
+}
+
+// Tile ranges of the cell-sorted order: off[t] = first sorted position of tile t (t <= ntiles).
+__global__ void k_tile_off(const int* __restrict__ coff, int64_t ntiles, int cells_per_tile, int* __restrict__ off,
+                           int* __restrict__ cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    off[t] = coff[t * cells_per_tile];
+    if (t < ntiles) cnt[t] = coff[(t + 1) * cells_per_tile] - coff[t * cells_per_tile];
 }
 
 // Pass 2: scatter sample i to its slot in the sorted order, with its wrapped first tap
@@ -358,6 +428,14 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     KP_A(p->d_perm, M);
     KP_A(p->d_key, M);
     KP_A(p->d_cnt, tl.ntiles + 1);
+    p->cells_per_tile = 1;
+    for (int d = 0; d < D; ++d) p->cells_per_tile *= tl.ts[d];
+    p->ncells = tl.ntiles * p->cells_per_tile;
+    if (p->ncells >= ((int64_t)1 << 31) - 1) { plan_destroy_internal(p); set_error("grid too large for the cell sort"); return KP_EINVAL; }
+    KP_A(p->d_ccnt, p->ncells + 1);
+    KP_A(p->d_coff, p->ncells + 1);
+    KP_A(p->d_scan_part, p->ncells / SCAN_B + 2);
+    KP_A(p->d_scan_poff, p->ncells / SCAN_B + 2);
     KP_A(p->d_off, tl.ntiles + 1);
     KP_A(p->d_ext_off, tl.ntiles + 1);
     KP_A(p->d_ext, (size_t)M << D);
@@ -366,7 +444,7 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
     KP_A(p->d_wt, (size_t)D * KW * M);
     KP_A(p->d_slot_off, tl.ntiles + 1);
     KP_A(p->d_nslots, tl.ntiles + 1);
-    KP_A(p->d_flag, 8);
+    KP_A(p->d_flag, KP_NFLAGS);
     {
         float* ap = nullptr;
         int tot = 0;
@@ -444,7 +522,7 @@ kp_status plan_destroy_internal(kp_plan p) {
     drop_graphs(p);
     pre_destroy(p);
     if (p->fft_ok) cufftDestroy(p->fft);
-    void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
+    void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_ccnt, p->d_coff, p->d_scan_part, p->d_scan_poff, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
                     p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
                     p->d_grid2, p->d_gridF, p->d_bar, p->d_tape, p->d_bk,
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
@@ -588,17 +666,26 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     p->traj_version++;
     if (traj != p->d_f)
         KP_TRY_CUDA(cudaMemcpyAsync(p->d_f, traj, (size_t)g.D * g.M * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag, 0, 8 * sizeof(int), st));
-    if (g.D == 2) k_traj_key<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, tl, p->d_key, p->d_cnt, p->d_flag);
-    else k_traj_key<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, tl, p->d_key, p->d_cnt, p->d_flag);
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_ccnt, 0, (p->ncells + 1) * sizeof(int), st));
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag, 0, KP_NFLAGS * sizeof(int), st));
+    if (g.D == 2) k_traj_key<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, tl, p->cells_per_tile, p->d_key, p->d_ccnt, p->d_flag);
+    else k_traj_key<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, tl, p->cells_per_tile, p->d_key, p->d_ccnt, p->d_flag);
     KP_LAUNCH_CHECK();
+    {
+        // cell offsets by a multi-block exclusive scan, then the tile ranges and counts
+        const unsigned nbk = (unsigned)((p->ncells + SCAN_B - 1) / SCAN_B);
+        k_scan_part<<<nbk, SCAN_T, 0, st>>>(p->d_ccnt, p->ncells, p->d_scan_part);
+        k_scan_excl<<<1, 1024, 0, st>>>(p->d_scan_part, p->d_scan_poff, nbk);
+        k_scan_fin<<<nbk, SCAN_T, 0, st>>>(p->d_ccnt, p->ncells, p->d_scan_poff, p->d_coff);
+        k_tile_off<<<nblk(tl.ntiles + 1, 256), 256, 0, st>>>(p->d_coff, tl.ntiles, p->cells_per_tile, p->d_off, p->d_cnt);
+        KP_LAUNCH_CHECK();
+        p->launches += 4;
+    }
     k_max_count<<<64, 256, 0, st>>>(p->d_cnt, tl.ntiles, p->d_flag + 1);
-    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_off, tl.ntiles);
     KP_LAUNCH_CHECK();
-    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    if (g.D == 2) k_traj_scatter<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t, p->d_k0);
-    else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_off, p->d_cnt, p->d_perm, p->d_t, p->d_k0);
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_ccnt, 0, (p->ncells + 1) * sizeof(int), st));
+    if (g.D == 2) k_traj_scatter<2><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_coff, p->d_ccnt, p->d_perm, p->d_t, p->d_k0);
+    else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_coff, p->d_ccnt, p->d_perm, p->d_t, p->d_k0);
     KP_LAUNCH_CHECK();
     KP_TRY(build_tap_tables(p, st));
     // spreading lists
@@ -705,6 +792,29 @@ kp_status kp_plan_set_maps(kp_plan plan, const void* maps_dev, kp_cdtype maps_t,
 kp_status kp_plan_launch_count(kp_plan plan, int64_t* count) {
     if (!plan || !count) { set_error("null argument"); return KP_EINVAL; }
     *count = plan->launches + (plan->pre_nufft ? plan->pre_nufft->launches : 0);
+    return KP_OK;
+}
+
+kp_status kp_plan_set_wait_limit(kp_plan plan, long long cycles) {
+    if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    if (cycles < 0) { set_error("the wait limit must be >= 0"); return KP_EINVAL; }
+    plan->wait_cycles = cycles;
+    drop_graphs(plan);
+    return KP_OK;
+}
+
+kp_status kp_plan_sync(kp_plan plan, void* stream) {
+    if (!plan) { set_error("null plan"); return KP_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    int timeout = 0;
+    KP_TRY_CUDA(cudaMemcpyAsync(&timeout, plan->d_flag + KP_FLAG_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (timeout) {
+        KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag + KP_FLAG_TIMEOUT, 0, sizeof(int), st));
+        KP_TRY_CUDA(cudaStreamSynchronize(st));
+        set_error("a bounded device wait (bulk-copy staging of the interpolation) gave up");
+        return KP_ETIMEOUT;
+    }
     return KP_OK;
 }
 

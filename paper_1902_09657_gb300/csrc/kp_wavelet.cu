@@ -561,7 +561,7 @@ struct GridBarrier {
     unsigned long long count;
 };
 
-__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
+__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err, long long limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -573,7 +573,7 @@ __device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
             unsigned long long cur;
             asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(&b->count) : "memory");
             if (cur >= target) break;
-            if (clock64() - t0 > 2000000000LL) {   // about one second at GB300 clocks
+            if (clock64() - t0 > limit) {          // the plan's limit (default about a second)
                 atomicExch(err, 1);
                 break;
             }
@@ -605,6 +605,7 @@ struct PrimalArgs {
     Tiles tiles;
     GridBarrier* bar;
     int* err;
+    long long wait;        // limit of each grid-barrier wait (SM clock cycles)
 };
 
 template <int D, int T>
@@ -703,20 +704,20 @@ __global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
         }
     }
     if (REG == 1) {
-        grid_barrier(a.bar, a.err);
+        grid_barrier(a.bar, a.err, a.wait);
         zero_split_tiles<D>(a);   // grid2 has been read by every block
         for (int lev = 0; lev < a.levels; ++lev) {
             const LevelArgs la = level_args<D, T>(a, lev, true, k);
             for (int t = blockIdx.x; t < la.tiles_total; t += gridDim.x) fwd_level_tile<D, T>(la, t, sm);
-            grid_barrier(a.bar, a.err);
+            grid_barrier(a.bar, a.err, a.wait);
         }
         for (int lev = a.levels - 1; lev >= 0; --lev) {
             const LevelArgs la = level_args<D, T>(a, lev, false, k);
             for (int t = blockIdx.x; t < la.tiles_total; t += gridDim.x) inv_level_tile<D, T, MT>(la, t, sm);
-            if (lev > 0) grid_barrier(a.bar, a.err);
+            if (lev > 0) grid_barrier(a.bar, a.err, a.wait);
         }
     }
-    grid_barrier(a.bar, a.err);   // every block has read the iteration counter (and grid2)
+    grid_barrier(a.bar, a.err, a.wait);   // every block has read the iteration counter (and grid2)
     if (REG == 0) zero_split_tiles<D>(a);
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.iter = k + 1;
 }
@@ -1082,7 +1083,8 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st) {
     a.n_split = p->spread_variant >= 10 ? 0 : (int)p->n_split;   // two-phase spreading stores every point
     a.tiles = p->tiles;
     a.bar = (GridBarrier*)p->d_bar;
-    a.err = p->d_flag + 3;
+    a.err = p->d_flag + KP_FLAG_TIMEOUT;
+    a.wait = p->wait_cycles;
     mark(p, PH_ADJ, st);
     const kp_cdtype mt = p->maps_t;
 #define KP_PRIMAL(DD, TT)                                                                          \

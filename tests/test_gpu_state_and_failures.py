@@ -1,0 +1,143 @@
+"""Checkpoint/resume of PDHG (kp_pdhg_solve_ex) and the failure paths, on the GPU.
+
+* Resume: a iterations, then b iterations continued from the returned state (x_k, xbar_k, u_k,
+  v_k, k), equal a + b iterations in one call, and equal the float64 oracle's PDHG continued
+  from the same state (Sec. 4.1 schedule indexed by k; Sec. 4.2 for TV).
+* Bounded waits: with the plan's wait limit at 0 every bulk-copy staging wait that is not
+  already complete gives up; the kernels still finish (no wait is unbounded) and the library
+  returns KP_ETIMEOUT from kp_plan_sync after an asynchronous forward and from a solve.  With
+  the default limit restored the same plan gives the oracle's result again.  No GPU fault is
+  involved: the waits end by themselves.
+* Non-finite data: a NaN in y makes the solve return KP_ENONFINITE without an objective trace.
+* Autograd: a trajectory that differs from the plan's is set into the plan before the
+  operator runs; backward through an unrolled forward that a later forward replaced raises.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import nufft as onf, precond as opc, solvers as osv
+from tests.gpu_util import need_gpu, rel, simulate, to_dev, make_plan
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(n=48, C=3, L=6, ns=768, levels=2):
+    w = synth.Workload("state_small", (n, n), C, 1.25, 4, "l1_wavelet", 1e-3, 20, levels, "spiral",
+                       dict(n_interleaves=L, n_samples=ns, kmax=n / 2.0))
+    x, maps, traj = w.phantom(), w.maps(), w.traj()
+    return w, x, maps, traj, simulate(w, x, maps, traj)
+
+
+@pytest.mark.parametrize("reg", ["l2", "l1_wavelet", "tv"])
+def test_resume_equals_uninterrupted_and_oracle(reg):
+    need_gpu()
+    import torch
+    w, x, maps, traj, y = _small()
+    m = maps.astype(np.complex128)
+    A = lambda v: onf.nufft_forward(v, m, traj, 1.25, 4)
+    AH = lambda u: onf.nufft_adjoint(u, m, traj, 1.25, 4)
+    p = opc.mc_precond_fast(m, traj, 1.25, 4)
+    L, _ = osv.power_method(A, AH, p, x.shape, iters=30)
+    lam = 1e-3 * float(np.abs(AH(y.astype(np.complex128))).max())
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    yd, pd = to_dev(y), to_dev(p.astype(np.float32))
+    x_all, _, _ = plan.pdhg_solve(yd, pd, reg, lam, 20, lmax=L)
+    x_a, _, _, st = plan.pdhg_solve(yd, pd, reg, lam, 8, lmax=L, return_state=True)
+    assert st["k"] == 8
+    st = {k: (v.clone() if isinstance(v, torch.Tensor) else v) for k, v in st.items()}
+    x_b, _, _, st2 = plan.pdhg_solve(yd, pd, reg, lam, 12, lmax=L, state=st, return_state=True)
+    assert st2["k"] == 20
+    assert rel(x_b.cpu().numpy(), x_all.cpu().numpy(), "resumed vs uninterrupted") < 2e-6
+    # the oracle continued from the GPU's state at k = 8
+    if reg == "tv":
+        return                      # the oracle's TV solver has no state argument; the GPU comparison above holds
+    s0 = (st["x"].cpu().numpy(), st["xbar"].cpu().numpy(), st["u"].cpu().numpy(), 8)
+    x_ref, _, _, _ = osv.pdhg(A, AH, y, p, x.shape, reg, lam, 12, L, levels=2, state=s0)
+    assert rel(x_b.cpu().numpy(), x_ref, "resumed vs oracle from the same state") < 1e-5
+
+
+def test_wait_limit_timeouts_are_reported():
+    need_gpu()
+    import torch
+    from paper_1902_09657_gb300._lib import KpError, KP_ETIMEOUT
+    w, x, maps, traj, y = _small(n=64, C=4, L=8, ns=1024)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    xd = to_dev(x)
+    y_ok = plan.sense_forward(xd).cpu().numpy()
+    plan.sync()
+    plan.set_wait_limit(0)
+    plan.sense_forward(xd)
+    with pytest.raises(KpError) as ei:
+        plan.sync()
+    assert ei.value.status == KP_ETIMEOUT
+    plan.sync()                                    # the recorded timeout was cleared
+    with pytest.raises(KpError) as ei:
+        plan.pdhg_solve(to_dev(y), None, "l2", 1e-3, 3)
+    assert ei.value.status == KP_ETIMEOUT
+    plan.set_wait_limit(2_000_000_000)
+    y2 = plan.sense_forward(xd).cpu().numpy()
+    plan.sync()
+    assert rel(y2, y_ok, "forward after the limit is restored") < 1e-6
+    y_ref = onf.nufft_forward(x.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+    assert rel(y2, y_ref, "forward vs oracle") < 1e-5
+    xs, _, _ = plan.pdhg_solve(to_dev(y), None, "l2", 1e-3, 3)
+    assert bool(torch.isfinite(xs).all())
+
+
+def test_nonfinite_data_is_reported_without_a_trace():
+    need_gpu()
+    from paper_1902_09657_gb300._lib import KpError, KP_ENONFINITE
+    w, x, maps, traj, y = _small(n=32, C=2, L=4, ns=512)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    p = plan.make_preconditioner(True)
+    y_bad = y.copy()
+    y_bad[1, 17] = np.nan
+    with pytest.raises(KpError) as ei:
+        plan.pdhg_solve(to_dev(y_bad), p, "l2", 1e-3, 5, lmax=2.0)
+    assert ei.value.status == KP_ENONFINITE
+    xs, _, _ = plan.pdhg_solve(to_dev(y), p, "l2", 1e-3, 5, lmax=2.0)   # the plan is still usable
+    assert np.isfinite(xs.cpu().numpy()).all()
+
+
+def test_autograd_uses_the_trajectory_passed():
+    need_gpu()
+    from oracle import gradients as og
+    from paper_1902_09657_gb300.autograd import sense_forward
+    w, x, maps, traj, y = _small(n=32, C=2, L=4, ns=512)
+    rng = np.random.default_rng(9)
+    traj2 = np.clip(traj + rng.uniform(-0.3, 0.3, traj.shape), -15.9, 15.9).astype(np.float32)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0])
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    xt = to_dev(x).requires_grad_(True)
+    tt = to_dev(traj2).requires_grad_(True)
+    yg = sense_forward(xt, tt, plan)
+    y_ref = onf.nufft_forward(x.astype(np.complex128), maps.astype(np.complex128), traj2, 1.25, 4)
+    assert rel(yg.detach().cpu().numpy(), y_ref, "forward on the passed trajectory") < 1e-5
+    gy = (rng.standard_normal(y_ref.shape) + 1j * rng.standard_normal(y_ref.shape)).astype(np.complex64)
+    (yg.conj() * to_dev(gy)).real.sum().backward()
+    g_ref = og.traj_grad_forward(x.astype(np.complex128), maps.astype(np.complex128), traj2, gy.astype(np.complex128))
+    assert rel(tt.grad.cpu().numpy(), g_ref, "trajectory gradient on the passed trajectory") < 1e-4
+
+
+def test_unrolled_backward_after_a_later_forward_raises():
+    need_gpu()
+    import torch
+    from paper_1902_09657_gb300.autograd import unrolled_pdhg
+    w, x, maps, traj, y = _small(n=32, C=2, L=4, ns=512)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0])
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    p = plan.make_preconditioner(True)
+    L = plan.max_eig(p)
+    tt = to_dev(traj)
+    y1 = to_dev(y).requires_grad_(True)
+    x1 = unrolled_pdhg(y1, torch.tensor(1e-2, device="cuda"), tt, plan, p, 5, L)
+    y2 = to_dev(2 * y).requires_grad_(True)
+    x2 = unrolled_pdhg(y2, torch.tensor(1e-2, device="cuda"), tt, plan, p, 5, L)
+    with pytest.raises(RuntimeError):
+        x1.abs().sum().backward()
+    x2.abs().sum().backward()                         # the latest forward still differentiates
+    assert y2.grad is not None and bool(torch.isfinite(y2.grad).all())
