@@ -39,7 +39,7 @@ import synth  # noqa: E402
 WORKLOAD = "ute3d_192"
 # (maps storage, measurement storage) of each timed workload: the 3D workload keeps its coil
 # maps in FP16 (FP32 arithmetic); the others are plain complex64
-STORAGE = {"ute3d_192": ("fp16", "c64")}
+STORAGE = {"ute3d_192": ("fp16", "c64"), "ute3d_160": ("fp16", "c64")}
 
 
 def storage_of(w):
@@ -357,10 +357,25 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
 # kernel code it was taken on; drop it when its kernel changes until it is captured again.
 NCU_TRAFFIC = {}
 
-# Relative l2 errors against the float64 oracle measured by the GPU parity tests (test id and
-# value) for the forms reported beside the plain solver.  Filled from the tests' error log of a
-# GPU run of this tree; the tests themselves hold the pass/fail tolerances.
-ORACLE_ERRORS = {}
+# Relative l2 errors against the float64 oracle measured by the GPU parity tests for the forms
+# reported beside the plain solver (the largest value each test logged, KPDHG_PARITY_LOG, on a
+# GB300 with the spreading and interpolation kernels of this tree).  "stored inputs": oracle fed
+# the same 16-bit values; "storage error": oracle on the unrounded inputs.  The tests hold the
+# pass/fail tolerances (1e-5 float32, 2e-3 storage).
+ORACLE_ERRORS = {
+    "ute3d_192_operators": {"forward": 3.06e-07, "adjoint": 7.99e-07,
+                            "test": "test_gpu_nufft.py::test_forward_adjoint_3d_ute_full_size (every sample)"},
+    "fp16_maps_3d_pdhg": {"stored_inputs": 3.08e-07, "storage_error": 1.2e-04,
+                          "test": "test_gpu_pdhg.py::test_pdhg_3d_fp16_maps (16^3 x 3 coils, 20 l1 iterations)"},
+    "spiral2d_256_pdhg_100": {"x": 3.68e-07, "test": "test_gpu_pdhg.py::test_pdhg_full_chain_workloads (GPU p and L)"},
+    "bf16_kspace_fp16_maps_pdhg": {"stored_inputs": 3.19e-07, "storage_error": 3.92e-04,
+                                   "test": "test_gpu_pdhg.py::test_pdhg_half_storage[bf16-fp16] (64^2 x 4, 30 l1 its)"},
+    "batched_bf16_kspace": {"stored_inputs": 6.96e-07, "storage_error": 1.23e-03,
+                            "test": "test_gpu_batch.py::test_batch_uneven_bf16_kspace_against_oracle (3 uneven cases)"},
+    "batched_c64": {"x": 1.42e-06, "test": "test_gpu_batch.py::test_batch_matches_oracle_and_single_solves"},
+    "unrolled_grad": {"x": 2.67e-07, "dL_dy": 1.42e-06, "dL_dtraj": 1.04e-06,
+                      "test": "test_gpu_autograd.py::test_unrolled_gradients_match_oracle"},
+}
 
 
 def _peaks():
@@ -510,15 +525,19 @@ def setup_and_solve(rc, stream):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     plan.set_trajectory(rc.traj_d).set_maps(rc.maps_d)
     torch.cuda.synchronize()
-    e0, e1, e2 = ev(), ev(), ev()
+    e0, ea, eb, e1, e2 = ev(), ev(), ev(), ev(), ev()
     e0.record(stream)
     plan.set_trajectory(rc.traj_d).set_maps(rc.maps_d)
+    ea.record(stream)
     p = plan.make_preconditioner(True)
+    eb.record(stream)
     L = plan.max_eig(p, iters=30)
     e1.record(stream)
     plan.pdhg_solve(rc.y_d, p, w.reg, rc.lam, w.iters, lmax=L)
     e2.record(stream)
     e2.synchronize()
+    rc.setup_parts = {"trajectory_and_maps_ms": e0.elapsed_time(ea), "preconditioner_ms": ea.elapsed_time(eb),
+                      "power_method_ms": eb.elapsed_time(e1)}
     return p, L, e0.elapsed_time(e1), e1.elapsed_time(e2)
 
 
@@ -599,6 +618,7 @@ def gpu_extras(rc, stream, flush, args, world):
     out["e2e"] = e2e_through_api(rc, stream, flush, max(1, min(args.steps, 5)))
     p, L, setup_ms, solve_ms = setup_and_solve(rc, stream)
     out["setup_ms"] = setup_ms
+    out["setup_parts"] = rc.setup_parts
     out["solve_only_iters_per_s"] = w.iters / (solve_ms / 1e3)
     ph = phase_profile(rc, p, L, 5 if w.name == "ute3d_192" else w.iters)
     out["roofline"], out["phase_per_iter"] = roofline(rc, ph)
@@ -650,23 +670,7 @@ def side_spiral(dev, stream, flush):
     res["roofline"], res["phase_per_iter"] = roofline(rc, ph)
     res["spread_config"] = plan.spread_config()
     res["time_to_1e-3"] = time_to_accuracy(rc, p, L, setup_ms, solve_ms, 400)
-    traces = {}
-    for name in ("none", "single_channel", "multi_channel"):
-        pp = torch.ones((rc.C, rc.M), dtype=torch.float32, device=dev) if name == "none" else \
-            plan.make_preconditioner(name == "multi_channel")
-        Lp = plan.max_eig(pp, iters=30)
-        _, trc, _ = plan.pdhg_solve(rc.y_d, pp, w.reg, rc.lam, 300, lmax=Lp, trace=True)
-        traces[name] = (list(trc), Lp)
-    Fs = min(min(t) for t, _ in traces.values())
-    conv = {}
-    for name, (trc, Lp) in traces.items():
-        rel_obj = [(f - Fs) / abs(Fs) for f in trc]
-        conv[name] = {"lmax": Lp,
-                      "iters_to_1e-2": next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-2), None),
-                      "iters_to_1e-3": next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-3), None),
-                      "rel_obj_at_30": rel_obj[29], "rel_obj_at_300": rel_obj[-1]}
-    conv["F_star"] = Fs
-    res["convergence_by_preconditioner"] = conv
+    res["comparison_sec6"] = method_comparison(rc, stream, flush, 300)
     plan.pdhg_solve(rc.y_d, p, "tv", rc.lam, w.iters, lmax=L)
     tv_ms = _timed(lambda: plan.pdhg_solve(rc.y_d, p, "tv", rc.lam, w.iters, lmax=L), stream, flush, 3)
     res["tv_solve_only"] = {"iters": w.iters, "ms": tv_ms, "iters_per_s": w.iters / (tv_ms * 1e-3),
@@ -682,11 +686,52 @@ def side_spiral(dev, stream, flush):
 
 
 def side_radial(dev, stream, flush):
-    """2D golden-angle radial l2 (128^2 x 4 coils, 64 x 256, alpha 2, 30 iterations)."""
+    """2D golden-angle radial l2 (128^2 x 4 coils, 64 x 256, alpha 2, 30 iterations), with the
+    comparison of Sec. 6 (CG, circulant-preconditioned CG, FISTA, PDHG without preconditioner,
+    single- and multi-channel)."""
     rc, p, L, setup_ms, solve_ms, res = whole_reconstruction("radial2d_128", dev, stream, flush, reps=10)
     res["time_to_1e-3"] = time_to_accuracy(rc, p, L, setup_ms, solve_ms, 400)
+    res["comparison_sec6"] = method_comparison(rc, stream, flush, 300)
     rc.close()
     return res
+
+
+def method_comparison(rc, stream, flush, iters):
+    """Sec. 6's comparison on one workload: objective traces of `iters` iterations of every
+    method, F* the least objective any reaches; per method the iterations and the time to a
+    relative objective (F - F*)/|F*| of 1e-2 and 1e-3, and the time per iteration (untraced
+    solves, L2 flushed).  Set-up (preconditioners, power method) is timed separately."""
+    import torch
+    w, plan, dev = rc.w, rc.plan, rc.dev
+    y, lam, reg = rc.y_d, rc.lam, w.reg
+    runs = {}
+    for name in ("none", "single_channel", "multi_channel"):
+        pp = torch.ones((rc.C, rc.M), dtype=torch.float32, device=dev) if name == "none" else \
+            plan.make_preconditioner(name == "multi_channel")
+        Lp = plan.max_eig(pp, iters=30)
+        _, trc, _ = plan.pdhg_solve(y, pp, reg, lam, iters, lmax=Lp, trace=True)
+        t = _timed(lambda: plan.pdhg_solve(y, pp, reg, lam, 50, lmax=Lp), stream, flush, 3) / 50
+        runs["pdhg_" + name] = (list(trc), t, {"lmax": Lp})
+    if reg == "l2":
+        for name, circ in (("cg", False), ("cg_circulant", True)):
+            plan.circulant_preconditioner()
+            _, trc = plan.cg_l2_solve(y, lam, iters, circulant=circ)
+            t = _timed(lambda: plan.cg_l2_solve(y, lam, 50, circulant=circ, trace=False), stream, flush, 3) / 50
+            runs[name] = (list(trc), t, {})
+    La = 1.01 * plan.max_eig(None, iters=30)
+    _, trc = plan.fista_solve(y, reg, lam, iters, lmax=La)
+    t = _timed(lambda: plan.fista_solve(y, reg, lam, 50, lmax=La, trace=False), stream, flush, 3) / 50
+    runs["fista"] = (list(trc), t, {"L": La})
+    Fs = min(min(tr) for tr, _, _ in runs.values())
+    out = {"F_star": Fs, "F_star_source": f"least objective of {iters} iterations of every method (float32 GPU)",
+           "iters": iters}
+    for name, (trc, t, extra) in runs.items():
+        rel_obj = [(f - Fs) / abs(Fs) for f in trc]
+        k2 = next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-2), None)
+        k3 = next((i + 1 for i, r in enumerate(rel_obj) if r < 1e-3), None)
+        out[name] = dict(extra, ms_per_iter=t, iters_to_1e_2=k2, iters_to_1e_3=k3,
+                         ms_to_1e_3=None if k3 is None else k3 * t, rel_obj_at_30=rel_obj[min(29, len(rel_obj) - 1)])
+    return out
 
 
 def _measure_y(plan, x, gen):

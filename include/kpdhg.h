@@ -213,6 +213,36 @@ kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const
 kp_status kp_dual_l2_solve(kp_plan plan, const void* y_dev, const float* p_dev, float lambda, int iters,
                            void* x_dev, double* res_trace, void* stream);
 
+/* Comparison systems of Sec. 6 (the experiments compare PDHG with the proposed k-space
+ * preconditioners against CG, CG with a circulant preconditioner and FISTA).
+ *
+ * l2-optimised circulant preconditioner (App. B): P = argmin over circulant P of
+ * ||A^H A - P||_F^2, P[m, n] = c[(m - n) mod N] per axis, c[k] = 1/N sum over s in {0,1}^ndim
+ * of r[k - s N] h[k - s N] with r[d] = N^{-1/2} sum_c sum_{m - n = d} s_c^*[m] s_c[n] (FFTs on the
+ * 2N grid, float64 sums) and h the point-spread function of Sec. 5.1.  The 1/N is the average
+ * over a circulant diagonal that the appendix's closed form leaves out (a uniform scale).  Kept in
+ * the plan as the eigenvalues of P (the DFT of c); eig_dev: float32 [N] copy of them, or NULL.
+ * Recomputed after a new trajectory or new maps.  Synchronous. */
+kp_status kp_make_circulant_preconditioner(kp_plan plan, float* eig_dev, void* stream);
+
+/* Conjugate gradients on (A^H A + lambda I) x = A^H y (the l2 problem of Eq. obj), from x = 0,
+ * plain (circulant = 0) or preconditioned by P + lambda I with P the circulant above
+ * (circulant = 1; computed first if the plan holds none for its trajectory and maps).
+ * y_dev complex64 [C][M] (trajectory order); x_dev complex64 [N] out; obj_trace host double[iters]
+ * receiving F(x_k) = 1/2 ||A x_k - y||^2 + lambda/2 ||x_k||^2 after each iteration (A x_k kept by
+ * recurrence), or NULL.  Uses the plan's PDHG work buffers.  Synchronous.
+ * Errors: KP_EINVAL, KP_ENONFINITE (objective not finite), KP_ETIMEOUT. */
+kp_status kp_cg_l2_solve(kp_plan plan, const void* y_dev, float lambda, int iters, int circulant, void* x_dev,
+                         double* obj_trace, void* stream);
+
+/* FISTA (Beck & Teboulle) on 1/2 ||A x - y||^2 + g(x), g = lambda ||x||^2/2 (KP_REG_L2) or
+ * lambda ||W x||_1 (KP_REG_L1_WAVELET), from x_0 = z_0 = 0, t_0 = 1, step 1/L with L = lmax, or,
+ * for lmax <= 0, 1.01 x the 30-iteration power-method estimate of lambda_max(A^H A).
+ * y_dev complex64 [C][M]; x_dev complex64 [N] out; obj_trace host double[iters] or NULL (an extra
+ * forward NUFFT per iteration).  Uses the plan's PDHG work buffers.  Synchronous. */
+kp_status kp_fista_solve(kp_plan plan, const void* y_dev, kp_reg reg, float lambda, int iters, double lmax,
+                         void* x_dev, double* obj_trace, void* stream);
+
 /* Trajectory gradient through y = A x (differentiable reconstruction; Sec. 6 operator with the
  * Kaiser-Bessel derivative phi'): gtraj[i][d] = Re sum_c conj(gy_c[i]) d y_c[i] / d f_{i,d},
  * taps held fixed (y jumps where a coordinate crosses a grid line, at the window edge).

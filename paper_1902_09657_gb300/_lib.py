@@ -69,6 +69,11 @@ _SIGS = {
                                         ctypes.c_double, ctypes.POINTER(KpState), ctypes.POINTER(KpState),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(KpStats), _vp]),
     "kp_plan_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "kp_make_circulant_preconditioner": (ctypes.c_int, [_vp, _vp, _vp]),
+    "kp_cg_l2_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_int, ctypes.c_int, _vp,
+                                      ctypes.POINTER(ctypes.c_double), _vp]),
+    "kp_fista_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_double, _vp,
+                                      ctypes.POINTER(ctypes.c_double), _vp]),
     "kp_plan_sync": (ctypes.c_int, [_vp, _vp]),
     "kp_wavelet": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "kp_plan_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),

@@ -292,6 +292,37 @@ class Plan:
             return out_t + (new_state,)
         return out_t
 
+    def circulant_preconditioner(self):
+        """Eigenvalues (float32 [*img]) of the App. B l2-optimised circulant preconditioner."""
+        out = torch.empty(self.img_shape, dtype=torch.float32, device=self.device)
+        L.check(self.lib.kp_make_circulant_preconditioner(self._h, _ptr(out), _stream(self.device)),
+                "kp_make_circulant_preconditioner")
+        return out
+
+    def cg_l2_solve(self, y, lam, iters, circulant=False, trace=True):
+        """CG on (A^H A + lam I) x = A^H y, plain or circulant-preconditioned (App. B).
+        Returns (x, objective trace or None)."""
+        yd = self._dev(y, "y")
+        if yd.dtype != torch.complex64 or tuple(yd.shape) != (self.ncoils, self.nsamples):
+            raise ValueError("y must be complex64 [C, M]")
+        x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
+        tr = (ctypes.c_double * max(int(iters), 1))() if trace else None
+        L.check(self.lib.kp_cg_l2_solve(self._h, _ptr(yd), float(lam), int(iters), int(bool(circulant)), _ptr(x), tr,
+                                        _stream(self.device)), "kp_cg_l2_solve")
+        return x, (list(tr)[: int(iters)] if trace else None)
+
+    def fista_solve(self, y, reg, lam, iters, lmax=0.0, trace=True):
+        """FISTA for reg "l2" or "l1_wavelet" with step 1/lmax (lmax <= 0: estimated).
+        Returns (x, objective trace or None)."""
+        yd = self._dev(y, "y")
+        if yd.dtype != torch.complex64 or tuple(yd.shape) != (self.ncoils, self.nsamples):
+            raise ValueError("y must be complex64 [C, M]")
+        x = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
+        tr = (ctypes.c_double * max(int(iters), 1))() if trace else None
+        L.check(self.lib.kp_fista_solve(self._h, _ptr(yd), _REG[reg], float(lam), int(iters), float(lmax), _ptr(x), tr,
+                                        _stream(self.device)), "kp_fista_solve")
+        return x, (list(tr)[: int(iters)] if trace else None)
+
     def set_wait_limit(self, cycles):
         """Limit (SM clock cycles) of every bounded device wait of this plan's kernels."""
         L.check(self.lib.kp_plan_set_wait_limit(self._h, int(cycles)), "kp_plan_set_wait_limit")

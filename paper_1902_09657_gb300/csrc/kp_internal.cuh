@@ -279,6 +279,8 @@ struct kp_plan_s {
     double* d_cg_trace = nullptr;    // residual norms of the last dual solve
     int64_t cg_cap = 0, cg_trace_cap = 0;
     int4* d_sort_tmp = nullptr;      // [8192] scratch of the item sort
+    void* d_lsort = nullptr;         // scratch of the counting sort of longer item lists
+    size_t lsort_cap = 0;
     int* d_split = nullptr;          // tiles whose list spans several work items
     int64_t n_split = 0, split_cap = 0;
     int* d_k0 = nullptr;             // [D][M] wrapped first tap ceil(t) - W/2 per sorted sample
@@ -353,6 +355,17 @@ struct kp_plan_s {
     kp_plan_s* pre_nufft = nullptr;  // NUFFT plan on the 2N image (preconditioner)
     cudaStream_t cap_stream = nullptr;
     long long wait_cycles = 2000000000LL;   // limit of every bounded device wait (SM clock cycles)
+    // comparison solvers of Sec. 6 (kp_compare.cu): App. B circulant preconditioner, CG, FISTA
+    float* d_circ_eig = nullptr;     // [N] eigenvalues of the circulant P (real part of the DFT of its kernel)
+    float2* d_circ = nullptr;        // [N] its kernel c[k], k_d in [0, N_d)
+    bool circ_ok = false;            // eigenvalues valid for the current trajectory and maps
+    int circ_version = -1;
+    cufftHandle fft_img = 0;         // N-point C2C on the image (circulant products)
+    bool fft_img_ok = false;
+    float2* d_cmp = nullptr;         // [2][N] image work vectors of CG and FISTA
+    double* d_cmp_s = nullptr;       // [16] their device scalars
+    double* d_cmp_trace = nullptr;   // objective trace of the last comparison solve
+    int cmp_trace_cap = 0;
 };
 
 namespace kp {
@@ -400,9 +413,16 @@ bool cluster_prox_ok(kp_plan p);
 kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st);
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
                       cudaStream_t st, int reg = 0, const kp_pdhg_state* start = nullptr);
+kp_status solve_setup_a(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, int iters, cudaStream_t st,
+                        const kp_pdhg_state* start);
+kp_status solve_setup_b(kp_plan plan, int iters, cudaStream_t st, int reg, const kp_pdhg_state* start);
+kp_status power_begin(kp_plan p, cudaStream_t st);
+kp_status power_step(kp_plan p, const float* ps_sorted, bool first, cudaStream_t st);
+kp_status power_end(kp_plan p, cudaStream_t st);
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status pdhg_iteration_concurrent(kp_plan p, int reg, float lambda, cudaStream_t st);
 kp_status build_spread_items(kp_plan p, int chunk, cudaStream_t st);
+kp_status build_spread_lists(kp_plan p, cudaStream_t st);
 kp_status make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st);
 kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);
@@ -415,5 +435,13 @@ void drop_graphs(kp_plan p);
 
 // kp_precond.cu
 void pre_destroy(kp_plan p);
+kp_status circulant_enqueue(kp_plan plan, cudaStream_t st);
+kp_status ensure_fft_img(kp_plan p);
+
+// kp_compare.cu
+void compare_destroy(kp_plan p);
+// Reports a bounded device wait that gave up: clears the plan's timeout flag (so the report is
+// consumed once), records `what` as the error message and returns KP_ETIMEOUT.
+kp_status report_timeout(kp_plan p, cudaStream_t st, const char* what);
 
 }  // namespace kp

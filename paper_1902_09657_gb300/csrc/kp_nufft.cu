@@ -255,12 +255,15 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
     // grid row offsets of the staged region along the slower axes (periodic), computed once
     __shared__ int rowoff[MAXD][R];
     if (threadIdx.x < (D - 1) * R) {
+        // axis d < D - 1 without indexing the parameter structs by a thread-dependent d
         const int d = threadIdx.x / R, l = threadIdx.x % R;
-        int pp = o[d] + l;
-        while (pp >= geo.g[d]) pp -= geo.g[d];
-        int64_t stride = 1;
-        for (int e = d + 1; e < D; ++e) stride *= geo.g[e];
-        rowoff[d][l] = (int)(tunshift(pp, tl.sh[d], geo.g[d]) * stride);
+        const int gd = d == 0 ? geo.g[0] : geo.g[1];
+        const int sd = d == 0 ? tl.sh[0] : tl.sh[1];
+        const int od = d == 0 ? o[0] : o[1 % D];
+        const int stride = D == 3 ? (d == 0 ? geo.g[1] * geo.g[2] : geo.g[2]) : (d == 0 ? geo.g[1] : 1);
+        int pp = od + l;
+        while (pp >= gd) pp -= gd;
+        rowoff[d][l] = tunshift(pp, sd, gd) * stride;
     }
     // first staged x (unshifted), rounded down to even; xo = its parity
     const int gx = geo.g[D - 1];
@@ -324,36 +327,35 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
         return;
     }
     if (!act) return;
+    // all coils of the group tap by tap: each tap's weight is formed once (no table of 64 weight
+    // products held across coils); each coil's sum runs over the taps in the same order
+    float2 accs[IP_CH];
+#pragma unroll
+    for (int c = 0; c < IP_CH; ++c) accs[c] = make_float2(0.f, 0.f);
+    const float2* base = sg + lb;
+#pragma unroll
+    for (int a = 0; a < KW; ++a)
+#pragma unroll
+        for (int b = 0; b < KW; ++b) {
+            const float wab = w[0][a] * w[1][b];
+#pragma unroll
+            for (int e = 0; e < (D == 2 ? 1 : KW); ++e) {
+                const float ww = D == 2 ? wab : wab * w[D - 1][e];
+                const int off = D == 2 ? a * rs0 + b : a * rs0 + b * rs1 + e;
+#pragma unroll
+                for (int c = 0; c < IP_CH; ++c) {
+                    if (c < cc) {
+                        const float2 v = base[c * Rtot + off];
+                        accs[c].x = fmaf(ww, v.x, accs[c].x);
+                        accs[c].y = fmaf(ww, v.y, accs[c].y);
+                    }
+                }
+            }
+        }
 #pragma unroll
     for (int c = 0; c < IP_CH; ++c) {
         if (c >= cc) break;
-        const float2* base = sg + c * Rtot + lb;
-        float2 acc = make_float2(0.f, 0.f);
-        if (D == 2) {
-#pragma unroll
-            for (int a = 0; a < KW; ++a)
-#pragma unroll
-                for (int b = 0; b < KW; ++b) {
-                    const float ww = w[0][a] * w[D - 1][b];
-                    const float2 v = base[a * rs0 + b];
-                    acc.x = fmaf(ww, v.x, acc.x);
-                    acc.y = fmaf(ww, v.y, acc.y);
-                }
-        } else {
-#pragma unroll
-            for (int a = 0; a < KW; ++a)
-#pragma unroll
-                for (int b = 0; b < KW; ++b) {
-                    const float wab = w[0][a] * w[1 % D][b];
-#pragma unroll
-                    for (int e = 0; e < KW; ++e) {
-                        const float ww = wab * w[D - 1][e];
-                        const float2 v = base[a * rs0 + b * rs1 + e];
-                        acc.x = fmaf(ww, v.x, acc.x);
-                        acc.y = fmaf(ww, v.y, acc.y);
-                    }
-                }
-        }
+        float2 acc = accs[c];
         acc.x *= geo.rsqrtN;
         acc.y *= geo.rsqrtN;
         const size_t os = (size_t)(c0 + c) * geo.M + s;
@@ -906,6 +908,9 @@ constexpr int OT_RS = 12;                      // float4 per padded row: x padde
 constexpr int OT_PS = PT * OT_RS;              // lanes (4 consecutive x, 2 rows) hit 8 different bank groups
 constexpr int OT_PAIR = PT * OT_PS;            // float4 per coil pair
 constexpr int OT_CHUNK = 128;                  // samples staged at a time
+// slot layout of a padded tile per coil: rows of SL_RS points (x padded from 11 to 12, so a row
+// is 96 bytes and the 8 points a gather warp reads from it sit in two aligned 32-byte sectors)
+constexpr int SL_RS = 12, SL_PS = PT * SL_RS, SL_P = PT * SL_PS;
 
 template <int NP>
 static size_t spread_own_smem() {
@@ -975,27 +980,38 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
                 for (int b = 0; b < KW; ++b) swyx[i * KW * KW + a * KW + b] = wy[a] * wx[b];
         }
         __syncthreads();
-        if (live) {
+        if (live && n > 0) {
             int run = -1;                                            // current run's key (sb value), warp-uniform
             float4* dst = nullptr;
             float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            // sample i's staged values are in registers before its turn: the loads of sample
+            // i + 1 are issued ahead of sample i's shared-memory update
+            int b = sb[0];
+            float wz = swz[((par ^ b) & 1) + 2 * jsel], wyx = swyx[yx];
+            float4 uv = su[pair];
             for (int i = 0; i < n; ++i) {
-                const int b = sb[i];
-                const int jzb = (par ^ b) & 1;                       // planes z0 + jz of this warp's parity: jz = jzb, jzb + 2
-                if (b != run) {
+                const int bi = b;
+                const float w = wz * wyx;
+                const float4 ui = uv;
+                if (i + 1 < n) {
+                    b = sb[i + 1];
+                    wz = swz[(i + 1) * KW + ((par ^ b) & 1) + 2 * jsel];
+                    wyx = swyx[(i + 1) * KW * KW + yx];
+                    uv = su[(i + 1) * NP + pair];
+                }
+                if (bi != run) {
                     if (dst) {
                         float4 v = *dst;
                         v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
                         *dst = v;
                     }
-                    run = b;
-                    dst = mine + (b >> 1) + jzb * OT_PS;
+                    run = bi;
+                    // planes z0 + jz of this warp's parity: jz = jzb, jzb + 2
+                    dst = mine + (bi >> 1) + ((par ^ bi) & 1) * OT_PS;
                     r = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                const float w = swz[i * KW + jzb + 2 * jsel] * swyx[i * KW * KW + yx];
-                const float4 uv = su[i * NP + pair];
-                r.x = fmaf(w, uv.x, r.x); r.y = fmaf(w, uv.y, r.y);
-                r.z = fmaf(w, uv.z, r.z); r.w = fmaf(w, uv.w, r.w);
+                r.x = fmaf(w, ui.x, r.x); r.y = fmaf(w, ui.y, r.y);
+                r.z = fmaf(w, ui.z, r.z); r.w = fmaf(w, ui.w, r.w);
             }
             if (dst) {
                 float4 v = *dst;
@@ -1005,27 +1021,30 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
         }
     }
     __syncthreads();
-    // padded tile -> slot, coil-major: halo[(slot * C + c) * PT3 + point]
+    // padded tile -> slot, coil-major: halo[(slot * C + c) * SL_P + (z * PT + y) * SL_RS + x]
+    // (the accumulator rows have the slot's row length, so the copy is row for row)
+    static_assert(OT_RS == SL_RS, "accumulator and slot rows have the same length");
     const int npair = (cc + 1) / 2;
-    for (int i = threadIdx.x; i < npair * PT3; i += NT) {
-        const int k = i / PT3, pt = i - k * PT3;
-        const int z = pt / (PT * PT), y = (pt / PT) % PT, x = pt % PT;
-        const float4 v = acc[k * OT_PAIR + z * OT_PS + y * OT_RS + x];
-        float2* d0 = halo + ((size_t)slot * geo.C + c0 + 2 * k) * PT3 + pt;
+    for (int i = threadIdx.x; i < npair * SL_P; i += NT) {
+        const int k = i / SL_P, pt = i - k * SL_P;
+        if (pt % SL_RS >= PT) continue;                             // the row's padding point
+        const float4 v = acc[k * OT_PAIR + pt];
+        float2* d0 = halo + ((size_t)slot * geo.C + c0 + 2 * k) * SL_P + pt;
         *d0 = make_float2(v.x, v.y);
-        if (2 * k + 1 < cc) d0[PT3] = make_float2(v.z, v.w);
+        if (2 * k + 1 < cc) d0[SL_P] = make_float2(v.z, v.w);
     }
 }
 
-// Phase B: one CTA per tile (empty tiles included, so every grid point is stored once).  For the
-// tile and its 7 lower neighbours (periodic) the CTA first looks up their slot ranges and the
-// padded offset at which the neighbour's halo meets this tile; then each thread takes (coil,
-// point) pairs of the tile and sums the slots that cover the point.
+// Phase B: one CTA per (tile, coil) (empty tiles included, so every grid point is stored once):
+// the work of a tile with many slots spreads over C CTAs.  The CTA first looks up the slot
+// ranges of the tile and its 7 lower neighbours (periodic) and the padded offset at which a
+// neighbour's halo meets this tile; then each thread sums, for its points, the slots that cover
+// them, four slots at a time into independent sums so the loads overlap.
 __global__ void __launch_bounds__(256)
 k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
               float2* __restrict__ grid) {
     __shared__ int nb_beg[8], nb_end[8], nb_off[8], org[3], ext[3];
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x, c = blockIdx.y;
     if (threadIdx.x < 8) {
         const int m = threadIdx.x;
         const int nt0 = tl.nt[0], nt1 = tl.nt[1], nt2 = tl.nt[2];
@@ -1038,7 +1057,7 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
         const int nb = (n0 * nt1 + n1) * nt2 + n2;
         nb_beg[m] = tslot[nb];
         nb_end[m] = tslot[nb + 1];
-        nb_off[m] = (b0 ? min(ts0, geo.g[0] - n0 * ts0) * PT * PT : 0) + (b1 ? min(ts1, geo.g[1] - n1 * ts1) * PT : 0) +
+        nb_off[m] = (b0 ? min(ts0, geo.g[0] - n0 * ts0) * SL_PS : 0) + (b1 ? min(ts1, geo.g[1] - n1 * ts1) * SL_RS : 0) +
                     (b2 ? min(ts2, geo.g[2] - n2 * ts2) : 0);
         if (m == 0) {
             org[0] = t0 * ts0; org[1] = t1 * ts1; org[2] = t2 * ts2;
@@ -1047,25 +1066,32 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
     }
     __syncthreads();
     const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
-    const size_t cstride = (size_t)geo.C * PT3;
-    const int total = geo.C * 512;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int c = i >> 9, lz = (i >> 6) & 7, ly = (i >> 3) & 7, lx = i & 7;
+    const size_t cstride = (size_t)geo.C * SL_P;
+    const float2* hc = halo + (size_t)c * SL_P;
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+        const int lz = i >> 6, ly = (i >> 3) & 7, lx = i & 7;
         if (lz >= e0 || ly >= e1 || lx >= e2) continue;
-        const int pt = (lz * PT + ly) * PT + lx;
+        const int pt = (lz * PT + ly) * SL_RS + lx;
         const int low = (lz < KW - 1 ? 4 : 0) | (ly < KW - 1 ? 2 : 0) | (lx < KW - 1 ? 1 : 0);
-        const float2* hc = halo + (size_t)c * PT3 + pt;
-        float2 sum = make_float2(0.f, 0.f);
-#pragma unroll
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+#pragma unroll 1
         for (int m = 0; m < 8; ++m) {
             if (m & ~low) continue;
-            const int e = nb_end[m], o = nb_off[m];
-            for (int sl = nb_beg[m]; sl < e; ++sl) {
-                const float2 v = hc[(size_t)sl * cstride + o];
-                sum.x += v.x;
-                sum.y += v.y;
+            const int e = nb_end[m];
+            const float2* src = hc + nb_off[m] + pt;
+            int sl = nb_beg[m];
+            for (; sl + 4 <= e; sl += 4) {
+                const float2 v0 = src[(size_t)sl * cstride], v1 = src[(size_t)(sl + 1) * cstride];
+                const float2 v2 = src[(size_t)(sl + 2) * cstride], v3 = src[(size_t)(sl + 3) * cstride];
+                s0.x += v0.x; s0.y += v0.y; s1.x += v1.x; s1.y += v1.y;
+                s2.x += v2.x; s2.y += v2.y; s3.x += v3.x; s3.y += v3.y;
+            }
+            for (; sl < e; ++sl) {
+                const float2 v = src[(size_t)sl * cstride];
+                s0.x += v.x; s0.y += v.y;
             }
         }
+        const float2 sum = make_float2((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y));
         const int gz = tunshift(org[0] + lz, tl.sh[0], geo.g[0]);
         const int gy = tunshift(org[1] + ly, tl.sh[1], geo.g[1]);
         const int gx = tunshift(org[2] + lx, tl.sh[2], geo.g[2]);
@@ -1773,7 +1799,7 @@ static kp_status launch_spread_own2(kp_plan p, const UT* u, const int* perm, cud
 template <int D, typename UT, int NP>
 static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cudaStream_t st) {
     const Geom& g = p->geo;
-    if (D != 3 || !p->d_halo || p->halo_cap < (size_t)p->n_oitems * g.C * PT3 || p->tiles.ts[0] > 8 ||
+    if (D != 3 || !p->d_halo || p->halo_cap < (size_t)p->n_oitems * g.C * SL_P || p->tiles.ts[0] > 8 ||
         p->tiles.ts[1] > 8 || p->tiles.ts[2] > 8) {
         set_error("two-phase spreading needs a 3D plan with tiles of at most 8 and its slot storage");
         return KP_EINTERNAL;
@@ -1786,7 +1812,7 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
             p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
     KP_LAUNCH_CHECK();
     mark(p, PH_SPREAD_RED, st);
-    k_halo_gather<<<(unsigned)p->tiles.ntiles, 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    k_halo_gather<<<dim3((unsigned)p->tiles.ntiles, (unsigned)g.C), 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
     KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;
@@ -1797,7 +1823,7 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
 static bool ensure_halo(kp_plan p) {
     const Geom& g = p->geo;
     if (p->n_oitems == 0) return false;
-    const size_t need = (size_t)p->n_oitems * g.C * (g.D == 3 ? PT3 : PT2SQ);
+    const size_t need = (size_t)p->n_oitems * g.C * (g.D == 3 ? SL_P : PT2SQ);
     if (p->d_halo && p->halo_cap >= need) return true;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
@@ -1839,6 +1865,7 @@ kp_status zero_split_only(kp_plan p, cudaStream_t st) {
     const Geom& g = p->geo;
     int P = 1;
     for (int d = 0; d < g.D; ++d) P *= p->tiles.ts[d];
+    if (p->spread_tuned && p->spread_variant >= 10) return KP_OK;   // two-phase spreading stores every point
     if (p->n_split > 0) {
         KP_DISPATCH_D(g.D, DD, k_zero_split<DD><<<(unsigned)p->n_split, 256, 0, st>>>(p->d_split, g, p->tiles, P,
                                                                                       p->d_grid2));
@@ -1910,8 +1937,12 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
 // with warp-private padded tiles (when their slot storage fits).  Larger items mean fewer split tiles (fewer global atomics) but fewer, longer CTAs.
 kp_status autotune_spread(kp_plan p, cudaStream_t st) {
     if (p->spread_tuned) {
-        // a new trajectory may need more slots than the two-phase variants hold
-        if (p->spread_variant >= 10 && !ensure_halo(p)) p->spread_variant = 0;
+        // a new trajectory may need more slots than the two-phase variants hold: fall back to the
+        // private-copy variant, whose lists were not built for a two-phase plan
+        if (p->spread_variant >= 10 && !ensure_halo(p)) {
+            p->spread_variant = 0;
+            KP_TRY(build_spread_lists(p, st));
+        }
         return KP_OK;
     }
     int force_v = -1, force_c = 0;

@@ -208,6 +208,8 @@ __global__ void k_unpermute_c64(const float2* __restrict__ in, float2* __restric
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
+__global__ void k_set_double(double* p, double v) { *p = v; }
+
 // flag = 1 if any of the n complex values is a NaN or an Inf
 __global__ void k_nonfinite(const float2* __restrict__ x, int64_t n, int* __restrict__ flag) {
     bool bad = false;
@@ -240,31 +242,42 @@ static kp_status reduce_norm2(kp_plan p, const float2* x, int64_t n, double* out
 // A^H P A to w / ||w|| without forming it: the forward pre-step reads w and the interpolation
 // divides by ||w||, taken from the device (the same vector up to rounding order); the norm
 // kernel also clears the split spreading tiles for the next spread.  L = ||w|| of the last
-// iteration, w = A^H P A v with v of unit norm.
-static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cudaStream_t st) {
+// iteration, w = A^H P A v with v of unit norm.  In three parts so that a batch can capture the
+// middle one for all its cases in one graph: begin (norm of the start vector), step (one
+// iteration; the first reads d_z, later ones d_w) and end (L = sqrt of the last norm).
+kp_status power_begin(kp_plan p, cudaStream_t st) {
+    KP_TRY(zero_split_only(p, st));
+    return reduce_norm2(p, p->d_z, p->geo.N, p->d_red, st);
+}
+
+kp_status power_step(kp_plan p, const float* ps_sorted, bool first, cudaStream_t st) {
     const Geom& g = p->geo;
     const int n_split = p->spread_variant >= 10 ? 0 : (int)p->n_split;   // 10-12 store every point
     const unsigned nb = (unsigned)std::min<int64_t>(nblk(g.N, 256), 1216);
-    KP_TRY(zero_split_only(p, st));
-    KP_TRY(reduce_norm2(p, p->d_z, g.N, p->d_red, st));
-    const float2* w = p->d_z;
-    for (int it = 0; it < iters; ++it) {
-        KP_TRY(forward_scaled(p, w, p->d_kt, ps_sorted, st, p->d_red));
-        KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st, /*splits_zeroed=*/true));
-        KP_TRY(grid_to_image(p, p->d_w, st));
-        KP_TRY_CUDA(cudaMemsetAsync(p->d_red, 0, sizeof(double), st));
-        if (g.D == 2)
-            k_norm2_clear<2><<<nb, 256, 0, st>>>(p->d_w, g.N, p->d_red, p->d_split, n_split, g, p->tiles, p->d_grid2);
-        else
-            k_norm2_clear<3><<<nb, 256, 0, st>>>(p->d_w, g.N, p->d_red, p->d_split, n_split, g, p->tiles, p->d_grid2);
-        KP_LAUNCH_CHECK();
-        p->launches += 1;
-        w = p->d_w;
-    }
+    KP_TRY(forward_scaled(p, first ? p->d_z : p->d_w, p->d_kt, ps_sorted, st, p->d_red));
+    KP_TRY(adjoint_to_grid(p, p->d_kt, KP_C64, nullptr, st, /*splits_zeroed=*/true));
+    KP_TRY(grid_to_image(p, p->d_w, st));
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_red, 0, sizeof(double), st));
+    if (g.D == 2)
+        k_norm2_clear<2><<<nb, 256, 0, st>>>(p->d_w, g.N, p->d_red, p->d_split, n_split, g, p->tiles, p->d_grid2);
+    else
+        k_norm2_clear<3><<<nb, 256, 0, st>>>(p->d_w, g.N, p->d_red, p->d_split, n_split, g, p->tiles, p->d_grid2);
+    KP_LAUNCH_CHECK();
+    p->launches += 1;
+    return KP_OK;
+}
+
+kp_status power_end(kp_plan p, cudaStream_t st) {
     k_store_sqrt<<<1, 1, 0, st>>>(p->d_red, p->d_schedd);
     KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;
+}
+
+static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cudaStream_t st) {
+    KP_TRY(power_begin(p, st));
+    for (int it = 0; it < iters; ++it) KP_TRY(power_step(p, ps_sorted, it == 0, st));
+    return power_end(p, st);
 }
 
 // One PDHG iteration (Sec. 4.1) from the forward grid of xbar already in d_grid:
@@ -380,13 +393,11 @@ kp_status ensure_tv_dual(kp_plan p) {
 // preconditioner in sorted order, min p, lambda_max (given, or 30 power iterations), the
 // step-size schedule, the initial iterates (zero, or a caller's state whose dual variable is
 // brought into sorted order) and the forward grid of xbar.
-kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st, int reg, const kp_pdhg_state* start) {
+kp_status solve_setup_a(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, int iters, cudaStream_t st,
+                        const kp_pdhg_state* start) {
     const Geom& g = plan->geo;
-    void* stream = (void*)st;
     const int k0 = start ? start->k : 0;
-    iters += k0;                       // the schedule runs from iteration 0; the run starts at k0
-    KP_TRY(ensure_sched(plan, std::max(iters, 1)));
+    KP_TRY(ensure_sched(plan, std::max(iters + k0, 1)));
     // measurements into sorted order
     plan->ys_t = y_t;
     if (y_t == KP_C64) k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>((const float2*)y_dev, (float2*)plan->d_ys, plan->d_perm, g.M, g.C);
@@ -412,14 +423,13 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
         KP_LAUNCH_CHECK();
     }
     plan->launches += 2;
-    // lambda_max(P A A^H)
-    if (lmax > 0) {
-        KP_TRY_CUDA(cudaMemcpyAsync(plan->d_schedd, &lmax, sizeof(double), cudaMemcpyHostToDevice, st));
-    } else {
-        KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st));
-        plan->launches += 1;
-        KP_TRY(power_method(plan, plan->d_ps, 30, st));
-    }
+    return KP_OK;
+}
+
+kp_status solve_setup_b(kp_plan plan, int iters, cudaStream_t st, int reg, const kp_pdhg_state* start) {
+    const Geom& g = plan->geo;
+    const int k0 = start ? start->k : 0;
+    iters += k0;                       // the schedule runs from iteration 0; the run starts at k0
     k_schedule<<<1, 1, 0, st>>>(plan->d_schedd, plan->d_flag + 4, std::max(iters, 1), plan->d_sched, plan->d_flag + 6,
                                 reg == KP_REG_TV ? g.D : 0);
     KP_LAUNCH_CHECK();
@@ -453,6 +463,28 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
     KP_TRY(zero_split_only(plan, st));
     (void)cluster_prox_ok(plan);   // decide the primal path here, outside any graph capture
     return KP_OK;
+}
+
+
+// Everything a PDHG run needs before its first iteration (Sec. 4.1): measurements and
+// preconditioner in sorted order, min p, lambda_max (given, or 30 power iterations), the
+// step-size schedule, the initial iterates (zero, or a caller's state whose dual variable is
+// brought into sorted order) and the forward grid of xbar.
+kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
+                      cudaStream_t st, int reg, const kp_pdhg_state* start) {
+    const Geom& g = plan->geo;
+    KP_TRY(solve_setup_a(plan, y_dev, y_t, p_dev, iters, st, start));
+    // lambda_max(P A A^H)
+    if (lmax > 0) {
+        k_set_double<<<1, 1, 0, st>>>(plan->d_schedd, lmax);
+        KP_LAUNCH_CHECK();
+        plan->launches += 1;
+    } else {
+        KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st));
+        plan->launches += 1;
+        KP_TRY(power_method(plan, plan->d_ps, 30, st));
+    }
+    return solve_setup_b(plan, iters, st, reg, start);
 }
 
 kp_status pdhg_iteration(kp_plan p, int reg, float lambda, cudaStream_t st) { return issue_iteration(p, reg, lambda, st); }
@@ -793,10 +825,9 @@ kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const
     }
     if (flags[KP_FLAG_P_BAD] != 0) { set_error(std::to_string(flags[KP_FLAG_P_BAD]) + " preconditioner entries are not positive and finite"); return KP_EINVAL; }
     if (flags[KP_FLAG_SCHED_BAD] != 0) { set_error("lambda_max or min p is not positive and finite"); return KP_EINVAL; }
-    if (flags[KP_FLAG_TIMEOUT] != 0) {
-        set_error("a bounded device wait (bulk-copy staging of the interpolation or a grid barrier of the primal kernel) gave up");
-        return KP_ETIMEOUT;
-    }
+    if (flags[KP_FLAG_TIMEOUT] != 0)
+        return report_timeout(plan, st, "a bounded device wait (bulk-copy staging of the interpolation or a grid barrier of "
+                                        "the primal kernel) gave up");
     if (status == KP_OK && flags[KP_FLAG_NONFINITE] != 0) { set_error("the reconstruction holds a NaN or an Inf"); return KP_ENONFINITE; }
     if (status == KP_ENONFINITE) set_error("the objective is not finite");
     if (status == KP_EDIVERGED) set_error("the objective grew above 1e3 times its first value");

@@ -521,6 +521,7 @@ kp_status plan_destroy_internal(kp_plan p) {
     cudaDeviceSynchronize();
     drop_graphs(p);
     pre_destroy(p);
+    compare_destroy(p);
     if (p->fft_ok) cufftDestroy(p->fft);
     void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_ccnt, p->d_coff, p->d_scan_part, p->d_scan_poff, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
                     p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
@@ -528,7 +529,7 @@ kp_status plan_destroy_internal(kp_plan p) {
                     p->d_maps, p->d_apod, p->d_grid, p->d_u, p->d_ys, p->d_ps, p->d_puser, p->d_kt,
                     p->d_x, p->d_xbar, p->d_z, p->d_w, p->d_wl0, p->d_wl1, p->d_red, p->d_sched, p->d_schedd, p->d_iter,
                     p->d_oitems, p->d_tslot, p->d_halo, p->d_sflag, p->d_spos, p->d_iitem_off, p->d_counts,
-                    p->d_sort_tmp, p->d_v, p->d_cg_r, p->d_cg_d, p->d_cg_trace};
+                    p->d_sort_tmp, p->d_lsort, p->d_v, p->d_cg_r, p->d_cg_d, p->d_cg_trace};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -539,9 +540,27 @@ kp_status plan_destroy_internal(kp_plan p) {
     return KP_OK;
 }
 
-// Reorders work items longest first (stable), so the CTAs that take longest start in the
-// first wave instead of forming a tail; items are independent, so the order is free.
-static kp_status sort_items_longest_first(kp_plan p, int4* d_items, int64_t n, cudaStream_t st) {
+// Reorders work items longest first, so the CTAs that take longest start in the first wave
+// instead of forming a tail; items are independent, so the order is free.  Up to SORT_MAX items:
+// one CTA's bitonic sort (stable); longer lists: a counting sort by length on the device
+// (lengths are at most the item size), equal lengths in any order.
+__global__ void k_len_hist(const int4* __restrict__ items, int64_t n, int maxlen, int* __restrict__ hist) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int len = max(0, min(items[i].z - items[i].y, maxlen));
+    atomicAdd(&hist[maxlen - len], 1);                    // bucket 0 holds the longest items
+}
+
+__global__ void k_len_scatter(const int4* __restrict__ items, int64_t n, int maxlen, const int* __restrict__ off,
+                              int* __restrict__ fill, int4* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 it = items[i];
+    const int b = maxlen - max(0, min(it.z - it.y, maxlen));
+    out[off[b] + atomicAdd(&fill[b], 1)] = it;
+}
+
+static kp_status sort_items_longest_first(kp_plan p, int4* d_items, int64_t n, int maxlen, cudaStream_t st) {
     if (n <= 1) return KP_OK;
     if (n <= SORT_MAX) {
         if (!p->d_sort_tmp) KP_TRY_CUDA(cudaMalloc(&p->d_sort_tmp, SORT_MAX * sizeof(int4)));
@@ -551,12 +570,27 @@ static kp_status sort_items_longest_first(kp_plan p, int4* d_items, int64_t n, c
         p->launches += 1;
         return KP_OK;
     }
-    std::vector<int4> h((size_t)n);
-    KP_TRY_CUDA(cudaMemcpyAsync(h.data(), d_items, n * sizeof(int4), cudaMemcpyDeviceToHost, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));
-    std::stable_sort(h.begin(), h.end(), [](const int4& a, const int4& b) { return (a.z - a.y) > (b.z - b.y); });
-    KP_TRY_CUDA(cudaMemcpyAsync(d_items, h.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
-    KP_TRY_CUDA(cudaStreamSynchronize(st));   // the host copy must outlive the transfer
+    // scratch: the sorted copy, then the length histogram, its scan and the fill counters
+    const size_t need = (size_t)n * sizeof(int4) + 3 * (size_t)(maxlen + 2) * sizeof(int);
+    if (need > p->lsort_cap) {
+        if (p->d_lsort) cudaFree(p->d_lsort);
+        p->d_lsort = nullptr;
+        p->lsort_cap = 0;
+        KP_TRY_CUDA(cudaMalloc(&p->d_lsort, need));
+        p->lsort_cap = need;
+    }
+    int4* out = (int4*)p->d_lsort;
+    int* hist = (int*)(out + n);
+    int* off = hist + (maxlen + 2);
+    int* fill = off + (maxlen + 2);
+    KP_TRY_CUDA(cudaMemsetAsync(hist, 0, (size_t)(maxlen + 2) * sizeof(int), st));
+    KP_TRY_CUDA(cudaMemsetAsync(fill, 0, (size_t)(maxlen + 2) * sizeof(int), st));
+    k_len_hist<<<nblk(n, 256), 256, 0, st>>>(d_items, n, maxlen, hist);
+    k_scan_excl<<<1, 1024, 0, st>>>(hist, off, maxlen + 1);
+    k_len_scatter<<<nblk(n, 256), 256, 0, st>>>(d_items, n, maxlen, off, fill, out);
+    KP_LAUNCH_CHECK();
+    KP_TRY_CUDA(cudaMemcpyAsync(d_items, out, n * sizeof(int4), cudaMemcpyDeviceToDevice, st));
+    p->launches += 3;
     return KP_OK;
 }
 
@@ -598,7 +632,7 @@ static kp_status spread_items_finish(kp_plan p, int chunk, int64_t n_items, int6
     k_items<<<tb, 256, 0, st>>>(p->d_ext_off, p->d_item_off, p->d_slot_off, p->d_nslots, tl.ntiles, chunk, p->d_items);
     KP_LAUNCH_CHECK();
     p->launches += 2;
-    return sort_items_longest_first(p, p->d_items, p->n_items, st);
+    return sort_items_longest_first(p, p->d_items, p->n_items, chunk, st);
 }
 
 // The four trajectory flags and the item counts into d_counts, read with one copy.
@@ -651,9 +685,34 @@ static kp_status own_items_finish(kp_plan p, int64_t n, cudaStream_t st) {
         k_slot_ids<<<nblk(p->n_oitems, 256), 256, 0, st>>>(p->d_oitems, p->n_oitems);
         KP_LAUNCH_CHECK();
         p->launches += 2;
-        KP_TRY(sort_items_longest_first(p, p->d_oitems, p->n_oitems, st));   // slot ids travel with the items
+        KP_TRY(sort_items_longest_first(p, p->d_oitems, p->n_oitems, p->own_chunk, st));   // slot ids travel with the items
     }
     return KP_OK;
+}
+
+// Per-tile lists of the sorted samples whose footprint touches the tile (d_ext_off, d_ext; the
+// longest list's length in d_flag[KP_FLAG_MAX_EXT]).
+static void spread_lists_enqueue(kp_plan p, cudaStream_t st) {
+    const Geom& g = p->geo;
+    const Tiles& tl = p->tiles;
+    const int T = 256;
+    cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st);
+    if (g.D == 2) k_ext<2, false><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, nullptr, nullptr);
+    else k_ext<3, false><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, nullptr, nullptr);
+    k_max_count<<<64, 256, 0, st>>>(p->d_cnt, tl.ntiles, p->d_flag + KP_FLAG_MAX_EXT);
+    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_ext_off, tl.ntiles);
+    cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st);
+    if (g.D == 2) k_ext<2, true><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
+    else k_ext<3, true><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
+    p->launches += 5;
+}
+
+// The lists and items of the single-pass spreading variants for the current trajectory (when a
+// plan tuned to a two-phase variant has to fall back to them).
+kp_status build_spread_lists(kp_plan p, cudaStream_t st) {
+    spread_lists_enqueue(p, st);
+    KP_LAUNCH_CHECK();
+    return build_spread_items(p, p->spread_chunk, st);
 }
 
 kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale, cudaStream_t st) {
@@ -664,6 +723,7 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     drop_graphs(p);
     p->traj_set = false;
     p->traj_version++;
+    p->circ_ok = false;
     if (traj != p->d_f)
         KP_TRY_CUDA(cudaMemcpyAsync(p->d_f, traj, (size_t)g.D * g.M * sizeof(float), cudaMemcpyDeviceToDevice, st));
     KP_TRY_CUDA(cudaMemsetAsync(p->d_ccnt, 0, (p->ncells + 1) * sizeof(int), st));
@@ -688,19 +748,13 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     else k_traj_scatter<3><<<nblk(g.M, T), T, 0, st>>>(traj, traj_scale, g, p->d_key, p->d_coff, p->d_ccnt, p->d_perm, p->d_t, p->d_k0);
     KP_LAUNCH_CHECK();
     KP_TRY(build_tap_tables(p, st));
-    // spreading lists
-    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    if (g.D == 2) k_ext<2, false><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, nullptr, nullptr);
-    else k_ext<3, false><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, nullptr, nullptr);
-    KP_LAUNCH_CHECK();
-    k_max_count<<<64, 256, 0, st>>>(p->d_cnt, tl.ntiles, p->d_flag + 2);
-    k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_ext_off, tl.ntiles);
-    KP_TRY_CUDA(cudaMemsetAsync(p->d_cnt, 0, (tl.ntiles + 1) * sizeof(int), st));
-    if (g.D == 2) k_ext<2, true><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
-    else k_ext<3, true><<<nblk(g.M, T), T, 0, st>>>(p->d_k0, g, tl, p->d_cnt, p->d_ext_off, p->d_ext);
-    KP_LAUNCH_CHECK();
-    // every count the host needs (flags, spreading, interpolation and own items), one copy
-    spread_items_counts(p, p->spread_chunk, st);
+    // per-tile spreading lists and items, used by the single-pass variants only: once the plan's
+    // spreading is tuned to a two-phase variant (10-12) they are not built
+    const bool lists = !(p->spread_tuned && p->spread_variant >= 10);
+    if (lists) {
+        spread_lists_enqueue(p, st);
+        spread_items_counts(p, p->spread_chunk, st);
+    }
     const unsigned tb = nblk(tl.ntiles, 256);
     k_ichunks<<<tb, 256, 0, st>>>(p->d_off, tl.ntiles, p->chunk, p->d_cnt);
     k_scan_excl<<<1, 1024, 0, st>>>(p->d_cnt, p->d_iitem_off, tl.ntiles);
@@ -716,8 +770,9 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
         p->traj_set = false;
         return KP_EINVAL;
     }
-    p->max_tile = cnt[2];
-    KP_TRY(spread_items_finish(p, p->spread_chunk, cnt[4], cnt[5], st));
+    p->max_tile = lists ? cnt[2] : cnt[1];
+    if (lists) KP_TRY(spread_items_finish(p, p->spread_chunk, cnt[4], cnt[5], st));
+    else p->n_split = 0;
     // interpolation items (own samples of each tile, pieces of at most chunk)
     p->n_iitems = cnt[6];
     if (p->n_iitems > p->iitems_cap) {
@@ -729,12 +784,21 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
     k_iitems<<<tb, 256, 0, st>>>(p->d_off, p->d_iitem_off, tl.ntiles, p->chunk, p->d_iitems);
     KP_LAUNCH_CHECK();
     p->launches += 1;
-    KP_TRY(sort_items_longest_first(p, p->d_iitems, p->n_iitems, st));
+    KP_TRY(sort_items_longest_first(p, p->d_iitems, p->n_iitems, p->chunk, st));
     KP_TRY(own_items_finish(p, cnt[7], st));
     p->traj_set = true;
     return autotune_spread(p, st);
 }
 
+}  // namespace kp
+
+namespace kp {
+kp_status report_timeout(kp_plan p, cudaStream_t st, const char* what) {
+    KP_TRY_CUDA(cudaMemsetAsync(p->d_flag + KP_FLAG_TIMEOUT, 0, sizeof(int), st));
+    KP_TRY_CUDA(cudaStreamSynchronize(st));
+    set_error(what);
+    return KP_ETIMEOUT;
+}
 }  // namespace kp
 
 using namespace kp;
@@ -784,6 +848,7 @@ kp_status kp_plan_set_maps(kp_plan plan, const void* maps_dev, kp_cdtype maps_t,
     plan->launches += 1;
     plan->maps_t = maps_t;
     plan->maps_set = true;
+    plan->circ_ok = false;
     // cached graphs bake the maps type in: drop them
     drop_graphs(plan);
     return KP_OK;
@@ -809,12 +874,7 @@ kp_status kp_plan_sync(kp_plan plan, void* stream) {
     int timeout = 0;
     KP_TRY_CUDA(cudaMemcpyAsync(&timeout, plan->d_flag + KP_FLAG_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));
-    if (timeout) {
-        KP_TRY_CUDA(cudaMemsetAsync(plan->d_flag + KP_FLAG_TIMEOUT, 0, sizeof(int), st));
-        KP_TRY_CUDA(cudaStreamSynchronize(st));
-        set_error("a bounded device wait (bulk-copy staging of the interpolation) gave up");
-        return KP_ETIMEOUT;
-    }
+    if (timeout) return report_timeout(plan, st, "a bounded device wait (bulk-copy staging of the interpolation) gave up");
     return KP_OK;
 }
 

@@ -302,9 +302,146 @@ __global__ void k_den_p(const float2* __restrict__ Vhat, const int* __restrict__
     for (int c = c_first; c < c_first + c_count; ++c) p[(size_t)c * g2.M + i] = val;
 }
 
+// ---------------------------------------------------------------- App. B circulant preconditioner
+// P = argmin over circulant P of ||A^H A - P||_F^2, P[m, n] = c[(m - n) mod N] (per axis):
+//   c[k] = 1/N sum over s in {0, 1}^D of r[k - s N] h[k - s N],  k_d in [0, N_d),
+//   r[d] = N^{-1/2} sum_c sum_{m - n = d} s_c^*[m] s_c[n]   (conjugate of IFFT(sum_c |FFT(s_c)|^2) on the 2N grid),
+//   h    = the point-spread function of Sec. 5.1 (type-1 NUFFT of ones at 2 f_j on the 2N image).
+// The 1/N is the average over the N entries of a circulant diagonal (the printed closed form
+// omits it; a uniform scale).  The eigenvalues of P are the DFT of c.
+
+// v[b][m] = s_{c0 + b}[j] with pixel j placed at the origin corner of the 2N grid (lags do not
+// depend on the placement), 0 elsewhere.
+template <typename MT>
+__global__ void k_pad_maps(const MT* __restrict__ maps, int c0, int nc, Geom geo, int D, int nb0, int nb1, int nb2,
+                           int64_t Nb, float2* __restrict__ v) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nb) return;
+    const int nb[3] = {nb0, nb1, nb2};
+    int64_t r = m, j = 0;
+    bool inside = true;
+    int ii[MAXD];
+    for (int d = D - 1; d >= 0; --d) { ii[d] = (int)(r % nb[d]); r /= nb[d]; }
+    for (int d = 0; d < D; ++d) {
+        if (ii[d] >= geo.n[d]) inside = false;
+        j = j * geo.n[d] + (inside ? ii[d] : 0);
+    }
+    for (int b = 0; b < nc; ++b)
+        v[(size_t)b * Nb + m] = inside ? ldc<MT>(maps, (size_t)(c0 + b) * geo.N + j) : make_float2(0.f, 0.f);
+}
+
+// R[m] += sum_b |V_b[m]|^2 (float64)
+__global__ void k_accum_abs2(const float2* __restrict__ V, int nc, int64_t Nb, double* __restrict__ R) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nb) return;
+    double acc = R[m];
+    for (int b = 0; b < nc; ++b) {
+        const float2 a = V[(size_t)b * Nb + m];
+        acc = fma((double)a.x, (double)a.x, acc);
+        acc = fma((double)a.y, (double)a.y, acc);
+    }
+    R[m] = acc;
+}
+
+// c[k] = scale sum over s in {0,1}^D of conj(rho[(k - s N) mod 2N]) h[k - s N + N]; rho the
+// normalised inverse FFT of R (uncentred 2N grid), h centred on the 2N image.
+__global__ void k_circ_fold(const float2* __restrict__ rho, const float2* __restrict__ h, Geom geo, int D,
+                            int nb0, int nb1, int nb2, float scale, float2* __restrict__ c) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= geo.N) return;
+    const int nb[3] = {nb0, nb1, nb2};
+    int kk[MAXD];
+    int64_t r = k;
+    for (int d = D - 1; d >= 0; --d) { kk[d] = (int)(r % geo.n[d]); r /= geo.n[d]; }
+    double ax = 0, ay = 0;
+    for (int s = 0; s < (1 << D); ++s) {
+        int64_t ri = 0, hi = 0;
+        for (int d = 0; d < D; ++d) {
+            const int lag = kk[d] - (((s >> d) & 1) ? geo.n[d] : 0);     // in [-N_d, N_d)
+            ri = ri * nb[d] + (lag < 0 ? lag + nb[d] : lag);
+            hi = hi * nb[d] + (lag + geo.n[d]);
+        }
+        const float2 a = rho[ri], b = h[hi];
+        // conj(a) * b
+        ax += (double)a.x * b.x + (double)a.y * b.y;
+        ay += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    c[k] = make_float2((float)(ax * scale), (float)(ay * scale));
+}
+
+__global__ void k_real_part(const float2* __restrict__ in, int64_t n, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i].x;
+}
+
+kp_status ensure_fft_img(kp_plan p) {
+    if (p->fft_img_ok) return KP_OK;
+    const Geom& g = p->geo;
+    int dims[3] = {g.n[0], g.n[1], g.n[2]};
+    KP_TRY_CUFFT(cufftPlanMany(&p->fft_img, g.D, dims, nullptr, 1, (int)g.N, nullptr, 1, (int)g.N, CUFFT_C2C, 1));
+    p->fft_img_ok = true;
+    return KP_OK;
+}
+
 }  // namespace kp
 
 using namespace kp;
+
+kp_status kp::circulant_enqueue(kp_plan plan, cudaStream_t st) {
+    if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
+    if (plan->unit_maps) { set_error("not available on an internal plan"); return KP_EINVAL; }
+    KP_TRY(pre_create(plan, st));
+    KP_TRY(ensure_fft_img(plan));
+    PrePlan* q = plan->pre;
+    kp_plan nu = plan->pre_nufft;
+    const Geom& g = plan->geo;
+    if (!plan->d_circ) KP_TRY_CUDA(cudaMalloc(&plan->d_circ, g.N * sizeof(float2)));
+    if (!plan->d_circ_eig) KP_TRY_CUDA(cudaMalloc(&plan->d_circ_eig, g.N * sizeof(float)));
+    if (q->traj_version != plan->traj_version) {
+        KP_TRY(set_trajectory_internal(nu, plan->d_f, 2.0f, st));
+        q->traj_version = plan->traj_version;
+    }
+    KP_TRY_CUFFT(cufftSetStream(q->fft_one, st));
+    KP_TRY_CUFFT(cufftSetStream(q->fft_coils, st));
+    KP_TRY_CUFFT(cufftSetStream(plan->fft_img, st));
+    // R = sum_c |FFT(pad(s_c))|^2 on the 2N grid, batch by batch of coils
+    KP_TRY_CUDA(cudaMemsetAsync(q->d_R, 0, (size_t)q->Nb * sizeof(double), st));
+    for (int c0 = 0; c0 < g.C; c0 += q->Cb) {
+        const int nc = g.C - c0 < q->Cb ? g.C - c0 : q->Cb;
+        switch (plan->maps_t) {
+            case KP_C64: k_pad_maps<float2><<<nblk(q->Nb, 256), 256, 0, st>>>((const float2*)plan->d_maps, c0, nc, g, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v); break;
+            case KP_C32_BF16: k_pad_maps<__nv_bfloat162><<<nblk(q->Nb, 256), 256, 0, st>>>((const __nv_bfloat162*)plan->d_maps, c0, nc, g, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v); break;
+            default: k_pad_maps<__half2><<<nblk(q->Nb, 256), 256, 0, st>>>((const __half2*)plan->d_maps, c0, nc, g, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v); break;
+        }
+        KP_LAUNCH_CHECK();
+        if (nc == q->Cb) KP_TRY_CUFFT(cufftExecC2C(q->fft_coils, (cufftComplex*)q->d_v, (cufftComplex*)q->d_v, CUFFT_FORWARD));
+        else for (int b = 0; b < nc; ++b)
+            KP_TRY_CUFFT(cufftExecC2C(q->fft_one, (cufftComplex*)(q->d_v + (size_t)b * q->Nb), (cufftComplex*)(q->d_v + (size_t)b * q->Nb), CUFFT_FORWARD));
+        k_accum_abs2<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_v, nc, q->Nb, q->d_R);
+        KP_LAUNCH_CHECK();
+        plan->launches += 2;
+    }
+    // rho = IFFT(R) / Nb
+    k_R_to_c<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_R, q->Nb, 1, q->d_r);
+    KP_LAUNCH_CHECK();
+    KP_TRY_CUFFT(cufftExecC2C(q->fft_one, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r, CUFFT_INVERSE));
+    // h on the 2N image: the 2N plan's adjoint carries (2^D N)^{-1/2}, h carries N^{-1/2}
+    KP_TRY(fill_image(nu->d_kt, nu->geo.M, make_float2(1.f, 0.f), st));
+    KP_TRY(adjoint_to_grid(nu, nu->d_kt, KP_C64, nullptr, st));
+    KP_TRY(grid_to_image(nu, q->d_h, st));
+    // c[k] = 1/N sum r h, r = conj(rho) / sqrt(N), h = 2^{D/2} x (the 2N adjoint of ones)
+    const double scale = std::pow(2.0, 0.5 * g.D) / ((double)g.N * std::sqrt((double)g.N));
+    k_circ_fold<<<nblk(g.N, 256), 256, 0, st>>>(q->d_r, q->d_h, g, g.D, q->nb[0], q->nb[1], q->nb[2], (float)scale, plan->d_circ);
+    KP_LAUNCH_CHECK();
+    // eigenvalues: the N-point DFT of c (real for the Hermitian P)
+    KP_TRY_CUFFT(cufftExecC2C(plan->fft_img, (cufftComplex*)plan->d_circ, (cufftComplex*)q->d_v, CUFFT_FORWARD));
+    k_real_part<<<nblk(g.N, 256), 256, 0, st>>>(q->d_v, g.N, plan->d_circ_eig);
+    KP_LAUNCH_CHECK();
+    plan->launches += 4;
+    plan->circ_ok = true;
+    plan->circ_version = plan->traj_version;
+    return KP_OK;
+}
 
 // Enqueues the whole construction on st without waiting; the number of non-positive
 // denominators (entries set to 0) is left in d_flag[7].

@@ -236,7 +236,8 @@ kp_status kp_unrolled_forward(kp_plan plan, const void* y_dev, const float* p_de
     KP_TRY_CUDA(cudaMemcpyAsync(flags, plan->d_flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
     KP_TRY_CUDA(cudaStreamSynchronize(st));
     if (flags[5] != 0 || flags[6] != 0) { set_error("preconditioner or lambda_max not positive and finite"); return KP_EINVAL; }
-    if (flags[KP_FLAG_TIMEOUT] != 0) { set_error("a bounded device wait (bulk-copy staging of the interpolation) gave up"); return KP_ETIMEOUT; }
+    if (flags[KP_FLAG_TIMEOUT] != 0)
+        return report_timeout(plan, st, "a bounded device wait (bulk-copy staging of the interpolation) gave up");
     plan->tape_iters = iters;
     plan->tape_lambda = lambda;
     return KP_OK;

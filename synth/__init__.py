@@ -187,6 +187,10 @@ WORKLOADS = {
     # 3D centre-out UTE radial, l1-wavelet, 192^3, 8 coils, 24000 x 256, alpha 1.25
     "ute3d_192": Workload("ute3d_192", (192, 192, 192), 8, 1.25, 4, "l1_wavelet", 1e-3, 30, 3,
                           "radial3d", dict(n_spokes=24000, n_readout=256, kmax=96.0)),
+    # the same 3D trajectory family at a size whose grids (200^3 x 8 coils, 512 MB) still exceed
+    # the L2 cache but keep a profiler capture within a few GB of device memory
+    "ute3d_160": Workload("ute3d_160", (160, 160, 160), 8, 1.25, 4, "l1_wavelet", 1e-3, 30, 3,
+                          "radial3d", dict(n_spokes=16000, n_readout=208, kmax=80.0)),
     # differentiable unrolled solver: 2D spiral 256^2, 16 coils, 16 x 4096, l2 lambda 1e-2
     "spiral2d_256_unrolled": Workload("spiral2d_256_unrolled", (256, 256), 16, 1.25, 4, "l2", 1e-2, 10, 0,
                                       "spiral", dict(n_interleaves=16, n_samples=4096, kmax=128.0)),

@@ -77,6 +77,7 @@ def test_wait_limit_timeouts_are_reported():
     with pytest.raises(KpError) as ei:
         plan.pdhg_solve(to_dev(y), None, "l2", 1e-3, 3)
     assert ei.value.status == KP_ETIMEOUT
+    plan.sync()                                    # the solve's report consumed the flag
     plan.set_wait_limit(2_000_000_000)
     y2 = plan.sense_forward(xd).cpu().numpy()
     plan.sync()
