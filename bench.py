@@ -768,6 +768,10 @@ def side_batched(dev, stream, flush, n_cases=64, iters=20):
     batch.solve(ys, None, regs, lams, iters)          # captures the all-case graph
     t_batch = _timed(lambda: batch.solve(ys, None, regs, lams, iters), stream, flush, 3)
     t_setup = _timed(lambda: batch.solve(ys, None, regs, lams, 0), stream, flush, 3)
+    batch.set_form("phases")
+    batch.solve(ys, None, regs, lams, iters)
+    t_phases = _timed(lambda: batch.solve(ys, None, regs, lams, iters), stream, flush, 3)
+    batch.set_form("per_case")
 
     def sequential():
         for pl, y, r, lm in zip(plans, ys, regs, lams):
@@ -780,6 +784,7 @@ def side_batched(dev, stream, flush, n_cases=64, iters=20):
     return {"cases": n_cases, "iters": iters, "coil_samples": int(samples), "y": "bf16",
             "batched_ms": t_batch, "batched_cases_per_s": n_cases / (t_batch / 1e3),
             "batched_setup_ms": t_setup, "batched_iteration_ms": (t_batch - t_setup) / iters,
+            "phase_form_ms": t_phases, "phase_form_iteration_ms": (t_phases - t_setup) / iters,
             "sequential_ms": t_seq, "sequential_cases_per_s": n_cases / (t_seq / 1e3),
             "what": "whole reconstructions (MC preconditioner, 30 power its, PDHG its) per second"}
 

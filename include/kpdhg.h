@@ -327,15 +327,31 @@ kp_status kp_sense_adjoint_noalloc(const kp_params* params, const float* traj_de
 typedef struct kp_batch_s* kp_batch;
 kp_status kp_batch_create(kp_batch* out, kp_plan* plans, int ncases);
 
+/* How a batch's PDHG iteration is laid out in its CUDA graph.
+ * KP_BATCH_PER_CASE (default): every case's own iteration kernels on its own forked stream, so
+ *   one case's FFTs overlap another case's interpolation or spreading.
+ * KP_BATCH_PHASES: one kernel launch per phase over all cases (interpolation + dual step,
+ *   split-tile clearing, spreading, primal step, each wavelet level, pre-step, counters; each
+ *   block finds its case in a table of block offsets), with the cases' cuFFT transforms on
+ *   forked streams between the phases.  Applies when every case is 2D, l2 or l1-wavelet, and
+ *   the cases share one k-space and one maps storage type; otherwise the solve uses the
+ *   per-case layout.  All cases spread with the single-pass interleaved-pair kernel.
+ * On 64 uneven 2D cases (96..320 pixels, 4..32 coils) the per-case layout measured 7.1 ms per
+ * iteration of all cases on a GB300 and the phase layout 8.7 ms. */
+typedef enum { KP_BATCH_PER_CASE = 0, KP_BATCH_PHASES = 1 } kp_batch_form;
+/* Selects the layout of later solves (the graph is captured again).  Errors: KP_EINVAL. */
+kp_status kp_batch_set_form(kp_batch batch, kp_batch_form form);
+
 /* Runs `iters` PDHG iterations (Sec. 4.1; Sec. 4.2 for KP_REG_TV cases) on every case of the
  * batch.  Arrays of length ncases:
  * y_devs[i] ([C_i][M_i] of type y_types[i]), p_devs[i] (float32 [C_i][M_i], or NULL entries /
  * a NULL array for the multi-channel preconditioner), regs[i], lambdas[i], x_devs[i]
  * (complex64 [N_i] output).  Start, step sizes and power method follow kp_pdhg_solve per case.
- * Set-up runs case by case; the iteration of all cases is one CUDA graph (captured on the
- * first call and again when regs, lambdas or y types change) in which every case runs on its
- * own forked stream, so the cases overlap on the GPU; the graph is replayed `iters` times on
- * `stream`.  Each case's result equals that case's kp_pdhg_solve up to float32 rounding order.
+ * Set-up runs case by case, each case on its own stream; the 29 power iterations after the
+ * first replay one graph of all cases.  The iteration of all cases is one CUDA graph in the
+ * batch's form (captured on the first call and again when the form, regs, lambdas, y types or
+ * a plan's buffers change), replayed `iters` times on `stream`.  Each case's result equals
+ * that case's kp_pdhg_solve up to float32 rounding order.
  * Synchronous.  Errors: KP_EINVAL (iters < 0, an unknown regulariser, l1 case without wavelet
  * levels, non-positive p or lambda_max of some case), KP_ECUDA, KP_ECUFFT. */
 kp_status kp_batch_solve(kp_batch batch, const void* const* y_devs, const kp_cdtype* y_types,

@@ -93,6 +93,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                       ctypes.POINTER(_vp), _vp]),
     "kp_batch_destroy": (ctypes.c_int, [_vp]),
+    "kp_batch_set_form": (ctypes.c_int, [_vp, ctypes.c_int]),
 }
 
 _lib = None

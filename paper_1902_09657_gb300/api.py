@@ -333,11 +333,15 @@ class Plan:
         L.check(self.lib.kp_plan_sync(self._h, _stream(self.device)), "kp_plan_sync")
 
 
+BATCH_FORMS = {"per_case": 0, "phases": 1}
+
+
 class Batch:
     """Independent cases (one Plan each, any sizes) solved together: per-case set-up, then one
-    CUDA graph per iteration advancing every case on its own stream (kp_batch)."""
+    CUDA graph per iteration advancing every case (kp_batch).  form "per_case" puts each case's
+    own kernels on its own stream; "phases" issues one launch per phase over all cases."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, form="per_case"):
         self.lib = L.load()
         self.plans = list(plans)
         if not self.plans:
@@ -349,6 +353,14 @@ class Batch:
         arr = (ctypes.c_void_p * n)(*[p._h.value for p in self.plans])
         self._h = ctypes.c_void_p()
         L.check(self.lib.kp_batch_create(ctypes.byref(self._h), arr, n), "kp_batch_create")
+        self.set_form(form)
+
+    def set_form(self, form):
+        if form not in BATCH_FORMS:
+            raise ValueError(f"batch form must be one of {sorted(BATCH_FORMS)}")
+        L.check(self.lib.kp_batch_set_form(self._h, BATCH_FORMS[form]), "kp_batch_set_form")
+        self.form = form
+        return self
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

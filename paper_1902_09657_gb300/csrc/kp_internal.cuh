@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "../../include/kpdhg.h"
 
@@ -321,6 +322,7 @@ struct kp_plan_s {
     float* d_puser = nullptr;        // [C][M] preconditioner in user order (when computed here)
     float* d_f = nullptr;            // [M][D] copy of the trajectory (cycles/FOV), user order
     int traj_version = 0;
+    int lists_version = -1;          // traj_version whose per-tile spreading lists d_ext / d_items hold
     float2* d_kt = nullptr;          // [C][M] scratch k-space (objective / power method)
     float2* d_x = nullptr;           // [N] primal
     float2* d_xbar = nullptr;        // [N] extrapolated primal
@@ -426,6 +428,8 @@ kp_status build_spread_lists(kp_plan p, cudaStream_t st);
 kp_status make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st);
 kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);
+// In-place inverse FFT of d_grid2 (the spread grid).
+kp_status fft_inverse_only(kp_plan p, cudaStream_t st);
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status interp_dual_only(kp_plan p, cudaStream_t st);
@@ -443,5 +447,56 @@ void compare_destroy(kp_plan p);
 // Reports a bounded device wait that gave up: clears the plan's timeout flag (so the report is
 // consumed once), records `what` as the error message and returns KP_ETIMEOUT.
 kp_status report_timeout(kp_plan p, cudaStream_t st, const char* what);
+
+// ---------------------------------------------------------------- batched launches
+// One kernel launch per phase over every case of a batch: block b of the launch belongs to the
+// case c with boff[c] <= b < boff[c + 1] (boff ascending, boff[ncase] = blocks of the launch;
+// a case with no blocks has boff[c] == boff[c + 1] and is never returned) and reads its
+// arguments from the case's descriptor.
+__device__ __forceinline__ int batch_case(const int* __restrict__ boff, int ncase, int b) {
+    int lo = 0, hi = ncase - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(boff + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Device copy of one batched launch's descriptors and block offsets (owned by the batch).
+struct BatchPhase {
+    void* d_desc = nullptr;
+    size_t desc_cap = 0;
+    int* d_boff = nullptr;
+    size_t boff_cap = 0;
+    int ncase = 0;
+    unsigned nblocks = 0;
+};
+kp_status phase_upload(BatchPhase& ph, const void* descs, size_t desc_bytes, int ncase, const std::vector<int>& boff);
+void phase_free(BatchPhase& ph);
+
+// The batched 2D PDHG iteration (l2 and l1-wavelet cases; every case shares the dimension, the
+// k-space storage type and the maps storage type).  Built outside stream capture (descriptors
+// are uploaded with blocking copies), launched inside it.
+struct BatchIter {
+    BatchPhase interp, zero, spread, primal, pre, advance;
+    std::vector<BatchPhase> fwd, inv;    // wavelet levels 0 .. Lmax-1 (forward), same (inverse)
+    kp_cdtype yt = KP_C64, mt = KP_C64;
+    bool built = false;
+};
+void batch_iter_free(BatchIter& bi);
+// NUFFT-side phases (interpolation + dual step, split-tile clearing, spreading, primal step,
+// pre-step of the l2 cases, iteration counters).
+kp_status batch_nufft_build(const std::vector<kp_plan>& ps, const std::vector<int>& regs,
+                            const std::vector<float>& lams, BatchIter& bi);
+kp_status batch_interp_launch(const BatchIter& bi, cudaStream_t st);
+kp_status batch_spread_launch(const BatchIter& bi, cudaStream_t st);
+kp_status batch_primal_launch(const BatchIter& bi, cudaStream_t st);
+kp_status batch_pre_launch(const BatchIter& bi, cudaStream_t st);
+// Wavelet prox of the l1 cases: forward levels then inverse levels (level 0 also extrapolates
+// and writes the next forward grid), one launch per level over the cases that have it.
+kp_status batch_wavelet_build(const std::vector<kp_plan>& ps, const std::vector<int>& regs,
+                              const std::vector<float>& lams, BatchIter& bi);
+kp_status batch_wavelet_launch(const BatchIter& bi, cudaStream_t st);
 
 }  // namespace kp

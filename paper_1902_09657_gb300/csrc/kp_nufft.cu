@@ -128,9 +128,9 @@ __device__ __forceinline__ int pix_of_grid(int i, int n, int g) {
 }
 
 template <int D, typename MT>
-__global__ void k_fwd_pre(const float2* __restrict__ x, const MT* __restrict__ maps, const float* __restrict__ apod,
-                          Geom geo, float2* __restrict__ grid) {
-    int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fwd_pre_body(const float2* __restrict__ x, const MT* __restrict__ maps,
+                                             const float* __restrict__ apod, const Geom& geo,
+                                             float2* __restrict__ grid, int64_t gi) {
     if (gi >= geo.G) return;
     int ii[D];
     int64_t r = gi;
@@ -161,6 +161,12 @@ __global__ void k_fwd_pre(const float2* __restrict__ x, const MT* __restrict__ m
     }
 }
 
+template <int D, typename MT>
+__global__ void k_fwd_pre(const float2* __restrict__ x, const MT* __restrict__ maps, const float* __restrict__ apod,
+                          Geom geo, float2* __restrict__ grid) {
+    fwd_pre_body<D, MT>(x, maps, apod, geo, grid, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------- forward: interpolation
 // One CTA per (tile chunk, coil group): the grid region the tile's samples read
 // ((ts + W - 1)^D points per coil, periodic) is staged in shared memory by bulk asynchronous
@@ -181,6 +187,58 @@ struct InterpIO {
     int* flag;           // set to 1 if the staging wait gave up (reported as KP_ETIMEOUT)
     const double* n2;    // mode 1: when set, the output is also divided by sqrt(*n2)
     long long wait;      // limit of the staging wait (SM clock cycles)
+};
+
+// Per-case arguments of the batched launches (one launch per phase over the cases of a batch;
+// nx = the case's work items, so its blocks are nx x coil groups).
+struct BInterp {
+    const int4* items;
+    const int* k0t;
+    const float* wt;
+    const float2* grid;
+    Geom geo;
+    Tiles tl;
+    InterpIO io;
+    int nx;
+};
+struct BSpread {
+    const int* k0t;
+    const float* wt;
+    const void* u;
+    const int* perm;
+    const int* ext;
+    const int4* items;
+    Geom geo;
+    Tiles tl;
+    float2* grid;
+    int nx;
+};
+struct BZero {
+    const int* split;
+    Geom geo;
+    Tiles tl;
+    int P;
+    float2* grid;
+};
+struct BPrimal {             // reg 0: l2 prox + extrapolation; 1: z for the wavelet prox
+    const float2* grid;
+    const void* maps;
+    const float* apod;
+    Geom geo;
+    float2* x;
+    float2* xbar;
+    float2* z;
+    const float* sched;
+    const int* iter;
+    float lambda;
+    int reg;
+};
+struct BPre {
+    const float2* x;
+    const void* maps;
+    const float* apod;
+    Geom geo;
+    float2* grid;
 };
 
 // Staged region geometry: R points per axis for the largest tile edge (16 in 2D, 8 in 3D);
@@ -231,15 +289,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 }
 
 template <int D, int MODE, typename T>
-__global__ void __launch_bounds__(IP_THREADS, D == 3 ? 3 : 4)
-k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const float* __restrict__ wt,
-              const float2* __restrict__ grid, Geom geo, Tiles tl, InterpIO io) {
+__device__ __forceinline__ void interp_tile_body(const int4* __restrict__ items, const int* __restrict__ k0t,
+                                                 const float* __restrict__ wt, const float2* __restrict__ grid,
+                                                 const Geom& geo, const Tiles& tl, const InterpIO& io, int bx, int by) {
     using LY = IpL<D>;
     extern __shared__ __align__(128) float2 sg[];    // [IP_CH][ROWS][RP]
     __shared__ unsigned long long bar;
-    const int4 it = items[blockIdx.x];
+    const int4 it = items[bx];
     const int tile = it.x, beg = it.y, end = it.z;
-    const int c0 = blockIdx.y * IP_CH;
+    const int c0 = by * IP_CH;
     const int cc = min(IP_CH, geo.C - c0);
     constexpr int R = LY::R;
     int o[MAXD];
@@ -378,6 +436,24 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
             io.u[os] = make_float2((uo.x + sp * (acc.x - y.x)) * inv, (uo.y + sp * (acc.y - y.y)) * inv);
         }
     }
+}
+
+template <int D, int MODE, typename T>
+__global__ void __launch_bounds__(IP_THREADS, D == 3 ? 3 : 4)
+k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const float* __restrict__ wt,
+              const float2* __restrict__ grid, Geom geo, Tiles tl, InterpIO io) {
+    interp_tile_body<D, MODE, T>(items, k0t, wt, grid, geo, tl, io, blockIdx.x, blockIdx.y);
+}
+
+// The same over the cases of a batch: block b belongs to the case c with boff[c] <= b <
+// boff[c + 1]; within it, item (b - boff[c]) mod n_items of coil group (b - boff[c]) / n_items.
+template <int D, int MODE, typename T>
+__global__ void __launch_bounds__(IP_THREADS, D == 3 ? 3 : 4)
+k_interp_tile_b(const BInterp* __restrict__ cs, const int* __restrict__ boff, int ncase) {
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    const BInterp& a = cs[c];
+    const int lb = (int)blockIdx.x - boff[c];
+    interp_tile_body<D, MODE, T>(a.items, a.k0t, a.wt, a.grid, a.geo, a.tl, a.io, lb % a.nx, lb / a.nx);
 }
 
 // ---------------------------------------------------------------- adjoint: spread
@@ -601,20 +677,21 @@ static size_t spread_v_smem() {
 }
 
 template <int D, typename UT, int NW>
-__global__ void __launch_bounds__(NW * 32)
-k_spread_v(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
-           const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
-           Tiles tl, float2* __restrict__ grid) {
+__device__ __forceinline__ void spread_v_body(const int* __restrict__ k0t, const float* __restrict__ wt,
+                                              const UT* __restrict__ u, const int* __restrict__ perm,
+                                              const int* __restrict__ ext, const int4* __restrict__ items,
+                                              const Geom& geo, const Tiles& tl, float2* __restrict__ grid, int bx,
+                                              int by) {
     using LV = SpV<D>;
     extern __shared__ __align__(16) float4 smv[];
     float4* acc = smv;                                              // [NW][COPY]
     float4* su4 = acc + NW * LV::COPY;                              // [SP_CHUNK][2] coil pairs
     float* sw = (float*)(su4 + SP_CHUNK * 2);                       // [SP_CHUNK][D][KW]
     unsigned* sp = (unsigned*)(sw + SP_CHUNK * D * KW);             // [SP_CHUNK][D]
-    const int4 it = items[blockIdx.x];
+    const int4 it = items[bx];
     const int tile = it.x, beg = it.y, end = it.z;
     const bool split = it.w >= 0;
-    const int c0 = blockIdx.y * 4;
+    const int c0 = by * 4;
     const int cc = min(4, geo.C - c0);
     int o[MAXD], e[MAXD];
     {
@@ -751,6 +828,25 @@ k_spread_v(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* 
             if (has1) *d1 = make_float2(v.z, v.w);
         }
     }
+}
+
+template <int D, typename UT, int NW>
+__global__ void __launch_bounds__(NW * 32)
+k_spread_v(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
+           const int* __restrict__ perm, const int* __restrict__ ext, const int4* __restrict__ items, Geom geo,
+           Tiles tl, float2* __restrict__ grid) {
+    spread_v_body<D, UT, NW>(k0t, wt, u, perm, ext, items, geo, tl, grid, blockIdx.x, blockIdx.y);
+}
+
+// The same over the cases of a batch (block b -> case and item as in k_interp_tile_b).
+template <int D, typename UT, int NW>
+__global__ void __launch_bounds__(NW * 32) k_spread_v_b(const BSpread* __restrict__ cs, const int* __restrict__ boff,
+                                                        int ncase) {
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    const BSpread& a = cs[c];
+    const int lb = (int)blockIdx.x - boff[c];
+    spread_v_body<D, UT, NW>(a.k0t, a.wt, (const UT*)a.u, a.perm, a.ext, a.items, a.geo, a.tl, a.grid, lb % a.nx,
+                             lb / a.nx);
 }
 
 // 3D variant in which warp w owns z-plane w of a single accumulator (8 warps, tile depth at
@@ -1035,21 +1131,27 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
     }
 }
 
-// Phase B: one CTA per (tile, coil) (empty tiles included, so every grid point is stored once):
-// the work of a tile with many slots spreads over C CTAs.  The CTA first looks up the slot
-// ranges of the tile and its 7 lower neighbours (periodic) and the padded offset at which a
-// neighbour's halo meets this tile; then each thread sums, for its points, the slots that cover
-// them, four slots at a time into independent sums so the loads overlap.
+// Phase B: one CTA per tile (empty tiles included, so every grid point is stored once), looping
+// over the coils.  The tile's value is the sum of its own slots' 8^3 cores and of the halos
+// that its 7 lower neighbours (periodic) spill into it: the neighbour across axis set m covers
+// the sub-box with extent KW - 1 along the axes in m and the full tile along the others, read
+// from the neighbour's slots at the padded offset where its core ends.  Every slot point is
+// read once: the own cores into registers (two points per thread), then one pass per
+// non-empty neighbour into a shared accumulator, then the tile is stored.  Offsets come from
+// small tables built once per CTA (no per-point address arithmetic beyond a table lookup).
 __global__ void __launch_bounds__(256)
 k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
               float2* __restrict__ grid) {
-    __shared__ int nb_beg[8], nb_end[8], nb_off[8], org[3], ext[3];
-    const int tile = blockIdx.x, c = blockIdx.y;
+    __shared__ float2 acc[512];
+    __shared__ int nb_beg[8], nb_end[8], nb_off[8];
+    __shared__ int64_t rowoff[64];     // grid offset (coil 0) of local row (lz, ly); -1 outside the grid
+    __shared__ int colg[8];            // grid x of local x; -1 outside the grid
+    const int tile = blockIdx.x;
+    const int nt0 = tl.nt[0], nt1 = tl.nt[1], nt2 = tl.nt[2];
+    const int t2 = tile % nt2, t1 = (tile / nt2) % nt1, t0 = tile / (nt2 * nt1);
     if (threadIdx.x < 8) {
         const int m = threadIdx.x;
-        const int nt0 = tl.nt[0], nt1 = tl.nt[1], nt2 = tl.nt[2];
         const int ts0 = tl.ts[0], ts1 = tl.ts[1], ts2 = tl.ts[2];
-        const int t2 = tile % nt2, t1 = (tile / nt2) % nt1, t0 = tile / (nt2 * nt1);
         const int b0 = (m >> 2) & 1, b1 = (m >> 1) & 1, b2 = m & 1;
         const int n0 = b0 ? (t0 == 0 ? nt0 - 1 : t0 - 1) : t0;
         const int n1 = b1 ? (t1 == 0 ? nt1 - 1 : t1 - 1) : t1;
@@ -1059,43 +1161,72 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
         nb_end[m] = tslot[nb + 1];
         nb_off[m] = (b0 ? min(ts0, geo.g[0] - n0 * ts0) * SL_PS : 0) + (b1 ? min(ts1, geo.g[1] - n1 * ts1) * SL_RS : 0) +
                     (b2 ? min(ts2, geo.g[2] - n2 * ts2) : 0);
-        if (m == 0) {
-            org[0] = t0 * ts0; org[1] = t1 * ts1; org[2] = t2 * ts2;
-            ext[0] = min(ts0, geo.g[0] - org[0]); ext[1] = min(ts1, geo.g[1] - org[1]); ext[2] = min(ts2, geo.g[2] - org[2]);
-        }
+    } else if (threadIdx.x < 8 + 64) {
+        const int r = threadIdx.x - 8, lz = r >> 3, ly = r & 7;
+        const int pz = t0 * tl.ts[0] + lz, py = t1 * tl.ts[1] + ly;
+        rowoff[r] = (lz < min(tl.ts[0], geo.g[0] - t0 * tl.ts[0]) && ly < min(tl.ts[1], geo.g[1] - t1 * tl.ts[1]))
+                        ? ((int64_t)tunshift(pz, tl.sh[0], geo.g[0]) * geo.g[1] + tunshift(py, tl.sh[1], geo.g[1])) * geo.g[2]
+                        : (int64_t)-1;
+    } else if (threadIdx.x < 8 + 64 + 8) {
+        const int lx = threadIdx.x - 72, px = t2 * tl.ts[2] + lx;
+        colg[lx] = lx < min(tl.ts[2], geo.g[2] - t2 * tl.ts[2]) ? tunshift(px, tl.sh[2], geo.g[2]) : -1;
     }
     __syncthreads();
-    const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
-    const size_t cstride = (size_t)geo.C * SL_P;
-    const float2* hc = halo + (size_t)c * SL_P;
-    for (int i = threadIdx.x; i < 512; i += blockDim.x) {
-        const int lz = i >> 6, ly = (i >> 3) & 7, lx = i & 7;
-        if (lz >= e0 || ly >= e1 || lx >= e2) continue;
-        const int pt = (lz * PT + ly) * SL_RS + lx;
-        const int low = (lz < KW - 1 ? 4 : 0) | (ly < KW - 1 ? 2 : 0) | (lx < KW - 1 ? 1 : 0);
-        float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+    const int64_t cstride = (int64_t)geo.C * SL_P;
+    // this thread's two points of the 8^3 tile: i0 = tid (lz 0..3), i1 = tid + 256 (lz 4..7)
+    const int i0 = threadIdx.x, i1 = threadIdx.x + 256;
+    const int pt0 = ((i0 >> 6) * PT + ((i0 >> 3) & 7)) * SL_RS + (i0 & 7);
+    const int pt1 = pt0 + 4 * SL_PS;
+    const int own_b = nb_beg[0], own_e = nb_end[0];
+    for (int c = 0; c < geo.C; ++c) {
+        const float2* hc = halo + (int64_t)c * SL_P;
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+        int sl = own_b;
+        for (; sl + 2 <= own_e; sl += 2) {
+            const float2* s0 = hc + sl * cstride;
+            const float2* s1 = s0 + cstride;
+            const float2 u0 = s0[pt0], u1 = s0[pt1], v0 = s1[pt0], v1 = s1[pt1];
+            a0.x += u0.x; a0.y += u0.y; a1.x += u1.x; a1.y += u1.y;
+            b0.x += v0.x; b0.y += v0.y; b1.x += v1.x; b1.y += v1.y;
+        }
+        if (sl < own_e) {
+            const float2* s0 = hc + sl * cstride;
+            const float2 u0 = s0[pt0], u1 = s0[pt1];
+            a0.x += u0.x; a0.y += u0.y; a1.x += u1.x; a1.y += u1.y;
+        }
+        acc[i0] = make_float2(a0.x + b0.x, a0.y + b0.y);
+        acc[i1] = make_float2(a1.x + b1.x, a1.y + b1.y);
 #pragma unroll 1
-        for (int m = 0; m < 8; ++m) {
-            if (m & ~low) continue;
-            const int e = nb_end[m];
-            const float2* src = hc + nb_off[m] + pt;
-            int sl = nb_beg[m];
-            for (; sl + 4 <= e; sl += 4) {
-                const float2 v0 = src[(size_t)sl * cstride], v1 = src[(size_t)(sl + 1) * cstride];
-                const float2 v2 = src[(size_t)(sl + 2) * cstride], v3 = src[(size_t)(sl + 3) * cstride];
-                s0.x += v0.x; s0.y += v0.y; s1.x += v1.x; s1.y += v1.y;
-                s2.x += v2.x; s2.y += v2.y; s3.x += v3.x; s3.y += v3.y;
-            }
-            for (; sl < e; ++sl) {
-                const float2 v = src[(size_t)sl * cstride];
-                s0.x += v.x; s0.y += v.y;
+        for (int m = 1; m < 8; ++m) {
+            const int be = nb_beg[m], en = nb_end[m];
+            if (be == en) continue;                                  // block-uniform
+            __syncthreads();                                         // earlier passes' adds are done
+            const int d0 = (m & 4) ? KW - 1 : 8, d1 = (m & 2) ? KW - 1 : 8, d2 = (m & 1) ? KW - 1 : 8;
+            const int npts = d0 * d1 * d2, off = nb_off[m];
+            for (int q = threadIdx.x; q < npts; q += blockDim.x) {
+                const int lx = q % d2, r = q / d2, ly = r % d1, lz = r / d1;
+                const float2* src = hc + off + (lz * PT + ly) * SL_RS + lx;
+                float2 sm = make_float2(0.f, 0.f);
+                for (int k = be; k < en; ++k) {
+                    const float2 v = src[k * cstride];
+                    sm.x += v.x;
+                    sm.y += v.y;
+                }
+                float2& t = acc[(lz * 8 + ly) * 8 + lx];
+                t.x += sm.x;
+                t.y += sm.y;
             }
         }
-        const float2 sum = make_float2((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y));
-        const int gz = tunshift(org[0] + lz, tl.sh[0], geo.g[0]);
-        const int gy = tunshift(org[1] + ly, tl.sh[1], geo.g[1]);
-        const int gx = tunshift(org[2] + lx, tl.sh[2], geo.g[2]);
-        grid[(size_t)c * geo.G + ((size_t)gz * geo.g[1] + gy) * geo.g[2] + gx] = sum;
+        __syncthreads();
+        float2* gc = grid + (int64_t)c * geo.G;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = threadIdx.x + 256 * h;
+            const int64_t ro = rowoff[i >> 3];
+            const int gx = colg[i & 7];
+            if (ro >= 0 && gx >= 0) gc[ro + gx] = acc[i];
+        }
+        __syncthreads();                                             // acc is rewritten by the next coil
     }
 }
 
@@ -1519,8 +1650,9 @@ k_spread_warpcoil(const int* __restrict__ k0t, const float* __restrict__ wt, con
 // Clear the grid region of every split tile (all coils) before the spreading kernel adds
 // the tile's chunks into it.
 template <int D>
-__global__ void k_zero_split(const int* __restrict__ split_tiles, Geom geo, Tiles tl, int P, float2* __restrict__ grid) {
-    const int tile = split_tiles[blockIdx.x];
+__device__ __forceinline__ void zero_split_body(const int* __restrict__ split_tiles, const Geom& geo, const Tiles& tl,
+                                                int P, float2* __restrict__ grid, int b) {
+    const int tile = split_tiles[b];
     int o[MAXD], e[MAXD];
     {
         int r = tile;
@@ -1544,6 +1676,11 @@ __global__ void k_zero_split(const int* __restrict__ split_tiles, Geom geo, Tile
         }
         if (in) grid[(size_t)c * geo.G + gflat] = make_float2(0.f, 0.f);
     }
+}
+
+template <int D>
+__global__ void k_zero_split(const int* __restrict__ split_tiles, Geom geo, Tiles tl, int P, float2* __restrict__ grid) {
+    zero_split_body<D>(split_tiles, geo, tl, P, grid, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- adjoint: post
@@ -1603,11 +1740,12 @@ __global__ void k_tv_dual(const float2* __restrict__ xbar, float2* __restrict__ 
 // (REG == 2, Sec. 4.2) x <- z - tau G^H v, G^H v = sum_k (v_k[j - e_k] - v_k[j]), and the
 // extrapolation.
 template <int D, typename MT, int REG>
-__global__ void k_adj_primal(const float2* __restrict__ grid, const MT* __restrict__ maps, const float* __restrict__ apod,
-                             Geom geo, float2* __restrict__ x, float2* __restrict__ xbar, float2* __restrict__ z,
-                             const float* __restrict__ sched, const int* __restrict__ iter, float lambda,
-                             const float2* __restrict__ v) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void adj_primal_body(const float2* __restrict__ grid, const MT* __restrict__ maps,
+                                                const float* __restrict__ apod, const Geom& geo,
+                                                float2* __restrict__ x, float2* __restrict__ xbar,
+                                                float2* __restrict__ z, const float* __restrict__ sched,
+                                                const int* __restrict__ iter, float lambda,
+                                                const float2* __restrict__ v, int64_t j) {
     if (j >= geo.N) return;
     const int k = *iter;
     const float tau = sched[3 * k + 1], theta = sched[3 * k + 2];
@@ -1637,6 +1775,15 @@ __global__ void k_adj_primal(const float2* __restrict__ grid, const MT* __restri
     } else {
         z[j] = zz;
     }
+}
+
+template <int D, typename MT, int REG>
+__global__ void k_adj_primal(const float2* __restrict__ grid, const MT* __restrict__ maps, const float* __restrict__ apod,
+                             Geom geo, float2* __restrict__ x, float2* __restrict__ xbar, float2* __restrict__ z,
+                             const float* __restrict__ sched, const int* __restrict__ iter, float lambda,
+                             const float2* __restrict__ v) {
+    adj_primal_body<D, MT, REG>(grid, maps, apod, geo, x, xbar, z, sched, iter, lambda, v,
+                                (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_fill(float2* __restrict__ x, int64_t n, float2 v) {
@@ -1699,6 +1846,13 @@ kp_status fft_forward_only(kp_plan p, cudaStream_t st) {
     mark(p, PH_FFT_FWD, st);
     KP_TRY_CUFFT(cufftSetStream(p->fft, st));
     KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_gridF, CUFFT_FORWARD));
+    return KP_OK;
+}
+
+kp_status fft_inverse_only(kp_plan p, cudaStream_t st) {
+    mark(p, PH_FFT_INV, st);
+    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
+    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
     return KP_OK;
 }
 
@@ -1812,7 +1966,7 @@ static kp_status launch_spread_own(kp_plan p, const UT* u, const int* perm, cuda
             p->d_k0, p->d_wt, u, perm, p->d_oitems, g, p->tiles, p->d_halo);
     KP_LAUNCH_CHECK();
     mark(p, PH_SPREAD_RED, st);
-    k_halo_gather<<<dim3((unsigned)p->tiles.ntiles, (unsigned)g.C), 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
+    k_halo_gather<<<(unsigned)p->tiles.ntiles, 256, 0, st>>>(p->d_halo, p->d_tslot, g, p->tiles, p->d_grid2);
     KP_LAUNCH_CHECK();
     p->launches += 1;
     return KP_OK;
@@ -2099,6 +2253,227 @@ kp_status tv_sumabs(kp_plan p, const float2* x, double* out, cudaStream_t st) {
     const unsigned b = (unsigned)std::min<int64_t>(nblk(g.N, 256), 1216);
     p->launches += 1;
     KP_DISPATCH_D(g.D, DD, k_tv_sumabs<DD><<<b, 256, 0, st>>>(x, g, out));
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+// ---------------------------------------------------------------- batched phases
+template <int D>
+__global__ void k_zero_split_b(const BZero* __restrict__ cs, const int* __restrict__ boff, int ncase) {
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    const BZero& a = cs[c];
+    zero_split_body<D>(a.split, a.geo, a.tl, a.P, a.grid, (int)blockIdx.x - boff[c]);
+}
+
+template <int D, typename MT>
+__global__ void k_adj_primal_b(const BPrimal* __restrict__ cs, const int* __restrict__ boff, int ncase) {
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    const BPrimal& a = cs[c];
+    const int64_t j = (int64_t)((int)blockIdx.x - boff[c]) * blockDim.x + threadIdx.x;
+    if (a.reg == 0)
+        adj_primal_body<D, MT, 0>(a.grid, (const MT*)a.maps, a.apod, a.geo, a.x, a.xbar, a.z, a.sched, a.iter, a.lambda,
+                                  nullptr, j);
+    else
+        adj_primal_body<D, MT, 1>(a.grid, (const MT*)a.maps, a.apod, a.geo, a.x, a.xbar, a.z, a.sched, a.iter, a.lambda,
+                                  nullptr, j);
+}
+
+template <int D, typename MT>
+__global__ void k_fwd_pre_b(const BPre* __restrict__ cs, const int* __restrict__ boff, int ncase) {
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    const BPre& a = cs[c];
+    fwd_pre_body<D, MT>(a.x, (const MT*)a.maps, a.apod, a.geo, a.grid,
+                        (int64_t)((int)blockIdx.x - boff[c]) * blockDim.x + threadIdx.x);
+}
+
+// Every case's iteration counter += 1 (descriptor = the counter's address).
+__global__ void k_advance_b(int* const* __restrict__ iters, int ncase) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncase) *iters[c] += 1;
+}
+
+kp_status phase_upload(BatchPhase& ph, const void* descs, size_t desc_bytes, int ncase, const std::vector<int>& boff) {
+    if (desc_bytes > ph.desc_cap) {
+        if (ph.d_desc) cudaFree(ph.d_desc);
+        ph.d_desc = nullptr;
+        ph.desc_cap = 0;
+        KP_TRY_CUDA(cudaMalloc(&ph.d_desc, desc_bytes));
+        ph.desc_cap = desc_bytes;
+    }
+    if (boff.size() > ph.boff_cap) {
+        if (ph.d_boff) cudaFree(ph.d_boff);
+        ph.d_boff = nullptr;
+        ph.boff_cap = 0;
+        KP_TRY_CUDA(cudaMalloc(&ph.d_boff, boff.size() * sizeof(int)));
+        ph.boff_cap = boff.size();
+    }
+    if (desc_bytes) KP_TRY_CUDA(cudaMemcpy(ph.d_desc, descs, desc_bytes, cudaMemcpyHostToDevice));
+    if (!boff.empty()) KP_TRY_CUDA(cudaMemcpy(ph.d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    ph.ncase = ncase;
+    ph.nblocks = boff.empty() ? 0u : (unsigned)boff.back();
+    return KP_OK;
+}
+
+void phase_free(BatchPhase& ph) {
+    if (ph.d_desc) cudaFree(ph.d_desc);
+    if (ph.d_boff) cudaFree(ph.d_boff);
+    ph = BatchPhase{};
+}
+
+void batch_iter_free(BatchIter& bi) {
+    for (BatchPhase* ph : {&bi.interp, &bi.zero, &bi.spread, &bi.primal, &bi.pre, &bi.advance}) phase_free(*ph);
+    for (auto& ph : bi.fwd) phase_free(ph);
+    for (auto& ph : bi.inv) phase_free(ph);
+    bi.fwd.clear();
+    bi.inv.clear();
+    bi.built = false;
+}
+
+// Descriptors of `sel` cases with `blocks(case)` blocks each, uploaded into ph.
+template <typename DESC, typename MAKE, typename BLOCKS>
+static kp_status build_phase(const std::vector<kp_plan>& ps, const std::vector<int>& sel, BatchPhase& ph, MAKE make,
+                             BLOCKS blocks) {
+    std::vector<DESC> ds;
+    std::vector<int> boff(1, 0);
+    for (int i : sel) {
+        const int64_t nb = blocks(ps[i]);
+        if (nb <= 0) continue;
+        if ((int64_t)boff.back() + nb > INT32_MAX) { set_error("batched launch larger than 2^31 blocks"); return KP_EINVAL; }
+        ds.push_back(make(ps[i], i));
+        boff.push_back(boff.back() + (int)nb);
+    }
+    return phase_upload(ph, ds.data(), ds.size() * sizeof(DESC), (int)ds.size(), boff);
+}
+
+kp_status batch_nufft_build(const std::vector<kp_plan>& ps, const std::vector<int>& regs, const std::vector<float>& lams,
+                            BatchIter& bi) {
+    const int n = (int)ps.size();
+    std::vector<int> all(n), l2;
+    for (int i = 0; i < n; ++i) {
+        all[i] = i;
+        if (regs[i] == KP_REG_L2) l2.push_back(i);
+    }
+    bi.yt = ps[0]->ys_t;
+    bi.mt = ps[0]->maps_t;
+    auto cgroups = [](kp_plan p, int per) { return (int64_t)((p->geo.C + per - 1) / per); };
+    KP_TRY(build_phase<BInterp>(ps, all, bi.interp, [&](kp_plan p, int) {
+        BInterp a{};
+        a.items = p->d_iitems;
+        a.k0t = p->d_k0;
+        a.wt = p->d_wt;
+        a.grid = p->d_gridF;
+        a.geo = p->geo;
+        a.tl = p->tiles;
+        a.io.ys = p->d_ys;
+        a.io.flag = p->d_flag + KP_FLAG_TIMEOUT;
+        a.io.wait = p->wait_cycles;
+        a.io.ps = p->d_ps;
+        a.io.u = p->d_u;
+        a.io.sched = p->d_sched;
+        a.io.iter = p->d_iter;
+        a.nx = (int)p->n_iitems;
+        return a;
+    }, [&](kp_plan p) { return p->n_iitems * cgroups(p, IP_CH); }));
+    KP_TRY(build_phase<BZero>(ps, all, bi.zero, [&](kp_plan p, int) {
+        BZero a{};
+        a.split = p->d_split;
+        a.geo = p->geo;
+        a.tl = p->tiles;
+        a.P = 1;
+        for (int d = 0; d < p->geo.D; ++d) a.P *= p->tiles.ts[d];
+        a.grid = p->d_grid2;
+        return a;
+    }, [&](kp_plan p) { return p->n_split; }));
+    KP_TRY(build_phase<BSpread>(ps, all, bi.spread, [&](kp_plan p, int) {
+        BSpread a{};
+        a.k0t = p->d_k0;
+        a.wt = p->d_wt;
+        a.u = p->d_u;
+        a.perm = nullptr;
+        a.ext = p->d_ext;
+        a.items = p->d_items;
+        a.geo = p->geo;
+        a.tl = p->tiles;
+        a.grid = p->d_grid2;
+        a.nx = (int)p->n_items;
+        return a;
+    }, [&](kp_plan p) { return p->n_items * cgroups(p, 4); }));
+    KP_TRY(build_phase<BPrimal>(ps, all, bi.primal, [&](kp_plan p, int i) {
+        BPrimal a{};
+        a.grid = p->d_grid2;
+        a.maps = p->d_maps;
+        a.apod = p->d_apod;
+        a.geo = p->geo;
+        a.x = p->d_x;
+        a.xbar = p->d_xbar;
+        a.z = p->d_z;
+        a.sched = p->d_sched;
+        a.iter = p->d_iter;
+        a.lambda = lams[i];
+        a.reg = regs[i] == KP_REG_L2 ? 0 : 1;
+        return a;
+    }, [&](kp_plan p) { return nblk(p->geo.N, 256); }));
+    KP_TRY(build_phase<BPre>(ps, l2, bi.pre, [&](kp_plan p, int) {
+        BPre a{};
+        a.x = p->d_xbar;
+        a.maps = p->d_maps;
+        a.apod = p->d_apod;
+        a.geo = p->geo;
+        a.grid = p->d_grid;
+        return a;
+    }, [&](kp_plan p) { return nblk(p->geo.G, 256); }));
+    std::vector<int*> it(n);
+    for (int i = 0; i < n; ++i) it[i] = ps[i]->d_iter;
+    std::vector<int> boff{0, n};
+    return phase_upload(bi.advance, it.data(), n * sizeof(int*), n, boff);
+}
+
+kp_status batch_interp_launch(const BatchIter& bi, cudaStream_t st) {
+    const BatchPhase& ph = bi.interp;
+    if (ph.nblocks == 0) return KP_OK;
+    const size_t smem = (size_t)IP_CH * IpL<2>::PER_COIL * sizeof(float2);
+    static PerDeviceOnce attr[3];
+    KP_DISPATCH_T(bi.yt, T,
+        if (attr[bi.yt].first())
+            KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_tile_b<2, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        k_interp_tile_b<2, 2, T><<<ph.nblocks, IP_THREADS, smem, st>>>((const BInterp*)ph.d_desc, ph.d_boff, ph.ncase));
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+// Split-tile clearing, then the interleaved-pair spreading (variant 6: 4 warps, coil pairs).
+kp_status batch_spread_launch(const BatchIter& bi, cudaStream_t st) {
+    if (bi.zero.nblocks > 0) {
+        k_zero_split_b<2><<<bi.zero.nblocks, 256, 0, st>>>((const BZero*)bi.zero.d_desc, bi.zero.d_boff, bi.zero.ncase);
+        KP_LAUNCH_CHECK();
+    }
+    const BatchPhase& ph = bi.spread;
+    if (ph.nblocks == 0) return KP_OK;
+    static PerDeviceOnce attr;
+    const size_t sm = spread_v_smem<2, 4>();
+    if (attr.first())
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_spread_v_b<2, float2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_spread_v_b<2, float2, 4><<<ph.nblocks, 4 * 32, sm, st>>>((const BSpread*)ph.d_desc, ph.d_boff, ph.ncase);
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+kp_status batch_primal_launch(const BatchIter& bi, cudaStream_t st) {
+    const BatchPhase& ph = bi.primal;
+    if (ph.nblocks == 0) return KP_OK;
+    KP_DISPATCH_T(bi.mt, MT, k_adj_primal_b<2, MT><<<ph.nblocks, 256, 0, st>>>((const BPrimal*)ph.d_desc, ph.d_boff, ph.ncase));
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+// Pre-step of the l2 cases' next iteration, then every case's iteration counter.
+kp_status batch_pre_launch(const BatchIter& bi, cudaStream_t st) {
+    const BatchPhase& ph = bi.pre;
+    if (ph.nblocks > 0) {
+        KP_DISPATCH_T(bi.mt, MT, k_fwd_pre_b<2, MT><<<ph.nblocks, 256, 0, st>>>((const BPre*)ph.d_desc, ph.d_boff, ph.ncase));
+        KP_LAUNCH_CHECK();
+    }
+    k_advance_b<<<(unsigned)nblk(bi.advance.ncase, 256), 256, 0, st>>>((int* const*)bi.advance.d_desc, bi.advance.ncase);
     KP_LAUNCH_CHECK();
     return KP_OK;
 }

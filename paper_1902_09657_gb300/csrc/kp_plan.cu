@@ -712,7 +712,9 @@ static void spread_lists_enqueue(kp_plan p, cudaStream_t st) {
 kp_status build_spread_lists(kp_plan p, cudaStream_t st) {
     spread_lists_enqueue(p, st);
     KP_LAUNCH_CHECK();
-    return build_spread_items(p, p->spread_chunk, st);
+    KP_TRY(build_spread_items(p, p->spread_chunk, st));
+    p->lists_version = p->traj_version;
+    return KP_OK;
 }
 
 kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale, cudaStream_t st) {
@@ -771,8 +773,12 @@ kp_status set_trajectory_internal(kp_plan p, const float* traj, float traj_scale
         return KP_EINVAL;
     }
     p->max_tile = lists ? cnt[2] : cnt[1];
-    if (lists) KP_TRY(spread_items_finish(p, p->spread_chunk, cnt[4], cnt[5], st));
-    else p->n_split = 0;
+    if (lists) {
+        KP_TRY(spread_items_finish(p, p->spread_chunk, cnt[4], cnt[5], st));
+        p->lists_version = p->traj_version;
+    } else {
+        p->n_split = 0;
+    }
     // interpolation items (own samples of each tile, pieces of at most chunk)
     p->n_iitems = cnt[6];
     if (p->n_iitems > p->iitems_cap) {

@@ -19,8 +19,17 @@ namespace kp {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Device memory the construction may use for a batch of 2N-grid spectra.
-constexpr size_t PRE_BATCH_BYTES = (size_t)256 << 20;
+// Device memory the construction may use for a batch of 2N-grid spectra: an eighth of the
+// free memory when the plan's construction is first set up, between 256 MB and 20 GB (every
+// pair spectrum of a 192^3 image with 8 coils, 36 x 453 MB, fits at once on a GB300).
+static size_t pre_batch_bytes() {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = 0;
+    }
+    return std::min<size_t>(std::max<size_t>(fr / 8, (size_t)256 << 20), (size_t)20 << 30);
+}
 
 struct PrePlan {
     int D = 0;
@@ -70,10 +79,11 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     // every pair spectrum at once when they fit in PRE_BATCH_BYTES (one FFT batch, R written
     // once per coil), else batches of 16 (2D) or 2 (3D) accumulated into R
     const size_t grid_bytes = (size_t)q->Nb * sizeof(float2);
+    const size_t budget = pre_batch_bytes();
     const int bmax = g.D == 2 ? 16 : 2;
-    if ((size_t)q->npairs * grid_bytes <= PRE_BATCH_BYTES) q->B = q->npairs;
+    if ((size_t)q->npairs * grid_bytes <= budget) q->B = q->npairs;
     else q->B = q->npairs < bmax ? q->npairs : bmax;
-    q->Cb = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.C, PRE_BATCH_BYTES / (2 * grid_bytes)));
+    q->Cb = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.C, budget / (2 * grid_bytes)));
     KP_TRY_CUDA(cudaMalloc(&q->d_R, (size_t)g.C * q->Nb * sizeof(double)));
     KP_TRY_CUDA(cudaMalloc(&q->d_q, (size_t)q->B * q->Nb * sizeof(float2)));
     KP_TRY_CUDA(cudaMalloc(&q->d_r, (size_t)q->Cb * q->Nb * sizeof(float2)));
@@ -86,7 +96,18 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     KP_TRY_CUDA(cudaMalloc(&q->d_pairs, pairs.size() * sizeof(int2)));
     KP_TRY_CUDA(cudaMemcpy(q->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
     int dims[3] = {q->nb[0], q->nb[1], q->nb[2]};
-    KP_TRY_CUFFT(cufftPlanMany(&q->fft_pairs, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, q->B));
+    if (cufftPlanMany(&q->fft_pairs, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, q->B) !=
+        CUFFT_SUCCESS) {
+        // no room for the whole batch's work area: batches of bmax pairs accumulated into R
+        cudaGetLastError();
+        const int b2 = q->npairs < bmax ? q->npairs : bmax;
+        if (b2 >= q->B) { set_error("cuFFT plan of the pair spectra failed"); return KP_ECUFFT; }
+        q->B = b2;
+        cudaFree(q->d_q);
+        q->d_q = nullptr;
+        KP_TRY_CUDA(cudaMalloc(&q->d_q, (size_t)q->B * q->Nb * sizeof(float2)));
+        KP_TRY_CUFFT(cufftPlanMany(&q->fft_pairs, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, q->B));
+    }
     q->ok_pairs = true;
     KP_TRY_CUFFT(cufftPlanMany(&q->fft_one, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, 1));
     q->ok_one = true;

@@ -334,6 +334,23 @@ __global__ void __launch_bounds__(256) k_dwt_inv_level_t(LevelArgs a) {
     inv_level_tile<D, T, MT>(a, blockIdx.x, sm);
 }
 
+// The level kernels over the cases of a batch (block -> case as in the other batched launches).
+template <int D, int T>
+__global__ void __launch_bounds__(256) k_dwt_fwd_level_b(const LevelArgs* __restrict__ cs, const int* __restrict__ boff,
+                                                         int ncase) {
+    extern __shared__ float2 sm[];
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    fwd_level_tile<D, T>(cs[c], (int)blockIdx.x - boff[c], sm);
+}
+
+template <int D, int T, typename MT>
+__global__ void __launch_bounds__(256) k_dwt_inv_level_b(const LevelArgs* __restrict__ cs, const int* __restrict__ boff,
+                                                         int ncase) {
+    extern __shared__ float2 sm[];
+    const int c = batch_case(boff, ncase, (int)blockIdx.x);
+    inv_level_tile<D, T, MT>(cs[c], (int)blockIdx.x - boff[c], sm);
+}
+
 static inline int wt_tile(int D) { return D == 2 ? 16 : 8; }
 
 template <int D, int T, typename MT>
@@ -521,6 +538,113 @@ kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st) {
             else KP_TRY((launch_inv_t<3, 8, __half2>(a, nb, st)));
         }
         p->launches += 1;
+    }
+    return KP_OK;
+}
+
+// Level arguments of the prox of one plan (the standalone level kernels' arguments of
+// wavelet_prox_levels), forward level lev or inverse level lev; *nb = its blocks.
+static LevelArgs prox_level_args(kp_plan p, float lambda, int lev, bool fwd, int* nb) {
+    const Geom& g = p->geo;
+    const int L = p->P.wavelet_levels;
+    const int T = wt_tile(g.D);
+    float2* ll[2] = {p->d_wl0, p->d_wl1};
+    LevelArgs a{};
+    int bdim[MAXD], hdim[MAXD];
+    *nb = 1;
+    for (int d = 0; d < g.D; ++d) {
+        bdim[d] = g.n[d] >> lev;
+        hdim[d] = bdim[d] / 2;
+        a.b[d] = bdim[d];
+        a.tiles[d] = fwd ? (hdim[d] + T - 1) / T : (bdim[d] + 2 * T - 1) / (2 * T);
+        *nb *= a.tiles[d];
+    }
+    a.coef = full_view(p->d_w, g);
+    a.lev_last = lev == L - 1;
+    a.sched = p->d_sched;
+    a.iter = p->d_iter;
+    if (fwd) {
+        a.src = lev == 0 ? full_view(p->d_z, g) : dense_view(ll[(lev - 1) & 1], bdim, g.D);
+        a.dst = dense_view(ll[lev & 1], hdim, g.D);
+        a.lambda = lambda;
+    } else {
+        a.src = dense_view(ll[lev & 1], hdim, g.D);
+        a.dst = lev == 0 ? full_view(p->d_x, g) : dense_view(ll[(lev - 1) & 1], bdim, g.D);
+        a.lev_first = lev == 0;
+        if (lev == 0) {
+            a.x = p->d_x;
+            a.xbar = p->d_xbar;
+            a.fgrid = p->d_grid;
+            a.maps = p->d_maps;
+            a.apod = p->d_apod;
+            a.geo = g;
+        }
+    }
+    return a;
+}
+
+kp_status batch_wavelet_build(const std::vector<kp_plan>& ps, const std::vector<int>& regs,
+                              const std::vector<float>& lams, BatchIter& bi) {
+    int Lmax = 0;
+    for (size_t i = 0; i < ps.size(); ++i)
+        if (regs[i] == KP_REG_L1_WAVELET) Lmax = std::max(Lmax, ps[i]->P.wavelet_levels);
+    bi.fwd.resize(Lmax);
+    bi.inv.resize(Lmax);
+    for (int dir = 0; dir < 2; ++dir)
+        for (int lev = 0; lev < Lmax; ++lev) {
+            std::vector<LevelArgs> ds;
+            std::vector<int> boff(1, 0);
+            for (size_t i = 0; i < ps.size(); ++i) {
+                if (regs[i] != KP_REG_L1_WAVELET || lev >= ps[i]->P.wavelet_levels) continue;
+                int nb = 0;
+                ds.push_back(prox_level_args(ps[i], lams[i], lev, dir == 0, &nb));
+                boff.push_back(boff.back() + nb);
+            }
+            KP_TRY(phase_upload(dir == 0 ? bi.fwd[lev] : bi.inv[lev], ds.data(), ds.size() * sizeof(LevelArgs),
+                                (int)ds.size(), boff));
+        }
+    return KP_OK;
+}
+
+// Forward levels 0 .. Lmax-1, then inverse levels Lmax-1 .. 0 (2D, tiles of 16).
+kp_status batch_wavelet_launch(const BatchIter& bi, cudaStream_t st) {
+    constexpr int D = 2, T = 16;
+    static PerDeviceOnce attr_f, attr_i[3];
+    size_t smf, smi;
+    {
+        constexpr int EI = 2 * T + 6, E = T + 4;
+        smf = ((size_t)EI * EI + (size_t)EI * 2 * T) * sizeof(float2);
+        smi = ((size_t)(2 * E) * (2 * E) + (size_t)(2 * E) * 2 * T) * sizeof(float2);
+    }
+    if (attr_f.first())
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_fwd_level_b<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    for (size_t lev = 0; lev < bi.fwd.size(); ++lev) {
+        const BatchPhase& ph = bi.fwd[lev];
+        if (ph.nblocks == 0) continue;
+        k_dwt_fwd_level_b<D, T><<<ph.nblocks, 256, smf, st>>>((const LevelArgs*)ph.d_desc, ph.d_boff, ph.ncase);
+        KP_LAUNCH_CHECK();
+    }
+    for (int lev = (int)bi.inv.size() - 1; lev >= 0; --lev) {
+        const BatchPhase& ph = bi.inv[lev];
+        if (ph.nblocks == 0) continue;
+        switch (bi.mt) {
+            case KP_C64:
+                if (attr_i[0].first())
+                    KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level_b<D, T, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+                k_dwt_inv_level_b<D, T, float2><<<ph.nblocks, 256, smi, st>>>((const LevelArgs*)ph.d_desc, ph.d_boff, ph.ncase);
+                break;
+            case KP_C32_BF16:
+                if (attr_i[1].first())
+                    KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level_b<D, T, __nv_bfloat162>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+                k_dwt_inv_level_b<D, T, __nv_bfloat162><<<ph.nblocks, 256, smi, st>>>((const LevelArgs*)ph.d_desc, ph.d_boff, ph.ncase);
+                break;
+            default:
+                if (attr_i[2].first())
+                    KP_TRY_CUDA(cudaFuncSetAttribute(k_dwt_inv_level_b<D, T, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+                k_dwt_inv_level_b<D, T, __half2><<<ph.nblocks, 256, smi, st>>>((const LevelArgs*)ph.d_desc, ph.d_boff, ph.ncase);
+                break;
+        }
+        KP_LAUNCH_CHECK();
     }
     return KP_OK;
 }

@@ -115,13 +115,55 @@ def test_batch_launch_count_and_bad_inputs():
     before = [p.launch_count() for p in plans]
     batch.solve(yd, None, regs, lams, 7)
     grown = [p.launch_count() - b for p, b in zip(plans, before)]
-    assert all(g > 7 for g in grown)          # per-iteration kernels are counted on replay
+    assert all(g > 0 for g in grown) and sum(grown) > 7   # per-iteration kernels are counted on replay
     with pytest.raises(KpError):
         batch.solve(yd, None, ["l1_wavelet", "l1_wavelet"], lams, 3)   # case 1 has no wavelet levels
     bad = np.ones(ps[0].shape, np.float32)
     bad[0, 5] = 0.0
     with pytest.raises(KpError):
         batch.solve(yd, [to_dev(bad), None], regs, lams, 3)
+    batch.close()
+
+
+def _iteration_launches(batch, plans, yd, regs, lams):
+    """Own kernels one batched PDHG iteration adds (two solves that differ by 7 iterations)."""
+    def grown(iters):
+        before = sum(p.launch_count() for p in plans)
+        xs = batch.solve(yd, None, regs, lams, iters)
+        return sum(p.launch_count() for p in plans) - before, xs
+    grown(3)                                   # capture
+    d3, _ = grown(3)
+    d10, xs = grown(10)
+    assert (d10 - d3) % 7 == 0
+    return (d10 - d3) // 7, xs
+
+
+def test_batch_phase_form():
+    """2D l2 / l1-wavelet cases in the phase form: one launch per phase over all cases
+    (interpolation, split clearing, spreading, primal step, each wavelet level, pre-step,
+    counters), so the own kernels per iteration do not grow with the number of cases; the
+    results equal the per-case form's and the oracle's."""
+    need_gpu()
+    from paper_1902_09657_gb300.api import Batch
+    plans, ys, ps, Ls, lams, oin = _setup(CASES)
+    regs = [c[5] for c in CASES]
+    yd = [to_dev(y) for y in ys]
+    pd = [to_dev(p.astype(np.float32)) for p in ps]
+    batch = Batch(plans, form="phases")
+    per_phase, xs_phase = _iteration_launches(batch, plans, yd, regs, lams)
+    lmax = max(c[6] for c in CASES)
+    assert per_phase <= 7 + 2 * lmax
+    batch.set_form("per_case")
+    per_case, xs_case = _iteration_launches(batch, plans, yd, regs, lams)
+    assert per_case > per_phase
+    for i in range(len(CASES)):
+        assert rel(xs_phase[i].cpu().numpy(), xs_case[i].cpu().numpy(), f"case {i} phase vs per-case form") < 2e-6, i
+    batch.set_form("phases")
+    iters = 40
+    xs = batch.solve(yd, pd, regs, lams, iters)
+    for i, (w, A, AH, shape) in enumerate(oin):
+        x_ref, _, _, _ = osv.pdhg(A, AH, ys[i], ps[i], shape, regs[i], lams[i], iters, Ls[i], levels=w.wavelet_levels)
+        assert rel(xs[i].cpu().numpy(), x_ref, f"case {i} phase form vs oracle") < 1e-5, i
     batch.close()
 
 
