@@ -91,6 +91,42 @@ __host__ __device__ __forceinline__ int tshift(int i, int sh, int g) { int p = i
 // grid index of shifted coordinate p (0 <= p < g)
 __host__ __device__ __forceinline__ int tunshift(int p, int sh, int g) { int i = p - sh; return i < 0 ? i + g : i; }
 
+// ---------------------------------------------------------------- float-float arithmetic
+// A value held as an unevaluated sum hi + lo of two float32 numbers (about 48 significant
+// bits), built from the error-free transformations of floating-point arithmetic: Knuth's
+// two-sum (a + b = s + e exactly, any a, b), the fast two-sum for |a| >= |b|, and the product
+// a b = p + e exactly through a fused multiply-add (Dekker's product with an FMA).  Used where
+// a sum needs more than float32 (denominator sums with cancellation) and the float64 pipe of
+// the GPU would be the bound.  The _rn intrinsics keep the compiler from contracting the
+// additions and products whose rounding errors these formulas recover.
+struct ff32 {
+    float hi, lo;
+};
+__device__ __forceinline__ ff32 ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff32 ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff32 ff_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// (x.hi + x.lo) * b, relative error about 2^-46
+__device__ __forceinline__ ff32 ff_mul(ff32 x, float b) {
+    ff32 p = ff_two_prod(x.hi, b);
+    return ff_fast_two_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+// x + y, error about 2^-46 of max(|x|, |y|)
+__device__ __forceinline__ ff32 ff_add(ff32 x, ff32 y) {
+    const ff32 s = ff_two_sum(x.hi, y.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ double ff_to_double(ff32 x) { return (double)x.hi + (double)x.lo; }
+
 // Once-per-device flag for host-side set-up that the runtime keeps per device, such as
 // cudaFuncSetAttribute (devices 0..63): first() is true the first time it is asked on the
 // current device.

@@ -133,9 +133,15 @@ __device__ __forceinline__ void fwd_pre_body(const float2* __restrict__ x, const
                                              float2* __restrict__ grid, int64_t gi) {
     if (gi >= geo.G) return;
     int ii[D];
-    int64_t r = gi;
+    if (geo.G < ((int64_t)1 << 31)) {        // 32-bit index arithmetic (64-bit division is slow)
+        unsigned r = (unsigned)gi;
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) { ii[d] = (int)(r % geo.g[d]); r /= geo.g[d]; }
+        for (int d = D - 1; d >= 0; --d) { ii[d] = (int)(r % (unsigned)geo.g[d]); r /= (unsigned)geo.g[d]; }
+    } else {
+        int64_t r = gi;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) { ii[d] = (int)(r % geo.g[d]); r /= geo.g[d]; }
+    }
     int64_t j = 0;
     float a = 1.f;
     bool inside = true;
@@ -1010,22 +1016,31 @@ constexpr int SL_RS = 12, SL_PS = PT * SL_RS, SL_P = PT * SL_PS;
 
 template <int NP>
 static size_t spread_own_smem() {
+    // accumulator + per staged sample (one sentinel slot more): NP coil pairs, the y x weight
+    // products, and per warp parity the plane offset and the two z weights
     return (size_t)NP * OT_PAIR * sizeof(float4) +
-           (size_t)OT_CHUNK * (NP * sizeof(float4) + (KW + KW * KW) * sizeof(float) + sizeof(int));
+           (size_t)(OT_CHUNK + 1) * (NP * sizeof(float4) + KW * KW * sizeof(float) + 2 * sizeof(int) + 4 * sizeof(float));
 }
 
+// Phase A: one CTA per own-sample item (the samples whose first tap lies in one tile, at most
+// OT_CHUNK at a time) and group of 2 NP coils.  Warp (pair, par) owns coil pair `pair` and the
+// padded z-planes of parity `par`; its 32 lanes are the (z, y, x) taps (jsel: the 2 z taps of
+// that parity, yx: the 16 (y, x) taps).  Staging computes per sample and parity the plane
+// offset of the first tap of that parity and the two z weights, so the inner loop only reads
+// them; consecutive samples with the same offset (same planes, rows and columns: a run) are
+// summed in registers and added to the accumulator once.
 template <typename UT, int NP>
 __global__ void __launch_bounds__(NP * 64)
 k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* __restrict__ u,
              const int* __restrict__ perm, const int4* __restrict__ items, Geom geo, Tiles tl,
              float2* __restrict__ halo) {
-    constexpr int D = 3, NT = NP * 64;
+    constexpr int D = 3, NT = NP * 64, CH = OT_CHUNK + 1;
     extern __shared__ __align__(16) float4 smo[];
     float4* acc = smo;                                              // [NP][PT][PT][OT_RS]
-    float4* su = acc + NP * OT_PAIR;                                // [OT_CHUNK][NP] coil pairs
-    float* swz = (float*)(su + OT_CHUNK * NP);                      // [OT_CHUNK][KW] z weights
-    float* swyx = swz + OT_CHUNK * KW;                              // [OT_CHUNK][KW * KW] y x weight products
-    int* sb = (int*)(swyx + OT_CHUNK * KW * KW);                    // [OT_CHUNK] (padded offset << 1) | z0 parity
+    float4* su = acc + NP * OT_PAIR;                                // [CH][NP] coil pairs
+    float* swyx = (float*)(su + CH * NP);                           // [CH][KW * KW] y x weight products
+    int* soff = (int*)(swyx + CH * KW * KW);                        // [2][CH] plane offset per parity
+    float* swz = (float*)(soff + 2 * CH);                           // [2][CH][2] z weights per parity
     const int4 it = items[blockIdx.x];
     const int tile = it.x, beg = it.y, end = it.z, slot = it.w;
     const int c0 = blockIdx.y * 2 * NP;
@@ -1044,13 +1059,19 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pair = warp % NP, par = warp / NP;
     const int jsel = lane >> 4, yx = lane & 15;
-    // this lane's tap relative to the sample's first tap: z offset jzb + 2 jsel (jzb from parity), y = yx >> 2, x = yx & 3
+    // this lane's tap relative to the first tap of the warp's parity: z + 2 jsel, y = yx >> 2, x = yx & 3
     float4* const mine = acc + pair * OT_PAIR + 2 * jsel * OT_PS + (yx >> 2) * OT_RS + (yx & 3);
+    const int* const offs = soff + par * CH;
+    const float* const wzs = swz + par * CH * 2 + jsel;
     const bool live = 2 * pair < cc;
     for (int s0 = beg; s0 < end; s0 += OT_CHUNK) {
         const int n = min(OT_CHUNK, end - s0);
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += NT) {
+        for (int i = threadIdx.x; i <= n; i += NT) {
+            if (i == n) {                                           // sentinel: read by the last prefetch only
+                soff[i] = soff[CH + i] = -1;
+                continue;
+            }
             const int s = s0 + i;
             const int64_t un = perm ? perm[s] : s;
 #pragma unroll
@@ -1062,11 +1083,10 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
             int l[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) l[d] = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];   // in [0, ts)
-            sb[i] = ((l[0] * OT_PS + l[1] * OT_RS + l[2]) << 1) | (l[0] & 1);
-            float wy[KW], wx[KW];
+            float wz[KW], wy[KW], wx[KW];
 #pragma unroll
             for (int j = 0; j < KW; ++j) {
-                swz[i * KW + j] = wt[(int64_t)j * geo.M + s];
+                wz[j] = wt[(int64_t)j * geo.M + s];
                 wy[j] = wt[(int64_t)(KW + j) * geo.M + s];
                 wx[j] = wt[(int64_t)(2 * KW + j) * geo.M + s];
             }
@@ -1074,45 +1094,48 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
             for (int a = 0; a < KW; ++a)
 #pragma unroll
                 for (int b = 0; b < KW; ++b) swyx[i * KW * KW + a * KW + b] = wy[a] * wx[b];
+            // parity q: the first z tap of that parity is jz0 = (q ^ l0) & 1, its plane l0 + jz0
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int jz0 = (q ^ l[0]) & 1;
+                soff[q * CH + i] = (l[0] + jz0) * OT_PS + l[1] * OT_RS + l[2];
+                swz[(q * CH + i) * 2] = wz[jz0];
+                swz[(q * CH + i) * 2 + 1] = wz[jz0 + 2];
+            }
         }
         __syncthreads();
         if (live && n > 0) {
-            int run = -1;                                            // current run's key (sb value), warp-uniform
-            float4* dst = nullptr;
+            int run = -1;                                            // current run's offset, warp-uniform
             float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-            // sample i's staged values are in registers before its turn: the loads of sample
-            // i + 1 are issued ahead of sample i's shared-memory update
-            int b = sb[0];
-            float wz = swz[((par ^ b) & 1) + 2 * jsel], wyx = swyx[yx];
+            // sample i's staged values are in registers before its turn (the sentinel makes the
+            // prefetch of sample n harmless)
+            int off = offs[0];
+            float wz = wzs[0], wyx = swyx[yx];
             float4 uv = su[pair];
             for (int i = 0; i < n; ++i) {
-                const int bi = b;
+                const int oi = off;
                 const float w = wz * wyx;
                 const float4 ui = uv;
-                if (i + 1 < n) {
-                    b = sb[i + 1];
-                    wz = swz[(i + 1) * KW + ((par ^ b) & 1) + 2 * jsel];
-                    wyx = swyx[(i + 1) * KW * KW + yx];
-                    uv = su[(i + 1) * NP + pair];
-                }
-                if (bi != run) {
-                    if (dst) {
-                        float4 v = *dst;
+                off = offs[i + 1];
+                wz = wzs[(i + 1) * 2];
+                wyx = swyx[(i + 1) * KW * KW + yx];
+                uv = su[(i + 1) * NP + pair];
+                if (oi != run) {
+                    if (run >= 0) {
+                        float4 v = mine[run];
                         v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
-                        *dst = v;
+                        mine[run] = v;
                     }
-                    run = bi;
-                    // planes z0 + jz of this warp's parity: jz = jzb, jzb + 2
-                    dst = mine + (bi >> 1) + ((par ^ bi) & 1) * OT_PS;
+                    run = oi;
                     r = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 r.x = fmaf(w, ui.x, r.x); r.y = fmaf(w, ui.y, r.y);
                 r.z = fmaf(w, ui.z, r.z); r.w = fmaf(w, ui.w, r.w);
             }
-            if (dst) {
-                float4 v = *dst;
+            if (run >= 0) {
+                float4 v = mine[run];
                 v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
-                *dst = v;
+                mine[run] = v;
             }
         }
     }

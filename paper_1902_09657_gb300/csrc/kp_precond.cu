@@ -75,6 +75,11 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     q->C = g.C;
     q->Nb = 1;
     for (int d = 0; d < g.D; ++d) { q->nb[d] = 2 * g.n[d]; q->Nb *= q->nb[d]; }
+    if (q->Nb >= ((int64_t)1 << 31)) {
+        // the construction indexes the 2N grid (and the 2N plan's oversampled grid) in 32 bits
+        set_error("preconditioner: the 2N image has 2^31 points or more");
+        return KP_EINVAL;
+    }
     q->npairs = g.C * (g.C + 1) / 2;
     // every pair spectrum at once when they fit in PRE_BATCH_BYTES (one FFT batch, R written
     // once per coil), else batches of 16 (2D) or 2 (3D) accumulated into R
@@ -119,6 +124,10 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     prm.wavelet_levels = 0;
     for (int d = 0; d < g.D; ++d) prm.img[d] = 2 * g.n[d];
     KP_TRY(plan_create_internal(&p->pre_nufft, &prm, true, st));
+    if (p->pre_nufft->geo.G >= ((int64_t)1 << 31)) {
+        set_error("preconditioner: the 2N image's oversampled grid has 2^31 points or more");
+        return KP_EINVAL;
+    }
     return KP_OK;
 }
 
@@ -182,42 +191,41 @@ __global__ void k_accum_R(const float2* __restrict__ Q, const int2* __restrict__
     }
 }
 
+// Index of the frequency -m (periodic) on the 2N grid, m < 2^31.
+__device__ __forceinline__ unsigned neg_index(unsigned m, int D, unsigned nb0, unsigned nb1, unsigned nb2) {
+    if (D == 2) {
+        const unsigned i1 = m % nb1, i0 = m / nb1;
+        return (i0 ? nb0 - i0 : 0u) * nb1 + (i1 ? nb1 - i1 : 0u);
+    }
+    const unsigned i2 = m % nb2, r = m / nb2, i1 = r % nb1, i0 = r / nb1;
+    return ((i0 ? nb0 - i0 : 0u) * nb1 + (i1 ? nb1 - i1 : 0u)) * nb2 + (i2 ? nb2 - i2 : 0u);
+}
+
+// |q|^2 as a float-float value (both squares exact, one rounding in the sum's low part)
+__device__ __forceinline__ ff32 ff_abs2(float2 q) { return ff_add(ff_two_prod(q.x, q.x), ff_two_prod(q.y, q.y)); }
+
 // With every pair's spectrum in Q (pair (c, d), c <= d, at index c C - c (c - 1) / 2 + d - c):
-// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, summed in float64 and written
-// once.  One thread per (m, c), c = blockIdx.y.
+// R_c[m] = sum_{d >= c} |Q_cd[m]|^2 + sum_{d < c} |Q_dc[-m]|^2, summed in float-float (about 48
+// bits: the float64 pipe would bound this pass) and written once as float64.  One thread per
+// (m, c), c = blockIdx.y; the 2N grid has fewer than 2^31 points (checked at set-up).
 __global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0, int nb1, int nb2, int64_t Nb,
                             double* __restrict__ R) {
-    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= Nb) return;
+    const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int64_t)m >= Nb) return;
     const int c = blockIdx.y;
-    const int nb[3] = {nb0, nb1, nb2};
-    int64_t r = m, mneg = 0, stride = 1;
-    for (int d = D - 1; d >= 0; --d) {
-        int i = (int)(r % nb[d]);
-        r /= nb[d];
-        int in = i == 0 ? 0 : nb[d] - i;
-        mneg += in * stride;
-        stride *= nb[d];
-    }
-    double acc = 0.0;
-    for (int d = 0; d < c; ++d) {
-        const float2 b = Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg];
-        acc = fma((double)b.x, (double)b.x, acc);
-        acc = fma((double)b.y, (double)b.y, acc);
-    }
+    const unsigned mneg = neg_index(m, D, (unsigned)nb0, (unsigned)nb1, (unsigned)nb2);
+    ff32 acc = {0.f, 0.f};
+    for (int d = 0; d < c; ++d)
+        acc = ff_add(acc, ff_abs2(Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg]));
     const size_t p0 = (size_t)(c * C - c * (c - 1) / 2);
-    for (int d = c; d < C; ++d) {
-        const float2 a = Q[(p0 + d - c) * Nb + m];
-        acc = fma((double)a.x, (double)a.x, acc);
-        acc = fma((double)a.y, (double)a.y, acc);
-    }
-    R[(size_t)c * Nb + m] = acc;
+    for (int d = c; d < C; ++d) acc = ff_add(acc, ff_abs2(Q[(p0 + d - c) * Nb + m]));
+    R[(size_t)c * Nb + m] = ff_to_double(acc);
 }
 
 // r_c = R_c / Nb for the coils c0 .. c0 + nc - 1 (grid c - c0 of out).
-__global__ void k_R_to_c(const double* __restrict__ R, int64_t Nb, int nc, float2* __restrict__ out) {
+__global__ void k_R_to_c(const double* __restrict__ R, int64_t Nb, int nc, double inv_nb, float2* __restrict__ out) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < Nb * nc) out[m] = make_float2((float)(R[m] / (double)Nb), 0.f);
+    if (m < Nb * nc) out[m] = make_float2((float)(R[m] * inv_nb), 0.f);
 }
 
 // v[j] = r[(j - n) mod 2n] * h[j] on the centred 2N image (lag k_d = j_d - n_d).
@@ -229,14 +237,14 @@ __global__ void k_rh(const float2* __restrict__ r, const float2* __restrict__ h,
     r += (size_t)blockIdx.y * Nb;
     v += (size_t)blockIdx.y * Nb;
     const int nb[3] = {nb0, nb1, nb2};
-    int64_t rr = j, ri = 0, stride = 1;
+    unsigned rr = (unsigned)j, ri = 0, stride = 1;     // the 2N grid has fewer than 2^31 points
     for (int d = D - 1; d >= 0; --d) {
-        int jd = (int)(rr % nb[d]);
-        rr /= nb[d];
-        int k = jd - nb[d] / 2;
-        int idx = k < 0 ? k + nb[d] : k;
+        const unsigned jd = rr % (unsigned)nb[d];
+        rr /= (unsigned)nb[d];
+        const int k = (int)jd - nb[d] / 2;
+        const unsigned idx = (unsigned)(k < 0 ? k + nb[d] : k);
         ri += idx * stride;
-        stride *= nb[d];
+        stride *= (unsigned)nb[d];
     }
     v[j] = cmul(r[ri], h[j]);
 }
@@ -278,11 +286,11 @@ __global__ void k_den_p(const float2* __restrict__ Vhat, const int* __restrict__
                         int c_first, int c_count, float* __restrict__ p, int* __restrict__ bad) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g2.M) return;
-    int64_t off[D][KW];
-    double w[D][KW];
+    int off[D][KW];                 // the 2N plan's grid has fewer than 2^31 points
+    float w[D][KW];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        int64_t stride = 1;
+        int stride = 1;
         for (int e = d + 1; e < D; ++e) stride *= g2.g[e];
         const int k0 = k0t[(int64_t)d * g2.M + s];
 #pragma unroll
@@ -290,28 +298,26 @@ __global__ void k_den_p(const float2* __restrict__ Vhat, const int* __restrict__
             int ix = k0 + j;
             if (ix >= g2.g[d]) ix -= g2.g[d];
             off[d][j] = ix * stride;
-            w[d][j] = (double)wt[(int64_t)(d * KW + j) * g2.M + s];
+            w[d][j] = wt[(int64_t)(d * KW + j) * g2.M + s];
         }
     }
-    double acc = 0.0;
-    if (D == 2) {
+    // sum over the taps of w_a w_b (w_e) Re(Vhat) in float-float: the products of two float32
+    // weights are exact, each further product and every addition keeps about 48 bits
+    ff32 acc = {0.f, 0.f};
 #pragma unroll
-        for (int a = 0; a < KW; ++a)
+    for (int a = 0; a < KW; ++a)
 #pragma unroll
-            for (int b = 0; b < KW; ++b)
-                acc = fma(w[0][a] * w[D - 1][b], (double)Vhat[off[0][a] + off[D - 1][b]].x, acc);
-    } else {
-#pragma unroll
-        for (int a = 0; a < KW; ++a)
-#pragma unroll
-            for (int b = 0; b < KW; ++b) {
-                const double wab = w[0][a] * w[1 % D][b];
+        for (int b = 0; b < KW; ++b) {
+            const ff32 wab = ff_two_prod(w[0][a], w[1 % D][b]);
+            if (D == 2) {
+                acc = ff_add(acc, ff_mul(wab, Vhat[off[0][a] + off[1 % D][b]].x));
+            } else {
 #pragma unroll
                 for (int e = 0; e < KW; ++e)
-                    acc = fma(wab * w[D - 1][e], (double)Vhat[off[0][a] + off[1 % D][b] + off[D - 1][e]].x, acc);
+                    acc = ff_add(acc, ff_mul(ff_mul(wab, w[D - 1][e]), Vhat[off[0][a] + off[1 % D][b] + off[D - 1][e]].x));
             }
-    }
-    const double dv = acc * (double)(1 << D) / sqrt((double)g2.N);
+        }
+    const double dv = ff_to_double(acc) * (double)(1 << D) / sqrt((double)g2.N);
     const int64_t i = perm[s];
     float val;
     if (dv > 0 && isfinite(dv)) {
@@ -443,7 +449,7 @@ kp_status kp::circulant_enqueue(kp_plan plan, cudaStream_t st) {
         plan->launches += 2;
     }
     // rho = IFFT(R) / Nb
-    k_R_to_c<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_R, q->Nb, 1, q->d_r);
+    k_R_to_c<<<nblk(q->Nb, 256), 256, 0, st>>>(q->d_R, q->Nb, 1, 1.0 / (double)q->Nb, q->d_r);
     KP_LAUNCH_CHECK();
     KP_TRY_CUFFT(cufftExecC2C(q->fft_one, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r, CUFFT_INVERSE));
     // h on the 2N image: the 2N plan's adjoint carries (2^D N)^{-1/2}, h carries N^{-1/2}
@@ -540,7 +546,7 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
     // NUFFT of v_c and p_c
     for (int c0 = 0; c0 < C; c0 += q->Cb) {
         const int nc = C - c0 < q->Cb ? C - c0 : q->Cb;
-        k_R_to_c<<<nblk(q->Nb * nc, 256), 256, 0, st>>>(q->d_R + (size_t)c0 * q->Nb, q->Nb, nc, q->d_r);
+        k_R_to_c<<<nblk(q->Nb * nc, 256), 256, 0, st>>>(q->d_R + (size_t)c0 * q->Nb, q->Nb, nc, 1.0 / (double)q->Nb, q->d_r);
         KP_LAUNCH_CHECK();
         KP_TRY_CUFFT(cufftExecC2C(nc == 1 ? q->fft_one : q->fft_coils, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r,
                                   CUFFT_INVERSE));
