@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkpdhg.so")
-SOURCES = ["kp_plan.cu", "kp_nufft.cu", "kp_pdhg.cu", "kp_precond.cu", "kp_wavelet.cu", "kp_unrolled.cu", "kp_noalloc.cu", "kp_batch.cu", "kp_compare.cu"]
+SOURCES = ["kp_plan.cu", "kp_nufft.cu", "kp_pdhg.cu", "kp_precond.cu", "kp_wavelet.cu", "kp_unrolled.cu", "kp_noalloc.cu", "kp_batch.cu", "kp_compare.cu", "kp_fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

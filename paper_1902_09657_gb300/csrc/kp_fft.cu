@@ -1,0 +1,385 @@
+// Own 3D FFT of a plan's oversampled grids (all coils at once), used in place of cuFFT for 3D
+// plans whose grid sizes factor into 2, 3 and 5 (Sec. 6's oversampled FFT, unnormalised in
+// both directions like cuFFT: forward e^{-2 pi i n k / g}, inverse e^{+2 pi i n k / g}).
+//
+// One pass per axis.  A CTA takes 16 lines of one axis (8 for axes longer than 256 points): rows
+// along x, or columns along y or z for 16 (8) consecutive x, so every global access is a 128-
+// (64-) byte row segment.  Each thread issues all its loads before storing them to shared
+// memory, where a self-sorting (Stockham) mixed-radix transform runs (radix 4, 2, 3 and 5
+// stages, twiddles from a table of the g-th roots of unity built on the host in float64); then
+// the lines are written back.
+//
+// The passes exploit the structure of the NUFFT's grids.  The image occupies n_d of the g_d
+// indices per axis (the band [0, n - n/2) and [g - n/2, g), where the pre-step puts it), and
+// the adjoint reads only that crop back:
+// * forward (x, then y, then z): the x pass transforms only the rows whose (z, y) lie in the
+//   band and reads only their band points; the y pass takes only the z planes of the band and
+//   reads only band rows; the z pass reads only band planes.  Points outside the band are zeros
+//   that are never read.
+// * inverse (z, then y, then x): the z pass writes only the band planes, the y pass transforms
+//   only band planes and writes only band rows, the x pass only band rows and writes only band
+//   points.  Afterwards only the crop holds the transform (the only part the adjoint reads).
+#include "kp_internal.cuh"
+
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+namespace kp {
+
+constexpr int FF_LINES = 16;     // lines per CTA (at most)
+// lines per CTA for length N: 16 up to 256 points (16 x = 128-byte row segments), else 8 so
+// that the two buffers stay near 64 KB and several CTAs share an SM
+constexpr int ff_lines(int N) { return N <= 256 ? 16 : 8; }
+constexpr int FF_T = 256;        // threads per CTA
+constexpr int FF_MAXN = 512;     // longest axis handled
+constexpr int FF_MAXST = 10;     // radix stages at most
+
+struct FfConst {                 // sqrt(3)/2, cos and sin of 2 pi/5 and of 4 pi/5 (float64 on the host, rounded once)
+    float s3, c51, s51, c52, s52;
+};
+
+struct FfAxis {
+    int N;                       // transform length (grid points along the axis)
+    int nband;                   // image points along the axis
+    int nst;                     // radix stages
+    int r[FF_MAXST];             // radices in the order applied
+    const float2* tw;            // e^{-2 pi i m / N}, m in [0, N)
+};
+
+struct Fft3Plan {
+    FfAxis ax[3];
+    float2* d_tw = nullptr;
+    FfConst k;
+};
+
+__device__ __forceinline__ bool in_band(int i, int n, int g) { return i < n - n / 2 || i >= g - n / 2; }
+__device__ __forceinline__ int band_index(int bi, int n, int g) { return bi < n - n / 2 ? bi : bi + (g - n); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * (-i s) for the forward sign (s = +1) or a * (+i) for the inverse (s = -1): (s a.y, -s a.x)
+__device__ __forceinline__ float2 cmul_mi(float2 a, float s) { return make_float2(s * a.y, -s * a.x); }
+
+// One R-point DFT of v[0..R-1] in place, sign s = +1 forward (omega = e^{-2 pi i / R}), -1 inverse.
+template <int R>
+__device__ __forceinline__ void small_dft(float2* v, float s, const FfConst& k) {
+    if (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const float2 t2 = cadd(v[1], v[3]), t3 = cmul_mi(csub(v[1], v[3]), s);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else if (R == 3) {
+        // y1,2 = a0 - (a1 + a2)/2 -/+ i s sqrt(3)/2 (a1 - a2)
+        const float2 sm = cadd(v[1], v[2]), d = cmul_mi(csub(v[1], v[2]), s * k.s3);
+        const float2 m = make_float2(v[0].x - 0.5f * sm.x, v[0].y - 0.5f * sm.y);
+        v[0] = cadd(v[0], sm);
+        v[1] = cadd(m, d);
+        v[2] = csub(m, d);
+    } else {
+        // R == 5: t1 = a1 + a4, t2 = a2 + a3, t3 = a1 - a4, t4 = a2 - a3;
+        // y1,4 = a0 + c1 t1 + c2 t2 -/+ i (s1 t3 + s2 t4), y2,3 = a0 + c2 t1 + c1 t2 -/+ i (s2 t3 - s1 t4)
+        const float2 a0 = v[0];
+        const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        const float2 p1 = make_float2(a0.x + k.c51 * t1.x + k.c52 * t2.x, a0.y + k.c51 * t1.y + k.c52 * t2.y);
+        const float2 p2 = make_float2(a0.x + k.c52 * t1.x + k.c51 * t2.x, a0.y + k.c52 * t1.y + k.c51 * t2.y);
+        const float2 q1 = cmul_mi(make_float2(k.s51 * t3.x + k.s52 * t4.x, k.s51 * t3.y + k.s52 * t4.y), s);
+        const float2 q2 = cmul_mi(make_float2(k.s52 * t3.x - k.s51 * t4.x, k.s52 * t3.y - k.s51 * t4.y), s);
+        v[0] = make_float2(a0.x + t1.x + t2.x, a0.y + t1.y + t2.y);
+        v[1] = cadd(p1, q1);
+        v[4] = csub(p1, q1);
+        v[2] = cadd(p2, q2);
+        v[3] = csub(p2, q2);
+    }
+}
+
+// Radices of N in the order applied (all 4s, then 2, 3, 5), at compile time.
+constexpr int fac_count(int N) {
+    int c = 0;
+    for (int f : {4, 2, 3, 5})
+        while (N % f == 0) { N /= f; ++c; }
+    return N == 1 ? c : -1;
+}
+constexpr int fac_at(int N, int i) {
+    int c = 0;
+    for (int f : {4, 2, 3, 5})
+        while (N % f == 0) {
+            if (c == i) return f;
+            N /= f;
+            ++c;
+        }
+    return 1;
+}
+
+// The CTA's lines, transformed in shared memory (buffers a and b, twiddles tw).  Element n of
+// line l sits at l * N + n when XL (rows along x), else n * LN + l (LN lines).  Stockham,
+// decimation in time: stage ST (radix r) combines r transforms of length L into one of length
+// L r; butterfly (j, kk) (j < m = N / (L r), kk < L) reads a[kk N / L + j + q m], q < r,
+// multiplies input q by w^(q kk m) (w = e^{-+2 pi i / N}), and writes its r-point DFT's output t
+// to b[(kk + L t) m + j].  N, the radices and every stride are compile-time constants.
+// Returns the buffer holding the result.
+template <int N, bool XL, int ST, int L>
+__device__ __forceinline__ float2* stockham(float2* a, float2* b, const float2* tw, float s, const FfConst& k) {
+    constexpr int LN = ff_lines(N);
+    if constexpr (ST == fac_count(N)) {
+        return a;
+    } else {
+        constexpr int r = fac_at(N, ST), Lr = L * r, m = N / Lr, nb = N / r, NL = N / L;
+        for (int it = threadIdx.x; it < LN * nb; it += FF_T) {
+            const int l = XL ? it / nb : it % LN;
+            const int bf = XL ? it - l * nb : it / LN;
+            const int j = bf % m, kk = bf / m;
+            float2 v[r];
+            const int base = kk * NL + j;
+#pragma unroll
+            for (int q = 0; q < r; ++q) {
+                const int idx = base + q * m;
+                float2 x = a[XL ? l * N + idx : idx * LN + l];
+                if (q > 0 && L > 1) {
+                    float2 w = tw[q * kk * m];
+                    w.y *= s;                                       // conjugate for the inverse
+                    x = make_float2(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
+                }
+                v[q] = x;
+            }
+            small_dft<r>(v, s, k);
+#pragma unroll
+            for (int t = 0; t < r; ++t) {
+                const int idx = (kk + L * t) * m + j;
+                b[XL ? l * N + idx : idx * LN + l] = v[t];
+            }
+        }
+        __syncthreads();
+        return stockham<N, XL, ST + 1, Lr>(b, a, tw, s, k);
+    }
+}
+
+// Pass along AXIS (0 = z, 1 = y, 2 = x) of every coil's grid; INV selects the inverse.  Line
+// selection and pruning as in the file header.
+template <int AXIS, bool INV, int N>
+__global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out, Geom geo, FfAxis ax, FfConst k) {
+    // (no __restrict__: the y, z and inverse passes work in place, each CTA on its own lines)
+    constexpr int LN = ff_lines(N), TOT = LN * N, PER = (TOT + FF_T - 1) / FF_T;
+    constexpr bool XL = AXIS == 2;
+    extern __shared__ __align__(16) float2 fsm[];
+    float2* A = fsm;
+    float2* B = fsm + TOT;
+    float2* tw = B + TOT;
+    for (int i = threadIdx.x; i < N; i += FF_T) tw[i] = ax.tw[i];
+    const int g0 = geo.g[0], g1 = geo.g[1], g2 = geo.g[2];
+    const int n0 = geo.n[0], n1 = geo.n[1], n2 = geo.n[2];
+    const bool load_band = !INV, store_band = INV;      // forward reads only the band, inverse writes only it
+    // per line: base offset of element 0, or -1 when the line does not exist; element n at base + n stride
+    __shared__ int64_t base_s[FF_LINES];
+    int64_t stride;
+    if (AXIS == 2) {
+        stride = 1;
+        if (threadIdx.x < LN) {
+            const int64_t row = (int64_t)blockIdx.x * LN + threadIdx.x;
+            const int64_t nrows = (int64_t)geo.C * n0 * n1;
+            if (row < nrows) {
+                const int c = (int)(row / ((int64_t)n0 * n1));
+                const int rem = (int)(row - (int64_t)c * n0 * n1);
+                const int z = band_index(rem / n1, n0, g0), y = band_index(rem % n1, n1, g1);
+                base_s[threadIdx.x] = (int64_t)c * geo.G + ((int64_t)z * g1 + y) * g2;
+            } else {
+                base_s[threadIdx.x] = -1;
+            }
+        }
+    } else {
+        // CTA: one (coil, outer index, x block); AXIS 1: outer = band plane z; AXIS 0: outer = row y
+        const int xblocks = (g2 + LN - 1) / LN;
+        const int outer_n = AXIS == 1 ? n0 : g1;
+        const int xb = blockIdx.x % xblocks;
+        const int rest = blockIdx.x / xblocks;
+        const int o = rest % outer_n, c = rest / outer_n;
+        stride = AXIS == 1 ? (int64_t)g2 : (int64_t)g1 * g2;
+        if (threadIdx.x < LN) {
+            const int x = xb * LN + threadIdx.x;
+            if (x < g2) {
+                const int64_t ob = AXIS == 1 ? (int64_t)band_index(o, n0, g0) * g1 * g2 : (int64_t)o * g2;
+                base_s[threadIdx.x] = (int64_t)c * geo.G + ob + x;
+            } else {
+                base_s[threadIdx.x] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    const int nb_axis = AXIS == 0 ? n0 : (AXIS == 1 ? n1 : n2);
+    // load: every load of this thread issued before any is used (zeros for missing lines and, in
+    // the forward direction, outside the band), then stored to shared memory
+    float2 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * FF_T;
+        v[u] = make_float2(0.f, 0.f);
+        if (i < TOT) {
+            const int l = XL ? i / N : i % LN;
+            const int n = XL ? i - l * N : i / LN;
+            const int64_t bs = base_s[l];
+            if (bs >= 0 && (!load_band || in_band(n, nb_axis, N))) v[u] = in[bs + n * stride];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * FF_T;
+        if (i < TOT) {
+            const int l = XL ? i / N : i % LN;
+            const int n = XL ? i - l * N : i / LN;
+            A[XL ? l * N + n : n * LN + l] = v[u];
+        }
+    }
+    __syncthreads();
+    const float2* R = stockham<N, XL, 0, 1>(A, B, tw, INV ? -1.f : 1.f, k);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * FF_T;
+        if (i < TOT) {
+            const int l = XL ? i / N : i % LN;
+            const int n = XL ? i - l * N : i / LN;
+            const int64_t bs = base_s[l];
+            if (bs >= 0 && (!store_band || in_band(n, nb_axis, N))) out[bs + n * stride] = R[XL ? l * N + n : n * LN + l];
+        }
+    }
+}
+
+static size_t pass_smem(int N) { return ((size_t)2 * (N <= 256 ? 16 : 8) * N + N) * sizeof(float2); }
+
+// Radices of N (4 first, then 2, 3, 5); false if N has another prime factor or too many stages.
+static bool factor(int N, FfAxis& ax) {
+    ax.nst = 0;
+    int r = N;
+    for (int f : {4, 2, 3, 5}) {
+        while (r % f == 0) {
+            if (ax.nst == FF_MAXST) return false;
+            ax.r[ax.nst++] = f;
+            r /= f;
+        }
+    }
+    return r == 1;
+}
+
+static bool size_compiled(int N);
+
+kp_status fft3_create(kp_plan p) {
+    const Geom& g = p->geo;
+    if (g.D != 3) return KP_OK;
+    const char* env = std::getenv("KPDHG_FFT");
+    if (!env || std::string(env) != "own") return KP_OK;         // cuFFT unless the own passes are asked for
+    Fft3Plan f{};
+    size_t tot = 0;
+    for (int d = 0; d < 3; ++d) {
+        FfAxis& ax = f.ax[d];
+        ax.N = g.g[d];
+        ax.nband = g.n[d];
+        if (ax.N > FF_MAXN || !factor(ax.N, ax) || !size_compiled(ax.N)) return KP_OK;   // cuFFT serves this plan
+        tot += ax.N;
+    }
+    // twiddle tables e^{-2 pi i m / N} in float64, rounded once
+    std::vector<float2> h(tot);
+    size_t o = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int N = f.ax[d].N;
+        for (int m = 0; m < N; ++m) {
+            const double a = -2.0 * M_PI * (double)m / (double)N;
+            h[o + m] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        o += N;
+    }
+    Fft3Plan* q = new (std::nothrow) Fft3Plan(f);
+    if (!q) { set_error("host allocation failed"); return KP_ENOMEM; }
+    if (cudaMalloc(&q->d_tw, tot * sizeof(float2)) != cudaSuccess) {
+        delete q;
+        set_error("cudaMalloc failed");
+        return KP_ENOMEM;
+    }
+    if (cudaMemcpy(q->d_tw, h.data(), tot * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(q->d_tw);
+        delete q;
+        set_error("cudaMemcpy failed");
+        return KP_ECUDA;
+    }
+    o = 0;
+    for (int d = 0; d < 3; ++d) {
+        q->ax[d].tw = q->d_tw + o;
+        o += q->ax[d].N;
+    }
+    q->k.s3 = (float)(std::sqrt(3.0) / 2.0);
+    q->k.c51 = (float)std::cos(2.0 * M_PI / 5.0);
+    q->k.s51 = (float)std::sin(2.0 * M_PI / 5.0);
+    q->k.c52 = (float)std::cos(4.0 * M_PI / 5.0);
+    q->k.s52 = (float)std::sin(4.0 * M_PI / 5.0);
+    p->fft3 = q;
+    return KP_OK;
+}
+
+void fft3_destroy(kp_plan p) {
+    if (!p->fft3) return;
+    if (p->fft3->d_tw) cudaFree(p->fft3->d_tw);
+    delete p->fft3;
+    p->fft3 = nullptr;
+}
+
+// Grid sizes with compiled passes (the 3D workloads' grids and their preconditioner's 2N grids,
+// and small test grids); a plan with another size keeps cuFFT.
+#define KP_FFT_SIZES(X) X(20) X(30) X(40) X(60) X(80) X(100) X(120) X(160) X(200) X(240) X(320) X(384) X(400) X(480)
+
+static bool size_compiled(int N) {
+    switch (N) {
+#define KP_FFT_CASE(n) case n:
+        KP_FFT_SIZES(KP_FFT_CASE)
+#undef KP_FFT_CASE
+        return true;
+        default: return false;
+    }
+}
+
+template <int AXIS, bool INV, int N>
+static kp_status launch_pass_n(kp_plan p, const float2* in, float2* out, unsigned nblocks, cudaStream_t st) {
+    static PerDeviceOnce attr;
+    if (attr.first())
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_fft_pass<AXIS, INV, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pass_smem(N)));
+    k_fft_pass<AXIS, INV, N><<<nblocks, FF_T, pass_smem(N), st>>>(in, out, p->geo, p->fft3->ax[AXIS], p->fft3->k);
+    KP_LAUNCH_CHECK();
+    return KP_OK;
+}
+
+template <int AXIS, bool INV>
+static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStream_t st) {
+    const Geom& g = p->geo;
+    int64_t nblocks;
+    const int ln = g.g[AXIS] <= 256 ? 16 : 8;           // ff_lines(N) of this pass
+    const int64_t xblocks = (g.g[2] + ln - 1) / ln;
+    if (AXIS == 2) nblocks = ((int64_t)g.C * g.n[0] * g.n[1] + ln - 1) / ln;
+    else if (AXIS == 1) nblocks = (int64_t)g.C * g.n[0] * xblocks;
+    else nblocks = (int64_t)g.C * g.g[1] * xblocks;
+    if (nblocks > INT32_MAX) { set_error("grid too large for the FFT passes"); return KP_EINVAL; }
+    p->launches += 1;
+    switch (g.g[AXIS]) {
+#define KP_FFT_CASE(n) case n: return launch_pass_n<AXIS, INV, n>(p, in, out, (unsigned)nblocks, st);
+        KP_FFT_SIZES(KP_FFT_CASE)
+#undef KP_FFT_CASE
+        default: set_error("FFT pass size without compiled kernel"); return KP_EINTERNAL;
+    }
+}
+
+kp_status fft3_forward(kp_plan p, const float2* in, float2* out, cudaStream_t st) {
+    KP_TRY((launch_pass<2, false>(p, in, out, st)));
+    KP_TRY((launch_pass<1, false>(p, out, out, st)));
+    return launch_pass<0, false>(p, out, out, st);
+}
+
+kp_status fft3_inverse(kp_plan p, float2* io, cudaStream_t st) {
+    KP_TRY((launch_pass<0, true>(p, io, io, st)));
+    KP_TRY((launch_pass<1, true>(p, io, io, st)));
+    return launch_pass<2, true>(p, io, io, st);
+}
+
+}  // namespace kp

@@ -272,6 +272,8 @@ struct Graph {
     int64_t launches = 0;    // own kernels per replay
 };
 
+struct Fft3Plan;                     // kp_fft.cu
+
 }  // namespace kp
 
 struct kp_plan_s {
@@ -349,6 +351,7 @@ struct kp_plan_s {
     unsigned int* d_bar = nullptr;   // grid-barrier state of the fused kernels
     cufftHandle fft = 0;
     bool fft_ok = false;
+    kp::Fft3Plan* fft3 = nullptr;    // own 3D FFT passes (kp_fft.cu) when the grid sizes allow, else cuFFT
 
     // solver state (sorted k-space order)
     float2* d_u = nullptr;           // [C][M] dual variable
@@ -466,6 +469,15 @@ kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st);
 kp_status fft_forward_only(kp_plan p, cudaStream_t st);
 // In-place inverse FFT of d_grid2 (the spread grid).
 kp_status fft_inverse_only(kp_plan p, cudaStream_t st);
+
+// kp_fft.cu: own 3D FFT of all coils' grids (3D plans whose grid sizes factor into 2, 3, 5,
+// when KPDHG_FFT=own at plan creation; cuFFT otherwise).  fft3_forward reads only the image band of `in` (zero
+// elsewhere) and writes the whole spectrum to `out`; fft3_inverse works in place and leaves the
+// transform valid on the image crop only.
+kp_status fft3_create(kp_plan p);
+void fft3_destroy(kp_plan p);
+kp_status fft3_forward(kp_plan p, const float2* in, float2* out, cudaStream_t st);
+kp_status fft3_inverse(kp_plan p, float2* io, cudaStream_t st);
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status interp_dual_only(kp_plan p, cudaStream_t st);

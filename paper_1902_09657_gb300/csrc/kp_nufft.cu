@@ -1154,18 +1154,24 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
     }
 }
 
-// Phase B: one CTA per tile (empty tiles included, so every grid point is stored once), looping
-// over the coils.  The tile's value is the sum of its own slots' 8^3 cores and of the halos
-// that its 7 lower neighbours (periodic) spill into it: the neighbour across axis set m covers
-// the sub-box with extent KW - 1 along the axes in m and the full tile along the others, read
-// from the neighbour's slots at the padded offset where its core ends.  Every slot point is
-// read once: the own cores into registers (two points per thread), then one pass per
-// non-empty neighbour into a shared accumulator, then the tile is stored.  Offsets come from
-// small tables built once per CTA (no per-point address arithmetic beyond a table lookup).
-__global__ void __launch_bounds__(256)
+// Phase B: one CTA per tile (empty tiles included, so every grid point is stored once).  The
+// tile's value is the sum of its own slots' 8^3 cores and of the halos that its 7 lower
+// neighbours (periodic) spill into it: the neighbour across axis set m covers the sub-box with
+// extent KW - 1 along the axes in m and the full tile along the others, read from the
+// neighbour's slots at the padded offset where its core ends.  Coils go GB_CB at a time, all
+// of a chunk at once (a slot holds its coils contiguously), so every pass issues independent
+// loads for GB_CB x 512 (point, coil) pairs and the CTA meets at one barrier per pass, not per
+// coil: the own cores into registers (16 pairs per thread), then one pass per non-empty
+// neighbour into the shared accumulator, then the chunk is stored.  Every slot point is read
+// once; offsets come from per-CTA tables.
+constexpr int GB_CB = 8;                       // coils per chunk (the accumulator holds GB_CB x 512 points)
+constexpr int GB_T = 256;                      // threads
+constexpr int GB_PER = GB_CB * 512 / GB_T;     // (point, coil) pairs per thread in the own pass
+
+__global__ void __launch_bounds__(GB_T)
 k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Geom geo, Tiles tl,
               float2* __restrict__ grid) {
-    __shared__ float2 acc[512];
+    __shared__ float2 acc[GB_CB * 512];
     __shared__ int nb_beg[8], nb_end[8], nb_off[8];
     __shared__ int64_t rowoff[64];     // grid offset (coil 0) of local row (lz, ly); -1 outside the grid
     __shared__ int colg[8];            // grid x of local x; -1 outside the grid
@@ -1195,61 +1201,60 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
         colg[lx] = lx < min(tl.ts[2], geo.g[2] - t2 * tl.ts[2]) ? tunshift(px, tl.sh[2], geo.g[2]) : -1;
     }
     __syncthreads();
-    const int64_t cstride = (int64_t)geo.C * SL_P;
-    // this thread's two points of the 8^3 tile: i0 = tid (lz 0..3), i1 = tid + 256 (lz 4..7)
-    const int i0 = threadIdx.x, i1 = threadIdx.x + 256;
-    const int pt0 = ((i0 >> 6) * PT + ((i0 >> 3) & 7)) * SL_RS + (i0 & 7);
-    const int pt1 = pt0 + 4 * SL_PS;
+    const int64_t sstride = (int64_t)geo.C * SL_P;       // one slot: all coils
     const int own_b = nb_beg[0], own_e = nb_end[0];
-    for (int c = 0; c < geo.C; ++c) {
-        const float2* hc = halo + (int64_t)c * SL_P;
-        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
-        int sl = own_b;
-        for (; sl + 2 <= own_e; sl += 2) {
-            const float2* s0 = hc + sl * cstride;
-            const float2* s1 = s0 + cstride;
-            const float2 u0 = s0[pt0], u1 = s0[pt1], v0 = s1[pt0], v1 = s1[pt1];
-            a0.x += u0.x; a0.y += u0.y; a1.x += u1.x; a1.y += u1.y;
-            b0.x += v0.x; b0.y += v0.y; b1.x += v1.x; b1.y += v1.y;
+    for (int c0 = 0; c0 < geo.C; c0 += GB_CB) {
+        const int cc = min(GB_CB, geo.C - c0);
+        const float2* hc = halo + (int64_t)c0 * SL_P;
+        // own cores: pair q = threadIdx.x + GB_T j holds coil q >> 9, point q & 511
+        float2 a[GB_PER];
+#pragma unroll
+        for (int j = 0; j < GB_PER; ++j) a[j] = make_float2(0.f, 0.f);
+        for (int sl = own_b; sl < own_e; ++sl) {
+            const float2* src = hc + sl * sstride;
+#pragma unroll
+            for (int j = 0; j < GB_PER; ++j) {
+                const int q = threadIdx.x + GB_T * j, c = q >> 9, p = q & 511;
+                if (c < cc) {
+                    const float2 v = src[c * SL_P + ((p >> 6) * PT + ((p >> 3) & 7)) * SL_RS + (p & 7)];
+                    a[j].x += v.x;
+                    a[j].y += v.y;
+                }
+            }
         }
-        if (sl < own_e) {
-            const float2* s0 = hc + sl * cstride;
-            const float2 u0 = s0[pt0], u1 = s0[pt1];
-            a0.x += u0.x; a0.y += u0.y; a1.x += u1.x; a1.y += u1.y;
-        }
-        acc[i0] = make_float2(a0.x + b0.x, a0.y + b0.y);
-        acc[i1] = make_float2(a1.x + b1.x, a1.y + b1.y);
+#pragma unroll
+        for (int j = 0; j < GB_PER; ++j) acc[threadIdx.x + GB_T * j] = a[j];
 #pragma unroll 1
         for (int m = 1; m < 8; ++m) {
             const int be = nb_beg[m], en = nb_end[m];
             if (be == en) continue;                                  // block-uniform
             __syncthreads();                                         // earlier passes' adds are done
-            const int d0 = (m & 4) ? KW - 1 : 8, d1 = (m & 2) ? KW - 1 : 8, d2 = (m & 1) ? KW - 1 : 8;
-            const int npts = d0 * d1 * d2, off = nb_off[m];
-            for (int q = threadIdx.x; q < npts; q += blockDim.x) {
-                const int lx = q % d2, r = q / d2, ly = r % d1, lz = r / d1;
-                const float2* src = hc + off + (lz * PT + ly) * SL_RS + lx;
+            const int d1 = (m & 2) ? KW - 1 : 8, d2 = (m & 1) ? KW - 1 : 8;
+            const int d0 = (m & 4) ? KW - 1 : 8;
+            const int per_c = d0 * d1 * d2, npts = per_c * cc, off = nb_off[m];
+            for (int q = threadIdx.x; q < npts; q += GB_T) {
+                const int c = q / per_c, r0 = q - c * per_c;
+                const int lx = r0 % d2, r = r0 / d2, ly = r % d1, lz = r / d1;
+                const float2* src = hc + c * SL_P + off + (lz * PT + ly) * SL_RS + lx;
                 float2 sm = make_float2(0.f, 0.f);
                 for (int k = be; k < en; ++k) {
-                    const float2 v = src[k * cstride];
+                    const float2 v = src[k * sstride];
                     sm.x += v.x;
                     sm.y += v.y;
                 }
-                float2& t = acc[(lz * 8 + ly) * 8 + lx];
+                float2& t = acc[c * 512 + (lz * 8 + ly) * 8 + lx];
                 t.x += sm.x;
                 t.y += sm.y;
             }
         }
         __syncthreads();
-        float2* gc = grid + (int64_t)c * geo.G;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = threadIdx.x + 256 * h;
-            const int64_t ro = rowoff[i >> 3];
-            const int gx = colg[i & 7];
-            if (ro >= 0 && gx >= 0) gc[ro + gx] = acc[i];
+        for (int q = threadIdx.x; q < cc * 512; q += GB_T) {
+            const int c = q >> 9, p = q & 511;
+            const int64_t ro = rowoff[p >> 3];
+            const int gx = colg[p & 7];
+            if (ro >= 0 && gx >= 0) grid[(int64_t)(c0 + c) * geo.G + ro + gx] = acc[q];
         }
-        __syncthreads();                                             // acc is rewritten by the next coil
+        __syncthreads();                                             // acc is rewritten by the next chunk
     }
 }
 
@@ -1827,6 +1832,21 @@ __global__ void k_fill(float2* __restrict__ x, int64_t n, float2 v) {
     if ((dv) == 2) { constexpr int DD = 2; __VA_ARGS__; }                         \
     else { constexpr int DD = 3; __VA_ARGS__; }
 
+// The grid FFTs of the NUFFT pair: the own 3D passes when the plan has them, else cuFFT.
+static kp_status grid_fft_forward(kp_plan p, cudaStream_t st) {
+    if (p->fft3) return fft3_forward(p, p->d_grid, p->d_gridF, st);
+    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
+    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_gridF, CUFFT_FORWARD));
+    return KP_OK;
+}
+
+static kp_status grid_fft_inverse(kp_plan p, cudaStream_t st) {
+    if (p->fft3) return fft3_inverse(p, p->d_grid2, st);
+    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
+    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
+    return KP_OK;
+}
+
 kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st) {
     k_fill<<<nblk(n, 256), 256, 0, st>>>(x, n, v);
     KP_LAUNCH_CHECK();
@@ -1843,9 +1863,7 @@ static kp_status fwd_grid(kp_plan p, const float2* x, cudaStream_t st) {
                                                          p->d_apod, g, p->d_grid)));
     KP_LAUNCH_CHECK();
     mark(p, PH_FFT_FWD, st);
-    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
-    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_gridF, CUFFT_FORWARD));
-    return KP_OK;
+    return grid_fft_forward(p, st);
 }
 
 // Forward grid spectrum of x (pre-step into d_grid, FFT into d_gridF), no interpolation.
@@ -1867,16 +1885,12 @@ kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st) {
 // iteration's pre-step there).
 kp_status fft_forward_only(kp_plan p, cudaStream_t st) {
     mark(p, PH_FFT_FWD, st);
-    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
-    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid, (cufftComplex*)p->d_gridF, CUFFT_FORWARD));
-    return KP_OK;
+    return grid_fft_forward(p, st);
 }
 
 kp_status fft_inverse_only(kp_plan p, cudaStream_t st) {
     mark(p, PH_FFT_INV, st);
-    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
-    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
-    return KP_OK;
+    return grid_fft_inverse(p, st);
 }
 
 template <int MODE>
@@ -2100,9 +2114,7 @@ kp_status adjoint_to_grid(kp_plan p, const void* u, kp_cdtype u_t, const int* pe
                           bool splits_zeroed) {
     KP_TRY(spread_only(p, u, u_t, perm, st, splits_zeroed));
     mark(p, PH_FFT_INV, st);
-    KP_TRY_CUFFT(cufftSetStream(p->fft, st));
-    KP_TRY_CUFFT(cufftExecC2C(p->fft, (cufftComplex*)p->d_grid2, (cufftComplex*)p->d_grid2, CUFFT_INVERSE));
-    return KP_OK;
+    return grid_fft_inverse(p, st);
 }
 
 // Picks the spreading variant and the samples per work item by timing the spreading kernels

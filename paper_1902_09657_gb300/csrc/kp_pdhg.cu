@@ -8,6 +8,8 @@
 // min p, so one captured CUDA graph replays every iteration.
 #include "kp_internal.cuh"
 
+#include <cstdlib>
+
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -280,6 +282,17 @@ static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cuda
     return power_end(p, st);
 }
 
+// Whether the primal step runs as separate kernels (combine + step, wavelet levels or pre-step,
+// counter) instead of one persistent cooperative kernel (one CTA per SM, grid barriers between
+// the phases).  KPDHG_PRIMAL=levels / fused chooses.
+static bool levels_primal(kp_plan p) {
+    const char* e = std::getenv("KPDHG_PRIMAL");
+    if (e && std::string(e) == "levels") return true;
+    if (e && std::string(e) == "fused") return false;
+    (void)p;
+    return false;
+}
+
 // One PDHG iteration (Sec. 4.1) from the forward grid of xbar already in d_grid:
 // FFT -> interpolation + dual update -> spreading + inverse FFT -> fused primal step
 // (adjoint combine, prox, extrapolation, next forward pre-step, counter).
@@ -291,6 +304,20 @@ static kp_status issue_iteration(kp_plan p, int reg, float lambda, cudaStream_t 
         KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st, /*splits_zeroed=*/false));
         KP_TRY(adjoint_primal(p, KP_REG_TV, lambda, st));
         KP_TRY(pre_only(p, p->d_xbar, st));
+        k_advance<<<1, 1, 0, st>>>(p->d_iter);
+        KP_LAUNCH_CHECK();
+        p->launches += 1;
+        mark(p, PH_OTHER, st);
+        return KP_OK;
+    }
+    if (levels_primal(p)) {
+        // the primal step as separate kernels over the whole GPU: combine + step (z, or x and
+        // xbar for l2), the wavelet levels (the last inverse level extrapolates and writes the
+        // next forward grid) or the pre-step, the counter
+        KP_TRY(adjoint_to_grid(p, p->d_u, KP_C64, nullptr, st, /*splits_zeroed=*/false));
+        KP_TRY(adjoint_primal(p, reg, lambda, st));
+        if (reg == KP_REG_L1_WAVELET) KP_TRY(wavelet_prox_levels(p, lambda, st));
+        else KP_TRY(pre_only(p, p->d_xbar, st));
         k_advance<<<1, 1, 0, st>>>(p->d_iter);
         KP_LAUNCH_CHECK();
         p->launches += 1;

@@ -506,6 +506,10 @@ kp_status plan_create_internal(kp_plan* out, const kp_params* prm, bool unit_map
         return fr == CUFFT_ALLOC_FAILED ? KP_ENOMEM : KP_ECUFFT;
     }
     p->fft_ok = true;
+    {
+        const kp_status fs = fft3_create(p);
+        if (fs != KP_OK) { plan_destroy_internal(p); return fs; }
+    }
     if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         plan_destroy_internal(p);
         set_error("cudaStreamCreate failed");
@@ -523,6 +527,7 @@ kp_status plan_destroy_internal(kp_plan p) {
     pre_destroy(p);
     compare_destroy(p);
     if (p->fft_ok) cufftDestroy(p->fft);
+    fft3_destroy(p);
     void* bufs[] = {p->d_t, p->d_f, p->d_perm, p->d_key, p->d_ccnt, p->d_coff, p->d_scan_part, p->d_scan_poff, p->d_cnt, p->d_off, p->d_ext_off, p->d_ext, p->d_flag,
                     p->d_items, p->d_iitems, p->d_item_off, p->d_slot_off, p->d_nslots, p->d_split, p->d_k0, p->d_wt,
                     p->d_grid2, p->d_gridF, p->d_bar, p->d_tape, p->d_bk,

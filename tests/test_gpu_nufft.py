@@ -201,3 +201,32 @@ def test_forward_adjoint_grid_sizes(shape):
     plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
     assert rel(plan.sense_forward(to_dev(x)).cpu().numpy(), y_ref) < 1e-5
     assert rel(plan.sense_adjoint(to_dev(u)).cpu().numpy(), x_ref) < 1e-5
+
+
+# 3D grids whose sizes factor into 2, 3 and 5 use the library's own FFT passes (pruned to the
+# image band); others fall back to cuFFT.  (15, 16, 24) -> grid (20, 20, 30): an odd image edge
+# and radix-5 and radix-3 stages; (20, 21, 32) -> grid (26, 28, 40): 26 = 2 x 13 is not
+# handled, so that plan runs cuFFT.
+@pytest.mark.parametrize("shape,C,M,seed", [((15, 16, 24), 3, 2500, 41), ((32, 32, 32), 2, 4000, 42),
+                                            ((20, 21, 32), 2, 1500, 43)])
+def test_own_fft_passes_match_oracle_and_cufft(shape, C, M, seed, monkeypatch):
+    need_gpu()
+    x, maps, traj = random_problem(shape, C, M, seed, edge=True)
+    monkeypatch.setenv("KPDHG_FFT", "own")
+    plan = make_plan(shape, C, M)
+    monkeypatch.setenv("KPDHG_FFT", "cufft")
+    ref_plan = make_plan(shape, C, M)
+    monkeypatch.delenv("KPDHG_FFT")
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    ref_plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    y = plan.sense_forward(to_dev(x)).cpu().numpy()
+    y_cu = ref_plan.sense_forward(to_dev(x)).cpu().numpy()
+    y_o = onf.nufft_forward(x.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+    assert rel(y, y_o, "forward, own FFT passes vs oracle") < 1e-5
+    assert rel(y, y_cu, "forward, own FFT passes vs cuFFT") < 2e-6
+    yr = (np.random.default_rng(seed).standard_normal(y.shape) + 1j * np.random.default_rng(seed + 1).standard_normal(y.shape)).astype(np.complex64)
+    xa = plan.sense_adjoint(to_dev(yr)).cpu().numpy()
+    xa_cu = ref_plan.sense_adjoint(to_dev(yr)).cpu().numpy()
+    xa_o = onf.nufft_adjoint(yr.astype(np.complex128), maps.astype(np.complex128), traj, 1.25, 4)
+    assert rel(xa, xa_o, "adjoint, own FFT passes vs oracle") < 1e-5
+    assert rel(xa, xa_cu, "adjoint, own FFT passes vs cuFFT") < 2e-6
