@@ -271,7 +271,7 @@ kp_status fft3_create(kp_plan p) {
     const Geom& g = p->geo;
     if (g.D != 3) return KP_OK;
     const char* env = std::getenv("KPDHG_FFT");
-    if (!env || std::string(env) != "own") return KP_OK;         // cuFFT unless the own passes are asked for
+    if (env && std::string(env) == "cufft") return KP_OK;        // cuFFT when asked for
     Fft3Plan f{};
     size_t tot = 0;
     for (int d = 0; d < 3; ++d) {

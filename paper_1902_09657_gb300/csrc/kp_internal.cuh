@@ -470,8 +470,8 @@ kp_status fft_forward_only(kp_plan p, cudaStream_t st);
 // In-place inverse FFT of d_grid2 (the spread grid).
 kp_status fft_inverse_only(kp_plan p, cudaStream_t st);
 
-// kp_fft.cu: own 3D FFT of all coils' grids (3D plans whose grid sizes factor into 2, 3, 5,
-// when KPDHG_FFT=own at plan creation; cuFFT otherwise).  fft3_forward reads only the image band of `in` (zero
+// kp_fft.cu: own 3D FFT of all coils' grids (3D plans whose grid sizes have compiled passes;
+// KPDHG_FFT=cufft at plan creation keeps cuFFT).  fft3_forward reads only the image band of `in` (zero
 // elsewhere) and writes the whole spectrum to `out`; fft3_inverse works in place and leaves the
 // transform valid on the image crop only.
 kp_status fft3_create(kp_plan p);

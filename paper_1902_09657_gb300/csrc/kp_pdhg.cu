@@ -284,7 +284,8 @@ static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cuda
 
 // Whether the primal step runs as separate kernels (combine + step, wavelet levels or pre-step,
 // counter) instead of one persistent cooperative kernel (one CTA per SM, grid barriers between
-// the phases).  KPDHG_PRIMAL=levels / fused chooses.
+// the phases).  KPDHG_PRIMAL=levels selects the separate kernels; the fused kernel is the default
+// (3D UTE 192^3 x 8 coils, l1: 1.62 ms against 2.15 ms per iteration).
 static bool levels_primal(kp_plan p) {
     const char* e = std::getenv("KPDHG_PRIMAL");
     if (e && std::string(e) == "levels") return true;
