@@ -355,7 +355,15 @@ def algorithmic_bytes(w, C, M, N, G, maps_bytes=8):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernels of the timed
 # workload from one ncu capture, keyed by (workload, phase).  An entry is valid only for the
 # kernel code it was taken on; drop it when its kernel changes until it is captured again.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # one capture of the full 3D UTE workload (192^3 x 8 coils, 6,144,000 samples; one pass per
+    # kernel, so allowed at full size): KPDHG_SPREAD_VARIANT=10 KPDHG_SPREAD_CHUNK=256 ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+    # -k "regex:k_spread_own|k_halo_gather" -s 10 -c 4 python bench.py --steps 1 --warmup 1 --no-extras
+    # k_spread_own<float2, 4>: 1.282 GB read + 1.440 GB written; k_halo_gather: 1.527 + 0.854 GB
+    ("ute3d_192", "spread"): {"bytes": 5103672448,
+                              "kernel": "k_spread_own<float2, 4> + k_halo_gather (one launch each, full 3D UTE workload)"},
+}
 
 # Relative l2 errors against the float64 oracle measured by the GPU parity tests for the forms
 # reported beside the plain solver (the largest value each test logged, KPDHG_PARITY_LOG, on a

@@ -53,7 +53,17 @@ struct Fft3Plan {
     FfConst k;
 };
 
+// The image samples the first forward pass forms itself (coil multiply and apodisation, the
+// NUFFT's pre-step fused into the FFT): x, the maps (null: unit maps) and 1/Phi per axis.
+struct PreSrc {
+    const float2* x;
+    const void* maps;
+    const float* apod;
+};
+
 __device__ __forceinline__ bool in_band(int i, int n, int g) { return i < n - n / 2 || i >= g - n / 2; }
+// pixel index of grid index i (i in the band)
+__device__ __forceinline__ int pix_index(int i, int n, int g) { return i < n - n / 2 ? i + n / 2 : i - g + n / 2; }
 __device__ __forceinline__ int band_index(int bi, int n, int g) { return bi < n - n / 2 ? bi : bi + (g - n); }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -162,9 +172,11 @@ __device__ __forceinline__ float2* stockham(float2* a, float2* b, const float2* 
 
 // Pass along AXIS (0 = z, 1 = y, 2 = x) of every coil's grid; INV selects the inverse.  Line
 // selection and pruning as in the file header.
-template <int AXIS, bool INV, int N>
-__global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out, Geom geo, FfAxis ax, FfConst k) {
+template <int AXIS, bool INV, int N, bool PRE = false, typename MT = float2>
+__global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out, Geom geo, FfAxis ax, FfConst k,
+                                                   PreSrc pre) {
     // (no __restrict__: the y, z and inverse passes work in place, each CTA on its own lines)
+    // PRE (first forward pass only): the band points are s_c x / Phi, formed from `pre`, not read
     constexpr int LN = ff_lines(N), TOT = LN * N, PER = (TOT + FF_T - 1) / FF_T;
     constexpr bool XL = AXIS == 2;
     extern __shared__ __align__(16) float2 fsm[];
@@ -177,6 +189,9 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
     const bool load_band = !INV, store_band = INV;      // forward reads only the band, inverse writes only it
     // per line: base offset of element 0, or -1 when the line does not exist; element n at base + n stride
     __shared__ int64_t base_s[FF_LINES];
+    __shared__ int64_t pix_s[FF_LINES];                 // PRE: maps offset of the row's first pixel
+    __shared__ int64_t img_s[FF_LINES];                 // PRE: image offset of the row's first pixel
+    __shared__ float apod_s[FF_LINES];                  // PRE: 1/Phi of the row's z and y
     int64_t stride;
     if (AXIS == 2) {
         stride = 1;
@@ -188,6 +203,12 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
                 const int rem = (int)(row - (int64_t)c * n0 * n1);
                 const int z = band_index(rem / n1, n0, g0), y = band_index(rem % n1, n1, g1);
                 base_s[threadIdx.x] = (int64_t)c * geo.G + ((int64_t)z * g1 + y) * g2;
+                if (PRE) {
+                    const int pz = pix_index(z, n0, g0), py = pix_index(y, n1, g1);
+                    img_s[threadIdx.x] = ((int64_t)pz * n1 + py) * n2;
+                    pix_s[threadIdx.x] = (int64_t)c * geo.N + img_s[threadIdx.x];
+                    apod_s[threadIdx.x] = pre.apod[pz] * pre.apod[n0 + py];
+                }
             } else {
                 base_s[threadIdx.x] = -1;
             }
@@ -223,7 +244,20 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
             const int l = XL ? i / N : i % LN;
             const int n = XL ? i - l * N : i / LN;
             const int64_t bs = base_s[l];
-            if (bs >= 0 && (!load_band || in_band(n, nb_axis, N))) v[u] = in[bs + n * stride];
+            if (bs >= 0 && (!load_band || in_band(n, nb_axis, N))) {
+                if constexpr (PRE) {
+                    // the pre-step's arithmetic, in its order: x (1/Phi_z 1/Phi_y 1/Phi_x), then s_c times it
+                    const int px = pix_index(n, n2, g2);
+                    const float a = apod_s[l] * pre.apod[n0 + n1 + px];
+                    float2 xv = pre.x[img_s[l] + px];
+                    xv.x *= a;
+                    xv.y *= a;
+                    const float2 sv = pre.maps ? ldc<MT>((const MT*)pre.maps, pix_s[l] + px) : make_float2(1.f, 0.f);
+                    v[u] = cmul(sv, xv);
+                } else {
+                    v[u] = in[bs + n * stride];
+                }
+            }
         }
     }
 #pragma unroll
@@ -340,19 +374,21 @@ static bool size_compiled(int N) {
     }
 }
 
-template <int AXIS, bool INV, int N>
-static kp_status launch_pass_n(kp_plan p, const float2* in, float2* out, unsigned nblocks, cudaStream_t st) {
+template <int AXIS, bool INV, int N, bool PRE = false, typename MT = float2>
+static kp_status launch_pass_n(kp_plan p, const float2* in, float2* out, unsigned nblocks, const PreSrc& pre,
+                               cudaStream_t st) {
     static PerDeviceOnce attr;
     if (attr.first())
-        KP_TRY_CUDA(cudaFuncSetAttribute(k_fft_pass<AXIS, INV, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        KP_TRY_CUDA(cudaFuncSetAttribute(k_fft_pass<AXIS, INV, N, PRE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pass_smem(N)));
-    k_fft_pass<AXIS, INV, N><<<nblocks, FF_T, pass_smem(N), st>>>(in, out, p->geo, p->fft3->ax[AXIS], p->fft3->k);
+    k_fft_pass<AXIS, INV, N, PRE, MT><<<nblocks, FF_T, pass_smem(N), st>>>(in, out, p->geo, p->fft3->ax[AXIS],
+                                                                         p->fft3->k, pre);
     KP_LAUNCH_CHECK();
     return KP_OK;
 }
 
-template <int AXIS, bool INV>
-static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStream_t st) {
+template <int AXIS, bool INV, bool PRE = false, typename MT = float2>
+static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStream_t st, const PreSrc& pre = PreSrc{}) {
     const Geom& g = p->geo;
     int64_t nblocks;
     const int ln = g.g[AXIS] <= 256 ? 16 : 8;           // ff_lines(N) of this pass
@@ -363,7 +399,7 @@ static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStrea
     if (nblocks > INT32_MAX) { set_error("grid too large for the FFT passes"); return KP_EINVAL; }
     p->launches += 1;
     switch (g.g[AXIS]) {
-#define KP_FFT_CASE(n) case n: return launch_pass_n<AXIS, INV, n>(p, in, out, (unsigned)nblocks, st);
+#define KP_FFT_CASE(n) case n: return launch_pass_n<AXIS, INV, n, PRE, MT>(p, in, out, (unsigned)nblocks, pre, st);
         KP_FFT_SIZES(KP_FFT_CASE)
 #undef KP_FFT_CASE
         default: set_error("FFT pass size without compiled kernel"); return KP_EINTERNAL;
@@ -372,6 +408,18 @@ static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStrea
 
 kp_status fft3_forward(kp_plan p, const float2* in, float2* out, cudaStream_t st) {
     KP_TRY((launch_pass<2, false>(p, in, out, st)));
+    KP_TRY((launch_pass<1, false>(p, out, out, st)));
+    return launch_pass<0, false>(p, out, out, st);
+}
+
+kp_status fft3_forward_image(kp_plan p, const float2* x, cudaStream_t st) {
+    const PreSrc pre{x, p->unit_maps ? nullptr : p->d_maps, p->d_apod};
+    float2* out = p->d_gridF;
+    switch (p->unit_maps ? KP_C64 : p->maps_t) {
+        case KP_C64: KP_TRY((launch_pass<2, false, true, float2>(p, nullptr, out, st, pre))); break;
+        case KP_C32_BF16: KP_TRY((launch_pass<2, false, true, __nv_bfloat162>(p, nullptr, out, st, pre))); break;
+        default: KP_TRY((launch_pass<2, false, true, __half2>(p, nullptr, out, st, pre))); break;
+    }
     KP_TRY((launch_pass<1, false>(p, out, out, st)));
     return launch_pass<0, false>(p, out, out, st);
 }

@@ -477,6 +477,9 @@ kp_status fft_inverse_only(kp_plan p, cudaStream_t st);
 kp_status fft3_create(kp_plan p);
 void fft3_destroy(kp_plan p);
 kp_status fft3_forward(kp_plan p, const float2* in, float2* out, cudaStream_t st);
+// The forward grid spectrum of image x into d_gridF, the pre-step (coil multiply, apodisation)
+// formed by the first pass from x and the maps (no d_grid involved).
+kp_status fft3_forward_image(kp_plan p, const float2* x, cudaStream_t st);
 kp_status fft3_inverse(kp_plan p, float2* io, cudaStream_t st);
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st);
 kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st);

@@ -1855,6 +1855,10 @@ kp_status fill_image(float2* x, int64_t n, float2 v, cudaStream_t st) {
 
 static kp_status fwd_grid(kp_plan p, const float2* x, cudaStream_t st) {
     const Geom& g = p->geo;
+    if (p->fft3) {                      // the own FFT's first pass forms the pre-step itself
+        mark(p, PH_FFT_FWD, st);
+        return fft3_forward_image(p, x, st);
+    }
     const kp_cdtype mt = p->unit_maps ? KP_C64 : p->maps_t;
     mark(p, PH_FWD_PRE, st);
     p->launches += 1;
@@ -1872,6 +1876,7 @@ kp_status forward_grid_only(kp_plan p, const float2* x, cudaStream_t st) { retur
 // Forward pre-step only (coil multiply, apodise, pad) of x into d_grid.
 kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st) {
     const Geom& g = p->geo;
+    if (p->fft3) return KP_OK;          // the own FFT forms the pre-step from the image itself
     const kp_cdtype mt = p->unit_maps ? KP_C64 : p->maps_t;
     p->launches += 1;
     KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(mt, MT,
@@ -1885,6 +1890,7 @@ kp_status pre_only(kp_plan p, const float2* x, cudaStream_t st) {
 // iteration's pre-step there).
 kp_status fft_forward_only(kp_plan p, cudaStream_t st) {
     mark(p, PH_FFT_FWD, st);
+    if (p->fft3) return fft3_forward_image(p, p->d_xbar, st);   // the pre-step of xbar, fused
     return grid_fft_forward(p, st);
 }
 

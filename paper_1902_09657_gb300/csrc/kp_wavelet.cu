@@ -522,7 +522,7 @@ kp_status wavelet_prox_levels(kp_plan p, float lambda, cudaStream_t st) {
         if (lev == 0) {
             a.x = p->d_x;
             a.xbar = p->d_xbar;
-            a.fgrid = p->d_grid;
+            a.fgrid = p->fft3 ? nullptr : p->d_grid;      // the own FFT forms the pre-step itself
             a.maps = p->d_maps;
             a.apod = p->d_apod;
             a.geo = g;
@@ -574,7 +574,7 @@ static LevelArgs prox_level_args(kp_plan p, float lambda, int lev, bool fwd, int
         if (lev == 0) {
             a.x = p->d_x;
             a.xbar = p->d_xbar;
-            a.fgrid = p->d_grid;
+            a.fgrid = p->fft3 ? nullptr : p->d_grid;      // the own FFT forms the pre-step itself
             a.maps = p->d_maps;
             a.apod = p->d_apod;
             a.geo = g;
@@ -822,7 +822,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
             const float2 xb = make_float2(xn.x + theta * (xn.x - xo.x), xn.y + theta * (xn.y - xo.y));
             a.x[j] = xn;
             a.xbar[j] = xb;
-            pre_pixel<D, MT>(a.fgrid, (const MT*)a.maps, a.apod, g, j, xb);
+            if (a.fgrid) pre_pixel<D, MT>(a.fgrid, (const MT*)a.maps, a.apod, g, j, xb);
         } else {
             a.z[j] = zz;
         }
@@ -1197,7 +1197,7 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st) {
     a.coef = p->d_w;
     a.ll0 = p->d_wl0;
     a.ll1 = p->d_wl1;
-    a.fgrid = p->d_grid;
+    a.fgrid = p->fft3 ? nullptr : p->d_grid;            // the own FFT forms the pre-step itself
     a.sched = p->d_sched;
     a.iter = p->d_iter;
     a.lambda = lambda;
