@@ -173,6 +173,17 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
                         kp_reg reg, float lambda, int iters, double lmax, void* x_dev,
                         double* obj_trace, kp_stats* stats, void* stream);
 
+/* kp_pdhg_solve with the measurements in page-locked host memory (y_host: [C][M] of type y_t,
+ * allocated with cudaHostAlloc or pinned).  The library copies y into its own device buffer on
+ * a copy stream of the plan while the preconditioner and the power method run, and waits for
+ * the copy only before the measurements are first read (the sorted load ahead of the first
+ * dual step), so the host-to-device transfer overlaps the set-up.  The copy starts after the
+ * work already queued on `stream`.  Same result as kp_pdhg_solve on a device copy of y.
+ * Synchronous.  Errors: those of kp_pdhg_solve; KP_EINVAL if y_host is not page-locked. */
+kp_status kp_pdhg_solve_host(kp_plan plan, const void* y_host, kp_cdtype y_t, const float* p_dev, kp_reg reg,
+                             float lambda, int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats,
+                             void* stream);
+
 /* State of a PDHG run (Sec. 4.1) between iterations, for checkpoints and warm starts: the
  * iterates x_k, xbar_k and the dual variable u_k, and the number k of iterations already taken
  * (the step sizes sigma_k, tau_k, theta_k follow from k, lambda_max and min p).  All pointers

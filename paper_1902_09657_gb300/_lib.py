@@ -65,6 +65,9 @@ _SIGS = {
     "kp_pdhg_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                      ctypes.c_double, _vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(KpStats), _vp]),
+    "kp_pdhg_solve_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                          ctypes.c_double, _vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(KpStats), _vp]),
     "kp_pdhg_solve_ex": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(KpState), ctypes.POINTER(KpState),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(KpStats), _vp]),

@@ -247,11 +247,36 @@ class Plan:
     def pdhg_solve(self, y, p=None, reg="l2", lam=0.0, iters=30, lmax=0.0, trace=False, out=None, state=None,
                    return_state=False):
         """Preconditioned PDHG; reg is "l2", "l1_wavelet" (Sec. 4.1) or "tv" (Sec. 4.2).  y may
-        live on the host (it is then copied in, and x copied back to the host).  state: None to
+        live on the host (it is then copied in, and x copied back to the host; page-locked y is
+        copied in by the library while the set-up runs, and a page-locked host `out` receives x).  state: None to
         start from zero, or a dict (x, xbar, u, v, k) returned by an earlier call with
         return_state=True, to continue that run (kp_pdhg_solve_ex).  Returns (x, objective trace
         or None, stats dict), plus the state dict after the last iteration when return_state."""
         host = not y.is_cuda
+        if host and y.is_pinned() and y.is_contiguous() and state is None and not return_state:
+            # page-locked host measurements: the library copies them in while the set-up runs
+            ct = _ctype_of(y)
+            if y.numel() * y.element_size() != self.ncoils * self.nsamples * (8 if ct == L.KP_C64 else 4):
+                raise ValueError("y must hold [C, M] complex values")
+            pd = self._dev(p, "p") if p is not None and p.is_cuda else (
+                p.to(self.device, non_blocking=True) if p is not None else None)
+            xd = torch.empty(self.img_shape, dtype=torch.complex64, device=self.device)
+            tr = (ctypes.c_double * max(int(iters), 1))() if trace else None
+            st = L.KpStats()
+            L.check(self.lib.kp_pdhg_solve_host(self._h, _ptr(y), _ctype_of(y), _ptr(pd) if pd is not None else None,
+                                                _REG[reg], float(lam), int(iters), float(lmax), _ptr(xd), tr,
+                                                ctypes.byref(st), _stream(self.device)), "kp_pdhg_solve_host")
+            stats = dict(iters=st.iters, lmax=st.lmax, pmin=st.pmin, sigma_last=st.sigma_last,
+                         tau_last=st.tau_last, final_obj=st.final_obj,
+                         phase_ms={n: st.phase_ms[i] for i, n in enumerate(L.PHASES)})
+            if out is not None and not out.is_cuda and out.is_pinned():
+                # a page-locked result buffer of the caller: one asynchronous copy
+                out.copy_(xd, non_blocking=True)
+                torch.cuda.current_stream(self.device).synchronize()
+                xh = out
+            else:
+                xh = xd.to("cpu")
+            return xh, (list(tr)[: int(iters)] if trace else None), stats
         yd = y.to(self.device, non_blocking=True) if host else y
         yd = self._dev(yd, "y")
         pd = None

@@ -41,7 +41,6 @@ struct FfConst {                 // sqrt(3)/2, cos and sin of 2 pi/5 and of 4 pi
 
 struct FfAxis {
     int N;                       // transform length (grid points along the axis)
-    int nband;                   // image points along the axis
     int nst;                     // radix stages
     int r[FF_MAXST];             // radices in the order applied
     const float2* tw;            // e^{-2 pi i m / N}, m in [0, N)
@@ -301,18 +300,17 @@ static bool factor(int N, FfAxis& ax) {
 
 static bool size_compiled(int N);
 
-kp_status fft3_create(kp_plan p) {
-    const Geom& g = p->geo;
-    if (g.D != 3) return KP_OK;
+// Passes and twiddle tables for grids of g[0] x g[1] x g[2] points; null when some length has no
+// compiled passes (or KPDHG_FFT=cufft).
+Fft3Plan* fft3_make(const int g[3]) {
     const char* env = std::getenv("KPDHG_FFT");
-    if (env && std::string(env) == "cufft") return KP_OK;        // cuFFT when asked for
+    if (env && std::string(env) == "cufft") return nullptr;       // cuFFT when asked for
     Fft3Plan f{};
     size_t tot = 0;
     for (int d = 0; d < 3; ++d) {
         FfAxis& ax = f.ax[d];
-        ax.N = g.g[d];
-        ax.nband = g.n[d];
-        if (ax.N > FF_MAXN || !factor(ax.N, ax) || !size_compiled(ax.N)) return KP_OK;   // cuFFT serves this plan
+        ax.N = g[d];
+        if (ax.N > FF_MAXN || !factor(ax.N, ax) || !size_compiled(ax.N)) return nullptr;
         tot += ax.N;
     }
     // twiddle tables e^{-2 pi i m / N} in float64, rounded once
@@ -327,17 +325,17 @@ kp_status fft3_create(kp_plan p) {
         o += N;
     }
     Fft3Plan* q = new (std::nothrow) Fft3Plan(f);
-    if (!q) { set_error("host allocation failed"); return KP_ENOMEM; }
+    if (!q) return nullptr;
     if (cudaMalloc(&q->d_tw, tot * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
         delete q;
-        set_error("cudaMalloc failed");
-        return KP_ENOMEM;
+        return nullptr;
     }
     if (cudaMemcpy(q->d_tw, h.data(), tot * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(q->d_tw);
         delete q;
-        set_error("cudaMemcpy failed");
-        return KP_ECUDA;
+        return nullptr;
     }
     o = 0;
     for (int d = 0; d < 3; ++d) {
@@ -349,14 +347,22 @@ kp_status fft3_create(kp_plan p) {
     q->k.s51 = (float)std::sin(2.0 * M_PI / 5.0);
     q->k.c52 = (float)std::cos(4.0 * M_PI / 5.0);
     q->k.s52 = (float)std::sin(4.0 * M_PI / 5.0);
-    p->fft3 = q;
+    return q;
+}
+
+void fft3_free(Fft3Plan* f) {
+    if (!f) return;
+    if (f->d_tw) cudaFree(f->d_tw);
+    delete f;
+}
+
+kp_status fft3_create(kp_plan p) {
+    if (p->geo.D == 3) p->fft3 = fft3_make(p->geo.g);
     return KP_OK;
 }
 
 void fft3_destroy(kp_plan p) {
-    if (!p->fft3) return;
-    if (p->fft3->d_tw) cudaFree(p->fft3->d_tw);
-    delete p->fft3;
+    fft3_free(p->fft3);
     p->fft3 = nullptr;
 }
 
@@ -375,21 +381,20 @@ static bool size_compiled(int N) {
 }
 
 template <int AXIS, bool INV, int N, bool PRE = false, typename MT = float2>
-static kp_status launch_pass_n(kp_plan p, const float2* in, float2* out, unsigned nblocks, const PreSrc& pre,
-                               cudaStream_t st) {
+static kp_status launch_pass_n(const Fft3Plan* f, const Geom& g, const float2* in, float2* out, unsigned nblocks,
+                               const PreSrc& pre, cudaStream_t st) {
     static PerDeviceOnce attr;
     if (attr.first())
         KP_TRY_CUDA(cudaFuncSetAttribute(k_fft_pass<AXIS, INV, N, PRE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pass_smem(N)));
-    k_fft_pass<AXIS, INV, N, PRE, MT><<<nblocks, FF_T, pass_smem(N), st>>>(in, out, p->geo, p->fft3->ax[AXIS],
-                                                                         p->fft3->k, pre);
+    k_fft_pass<AXIS, INV, N, PRE, MT><<<nblocks, FF_T, pass_smem(N), st>>>(in, out, g, f->ax[AXIS], f->k, pre);
     KP_LAUNCH_CHECK();
     return KP_OK;
 }
 
 template <int AXIS, bool INV, bool PRE = false, typename MT = float2>
-static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStream_t st, const PreSrc& pre = PreSrc{}) {
-    const Geom& g = p->geo;
+static kp_status launch_pass(const Fft3Plan* f, const Geom& g, int64_t& launches, const float2* in, float2* out,
+                             cudaStream_t st, const PreSrc& pre = PreSrc{}) {
     int64_t nblocks;
     const int ln = g.g[AXIS] <= 256 ? 16 : 8;           // ff_lines(N) of this pass
     const int64_t xblocks = (g.g[2] + ln - 1) / ln;
@@ -397,37 +402,48 @@ static kp_status launch_pass(kp_plan p, const float2* in, float2* out, cudaStrea
     else if (AXIS == 1) nblocks = (int64_t)g.C * g.n[0] * xblocks;
     else nblocks = (int64_t)g.C * g.g[1] * xblocks;
     if (nblocks > INT32_MAX) { set_error("grid too large for the FFT passes"); return KP_EINVAL; }
-    p->launches += 1;
+    launches += 1;
     switch (g.g[AXIS]) {
-#define KP_FFT_CASE(n) case n: return launch_pass_n<AXIS, INV, n, PRE, MT>(p, in, out, (unsigned)nblocks, pre, st);
+#define KP_FFT_CASE(n) case n: return launch_pass_n<AXIS, INV, n, PRE, MT>(f, g, in, out, (unsigned)nblocks, pre, st);
         KP_FFT_SIZES(KP_FFT_CASE)
 #undef KP_FFT_CASE
         default: set_error("FFT pass size without compiled kernel"); return KP_EINTERNAL;
     }
 }
 
+kp_status fft3_forward_geo(const Fft3Plan* f, const Geom& g, const float2* in, float2* out, int64_t& launches,
+                           cudaStream_t st) {
+    KP_TRY((launch_pass<2, false>(f, g, launches, in, out, st)));
+    KP_TRY((launch_pass<1, false>(f, g, launches, out, out, st)));
+    return launch_pass<0, false>(f, g, launches, out, out, st);
+}
+
+kp_status fft3_inverse_geo(const Fft3Plan* f, const Geom& g, float2* io, int64_t& launches, cudaStream_t st) {
+    KP_TRY((launch_pass<0, true>(f, g, launches, io, io, st)));
+    KP_TRY((launch_pass<1, true>(f, g, launches, io, io, st)));
+    return launch_pass<2, true>(f, g, launches, io, io, st);
+}
+
 kp_status fft3_forward(kp_plan p, const float2* in, float2* out, cudaStream_t st) {
-    KP_TRY((launch_pass<2, false>(p, in, out, st)));
-    KP_TRY((launch_pass<1, false>(p, out, out, st)));
-    return launch_pass<0, false>(p, out, out, st);
+    return fft3_forward_geo(p->fft3, p->geo, in, out, p->launches, st);
 }
 
 kp_status fft3_forward_image(kp_plan p, const float2* x, cudaStream_t st) {
     const PreSrc pre{x, p->unit_maps ? nullptr : p->d_maps, p->d_apod};
+    const Fft3Plan* f = p->fft3;
+    const Geom& g = p->geo;
     float2* out = p->d_gridF;
     switch (p->unit_maps ? KP_C64 : p->maps_t) {
-        case KP_C64: KP_TRY((launch_pass<2, false, true, float2>(p, nullptr, out, st, pre))); break;
-        case KP_C32_BF16: KP_TRY((launch_pass<2, false, true, __nv_bfloat162>(p, nullptr, out, st, pre))); break;
-        default: KP_TRY((launch_pass<2, false, true, __half2>(p, nullptr, out, st, pre))); break;
+        case KP_C64: KP_TRY((launch_pass<2, false, true, float2>(f, g, p->launches, nullptr, out, st, pre))); break;
+        case KP_C32_BF16: KP_TRY((launch_pass<2, false, true, __nv_bfloat162>(f, g, p->launches, nullptr, out, st, pre))); break;
+        default: KP_TRY((launch_pass<2, false, true, __half2>(f, g, p->launches, nullptr, out, st, pre))); break;
     }
-    KP_TRY((launch_pass<1, false>(p, out, out, st)));
-    return launch_pass<0, false>(p, out, out, st);
+    KP_TRY((launch_pass<1, false>(f, g, p->launches, out, out, st)));
+    return launch_pass<0, false>(f, g, p->launches, out, out, st);
 }
 
 kp_status fft3_inverse(kp_plan p, float2* io, cudaStream_t st) {
-    KP_TRY((launch_pass<0, true>(p, io, io, st)));
-    KP_TRY((launch_pass<1, true>(p, io, io, st)));
-    return launch_pass<2, true>(p, io, io, st);
+    return fft3_inverse_geo(p->fft3, p->geo, io, p->launches, st);
 }
 
 }  // namespace kp

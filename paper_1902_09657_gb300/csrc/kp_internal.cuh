@@ -182,9 +182,15 @@ template <int D, typename MT>
 __device__ __forceinline__ float2 adj_pixel(const float2* __restrict__ grid, const MT* __restrict__ maps,
                                             const float* __restrict__ apod, const Geom& geo, int64_t j) {
     int jj[D];
-    int64_t r = j;
+    if (geo.N < ((int64_t)1 << 31)) {          // 32-bit index arithmetic (64-bit division is slow)
+        unsigned r = (unsigned)j;
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) { jj[d] = (int)(r % geo.n[d]); r /= geo.n[d]; }
+        for (int d = D - 1; d >= 0; --d) { jj[d] = (int)(r % (unsigned)geo.n[d]); r /= (unsigned)geo.n[d]; }
+    } else {
+        int64_t r = j;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) { jj[d] = (int)(r % geo.n[d]); r /= geo.n[d]; }
+    }
     int64_t gi = 0;
     float a = geo.rsqrtN;
     int ao = 0;
@@ -196,8 +202,30 @@ __device__ __forceinline__ float2 adj_pixel(const float2* __restrict__ grid, con
         a *= apod[ao + jj[d]];
         ao += geo.n[d];
     }
+    // coils four at a time: every load of a group is issued before its products are summed
+    // (the sum still runs over c = 0, 1, 2, ... in order)
     float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < geo.C; ++c) {
+    int c = 0;
+    for (; c + 4 <= geo.C; c += 4) {
+        float2 gv[4], s[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            gv[q] = grid[(size_t)(c + q) * geo.G + gi];
+            s[q] = maps ? ldc<MT>(maps, (size_t)(c + q) * geo.N + j) : make_float2(1.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (maps) {
+                const float2 v = cmulc(s[q], gv[q]);
+                acc.x += v.x;
+                acc.y += v.y;
+            } else {
+                acc.x += gv[q].x;
+                acc.y += gv[q].y;
+            }
+        }
+    }
+    for (; c < geo.C; ++c) {
         float2 gv = grid[(size_t)c * geo.G + gi];
         if (maps) {
             float2 s = ldc<MT>(maps, (size_t)c * geo.N + j);
@@ -352,6 +380,10 @@ struct kp_plan_s {
     cufftHandle fft = 0;
     bool fft_ok = false;
     kp::Fft3Plan* fft3 = nullptr;    // own 3D FFT passes (kp_fft.cu) when the grid sizes allow, else cuFFT
+    void* d_ystage = nullptr;        // measurements copied in from host memory (kp_pdhg_solve_host)
+    size_t ystage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copy_in = nullptr, ev_copy_done = nullptr;
 
     // solver state (sorted k-space order)
     float2* d_u = nullptr;           // [C][M] dual variable
@@ -453,7 +485,8 @@ kp_status primal_fused(kp_plan p, int reg, float lambda, cudaStream_t st);
 bool cluster_prox_ok(kp_plan p);
 kp_status primal_cluster(kp_plan p, float lambda, cudaStream_t st);
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st, int reg = 0, const kp_pdhg_state* start = nullptr);
+                      cudaStream_t st, int reg = 0, const kp_pdhg_state* start = nullptr, cudaEvent_t y_ready = nullptr);
+kp_status solve_measurements(kp_plan plan, const void* y_dev, kp_cdtype y_t, cudaStream_t st);
 kp_status solve_setup_a(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, int iters, cudaStream_t st,
                         const kp_pdhg_state* start);
 kp_status solve_setup_b(kp_plan plan, int iters, cudaStream_t st, int reg, const kp_pdhg_state* start);
@@ -476,6 +509,14 @@ kp_status fft_inverse_only(kp_plan p, cudaStream_t st);
 // transform valid on the image crop only.
 kp_status fft3_create(kp_plan p);
 void fft3_destroy(kp_plan p);
+// The same passes for any batch of 3D grids (geo.C grids of geo.g points, image band geo.n per
+// axis; a band as long as the axis means no pruning): fft3_make returns null when a length has
+// no compiled passes.
+Fft3Plan* fft3_make(const int g[3]);
+void fft3_free(Fft3Plan* f);
+kp_status fft3_forward_geo(const Fft3Plan* f, const Geom& g, const float2* in, float2* out, int64_t& launches,
+                           cudaStream_t st);
+kp_status fft3_inverse_geo(const Fft3Plan* f, const Geom& g, float2* io, int64_t& launches, cudaStream_t st);
 kp_status fft3_forward(kp_plan p, const float2* in, float2* out, cudaStream_t st);
 // The forward grid spectrum of image x into d_gridF, the pre-step (coil multiply, apodisation)
 // formed by the first pass from x and the maps (no d_grid involved).

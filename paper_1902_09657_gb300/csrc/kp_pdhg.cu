@@ -421,17 +421,24 @@ kp_status ensure_tv_dual(kp_plan p) {
 // preconditioner in sorted order, min p, lambda_max (given, or 30 power iterations), the
 // step-size schedule, the initial iterates (zero, or a caller's state whose dual variable is
 // brought into sorted order) and the forward grid of xbar.
-kp_status solve_setup_a(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, int iters, cudaStream_t st,
-                        const kp_pdhg_state* start) {
+// The measurements into sorted order (their first reader is the first dual step).
+kp_status solve_measurements(kp_plan plan, const void* y_dev, kp_cdtype y_t, cudaStream_t st) {
     const Geom& g = plan->geo;
-    const int k0 = start ? start->k : 0;
-    KP_TRY(ensure_sched(plan, std::max(iters + k0, 1)));
-    // measurements into sorted order
     plan->ys_t = y_t;
     if (y_t == KP_C64) k_permute<float2><<<nblk(g.M, 256), 256, 0, st>>>((const float2*)y_dev, (float2*)plan->d_ys, plan->d_perm, g.M, g.C);
     else k_permute<unsigned><<<nblk(g.M, 256), 256, 0, st>>>((const unsigned*)y_dev, (unsigned*)plan->d_ys, plan->d_perm, g.M, g.C);
     KP_LAUNCH_CHECK();
     plan->launches += 1;
+    return KP_OK;
+}
+
+kp_status solve_setup_a(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, int iters, cudaStream_t st,
+                        const kp_pdhg_state* start) {
+    const Geom& g = plan->geo;
+    const int k0 = start ? start->k : 0;
+    KP_TRY(ensure_sched(plan, std::max(iters + k0, 1)));
+    plan->ys_t = y_t;
+    if (y_dev) KP_TRY(solve_measurements(plan, y_dev, y_t, st));
     // preconditioner
     const float* pu = p_dev;
     if (!pu) {
@@ -499,9 +506,10 @@ kp_status solve_setup_b(kp_plan plan, int iters, cudaStream_t st, int reg, const
 // step-size schedule, the initial iterates (zero, or a caller's state whose dual variable is
 // brought into sorted order) and the forward grid of xbar.
 kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, double lmax, int iters,
-                      cudaStream_t st, int reg, const kp_pdhg_state* start) {
+                      cudaStream_t st, int reg, const kp_pdhg_state* start, cudaEvent_t y_ready) {
     const Geom& g = plan->geo;
-    KP_TRY(solve_setup_a(plan, y_dev, y_t, p_dev, iters, st, start));
+    // with y_ready (measurements still being copied in), they are loaded after the power method
+    KP_TRY(solve_setup_a(plan, y_ready ? nullptr : y_dev, y_t, p_dev, iters, st, start));
     // lambda_max(P A A^H)
     if (lmax > 0) {
         k_set_double<<<1, 1, 0, st>>>(plan->d_schedd, lmax);
@@ -511,6 +519,10 @@ kp_status solve_setup(kp_plan plan, const void* y_dev, kp_cdtype y_t, const floa
         KP_TRY(fill_image(plan->d_z, g.N, make_float2(1.f, 0.f), st));
         plan->launches += 1;
         KP_TRY(power_method(plan, plan->d_ps, 30, st));
+    }
+    if (y_ready) {
+        KP_TRY_CUDA(cudaStreamWaitEvent(st, y_ready, 0));
+        KP_TRY(solve_measurements(plan, y_dev, y_t, st));
     }
     return solve_setup_b(plan, iters, st, reg, start);
 }
@@ -770,9 +782,20 @@ static kp_status ensure_events(kp_plan p, int n) {
     return KP_OK;
 }
 
+static kp_status pdhg_solve_impl(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg,
+                                 float lambda, int iters, double lmax, const kp_pdhg_state* start, kp_pdhg_state* end,
+                                 double* obj_trace, kp_stats* stats, void* stream, cudaEvent_t y_ready);
+
 kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg,
                            float lambda, int iters, double lmax, const kp_pdhg_state* start, kp_pdhg_state* end,
                            double* obj_trace, kp_stats* stats, void* stream) {
+    return pdhg_solve_impl(plan, y_dev, y_t, p_dev, reg, lambda, iters, lmax, start, end, obj_trace, stats, stream,
+                           nullptr);
+}
+
+static kp_status pdhg_solve_impl(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg,
+                                 float lambda, int iters, double lmax, const kp_pdhg_state* start, kp_pdhg_state* end,
+                                 double* obj_trace, kp_stats* stats, void* stream, cudaEvent_t y_ready) {
     if (!plan || !y_dev || !end || !end->x) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
@@ -787,7 +810,7 @@ kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const
     cudaStream_t st = (cudaStream_t)stream;
     const Geom& g = plan->geo;
     const int k0 = start ? start->k : 0;
-    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st, (int)reg, start));
+    KP_TRY(solve_setup(plan, y_dev, y_t, p_dev, lmax, iters, st, (int)reg, start, y_ready));
     kp_status status = KP_OK;
     double F0 = 0, F = NAN;
     double phase_ms[PH_N] = {0};
@@ -867,6 +890,43 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
     if (!x_dev) { set_error("null argument"); return KP_EINVAL; }
     kp_pdhg_state end{x_dev, nullptr, nullptr, nullptr, 0};
     return kp_pdhg_solve_ex(plan, y_dev, y_t, p_dev, reg, lambda, iters, lmax, nullptr, &end, obj_trace, stats, stream);
+}
+
+kp_status kp_pdhg_solve_host(kp_plan plan, const void* y_host, kp_cdtype y_t, const float* p_dev, kp_reg reg,
+                             float lambda, int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats,
+                             void* stream) {
+    if (!plan || !y_host || !x_dev) { set_error("null argument"); return KP_EINVAL; }
+    if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, y_host) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        set_error("y_host must be page-locked host memory");
+        return KP_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)plan->geo.C * plan->geo.M * (y_t == KP_C64 ? sizeof(float2) : sizeof(unsigned));
+    if (!plan->d_ystage || plan->ystage_bytes < bytes) {
+        if (plan->d_ystage) {
+            KP_TRY_CUDA(cudaStreamSynchronize(st));
+            cudaFree(plan->d_ystage);
+        }
+        plan->d_ystage = nullptr;
+        plan->ystage_bytes = 0;
+        KP_TRY_CUDA(cudaMalloc(&plan->d_ystage, bytes));
+        plan->ystage_bytes = bytes;
+    }
+    if (!plan->copy_stream) KP_TRY_CUDA(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+    if (!plan->ev_copy_in) KP_TRY_CUDA(cudaEventCreateWithFlags(&plan->ev_copy_in, cudaEventDisableTiming));
+    if (!plan->ev_copy_done) KP_TRY_CUDA(cudaEventCreateWithFlags(&plan->ev_copy_done, cudaEventDisableTiming));
+    // the copy starts once earlier work on `stream` (which may still read the staging buffer) is done
+    KP_TRY_CUDA(cudaEventRecord(plan->ev_copy_in, st));
+    KP_TRY_CUDA(cudaStreamWaitEvent(plan->copy_stream, plan->ev_copy_in, 0));
+    KP_TRY_CUDA(cudaMemcpyAsync(plan->d_ystage, y_host, bytes, cudaMemcpyHostToDevice, plan->copy_stream));
+    KP_TRY_CUDA(cudaEventRecord(plan->ev_copy_done, plan->copy_stream));
+    kp_pdhg_state end{};
+    end.x = x_dev;
+    return pdhg_solve_impl(plan, plan->d_ystage, y_t, p_dev, reg, lambda, iters, lmax, nullptr, &end, obj_trace, stats,
+                           stream, plan->ev_copy_done);
 }
 
 }  // extern "C"

@@ -538,6 +538,10 @@ kp_status plan_destroy_internal(kp_plan p) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->ev_copy_in) cudaEventDestroy(p->ev_copy_in);
+    if (p->ev_copy_done) cudaEventDestroy(p->ev_copy_done);
+    if (p->d_ystage) cudaFree(p->d_ystage);
     for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
     delete[] p->ev;
     delete[] p->ev_phase;

@@ -48,6 +48,7 @@ struct PrePlan {
     int npairs = 0;
     cufftHandle fft_pairs = 0, fft_one = 0, fft_coils = 0;
     bool ok_pairs = false, ok_one = false, ok_coils = false;
+    Fft3Plan* f3 = nullptr;     // own passes on the 2N grid (3D, compiled lengths), else the cuFFT plans
     int traj_version = -1;
 };
 
@@ -58,11 +59,28 @@ void pre_destroy(kp_plan p) {
     if (q->ok_pairs) cufftDestroy(q->fft_pairs);
     if (q->ok_one) cufftDestroy(q->fft_one);
     if (q->ok_coils) cufftDestroy(q->fft_coils);
+    fft3_free(q->f3);
     void* bufs[] = {q->d_R, q->d_q, q->d_r, q->d_h, q->d_v, q->d_norm, q->d_pairs};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete q;
     p->pre = nullptr;
+}
+
+// Geometry of `count` 2N grids for the own FFT passes: image band of the owning plan's image
+// (the products' support), or the whole grid (full = true: no pruning).
+static Geom pre_geo(const PrePlan* q, const Geom& g, int count, bool full) {
+    Geom r{};
+    r.D = 3;
+    r.C = count;
+    r.N = 1;
+    for (int d = 0; d < 3; ++d) {
+        r.g[d] = q->nb[d];
+        r.n[d] = full ? q->nb[d] : g.n[d];
+        r.N *= r.n[d];
+    }
+    r.G = q->Nb;
+    return r;
 }
 
 static kp_status pre_create(kp_plan p, cudaStream_t st) {
@@ -118,6 +136,7 @@ static kp_status pre_create(kp_plan p, cudaStream_t st) {
     q->ok_one = true;
     KP_TRY_CUFFT(cufftPlanMany(&q->fft_coils, g.D, dims, nullptr, 1, (int)q->Nb, nullptr, 1, (int)q->Nb, CUFFT_C2C, q->Cb));
     q->ok_coils = true;
+    if (g.D == 3) q->f3 = fft3_make(q->nb);
     // NUFFT on the 2N image with unit maps and one coil
     kp_params prm = p->P;
     prm.ncoils = 1;
@@ -525,8 +544,13 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
                 break;
         }
         KP_LAUNCH_CHECK();
-        KP_TRY_CUFFT(cufftExecC2C(nwrite == 1 ? q->fft_one : q->fft_pairs, (cufftComplex*)q->d_q, (cufftComplex*)q->d_q,
-                                  CUFFT_FORWARD));
+        if (q->f3) {
+            // the products are zero outside the image band of the 2N grid (k_make_q's placement)
+            KP_TRY(fft3_forward_geo(q->f3, pre_geo(q, g, nwrite, false), q->d_q, q->d_q, plan->launches, st));
+        } else {
+            KP_TRY_CUFFT(cufftExecC2C(nwrite == 1 ? q->fft_one : q->fft_pairs, (cufftComplex*)q->d_q, (cufftComplex*)q->d_q,
+                                      CUFFT_FORWARD));
+        }
         if (all_at_once)
             k_accum_all<<<dim3(nblk(q->Nb, 256), C), 256, 0, st>>>(q->d_q, C, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb,
                                                                    q->d_R);
@@ -548,8 +572,9 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
         const int nc = C - c0 < q->Cb ? C - c0 : q->Cb;
         k_R_to_c<<<nblk(q->Nb * nc, 256), 256, 0, st>>>(q->d_R + (size_t)c0 * q->Nb, q->Nb, nc, 1.0 / (double)q->Nb, q->d_r);
         KP_LAUNCH_CHECK();
-        KP_TRY_CUFFT(cufftExecC2C(nc == 1 ? q->fft_one : q->fft_coils, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r,
-                                  CUFFT_INVERSE));
+        if (q->f3) KP_TRY(fft3_inverse_geo(q->f3, pre_geo(q, g, nc, true), q->d_r, plan->launches, st));   // every lag
+        else KP_TRY_CUFFT(cufftExecC2C(nc == 1 ? q->fft_one : q->fft_coils, (cufftComplex*)q->d_r, (cufftComplex*)q->d_r,
+                                       CUFFT_INVERSE));
         k_rh<<<dim3(nblk(q->Nb, 256), nc), 256, 0, st>>>(q->d_r, q->d_h, g.D, q->nb[0], q->nb[1], q->nb[2], q->Nb, q->d_v);
         KP_LAUNCH_CHECK();
         plan->launches += 2;

@@ -772,7 +772,7 @@ __device__ __forceinline__ LevelArgs level_args(const PrimalArgs& a, int lev, bo
     return la;
 }
 
-constexpr int PF_THREADS = 512;
+constexpr int PF_THREADS = 1024;
 
 // Clears the split spreading tiles' regions of grid2 (all coils), CTA-strided over tiles, so
 // the next spread can accumulate into them without a separate clearing kernel.
@@ -806,7 +806,7 @@ __device__ void zero_split_tiles(const PrimalArgs& a) {
 }
 
 template <int D, int T, typename MT, int REG>
-__global__ void __launch_bounds__(PF_THREADS) k_primal_fused(PrimalArgs a) {
+__global__ void __launch_bounds__(PF_THREADS, 1) k_primal_fused(PrimalArgs a) {
     extern __shared__ float2 sm[];
     const Geom& g = a.geo;
     const int k = *a.iter;

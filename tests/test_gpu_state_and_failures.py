@@ -142,3 +142,36 @@ def test_unrolled_backward_after_a_later_forward_raises():
         x1.abs().sum().backward()
     x2.abs().sum().backward()                         # the latest forward still differentiates
     assert y2.grad is not None and bool(torch.isfinite(y2.grad).all())
+
+
+def test_host_measurements_overlap_the_setup():
+    """kp_pdhg_solve_host (pinned host y, copied in on the plan's copy stream during the set-up)
+    gives the device-y solve's result (itself checked against the oracle elsewhere); unpinned
+    host memory is refused by the C entry point."""
+    need_gpu()
+    import torch
+    from paper_1902_09657_gb300._lib import KpError, KP_EINVAL
+    from paper_1902_09657_gb300.api import to_storage
+    w, x, maps, traj, y = _small(n=64, C=4, L=8, ns=1024)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
+    plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
+    lam = 1e-3
+    xd, _, _ = plan.pdhg_solve(to_dev(y), None, "l2", lam, 20)
+    yh = torch.from_numpy(y.astype(np.complex64)).pin_memory()
+    xh, _, _ = plan.pdhg_solve(yh, None, "l2", lam, 20)
+    assert not xh.is_cuda
+    assert rel(xh.numpy(), xd.cpu().numpy(), "host y vs device y") < 1e-6
+    # bf16 storage from pinned host memory
+    yb = to_storage(to_dev(y), "bf16")
+    xb_d, _, _ = plan.pdhg_solve(yb, None, "l1_wavelet", lam, 20)
+    xb_h, _, _ = plan.pdhg_solve(yb.cpu().pin_memory(), None, "l1_wavelet", lam, 20)
+    assert rel(xb_h.numpy(), xb_d.cpu().numpy(), "bf16 host y vs device y") < 1e-6
+    out = torch.empty(x.shape, dtype=torch.complex64, device="cuda")
+    unpinned = torch.from_numpy(y.astype(np.complex64))
+    import ctypes
+    from paper_1902_09657_gb300 import _lib as L
+    st = L.KpStats()
+    status = plan.lib.kp_pdhg_solve_host(plan._h, ctypes.c_void_p(unpinned.data_ptr()), L.KP_C64, None, 0,
+                                         ctypes.c_float(lam), 3, ctypes.c_double(0.0), ctypes.c_void_p(out.data_ptr()),
+                                         None, ctypes.byref(st), None)
+    assert status == KP_EINVAL
