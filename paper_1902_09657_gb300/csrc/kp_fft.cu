@@ -5,9 +5,9 @@
 // One pass per axis.  A CTA takes 16 lines of one axis (8 for axes longer than 256 points): rows
 // along x, or columns along y or z for 16 (8) consecutive x, so every global access is a 128-
 // (64-) byte row segment.  Each thread issues all its loads before storing them to shared
-// memory, where a self-sorting (Stockham) mixed-radix transform runs (radix 4, 2, 3 and 5
-// stages, twiddles from a table of the g-th roots of unity built on the host in float64); then
-// the lines are written back.
+// memory, where a self-sorting (Stockham) mixed-radix transform runs (radix 16, 8, 4, 2, 3
+// and 5 stages, 16 and 8 done as 4 x 4 and 4 x 2 in registers; twiddles from a table of the
+// g-th roots of unity built on the host in float64); then the lines are written back.
 //
 // The passes exploit the structure of the NUFFT's grids.  The image occupies n_d of the g_d
 // indices per axis (the band [0, n - n/2) and [g - n/2, g), where the pre-step puts it), and
@@ -35,8 +35,9 @@ constexpr int FF_T = 256;        // threads per CTA
 constexpr int FF_MAXN = 512;     // longest axis handled
 constexpr int FF_MAXST = 10;     // radix stages at most
 
-struct FfConst {                 // sqrt(3)/2, cos and sin of 2 pi/5 and of 4 pi/5 (float64 on the host, rounded once)
-    float s3, c51, s51, c52, s52;
+struct FfConst {                 // float64 on the host, rounded once
+    float s3, c51, s51, c52, s52;   // sqrt(3)/2, cos and sin of 2 pi/5 and of 4 pi/5
+    float2 w16[10];                 // (cos, sin) of 2 pi j / 16, j = 0..9 (radix-16 and radix-8 twiddles)
 };
 
 struct FfAxis {
@@ -70,10 +71,73 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 // a * (-i s) for the forward sign (s = +1) or a * (+i) for the inverse (s = -1): (s a.y, -s a.x)
 __device__ __forceinline__ float2 cmul_mi(float2 a, float s) { return make_float2(s * a.y, -s * a.x); }
 
+// a e^{-s 2 pi i j / 16} for cs = (cos, sin)(2 pi j / 16)
+__device__ __forceinline__ float2 cmul_w(float2 a, float2 cs, float s) {
+    const float wy = -s * cs.y;
+    return make_float2(a.x * cs.x - a.y * wy, a.x * wy + a.y * cs.x);
+}
+
+template <int R>
+__device__ __forceinline__ void small_dft(float2* v, float s, const FfConst& k);
+
+// 4-point DFT of (a, b, c, d) in place, outputs in natural order
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d, float s) {
+    const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = cmul_mi(csub(b, d), s);
+    a = cadd(t0, t2);
+    c = csub(t0, t2);
+    b = cadd(t1, t3);
+    d = csub(t1, t3);
+}
+
 // One R-point DFT of v[0..R-1] in place, sign s = +1 forward (omega = e^{-2 pi i / R}), -1 inverse.
+// R = 16 and 8 run as 4 x 4 and 4 x 2 in registers: with q = 4 q1 + q2 (resp. 2 q1 + q2) and
+// k = k1 + 4 k2, X[k] = sum_q2 w_R^(q2 k1) w^(q2 k2) [sum_q1 v[.] w_4^(q1 k1)].
 template <int R>
 __device__ __forceinline__ void small_dft(float2* v, float s, const FfConst& k) {
-    if (R == 2) {
+    if (R == 16) {
+        float2 y[4][4];
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+            float2 a = v[q2], b = v[4 + q2], c = v[8 + q2], d = v[12 + q2];
+            dft4(a, b, c, d, s);
+            y[q2][0] = a;
+            y[q2][1] = b;
+            y[q2][2] = c;
+            y[q2][3] = d;
+        }
+#pragma unroll
+        for (int q2 = 1; q2 < 4; ++q2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) y[q2][k1] = cmul_w(y[q2][k1], k.w16[q2 * k1], s);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 a = y[0][k1], b = y[1][k1], c = y[2][k1], d = y[3][k1];
+            dft4(a, b, c, d, s);
+            v[k1] = a;
+            v[k1 + 4] = b;
+            v[k1 + 8] = c;
+            v[k1 + 12] = d;
+        }
+    } else if (R == 8) {
+        float2 y0[4], y1[4];
+        {
+            float2 a = v[0], b = v[2], c = v[4], d = v[6];
+            dft4(a, b, c, d, s);
+            y0[0] = a; y0[1] = b; y0[2] = c; y0[3] = d;
+        }
+        {
+            float2 a = v[1], b = v[3], c = v[5], d = v[7];
+            dft4(a, b, c, d, s);
+            y1[0] = a; y1[1] = b; y1[2] = c; y1[3] = d;
+        }
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) y1[k1] = cmul_w(y1[k1], k.w16[2 * k1], s);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            v[k1] = cadd(y0[k1], y1[k1]);
+            v[k1 + 4] = csub(y0[k1], y1[k1]);
+        }
+    } else if (R == 2) {
         const float2 a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
@@ -108,16 +172,16 @@ __device__ __forceinline__ void small_dft(float2* v, float s, const FfConst& k) 
     }
 }
 
-// Radices of N in the order applied (all 4s, then 2, 3, 5), at compile time.
+// Radices of N in the order applied (16s, 8s, 4s, 2s, then 3, 5), at compile time.
 constexpr int fac_count(int N) {
     int c = 0;
-    for (int f : {4, 2, 3, 5})
+    for (int f : {16, 8, 4, 2, 3, 5})
         while (N % f == 0) { N /= f; ++c; }
     return N == 1 ? c : -1;
 }
 constexpr int fac_at(int N, int i) {
     int c = 0;
-    for (int f : {4, 2, 3, 5})
+    for (int f : {16, 8, 4, 2, 3, 5})
         while (N % f == 0) {
             if (c == i) return f;
             N /= f;
@@ -198,8 +262,10 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
             const int64_t row = (int64_t)blockIdx.x * LN + threadIdx.x;
             const int64_t nrows = (int64_t)geo.C * n0 * n1;
             if (row < nrows) {
-                const int c = (int)(row / ((int64_t)n0 * n1));
-                const int rem = (int)(row - (int64_t)c * n0 * n1);
+                // coil fastest: a CTA's rows are few image rows in every coil, so the fused
+                // pre-step's image and 1/Phi loads of a row are shared by its coils
+                const int c = (int)(row % geo.C);
+                const int rem = (int)(row / geo.C);
                 const int z = band_index(rem / n1, n0, g0), y = band_index(rem % n1, n1, g1);
                 base_s[threadIdx.x] = (int64_t)c * geo.G + ((int64_t)z * g1 + y) * g2;
                 if (PRE) {
@@ -284,11 +350,11 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
 
 static size_t pass_smem(int N) { return ((size_t)2 * (N <= 256 ? 16 : 8) * N + N) * sizeof(float2); }
 
-// Radices of N (4 first, then 2, 3, 5); false if N has another prime factor or too many stages.
+// Radices of N (16, 8, 4, 2, then 3, 5); false if N has another prime factor or too many stages.
 static bool factor(int N, FfAxis& ax) {
     ax.nst = 0;
     int r = N;
-    for (int f : {4, 2, 3, 5}) {
+    for (int f : {16, 8, 4, 2, 3, 5}) {
         while (r % f == 0) {
             if (ax.nst == FF_MAXST) return false;
             ax.r[ax.nst++] = f;
@@ -347,6 +413,8 @@ Fft3Plan* fft3_make(const int g[3]) {
     q->k.s51 = (float)std::sin(2.0 * M_PI / 5.0);
     q->k.c52 = (float)std::cos(4.0 * M_PI / 5.0);
     q->k.s52 = (float)std::sin(4.0 * M_PI / 5.0);
+    for (int j = 0; j < 10; ++j)
+        q->k.w16[j] = make_float2((float)std::cos(2.0 * M_PI * j / 16.0), (float)std::sin(2.0 * M_PI * j / 16.0));
     return q;
 }
 
