@@ -58,12 +58,27 @@ def test_resume_equals_uninterrupted_and_oracle(reg):
     assert rel(x_b.cpu().numpy(), x_ref, "resumed vs oracle from the same state") < 1e-5
 
 
-def test_wait_limit_timeouts_are_reported():
+def _small3d(n=16, C=3, spokes=300, readout=24):
+    w = synth.Workload("state_small3d", (n, n, n), C, 1.25, 4, "l1_wavelet", 1e-3, 20, 1, "radial3d",
+                       dict(n_spokes=spokes, n_readout=readout, kmax=n / 2.0))
+    x, maps, traj = w.phantom(), w.maps(), w.traj()
+    return w, x, maps, traj, simulate(w, x, maps, traj)
+
+
+@pytest.mark.parametrize("case", ["2d", "3d-taps"])
+def test_wait_limit_timeouts_are_reported(case, monkeypatch):
+    """A wait limit of 0 makes every staging wait that is not already complete give up at once
+    (the interpolation kernels, including the 3D lane-per-tap form, end by themselves and drain
+    their copies); the timeout is reported once and the plan works again with the limit restored."""
     need_gpu()
     import torch
     from paper_1902_09657_gb300._lib import KpError, KP_ETIMEOUT
-    w, x, maps, traj, y = _small(n=64, C=4, L=8, ns=1024)
-    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=2)
+    if case == "3d-taps":
+        monkeypatch.setenv("KPDHG_INTERP", "taps")
+        w, x, maps, traj, y = _small3d()
+    else:
+        w, x, maps, traj, y = _small(n=64, C=4, L=8, ns=1024)
+    plan = make_plan(x.shape, maps.shape[0], traj.shape[0], levels=1 if case == "3d-taps" else 2)
     plan.set_trajectory(to_dev(traj)).set_maps(to_dev(maps))
     xd = to_dev(x)
     y_ok = plan.sense_forward(xd).cpu().numpy()
