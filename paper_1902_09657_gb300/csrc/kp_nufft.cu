@@ -1,15 +1,16 @@
 // Multi-coil SENSE NUFFT pair A = F_nu S and A^H on sm_103a (Sec. 2 Eq. model_i;
 // Sec. 6: Kaiser-Bessel gridding following Beatty et al., oversampling g/n, width 4).
 //
-// Forward:  fwd_pre (coil multiply, 1/Phi apodisation, centred zero padding; writes the
-//           whole grid) -> cuFFT C2C forward, batch C -> interp (W^D taps per sample,
-//           one thread per sorted sample, all coils, N^{-1/2}).
-// Adjoint:  spread into a second grid (one CTA per (tile, chunk) work item; each sample is
-//           taken by a group of lanes, one lane per tap, looping over coils, so shared-memory
-//           atomics of one sample never collide; single-chunk tiles store straight to the
-//           grid, chunks of split tiles add their tile with global atomics into a region
-//           cleared just before) -> cuFFT C2C inverse -> adj_post (crop, 1/Phi, conj(s_c)
-//           coil combine, N^{-1/2}).
+// Forward:  pre-step (coil multiply, 1/Phi apodisation, centred zero padding) -> forward FFT
+//           of every coil's grid (2D: cuFFT; 3D: the own passes of kp_fft.cu, whose first pass
+//           forms the pre-step itself) -> interpolation (one CTA per (tile item, 4 coils), the
+//           tile's grid region staged in shared memory, one thread per sorted sample, W^D taps,
+//           N^{-1/2}).
+// Adjoint:  spreading into a second grid (variants chosen per plan by the autotuner: private
+//           tile copies per warp, or in 3D the two-phase padded tiles + gather; no zero-fill of
+//           the grid, split tiles cleared before they are accumulated) -> inverse FFT (cuFFT or
+//           the own passes, which leave only the crop valid) -> crop, 1/Phi, conj(s_c) coil
+//           combine, N^{-1/2} (fused into the primal step inside a PDHG iteration).
 // The Kaiser-Bessel weights and first taps of every sample are tabulated once per
 // trajectory (sorted order, structure of arrays), so no Bessel function is evaluated
 // inside the iteration.
@@ -473,126 +474,6 @@ k_interp_tile_b(const BInterp* __restrict__ cs, const int* __restrict__ boff, in
     const BInterp& a = cs[c];
     const int lb = (int)blockIdx.x - boff[c];
     interp_tile_body<D, MODE, T>(a.items, a.k0t, a.wt, a.grid, a.geo, a.tl, a.io, lb % a.nx, lb / a.nx);
-}
-
-// 3D interpolation with lanes on taps: the same staging, then each half-warp takes one sample at
-// a time, its 16 lanes the (z, x) taps (a, e) of the 4 x 4 x 4 footprint, each lane summing its
-// 4 y taps for the CTA's coils.  With the staged plane stride R RP = 132 points (4 mod 16), the
-// 16 lanes read 16 different bank pairs (4 a + e), so the staged reads have no conflicts; the
-// lanes' sums are combined by a shuffle reduction and lanes 0 .. cc-1 finish one coil each.
-// The samples' first-tap offsets and weights are staged in shared memory while the grid
-// region is in flight.
-template <int MODE, typename T>
-__device__ __forceinline__ void interp_taps_body(const int4* __restrict__ items, const int* __restrict__ k0t,
-                                                 const float* __restrict__ wt, const float2* __restrict__ grid,
-                                                 const Geom& geo, const Tiles& tl, const InterpIO& io, int bx, int by) {
-    constexpr int D = 3;
-    using LY = IpL<3>;
-    constexpr int R = LY::R, rs0 = R * LY::RP, rs1 = LY::RP, Rtot = LY::PER_COIL;
-    static_assert((R * LY::RP) % 16 == 4, "the lane pattern 4 a + e needs a plane stride of 4 mod 16 points");
-    extern __shared__ __align__(128) float2 sg[];    // [IP_CH][ROWS][RP]
-    __shared__ unsigned long long bar;
-    __shared__ int sbase[IP_THREADS];                 // first-tap offset of each staged sample
-    __shared__ float sw[IP_THREADS][D * KW];          // its tap weights
-    const int4 it = items[bx];
-    const int tile = it.x, beg = it.y, end = it.z;
-    const int c0 = by * IP_CH;
-    const int cc = min(IP_CH, geo.C - c0);
-    int o[MAXD], xo;
-    interp_stage<D>(tile, c0, cc, grid, geo, tl, sg, &bar, o, xo);
-    {
-        const int s = beg + (int)threadIdx.x;
-        if (s < end) {
-            int lb = xo;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int p0 = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]);
-                lb += (p0 - o[d]) * (d == 0 ? rs0 : (d == 1 ? rs1 : 1));
-#pragma unroll
-                for (int j = 0; j < KW; ++j) sw[threadIdx.x][d * KW + j] = wt[(int64_t)(d * KW + j) * geo.M + s];
-            }
-            sbase[threadIdx.x] = lb;
-        }
-    }
-    const float sigma = MODE == 2 ? io.sched[3 * (*io.iter)] : 0.f;
-    __syncthreads();                                  // the staged samples are visible
-    // the give-up decision is taken per warp (all lanes or none), so no lane leaves a warp whose
-    // other lanes go on to the shuffles below
-    const bool staged = __all_sync(0xffffffffu, mbar_wait_bounded(&bar, 0, io.wait));
-    if (!staged) {
-        if (io.flag) atomicExch(io.flag, 1);
-        mbar_wait_bounded(&bar, 0, KP_DRAIN_CYCLES);  // copies still in flight land in this CTA's memory
-        return;
-    }
-    const int n = end - beg;
-    const int warp = threadIdx.x >> 5, half = (threadIdx.x >> 4) & 1, lid = threadIdx.x & 15;
-    const int a = lid >> 2, e = lid & 3;
-    // warp-uniform loop (both half-warps take part in every shuffle)
-    for (int i0 = 2 * warp; i0 < n; i0 += IP_THREADS / 16) {
-        const int i = i0 + half;
-        const bool act = i < n;
-        float2 acc[IP_CH];
-#pragma unroll
-        for (int c = 0; c < IP_CH; ++c) acc[c] = make_float2(0.f, 0.f);
-        if (act) {
-            const float wae = sw[i][a] * sw[i][2 * KW + e];
-            const float2* base = sg + sbase[i] + a * rs0 + e;
-#pragma unroll
-            for (int b = 0; b < KW; ++b) {
-                const float wv = wae * sw[i][KW + b];
-#pragma unroll
-                for (int c = 0; c < IP_CH; ++c) {
-                    if (c < cc) {
-                        const float2 v = base[c * Rtot + b * rs1];
-                        acc[c].x = fmaf(wv, v.x, acc[c].x);
-                        acc[c].y = fmaf(wv, v.y, acc[c].y);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < IP_CH; ++c)
-#pragma unroll
-            for (int off = 8; off > 0; off >>= 1) {
-                acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, off);
-                acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, off);
-            }
-        if (act && lid < cc) {
-            float2 r = acc[0];
-            if (lid == 1) r = acc[1];
-            if (lid == 2) r = acc[2];
-            if (lid == 3) r = acc[3];
-            r.x *= geo.rsqrtN;
-            r.y *= geo.rsqrtN;
-            const int s = beg + i;
-            const size_t os = (size_t)(c0 + lid) * geo.M + s;
-            if (MODE == 0) {
-                const int64_t oi = io.perm ? io.perm[s] : s;
-                stc<T>((T*)io.out, (size_t)(c0 + lid) * geo.M + oi, r);
-            } else if (MODE == 1) {
-                float sc = io.ps ? io.ps[os] : 1.f;
-                if (io.n2) {
-                    const float q = (float)*io.n2;
-                    sc *= q > 0.f ? rsqrtf(q) : 0.f;
-                }
-                io.outs[os] = make_float2(r.x * sc, r.y * sc);
-            } else {
-                // PDHG dual step (Sec. 4.1): u <- (u + sigma p (A xbar - y)) / (1 + sigma p)
-                const float2 y = ldc<T>((const T*)io.ys, os);
-                const float sp = sigma * io.ps[os];
-                const float inv = 1.f / (1.f + sp);
-                const float2 uo = io.u[os];
-                io.u[os] = make_float2((uo.x + sp * (r.x - y.x)) * inv, (uo.y + sp * (r.y - y.y)) * inv);
-            }
-        }
-    }
-}
-
-template <int MODE, typename T>
-__global__ void __launch_bounds__(IP_THREADS, 3)
-k_interp_taps(const int4* __restrict__ items, const int* __restrict__ k0t, const float* __restrict__ wt,
-              const float2* __restrict__ grid, Geom geo, Tiles tl, InterpIO io) {
-    interp_taps_body<MODE, T>(items, k0t, wt, grid, geo, tl, io, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- adjoint: spread
@@ -2032,13 +1913,6 @@ kp_status fft_inverse_only(kp_plan p, cudaStream_t st) {
     return grid_fft_inverse(p, st);
 }
 
-// 3D interpolation with lanes on taps (k_interp_taps) instead of one sample per thread:
-// KPDHG_INTERP=taps.
-static bool interp_taps() {
-    const char* e = std::getenv("KPDHG_INTERP");
-    return e && std::string(e) == "taps";
-}
-
 template <int MODE>
 static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaStream_t st) {
     const Geom& g = p->geo;
@@ -2050,15 +1924,6 @@ static kp_status launch_interp(kp_plan p, kp_cdtype t, const InterpIO& io, cudaS
     p->launches += 1;
     if (p->n_iitems == 0) return KP_OK;
     if (p->chunk > IP_THREADS) { set_error("interpolation items larger than the block"); return KP_EINTERNAL; }
-    if (g.D == 3 && interp_taps()) {
-        static PerDeviceOnce attr_t[3][3];
-        KP_DISPATCH_T(t, T,
-            if (attr_t[MODE][t].first())
-                KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_taps<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            k_interp_taps<MODE, T><<<grid, IP_THREADS, smem, st>>>(p->d_iitems, p->d_k0, p->d_wt, p->d_gridF, g, p->tiles, io));
-        KP_LAUNCH_CHECK();
-        return KP_OK;
-    }
     KP_DISPATCH_D(g.D, DD, KP_DISPATCH_T(t, T,
         if (attr[DD - 2][MODE][t].first())
             KP_TRY_CUDA(cudaFuncSetAttribute(k_interp_tile<DD, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
