@@ -79,9 +79,15 @@ def kb_apod(n, G, W, beta):
 
 
 def grid_coords(traj, img_shape, gshape):
-    """t_{i,d} = f_{i,d} * (G_d / N_d) in float64 (the operator as the paper defines it)."""
+    """t_{i,d} = f_{i,d} G_d / N_d in float64 (the operator as the paper defines it), rounded
+    once: f G is exact for a float32 f and an integer G below 2^29, so the division returns
+    the float64 number nearest the exact t, and a t that is exactly an integer (a sample on a
+    grid point, where the truncated window's first-tap choice decides which edge tap is
+    taken) comes out as that integer."""
     traj = np.asarray(traj, dtype=np.float64)
-    return traj * np.array([g / n for g, n in zip(gshape, img_shape)])[None, :]
+    g = np.array(gshape, dtype=np.float64)[None, :]
+    n = np.array(img_shape, dtype=np.float64)[None, :]
+    return traj * g / n
 
 
 def first_tap(t, W):

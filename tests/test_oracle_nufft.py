@@ -102,3 +102,19 @@ def test_first_tap_is_exact_and_inside_window():
     k0 = nf.first_tap(t, 4)
     u0 = t.astype(np.float64) - k0
     assert np.all(u0 > 1.0 - 1e-12) and np.all(u0 <= 2.0)
+
+
+def test_grid_coords_are_the_rounded_exact_value():
+    """t = f G / N is the float64 number nearest the exact rational value (brute force with
+    fractions), so samples at +-N/2 of an odd N land exactly on the grid points +-G/2."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    img, grid = (307, 15, 64), (384, 20, 80)
+    f = np.stack([rng.uniform(-n / 2, n / 2, 200) for n in img], -1).astype(np.float32)
+    f[0] = [153.5, 7.5, 32.0]
+    f[1] = [-153.5, -7.5, -32.0]
+    t = nf.grid_coords(f, img, grid)
+    for i in range(f.shape[0]):
+        for d in range(3):
+            assert t[i, d] == float(Fraction(float(f[i, d])) * grid[d] / img[d])
+    assert list(t[0]) == [192.0, 10.0, 40.0] and list(t[1]) == [-192.0, -10.0, -40.0]
