@@ -4,10 +4,12 @@
 //
 // One pass per axis.  A CTA takes 16 lines of one axis (8 for axes longer than 256 points): rows
 // along x, or columns along y or z for 16 (8) consecutive x, so every global access is a 128-
-// (64-) byte row segment.  Each thread issues all its loads before storing them to shared
-// memory, where a self-sorting (Stockham) mixed-radix transform runs (radix 16, 8, 4, 2, 3
-// and 5 stages, 16 and 8 done as 4 x 4 and 4 x 2 in registers; twiddles from a table of the
-// g-th roots of unity built on the host in float64); then the lines are written back.
+// (64-) byte row segment.  The transform is a self-sorting (Stockham) mixed-radix one (radix 16,
+// 8, 4, 2, 3 and 5 stages, 16 and 8 done as 4 x 4 and 4 x 2 in registers; twiddles from a
+// table of the g-th roots of unity built on the host in float64).  Its first stage runs on the
+// values each thread loads (all of its loads issued before any is used) and its last stage
+// stores to global memory, so only the stages between them pass through shared memory, in
+// place in one buffer of the CTA's lines.
 //
 // The passes exploit the structure of the NUFFT's grids.  The image occupies n_d of the g_d
 // indices per axis (the band [0, n - n/2) and [g - n/2, g), where the pre-step puts it), and
@@ -190,46 +192,62 @@ constexpr int fac_at(int N, int i) {
     return 1;
 }
 
-// The CTA's lines, transformed in shared memory (buffers a and b, twiddles tw).  Element n of
-// line l sits at l * N + n when XL (rows along x), else n * LN + l (LN lines).  Stockham,
-// decimation in time: stage ST (radix r) combines r transforms of length L into one of length
-// L r; butterfly (j, kk) (j < m = N / (L r), kk < L) reads a[kk N / L + j + q m], q < r,
-// multiplies input q by w^(q kk m) (w = e^{-+2 pi i / N}), and writes its r-point DFT's output t
-// to b[(kk + L t) m + j].  N, the radices and every stride are compile-time constants.
-// Returns the buffer holding the result.
+// Shared-memory position of element n of line l: l * N + n when XL (rows along x), else
+// n * LN + l (LN lines side by side, as they lie in global memory).
+template <int N, bool XL>
+__device__ __forceinline__ int sidx(int l, int n) { return XL ? l * N + n : n * ff_lines(N) + l; }
+
+// a * w for the twiddle w = tw[e] = e^{-2 pi i e / N}, conjugated for the inverse (s = -1)
+__device__ __forceinline__ float2 twiddle(float2 x, float2 w, float s) {
+    w.y *= s;
+    return make_float2(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
+}
+
+// Stockham, decimation in time: stage ST (radix r) combines r transforms of length L into one
+// of length L r; butterfly (j, kk) (j < m = N / (L r), kk < L) takes elements kk N / L + j + q m,
+// q < r, multiplies input q by w^(q kk m) (w = e^{-+2 pi i / N}) and puts output t of its r-point
+// DFT at (kk + L t) m + j.  The first stage (L = 1, no twiddles) runs on the values loaded from
+// global memory and the last one (m = 1) stores to global memory, so only the stages between
+// them go through shared memory: here, in place in `a`, every thread reading all its
+// butterflies' inputs (and transforming them) before the CTA's barrier, then writing.
 template <int N, bool XL, int ST, int L>
-__device__ __forceinline__ float2* stockham(float2* a, float2* b, const float2* tw, float s, const FfConst& k) {
+__device__ __forceinline__ void stockham_mid(float2* a, const float2* tw, float s, const FfConst& k) {
     constexpr int LN = ff_lines(N);
-    if constexpr (ST == fac_count(N)) {
-        return a;
+    if constexpr (ST + 1 >= fac_count(N)) {
+        return;
     } else {
         constexpr int r = fac_at(N, ST), Lr = L * r, m = N / Lr, nb = N / r, NL = N / L;
-        for (int it = threadIdx.x; it < LN * nb; it += FF_T) {
-            const int l = XL ? it / nb : it % LN;
-            const int bf = XL ? it - l * nb : it / LN;
-            const int j = bf % m, kk = bf / m;
-            float2 v[r];
-            const int base = kk * NL + j;
+        constexpr int NB = LN * nb, BPT = (NB + FF_T - 1) / FF_T;
+        float2 v[BPT][r];
 #pragma unroll
-            for (int q = 0; q < r; ++q) {
-                const int idx = base + q * m;
-                float2 x = a[XL ? l * N + idx : idx * LN + l];
-                if (q > 0 && L > 1) {
-                    float2 w = tw[q * kk * m];
-                    w.y *= s;                                       // conjugate for the inverse
-                    x = make_float2(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
+        for (int b = 0; b < BPT; ++b) {
+            const int it = threadIdx.x + b * FF_T;
+            if (it < NB) {
+                const int l = XL ? it / nb : it % LN;
+                const int bf = XL ? it - l * nb : it / LN;
+                const int j = bf % m, kk = bf / m;
+#pragma unroll
+                for (int q = 0; q < r; ++q) {
+                    const float2 x = a[sidx<N, XL>(l, kk * NL + j + q * m)];
+                    v[b][q] = q > 0 ? twiddle(x, tw[q * kk * m], s) : x;
                 }
-                v[q] = x;
-            }
-            small_dft<r>(v, s, k);
-#pragma unroll
-            for (int t = 0; t < r; ++t) {
-                const int idx = (kk + L * t) * m + j;
-                b[XL ? l * N + idx : idx * LN + l] = v[t];
+                small_dft<r>(v[b], s, k);
             }
         }
         __syncthreads();
-        return stockham<N, XL, ST + 1, Lr>(b, a, tw, s, k);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int it = threadIdx.x + b * FF_T;
+            if (it < NB) {
+                const int l = XL ? it / nb : it % LN;
+                const int bf = XL ? it - l * nb : it / LN;
+                const int j = bf % m, kk = bf / m;
+#pragma unroll
+                for (int t = 0; t < r; ++t) a[sidx<N, XL>(l, (kk + L * t) * m + j)] = v[b][t];
+            }
+        }
+        __syncthreads();
+        stockham_mid<N, XL, ST + 1, Lr>(a, tw, s, k);
     }
 }
 
@@ -238,14 +256,15 @@ __device__ __forceinline__ float2* stockham(float2* a, float2* b, const float2* 
 template <int AXIS, bool INV, int N, bool PRE = false, typename MT = float2>
 __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out, Geom geo, FfAxis ax, FfConst k,
                                                    PreSrc pre) {
-    // (no __restrict__: the y, z and inverse passes work in place, each CTA on its own lines)
+    // (no __restrict__: the y, z and inverse passes work in place, each CTA on its own lines, all
+    // of whose loads are issued in the first stage, before the barrier that precedes any store)
     // PRE (first forward pass only): the band points are s_c x / Phi, formed from `pre`, not read
-    constexpr int LN = ff_lines(N), TOT = LN * N, PER = (TOT + FF_T - 1) / FF_T;
+    constexpr int LN = ff_lines(N), NST = fac_count(N);
+    static_assert(NST >= 2, "the first and last stages are distinct");
     constexpr bool XL = AXIS == 2;
     extern __shared__ __align__(16) float2 fsm[];
-    float2* A = fsm;
-    float2* B = fsm + TOT;
-    float2* tw = B + TOT;
+    float2* A = fsm;                                    // [LN lines][N]
+    float2* tw = A + LN * N;
     for (int i = threadIdx.x; i < N; i += FF_T) tw[i] = ax.tw[i];
     const int g0 = geo.g[0], g1 = geo.g[1], g2 = geo.g[2];
     const int n0 = geo.n[0], n1 = geo.n[1], n2 = geo.n[2];
@@ -298,57 +317,85 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
     }
     __syncthreads();
     const int nb_axis = AXIS == 0 ? n0 : (AXIS == 1 ? n1 : n2);
-    // load: every load of this thread issued before any is used (zeros for missing lines and, in
-    // the forward direction, outside the band), then stored to shared memory
-    float2 v[PER];
+    const float s = INV ? -1.f : 1.f;
+    // first stage (radix r0, L = 1) on the loaded values: every load of this thread is issued
+    // before any is used (zeros for missing lines and, in the forward direction, outside the
+    // band); butterfly j of line l takes elements j + q m0 (consecutive threads: consecutive j
+    // of a row, or consecutive lines, so each load instruction reads whole row segments)
+    {
+        constexpr int r0 = fac_at(N, 0), m0 = N / r0, NB = LN * m0, BPT = (NB + FF_T - 1) / FF_T;
+        float2 v[BPT][r0];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int i = threadIdx.x + u * FF_T;
-        v[u] = make_float2(0.f, 0.f);
-        if (i < TOT) {
-            const int l = XL ? i / N : i % LN;
-            const int n = XL ? i - l * N : i / LN;
-            const int64_t bs = base_s[l];
-            if (bs >= 0 && (!load_band || in_band(n, nb_axis, N))) {
-                if constexpr (PRE) {
-                    // the pre-step's arithmetic, in its order: x (1/Phi_z 1/Phi_y 1/Phi_x), then s_c times it
-                    const int px = pix_index(n, n2, g2);
-                    const float a = apod_s[l] * pre.apod[n0 + n1 + px];
-                    float2 xv = pre.x[img_s[l] + px];
-                    xv.x *= a;
-                    xv.y *= a;
-                    const float2 sv = pre.maps ? ldc<MT>((const MT*)pre.maps, pix_s[l] + px) : make_float2(1.f, 0.f);
-                    v[u] = cmul(sv, xv);
-                } else {
-                    v[u] = in[bs + n * stride];
+        for (int b = 0; b < BPT; ++b) {
+            const int it = threadIdx.x + b * FF_T;
+            const int l = XL ? it / m0 : it % LN;
+            const int j = XL ? it - l * m0 : it / LN;
+            const int64_t bs = it < NB ? base_s[l] : -1;
+#pragma unroll
+            for (int q = 0; q < r0; ++q) {
+                const int n = j + q * m0;
+                v[b][q] = make_float2(0.f, 0.f);
+                if (bs >= 0 && (!load_band || in_band(n, nb_axis, N))) {
+                    if constexpr (PRE) {
+                        // the pre-step's arithmetic, in its order: x (1/Phi_z 1/Phi_y 1/Phi_x), then s_c times it
+                        const int px = pix_index(n, n2, g2);
+                        const float a = apod_s[l] * pre.apod[n0 + n1 + px];
+                        float2 xv = pre.x[img_s[l] + px];
+                        xv.x *= a;
+                        xv.y *= a;
+                        const float2 sv = pre.maps ? ldc<MT>((const MT*)pre.maps, pix_s[l] + px) : make_float2(1.f, 0.f);
+                        v[b][q] = cmul(sv, xv);
+                    } else {
+                        v[b][q] = in[bs + n * stride];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int it = threadIdx.x + b * FF_T;
+            if (it < NB) {
+                const int l = XL ? it / m0 : it % LN;
+                const int j = XL ? it - l * m0 : it / LN;
+                small_dft<r0>(v[b], s, k);
+#pragma unroll
+                for (int t = 0; t < r0; ++t) A[sidx<N, XL>(l, t * m0 + j)] = v[b][t];
+            }
+        }
+    }
+    __syncthreads();
+    stockham_mid<N, XL, 1, fac_at(N, 0)>(A, tw, s, k);
+    // last stage (radix rl, m = 1): butterfly kk of line l takes elements kk rl + q and stores
+    // output t at kk + L t, straight to global memory (the inverse only inside the band)
+    {
+        constexpr int rl = fac_at(N, NST - 1), L = N / rl, NB = LN * L, BPT = (NB + FF_T - 1) / FF_T;
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int it = threadIdx.x + b * FF_T;
+            if (it < NB) {
+                const int l = XL ? it / L : it % LN;
+                const int kk = XL ? it - l * L : it / LN;
+                float2 v[rl];
+#pragma unroll
+                for (int q = 0; q < rl; ++q) {
+                    const float2 x = A[sidx<N, XL>(l, kk * rl + q)];
+                    v[q] = q > 0 ? twiddle(x, tw[q * kk], s) : x;
+                }
+                small_dft<rl>(v, s, k);
+                const int64_t bs = base_s[l];
+                if (bs >= 0) {
+#pragma unroll
+                    for (int t = 0; t < rl; ++t) {
+                        const int n = kk + L * t;
+                        if (!store_band || in_band(n, nb_axis, N)) out[bs + n * stride] = v[t];
+                    }
                 }
             }
         }
     }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int i = threadIdx.x + u * FF_T;
-        if (i < TOT) {
-            const int l = XL ? i / N : i % LN;
-            const int n = XL ? i - l * N : i / LN;
-            A[XL ? l * N + n : n * LN + l] = v[u];
-        }
-    }
-    __syncthreads();
-    const float2* R = stockham<N, XL, 0, 1>(A, B, tw, INV ? -1.f : 1.f, k);
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int i = threadIdx.x + u * FF_T;
-        if (i < TOT) {
-            const int l = XL ? i / N : i % LN;
-            const int n = XL ? i - l * N : i / LN;
-            const int64_t bs = base_s[l];
-            if (bs >= 0 && (!store_band || in_band(n, nb_axis, N))) out[bs + n * stride] = R[XL ? l * N + n : n * LN + l];
-        }
-    }
 }
 
-static size_t pass_smem(int N) { return ((size_t)2 * (N <= 256 ? 16 : 8) * N + N) * sizeof(float2); }
+static size_t pass_smem(int N) { return ((size_t)(N <= 256 ? 16 : 8) * N + N) * sizeof(float2); }
 
 // Radices of N (16, 8, 4, 2, then 3, 5); false if N has another prime factor or too many stages.
 static bool factor(int N, FfAxis& ax) {

@@ -206,9 +206,13 @@ def test_forward_adjoint_grid_sizes(shape):
 # 3D grids whose sizes factor into 2, 3 and 5 use the library's own FFT passes (pruned to the
 # image band); others fall back to cuFFT.  (15, 16, 24) -> grid (20, 20, 30): an odd image edge
 # and radix-5 and radix-3 stages; (20, 21, 32) -> grid (26, 28, 40): 26 = 2 x 13 is not
-# handled, so that plan runs cuFFT.
+# handled, so that plan runs cuFFT.  The other shapes give every compiled pass length: (48, 64,
+# 80) -> 60, 80, 100; (96, 128, 160) -> 120, 160, 200; (192, 256, 307) -> 240, 320, 384 (the
+# 192^3 workload's grid edge and its preconditioner's); (320, 16, 384) -> 400, 20, 480.
 @pytest.mark.parametrize("shape,C,M,seed", [((15, 16, 24), 3, 2500, 41), ((32, 32, 32), 2, 4000, 42),
-                                            ((20, 21, 32), 2, 1500, 43)])
+                                            ((20, 21, 32), 2, 1500, 43), ((48, 64, 80), 2, 3000, 44),
+                                            ((96, 128, 160), 2, 3000, 45), ((192, 256, 307), 1, 2000, 46),
+                                            ((320, 16, 384), 2, 2000, 47)])
 def test_own_fft_passes_match_oracle_and_cufft(shape, C, M, seed, monkeypatch):
     need_gpu()
     x, maps, traj = random_problem(shape, C, M, seed, edge=True)
