@@ -5,8 +5,9 @@
 // One pass per axis.  A CTA takes 16 lines of one axis (8 for axes longer than 256 points): rows
 // along x, or columns along y or z for 16 (8) consecutive x, so every global access is a 128-
 // (64-) byte row segment.  The transform is a self-sorting (Stockham) mixed-radix one (radix 16,
-// 8, 4, 2, 3 and 5 stages, 16 and 8 done as 4 x 4 and 4 x 2 in registers; twiddles from a
-// table of the g-th roots of unity built on the host in float64).  Its first stage runs on the
+// 8, 4, 2, 3 and 5 stages, and 10 and 15 where the odd part of the length fits one stage;
+// 16, 8, 10 and 15 done as 4 x 4, 4 x 2, 2 x 5 and 3 x 5 in registers; twiddles from a table of
+// the g-th roots of unity built on the host in float64).  Its first stage runs on the
 // values each thread loads (all of its loads issued before any is used) and its last stage
 // stores to global memory, so only the stages between them pass through shared memory, in
 // place in one buffer of the CTA's lines.
@@ -96,6 +97,7 @@ __device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d,
 // k = k1 + 4 k2, X[k] = sum_q2 w_R^(q2 k1) w^(q2 k2) [sum_q1 v[.] w_4^(q1 k1)].
 template <int R>
 __device__ __forceinline__ void small_dft(float2* v, float s, const FfConst& k) {
+    static_assert(R == 2 || R == 3 || R == 4 || R == 5 || R == 8 || R == 16, "basic radix");
     if (R == 16) {
         float2 y[4][4];
 #pragma unroll
@@ -174,22 +176,82 @@ __device__ __forceinline__ void small_dft(float2* v, float s, const FfConst& k) 
     }
 }
 
-// Radices of N in the order applied (16s, 8s, 4s, 2s, then 3, 5), at compile time.
-constexpr int fac_count(int N) {
+// Radices of N in the order applied, at compile time (-1: N is not handled).  The
+// power-of-two part goes greedily in 16s, 8s, 4s and 2s, then the odd part in 3s and 5s.  Where
+// the last stage would still give every thread of the CTA a butterfly, the odd part runs as one
+// radix instead (15 or 25, or 3 or 5 joined to the last power-of-two radix), which saves a
+// round trip through shared memory: 240 = 16 x 15, 160 = 16 x 10, 480 = 16 x 2 x 15.  (Merges
+// that leave threads idle in the last stage measured slower: 200 = 8 x 25 against 8 x 5 x 5,
+// and the 320, 384 and 400 passes likewise.)  Radices 10, 15, 20, 24 and 25 are DFTs of two
+// factors in registers (cdft).
+constexpr int rad_list(int N, int* out) {
+    int p = 1, o = N;
+    while (o % 2 == 0) { o /= 2; p *= 2; }
     int c = 0;
-    for (int f : {16, 8, 4, 2, 3, 5})
-        while (N % f == 0) { N /= f; ++c; }
-    return N == 1 ? c : -1;
+    for (int f : {16, 8, 4, 2})
+        while (p % f == 0) { p /= f; out[c++] = f; }
+    int last = 0;                                   // the merged plan's last radix, 0: none
+    if (o == 15 || o == 25) last = o;
+    else if ((o == 3 || o == 5) && c >= 2) last = out[c - 1] * o;
+    if (last && ff_lines(N) * (N / last) >= FF_T) {
+        if (last == o) out[c++] = o;
+        else out[c - 1] = last;
+        return c;
+    }
+    for (int f : {3, 5})
+        while (o % f == 0) { o /= f; out[c++] = f; }
+    return o == 1 ? c : -1;
 }
-constexpr int fac_at(int N, int i) {
-    int c = 0;
-    for (int f : {16, 8, 4, 2, 3, 5})
-        while (N % f == 0) {
-            if (c == i) return f;
-            N /= f;
-            ++c;
+constexpr int rad_count(int N) {
+    int r[16] = {};
+    return rad_list(N, r);
+}
+constexpr int rad_at(int N, int i) {
+    int r[16] = {};
+    const int c = rad_list(N, r);
+    return i < c ? r[i] : 1;
+}
+
+// Factors (P, Q) of a radix done as a two-factor DFT; P = 0 for the basic radices.
+constexpr int split_p(int R) { return R == 10 ? 2 : R == 15 ? 3 : R == 20 ? 4 : R == 24 ? 8 : R == 25 ? 5 : 0; }
+
+// R-point DFT of v in place for a radix of length-N passes.  A radix R = P Q of split_p runs as
+// Cooley-Tukey in registers: with q = Q q1 + q2 and k = k1 + P k2, X[k] = sum_q2 w_R^(q2 k1)
+// w_Q^(q2 k2) [sum_q1 v[q] w_P^(q1 k1)]; the w_R twiddles are the table's w_N^(q2 k1 N / R).
+template <int R, int N>
+__device__ __forceinline__ void cdft(float2* v, float s, const FfConst& k, const float2* tw) {
+    constexpr int P = split_p(R);
+    if constexpr (P == 0) {
+        small_dft<R>(v, s, k);
+    } else {
+        constexpr int Q = R / P;
+        static_assert(P * Q == R && N % R == 0, "radix splits and divides the length");
+        float2 y[Q][P];
+#pragma unroll
+        for (int q2 = 0; q2 < Q; ++q2) {
+#pragma unroll
+            for (int q1 = 0; q1 < P; ++q1) y[q2][q1] = v[Q * q1 + q2];
+            small_dft<P>(y[q2], s, k);
         }
-    return 1;
+#pragma unroll
+        for (int q2 = 1; q2 < Q; ++q2)
+#pragma unroll
+            for (int k1 = 1; k1 < P; ++k1) {
+                float2 w = tw[q2 * k1 * (N / R)];
+                w.y *= s;
+                const float2 a = y[q2][k1];
+                y[q2][k1] = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+            }
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            float2 b[Q];
+#pragma unroll
+            for (int q2 = 0; q2 < Q; ++q2) b[q2] = y[q2][k1];
+            small_dft<Q>(b, s, k);
+#pragma unroll
+            for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = b[k2];
+        }
+    }
 }
 
 // Shared-memory position of element n of line l: l * N + n when XL (rows along x), else
@@ -213,10 +275,10 @@ __device__ __forceinline__ float2 twiddle(float2 x, float2 w, float s) {
 template <int N, bool XL, int ST, int L>
 __device__ __forceinline__ void stockham_mid(float2* a, const float2* tw, float s, const FfConst& k) {
     constexpr int LN = ff_lines(N);
-    if constexpr (ST + 1 >= fac_count(N)) {
+    if constexpr (ST + 1 >= rad_count(N)) {
         return;
     } else {
-        constexpr int r = fac_at(N, ST), Lr = L * r, m = N / Lr, nb = N / r, NL = N / L;
+        constexpr int r = rad_at(N, ST), Lr = L * r, m = N / Lr, nb = N / r, NL = N / L;
         constexpr int NB = LN * nb, BPT = (NB + FF_T - 1) / FF_T;
         float2 v[BPT][r];
 #pragma unroll
@@ -231,7 +293,7 @@ __device__ __forceinline__ void stockham_mid(float2* a, const float2* tw, float 
                     const float2 x = a[sidx<N, XL>(l, kk * NL + j + q * m)];
                     v[b][q] = q > 0 ? twiddle(x, tw[q * kk * m], s) : x;
                 }
-                small_dft<r>(v[b], s, k);
+                cdft<r, N>(v[b], s, k, tw);
             }
         }
         __syncthreads();
@@ -259,7 +321,7 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
     // (no __restrict__: the y, z and inverse passes work in place, each CTA on its own lines, all
     // of whose loads are issued in the first stage, before the barrier that precedes any store)
     // PRE (first forward pass only): the band points are s_c x / Phi, formed from `pre`, not read
-    constexpr int LN = ff_lines(N), NST = fac_count(N);
+    constexpr int LN = ff_lines(N), NST = rad_count(N);
     static_assert(NST >= 2, "the first and last stages are distinct");
     constexpr bool XL = AXIS == 2;
     extern __shared__ __align__(16) float2 fsm[];
@@ -323,7 +385,7 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
     // band); butterfly j of line l takes elements j + q m0 (consecutive threads: consecutive j
     // of a row, or consecutive lines, so each load instruction reads whole row segments)
     {
-        constexpr int r0 = fac_at(N, 0), m0 = N / r0, NB = LN * m0, BPT = (NB + FF_T - 1) / FF_T;
+        constexpr int r0 = rad_at(N, 0), m0 = N / r0, NB = LN * m0, BPT = (NB + FF_T - 1) / FF_T;
         float2 v[BPT][r0];
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
@@ -357,18 +419,18 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
             if (it < NB) {
                 const int l = XL ? it / m0 : it % LN;
                 const int j = XL ? it - l * m0 : it / LN;
-                small_dft<r0>(v[b], s, k);
+                cdft<r0, N>(v[b], s, k, tw);
 #pragma unroll
                 for (int t = 0; t < r0; ++t) A[sidx<N, XL>(l, t * m0 + j)] = v[b][t];
             }
         }
     }
     __syncthreads();
-    stockham_mid<N, XL, 1, fac_at(N, 0)>(A, tw, s, k);
+    stockham_mid<N, XL, 1, rad_at(N, 0)>(A, tw, s, k);
     // last stage (radix rl, m = 1): butterfly kk of line l takes elements kk rl + q and stores
     // output t at kk + L t, straight to global memory (the inverse only inside the band)
     {
-        constexpr int rl = fac_at(N, NST - 1), L = N / rl, NB = LN * L, BPT = (NB + FF_T - 1) / FF_T;
+        constexpr int rl = rad_at(N, NST - 1), L = N / rl, NB = LN * L, BPT = (NB + FF_T - 1) / FF_T;
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
             const int it = threadIdx.x + b * FF_T;
@@ -381,7 +443,7 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
                     const float2 x = A[sidx<N, XL>(l, kk * rl + q)];
                     v[q] = q > 0 ? twiddle(x, tw[q * kk], s) : x;
                 }
-                small_dft<rl>(v, s, k);
+                cdft<rl, N>(v, s, k, tw);
                 const int64_t bs = base_s[l];
                 if (bs >= 0) {
 #pragma unroll
@@ -397,18 +459,14 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
 
 static size_t pass_smem(int N) { return ((size_t)(N <= 256 ? 16 : 8) * N + N) * sizeof(float2); }
 
-// Radices of N (16, 8, 4, 2, then 3, 5); false if N has another prime factor or too many stages.
+// Radices of N as the passes apply them (rad_list); false if N is not handled.
 static bool factor(int N, FfAxis& ax) {
-    ax.nst = 0;
-    int r = N;
-    for (int f : {16, 8, 4, 2, 3, 5}) {
-        while (r % f == 0) {
-            if (ax.nst == FF_MAXST) return false;
-            ax.r[ax.nst++] = f;
-            r /= f;
-        }
-    }
-    return r == 1;
+    int r[16] = {};
+    const int c = rad_list(N, r);
+    if (c < 2 || c > FF_MAXST) return false;
+    ax.nst = c;
+    for (int i = 0; i < c; ++i) ax.r[i] = r[i];
+    return true;
 }
 
 static bool size_compiled(int N);
