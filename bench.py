@@ -39,7 +39,7 @@ import synth  # noqa: E402
 WORKLOAD = "ute3d_192"
 # (maps storage, measurement storage) of each timed workload: the 3D workload keeps its coil
 # maps in FP16 (FP32 arithmetic); the others are plain complex64
-STORAGE = {"ute3d_192": ("fp16", "c64"), "ute3d_160": ("fp16", "c64")}
+STORAGE = {"ute3d_192": ("fp16", "c64"), "ute3d_160": ("fp16", "c64"), "ute3d_192_c2": ("fp16", "c64")}
 
 
 def storage_of(w):

@@ -310,6 +310,16 @@ kp_status kp_plan_sync(kp_plan plan, void* stream);
  * inside replayed CUDA graphs included; cuFFT's kernels not included). */
 kp_status kp_plan_launch_count(kp_plan plan, int64_t* count);
 
+/* Out-of-range accesses recorded by the bounds-checked build of this library
+ * (libkpdhg_checked.so, compiled with -DKP_CHECKED as a stand-in for a memory checker: the
+ * hot kernels test each computed global-memory index against its buffer's extent, skip an
+ * access out of range and record it).  Synchronises the device, then returns and clears the
+ * records: *checked = 1 for the checked build, 0 for the release build (whose records are
+ * always empty); *count = accesses skipped since the last call; *first_site and *first_index
+ * = the first one's check site (numbered in the library's internal header) and index, 0 when
+ * none.  Any pointer may be NULL.  Errors: KP_ECUDA if the device reports an error. */
+kp_status kp_bounds_report(int* checked, uint32_t* count, uint32_t* first_site, int64_t* first_index);
+
 /* x = A^H y like kp_sense_adjoint, but with no plan and no device allocation: for callers
  * that reserve all device memory up front and may not let a library allocate afterwards
  * (for example a real-time reconstruction service with a fixed memory pool).  The paper has

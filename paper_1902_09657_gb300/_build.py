@@ -1,7 +1,8 @@
 """In-tree build of libkpdhg.so for sm_103a (nvcc, one -gencode, TUs compiled in parallel).
 
 Usage: ``python -m paper_1902_09657_gb300._build`` or ``build()`` from Python.  The shared
-library lands next to this file; object files go to ``_build/`` (both git-ignored).
+library lands next to this file; object files go to ``_build/`` (``_build_checked/`` for the
+bounds-checked variant, ``--checked``; all git-ignored).
 """
 from __future__ import annotations
 
@@ -16,6 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkpdhg.so")
+# the bounds-checked variant (-DKP_CHECKED): every hot kernel tests its computed global-memory
+# indices and records an access out of range instead of making it (kp_bounds_report)
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libkpdhg_checked.so")
 SOURCES = ["kp_plan.cu", "kp_nufft.cu", "kp_pdhg.cu", "kp_precond.cu", "kp_wavelet.cu", "kp_unrolled.cu", "kp_noalloc.cu", "kp_batch.cu", "kp_compare.cu", "kp_fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -44,23 +49,26 @@ def _deps():
     return deps
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False):
-    """Compile every CUDA translation unit for sm_103a and link libkpdhg.so."""
-    if not force and up_to_date():
-        return LIB
+def build(force=False, verbose=False, checked=False):
+    """Compile every CUDA translation unit for sm_103a and link libkpdhg.so (or, checked=True,
+    the bounds-checked libkpdhg_checked.so)."""
+    lib, bdir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
+    extra = ["-DKP_CHECKED"] if checked else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -71,15 +79,15 @@ def build(force=False, verbose=False):
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     libdir = _cuda_lib_dir(nvcc)
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, f"-L{libdir}", "-lcufft",
+    tmp = lib + ".tmp"
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, f"-L{libdir}", "-lcufft", "-ldl",
            "-Xlinker", f"-rpath={libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

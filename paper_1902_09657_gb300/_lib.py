@@ -5,7 +5,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libkpdhg.so")
+# KPDHG_CHECKED=1 loads the bounds-checked build (libkpdhg_checked.so, `_build --checked`)
+LIB_PATH = os.path.join(HERE, "libkpdhg_checked.so" if os.environ.get("KPDHG_CHECKED") == "1" else "libkpdhg.so")
 
 KP_OK, KP_EINVAL, KP_ENOMEM, KP_ECUDA, KP_ECUFFT, KP_EDIVERGED, KP_ENONFINITE, KP_ETIMEOUT, KP_EINTERNAL = range(9)
 KP_C64, KP_C32_BF16, KP_C32_FP16 = 0, 1, 2
@@ -81,6 +82,8 @@ _SIGS = {
     "kp_wavelet": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "kp_plan_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "kp_plan_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "kp_bounds_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64)]),
     "kp_sense_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(KpParams), _vp, _vp, _vp, _vp, _vp]),
     "kp_sense_forward_traj_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "kp_sense_adjoint_traj_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -114,8 +117,9 @@ def load():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"libkpdhg.so is not built ({LIB_PATH} missing); run "
-                           "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        raise RuntimeError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH} missing); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` first (the checked "
+                           "variant: `python -m paper_1902_09657_gb300._build --checked`)")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in _SIGS.items():
         f = getattr(lib, name)

@@ -417,3 +417,14 @@ class Batch:
             int(iters), VP(*[x.data_ptr() for x in xs]), _stream(self.device))
         L.check(st, "kp_batch_solve")
         return xs
+
+
+def bounds_report():
+    """Out-of-range accesses the bounds-checked build recorded since the last call
+    (kp_bounds_report): dict(checked, count, first_site, first_index); checked is False and
+    count 0 for the release build."""
+    lib = L.load()
+    ck, n, site, idx = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+    L.check(lib.kp_bounds_report(ctypes.byref(ck), ctypes.byref(n), ctypes.byref(site), ctypes.byref(idx)),
+            "kp_bounds_report")
+    return dict(checked=bool(ck.value), count=int(n.value), first_site=int(site.value), first_index=int(idx.value))

@@ -149,6 +149,7 @@ using namespace kp;
 extern "C" {
 
 kp_status kp_batch_create(kp_batch* out, kp_plan* plans, int ncases) {
+    KP_RANGE("kp_batch_create");
     if (!out || !plans || ncases < 1) { set_error("null argument or ncases < 1"); return KP_EINVAL; }
     *out = nullptr;
     kp_batch b = new (std::nothrow) kp_batch_s();
@@ -202,6 +203,7 @@ kp_status kp_batch_destroy(kp_batch b) {
 
 kp_status kp_batch_solve(kp_batch b, const void* const* y_devs, const kp_cdtype* y_types, const float* const* p_devs,
                          const kp_reg* regs, const float* lambdas, int iters, void* const* x_devs, void* stream) {
+    KP_RANGE("kp_batch_solve");
     if (!b || !y_devs || !y_types || !regs || !lambdas || !x_devs) { set_error("null argument"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;

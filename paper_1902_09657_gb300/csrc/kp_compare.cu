@@ -381,6 +381,7 @@ using namespace kp;
 extern "C" {
 
 kp_status kp_make_circulant_preconditioner(kp_plan plan, float* eig_dev, void* stream) {
+    KP_RANGE("kp_make_circulant_preconditioner");
     if (!plan) { set_error("null plan"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
     KP_TRY(circulant_enqueue(plan, st));
@@ -392,6 +393,7 @@ kp_status kp_make_circulant_preconditioner(kp_plan plan, float* eig_dev, void* s
 
 kp_status kp_cg_l2_solve(kp_plan plan, const void* y_dev, float lambda, int iters, int circulant, void* x_dev,
                          double* obj_trace, void* stream) {
+    KP_RANGE("kp_cg_l2_solve");
     if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
@@ -402,6 +404,7 @@ kp_status kp_cg_l2_solve(kp_plan plan, const void* y_dev, float lambda, int iter
 
 kp_status kp_fista_solve(kp_plan plan, const void* y_dev, kp_reg reg, float lambda, int iters, double lmax, void* x_dev,
                          double* obj_trace, void* stream) {
+    KP_RANGE("kp_fista_solve");
     if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }

@@ -401,13 +401,16 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
                     if constexpr (PRE) {
                         // the pre-step's arithmetic, in its order: x (1/Phi_z 1/Phi_y 1/Phi_x), then s_c times it
                         const int px = pix_index(n, n2, g2);
-                        const float a = apod_s[l] * pre.apod[n0 + n1 + px];
-                        float2 xv = pre.x[img_s[l] + px];
-                        xv.x *= a;
-                        xv.y *= a;
-                        const float2 sv = pre.maps ? ldc<MT>((const MT*)pre.maps, pix_s[l] + px) : make_float2(1.f, 0.f);
-                        v[b][q] = cmul(sv, xv);
-                    } else {
+                        if (KP_INB(3, px, n2) && KP_INB(3, img_s[l] + px, geo.N) &&
+                            (!pre.maps || KP_INB(3, pix_s[l] + px, (int64_t)geo.C * geo.N))) {
+                            const float a = apod_s[l] * pre.apod[n0 + n1 + px];
+                            float2 xv = pre.x[img_s[l] + px];
+                            xv.x *= a;
+                            xv.y *= a;
+                            const float2 sv = pre.maps ? ldc<MT>((const MT*)pre.maps, pix_s[l] + px) : make_float2(1.f, 0.f);
+                            v[b][q] = cmul(sv, xv);
+                        }
+                    } else if (KP_INB(1, bs + n * stride, (int64_t)geo.C * geo.G)) {
                         v[b][q] = in[bs + n * stride];
                     }
                 }
@@ -449,7 +452,8 @@ __global__ void __launch_bounds__(FF_T) k_fft_pass(const float2* in, float2* out
 #pragma unroll
                     for (int t = 0; t < rl; ++t) {
                         const int n = kk + L * t;
-                        if (!store_band || in_band(n, nb_axis, N)) out[bs + n * stride] = v[t];
+                        if ((!store_band || in_band(n, nb_axis, N)) && KP_INB(2, bs + n * stride, (int64_t)geo.C * geo.G))
+                            out[bs + n * stride] = v[t];
                     }
                 }
             }

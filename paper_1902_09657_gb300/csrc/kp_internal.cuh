@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -16,6 +17,66 @@
 #include "../../include/kpdhg.h"
 
 namespace kp {
+
+// A named NVTX range over a scope.  NVTX v3 is header-only and inert unless a tool (ncu,
+// Nsight Systems) attaches its injection library; every entry point of the C ABI opens one
+// named after itself, so a profile can select one entry point's kernels, e.g.
+// ncu --nvtx --nvtx-include "kp_max_eig/" for the power method's.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+#define KP_RANGE(name) ::kp::NvtxScope kp_nvtx_scope_(name)
+// A phase of the reconstruction (preconditioner, power method, PDHG iterations) as an NVTX
+// start/end range, which a filter selects regardless of the entry point it runs under
+// (ncu --nvtx --nvtx-include "power_method": start/end ranges take no trailing slash).
+struct NvtxPhase {
+    nvtxRangeId_t id;
+    explicit NvtxPhase(const char* name) : id(nvtxRangeStartA(name)) {}
+    ~NvtxPhase() { nvtxRangeEnd(id); }
+    NvtxPhase(const NvtxPhase&) = delete;
+    NvtxPhase& operator=(const NvtxPhase&) = delete;
+};
+#define KP_PHASE(name) ::kp::NvtxPhase kp_nvtx_phase_(name)
+
+// Bounds-checked build (-DKP_CHECKED, the library libkpdhg_checked.so): the hot kernels test
+// each computed global-memory index against its buffer's extent before the access, skip an
+// access out of range and record it: a count and the first one's site and index, in device
+// words of each translation unit, which kp_bounds_report gathers and clears.  In the release
+// build KP_INB is the constant true and the checks compile away.  Sites:
+//   1 FFT pass load      2 FFT pass store        3 FFT pre-step image / maps / 1/Phi
+//   4 interp staged row  5 interp sample I/O     6 spread own: sample values
+//   7 spread own: slot   8 gather: slot read     9 gather: grid store
+//  10 spread (one-phase) grid update            11 forward pre-step: image / maps / grid
+//  12 adjoint combine: grid / maps / image       13 fused primal step: grid / maps / image
+//  14 preconditioner: pair spectra / R          15 preconditioner: den / p
+#ifdef KP_CHECKED
+static __device__ unsigned int kp_oob_count;              // this translation unit's records
+static __device__ unsigned long long kp_oob_first;        // site << 48 | (index mod 2^48)
+__device__ __forceinline__ bool kp_in_bounds(int site, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    if (atomicAdd(&kp_oob_count, 1u) == 0)
+        atomicExch(&kp_oob_first, ((unsigned long long)site << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull));
+    return false;
+}
+#define KP_INB(site, i, n) ::kp::kp_in_bounds((site), (long long)(i), (long long)(n))
+// Reads and clears this translation unit's records (after a device synchronisation).
+static cudaError_t kp_oob_take(unsigned int* count, unsigned long long* first) {
+    const unsigned int z = 0;
+    const unsigned long long zz = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(count, kp_oob_count, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(first, kp_oob_first, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(kp_oob_count, &z, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(kp_oob_first, &zz, sizeof(unsigned long long));
+    return e;
+}
+bool oob_register(cudaError_t (*take)(unsigned int*, unsigned long long*));
+static const bool kp_oob_registered = oob_register(&kp_oob_take);
+#else
+#define KP_INB(site, i, n) true
+#endif
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
@@ -202,6 +263,7 @@ __device__ __forceinline__ float2 adj_pixel(const float2* __restrict__ grid, con
         a *= apod[ao + jj[d]];
         ao += geo.n[d];
     }
+    if (!(KP_INB(12, j, geo.N) && KP_INB(12, gi, geo.G))) return make_float2(0.f, 0.f);
     // coils four at a time: every load of a group is issued before its products are summed
     // (the sum still runs over c = 0, 1, 2, ... in order)
     float2 acc = make_float2(0.f, 0.f);
@@ -260,6 +322,7 @@ __device__ __forceinline__ void pre_pixel(float2* __restrict__ grid, const MT* _
         a *= apod[ao + jj[d]];
         ao += geo.n[d];
     }
+    if (!(KP_INB(13, j, geo.N) && KP_INB(13, gi, geo.G))) return;
     v.x *= a;
     v.y *= a;
     for (int c = 0; c < geo.C; ++c) {

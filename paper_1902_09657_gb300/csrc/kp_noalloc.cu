@@ -183,6 +183,7 @@ using namespace kp;
 
 extern "C" kp_status kp_sense_adjoint_noalloc(const kp_params* params, const float* traj_dev, const void* maps_dev,
                                               const void* y_dev, void* x_dev, void* stream) {
+    KP_RANGE("kp_sense_adjoint_noalloc");
     using namespace kp::noalloc;
     if (!params || !traj_dev || !maps_dev || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
     const int D = params->ndim;

@@ -159,6 +159,7 @@ __device__ __forceinline__ void fwd_pre_body(const float2* __restrict__ x, const
         for (int c = 0; c < geo.C; ++c) grid[(size_t)c * geo.G + gi] = make_float2(0.f, 0.f);
         return;
     }
+    if (!KP_INB(11, j, geo.N)) return;
     float2 xv = x[j];
     xv.x *= a;
     xv.y *= a;
@@ -346,7 +347,11 @@ __device__ __forceinline__ void interp_stage(int tile, int c0, int cc, const flo
         // are even in length because the grid extent and the start are even)
         for (int pos = 0, x = xlo; pos < LY::RP; x = 0) {
             const int n = min(LY::RP - pos, gx - x);
-            bulk_g2s(dst + pos, src + x, (unsigned)(n * sizeof(float2)), bar);
+            const int64_t o0 = (int64_t)(c0 + c) * geo.G + off + x;
+            // (checked build: a piece out of range copies the grid's first points instead, so the
+            // barrier still receives the bytes it expects)
+            const bool ok = KP_INB(4, o0, (int64_t)geo.C * geo.G) && KP_INB(4, o0 + n - 1, (int64_t)geo.C * geo.G);
+            bulk_g2s(dst + pos, ok ? src + x : grid, (unsigned)(n * sizeof(float2)), bar);
             pos += n;
         }
     }
@@ -371,7 +376,7 @@ __device__ __forceinline__ void interp_tile_body(const int4* __restrict__ items,
     // While the grid region is in flight: this thread's sample (items hold at most blockDim.x
     // samples), its tap tables and, for the dual step in 2D, its y, p and u.
     const int s = beg + (int)threadIdx.x;
-    const bool act = s < end;
+    bool act = s < end && KP_INB(5, s, geo.M);
     float w[D][KW];
     int lb = xo;
     constexpr bool PRE = MODE == 2 && D == 2;     // 3D keeps registers for the 64 taps
@@ -386,6 +391,8 @@ __device__ __forceinline__ void interp_tile_body(const int4* __restrict__ items,
 #pragma unroll
             for (int j = 0; j < KW; ++j) w[d][j] = wt[(int64_t)(d * KW + j) * geo.M + s];
         }
+        // the footprint lies in the staged region (the sample's first tap is in this tile)
+        act = KP_INB(4, lb, Rtot) && KP_INB(4, lb + (KW - 1) * (rs0 + (D == 3 ? rs1 : 0) + 1), Rtot);
         if (MODE == 2) sigma = io.sched[3 * (*io.iter)];
         if (PRE) {
 #pragma unroll
@@ -439,7 +446,7 @@ __device__ __forceinline__ void interp_tile_body(const int4* __restrict__ items,
         const size_t os = (size_t)(c0 + c) * geo.M + s;
         if (MODE == 0) {
             const int64_t oi = io.perm ? io.perm[s] : s;
-            stc<T>((T*)io.out, (size_t)(c0 + c) * geo.M + oi, acc);
+            if (KP_INB(5, oi, geo.M)) stc<T>((T*)io.out, (size_t)(c0 + c) * geo.M + oi, acc);
         } else if (MODE == 1) {
             float sc = io.ps ? io.ps[os] : 1.f;
             if (io.n2) {   // float reciprocal square root: fp64 division here costs more than the taps
@@ -731,11 +738,14 @@ __device__ __forceinline__ void spread_v_body(const int* __restrict__ k0t, const
         const int n = min(SP_CHUNK, end - sb);
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int s = ext[sb + i];
+            int s = ext[sb + i];
+            bool ok = KP_INB(10, s, geo.M);
+            if (!ok) s = 0;                                   // (checked build: adds zeros)
             const int64_t un = perm ? perm[s] : s;
+            ok = ok && KP_INB(10, un, geo.M);
             float2 uc[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) uc[c] = c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
+            for (int c = 0; c < 4; ++c) uc[c] = ok && c < cc ? ldc<UT>(u, (size_t)(c0 + c) * geo.M + un) : make_float2(0.f, 0.f);
             su4[i * 2] = make_float4(uc[0].x, uc[0].y, uc[1].x, uc[1].y);
             su4[i * 2 + 1] = make_float4(uc[2].x, uc[2].y, uc[3].x, uc[3].y);
 #pragma unroll
@@ -827,7 +837,7 @@ __device__ __forceinline__ void spread_v_body(const int* __restrict__ k0t, const
             if (lidx[d] >= e[d]) in = false;
             gflat = gflat * geo.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], geo.g[d]);
         }
-        if (!in) continue;
+        if (!in || !KP_INB(10, (int64_t)(c0 + 2 * k + (2 * k + 1 < cc)) * geo.G + gflat, (int64_t)geo.C * geo.G)) continue;
         const int li = D == 2 ? LV::idx(lidx[0], lidx[D - 1], 0, k) : LV::idx(lidx[0], lidx[1 % D], lidx[D - 1], k);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -1088,15 +1098,19 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
             }
             const int s = s0 + i;
             const int64_t un = perm ? perm[s] : s;
+            int l[D];
+            bool ok = KP_INB(6, un, geo.M);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                l[d] = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];   // in [0, ts)
+                if (!KP_INB(7, l[d], tl.ts[d])) { ok = false; l[d] = 0; }   // (checked build: adds zeros)
+            }
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                const float2 ua = 2 * k < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k) * geo.M + un) : make_float2(0.f, 0.f);
-                const float2 ub = 2 * k + 1 < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k + 1) * geo.M + un) : make_float2(0.f, 0.f);
+                const float2 ua = ok && 2 * k < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k) * geo.M + un) : make_float2(0.f, 0.f);
+                const float2 ub = ok && 2 * k + 1 < cc ? ldc<UT>(u, (size_t)(c0 + 2 * k + 1) * geo.M + un) : make_float2(0.f, 0.f);
                 su[i * NP + k] = make_float4(ua.x, ua.y, ub.x, ub.y);
             }
-            int l[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) l[d] = tshift(k0t[(int64_t)d * geo.M + s], tl.sh[d], geo.g[d]) - o[d];   // in [0, ts)
             float wz[KW], wy[KW], wx[KW];
 #pragma unroll
             for (int j = 0; j < KW; ++j) {
@@ -1158,6 +1172,7 @@ k_spread_own(const int* __restrict__ k0t, const float* __restrict__ wt, const UT
     // (the accumulator rows have the slot's row length, so the copy is row for row)
     static_assert(OT_RS == SL_RS, "accumulator and slot rows have the same length");
     const int npair = (cc + 1) / 2;
+    if (!KP_INB(7, slot, gridDim.x)) return;                       // one slot per item
     for (int i = threadIdx.x; i < npair * SL_P; i += NT) {
         const int k = i / SL_P, pt = i - k * SL_P;
         if (pt % SL_RS >= PT) continue;                             // the row's padding point
@@ -1202,6 +1217,9 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
         const int nb = (n0 * nt1 + n1) * nt2 + n2;
         nb_beg[m] = tslot[nb];
         nb_end[m] = tslot[nb + 1];
+        // (checked build: a slot range beyond the slots the own phase wrote is skipped)
+        if (nb_end[m] > nb_beg[m] && !(KP_INB(8, nb_beg[m], tslot[tl.ntiles]) && KP_INB(8, nb_end[m] - 1, tslot[tl.ntiles])))
+            nb_end[m] = nb_beg[m];
         nb_off[m] = (b0 ? min(ts0, geo.g[0] - n0 * ts0) * SL_PS : 0) + (b1 ? min(ts1, geo.g[1] - n1 * ts1) * SL_RS : 0) +
                     (b2 ? min(ts2, geo.g[2] - n2 * ts2) : 0);
     } else if (threadIdx.x < 8 + 64) {
@@ -1266,7 +1284,8 @@ k_halo_gather(const float2* __restrict__ halo, const int* __restrict__ tslot, Ge
             const int c = q >> 9, p = q & 511;
             const int64_t ro = rowoff[p >> 3];
             const int gx = colg[p & 7];
-            if (ro >= 0 && gx >= 0) grid[(int64_t)(c0 + c) * geo.G + ro + gx] = acc[q];
+            if (ro >= 0 && gx >= 0 && KP_INB(9, (int64_t)(c0 + c) * geo.G + ro + gx, (int64_t)geo.C * geo.G))
+                grid[(int64_t)(c0 + c) * geo.G + ro + gx] = acc[q];
         }
         __syncthreads();                                             // acc is rewritten by the next chunk
     }
@@ -2540,6 +2559,7 @@ using namespace kp;
 extern "C" {
 
 kp_status kp_sense_forward(kp_plan plan, const void* x_dev, void* y_dev, kp_cdtype y_t, void* stream) {
+    KP_RANGE("kp_sense_forward");
     if (!plan || !x_dev || !y_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || (!plan->maps_set && !plan->unit_maps)) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
@@ -2547,6 +2567,7 @@ kp_status kp_sense_forward(kp_plan plan, const void* x_dev, void* y_dev, kp_cdty
 }
 
 kp_status kp_sense_adjoint(kp_plan plan, const void* y_dev, kp_cdtype y_t, void* x_dev, void* stream) {
+    KP_RANGE("kp_sense_adjoint");
     if (!plan || !x_dev || !y_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || (!plan->maps_set && !plan->unit_maps)) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }

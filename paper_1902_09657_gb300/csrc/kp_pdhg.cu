@@ -277,6 +277,7 @@ kp_status power_end(kp_plan p, cudaStream_t st) {
 }
 
 static kp_status power_method(kp_plan p, const float* ps_sorted, int iters, cudaStream_t st) {
+    KP_PHASE("power_method");
     KP_TRY(power_begin(p, st));
     for (int it = 0; it < iters; ++it) KP_TRY(power_step(p, ps_sorted, it == 0, st));
     return power_end(p, st);
@@ -734,6 +735,7 @@ extern "C" {
 
 kp_status kp_dual_l2_solve(kp_plan plan, const void* y_dev, const float* p_dev, float lambda, int iters, void* x_dev,
                            double* res_trace, void* stream) {
+    KP_RANGE("kp_dual_l2_solve");
     if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 0) { set_error("iters must be >= 0"); return KP_EINVAL; }
@@ -742,12 +744,14 @@ kp_status kp_dual_l2_solve(kp_plan plan, const void* y_dev, const float* p_dev, 
 }
 
 kp_status kp_wavelet(kp_plan plan, const void* in_dev, void* out_dev, int forward, void* stream) {
+    KP_RANGE("kp_wavelet");
     if (!plan || !in_dev || !out_dev) { set_error("null argument"); return KP_EINVAL; }
     if (plan->P.wavelet_levels < 1) { set_error("plan has wavelet_levels = 0"); return KP_EINVAL; }
     return wavelet_apply(plan, (const float2*)in_dev, (float2*)out_dev, forward != 0, (cudaStream_t)stream);
 }
 
 kp_status kp_max_eig(kp_plan plan, const float* p_dev, const void* v0_dev, int iters, double* lmax, void* stream) {
+    KP_RANGE("kp_max_eig");
     if (!plan || !lmax) { set_error("null argument"); return KP_EINVAL; }
     if (iters < 1) { set_error("iters must be >= 1"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
@@ -789,6 +793,7 @@ static kp_status pdhg_solve_impl(kp_plan plan, const void* y_dev, kp_cdtype y_t,
 kp_status kp_pdhg_solve_ex(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg,
                            float lambda, int iters, double lmax, const kp_pdhg_state* start, kp_pdhg_state* end,
                            double* obj_trace, kp_stats* stats, void* stream) {
+    KP_RANGE("kp_pdhg_solve_ex");
     return pdhg_solve_impl(plan, y_dev, y_t, p_dev, reg, lambda, iters, lmax, start, end, obj_trace, stats, stream,
                            nullptr);
 }
@@ -814,6 +819,7 @@ static kp_status pdhg_solve_impl(kp_plan plan, const void* y_dev, kp_cdtype y_t,
     kp_status status = KP_OK;
     double F0 = 0, F = NAN;
     double phase_ms[PH_N] = {0};
+    KP_PHASE("pdhg_iterations");
     if (iters > 0) {
         Graph* gr = nullptr;
         if (!plan->profiling) KP_TRY(get_graph(plan, (int)reg, lambda, &gr));
@@ -887,6 +893,7 @@ static kp_status pdhg_solve_impl(kp_plan plan, const void* y_dev, kp_cdtype y_t,
 
 kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const float* p_dev, kp_reg reg, float lambda,
                         int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats, void* stream) {
+    KP_RANGE("kp_pdhg_solve");
     if (!x_dev) { set_error("null argument"); return KP_EINVAL; }
     kp_pdhg_state end{x_dev, nullptr, nullptr, nullptr, 0};
     return kp_pdhg_solve_ex(plan, y_dev, y_t, p_dev, reg, lambda, iters, lmax, nullptr, &end, obj_trace, stats, stream);
@@ -895,6 +902,7 @@ kp_status kp_pdhg_solve(kp_plan plan, const void* y_dev, kp_cdtype y_t, const fl
 kp_status kp_pdhg_solve_host(kp_plan plan, const void* y_host, kp_cdtype y_t, const float* p_dev, kp_reg reg,
                              float lambda, int iters, double lmax, void* x_dev, double* obj_trace, kp_stats* stats,
                              void* stream) {
+    KP_RANGE("kp_pdhg_solve_host");
     if (!plan || !y_host || !x_dev) { set_error("null argument"); return KP_EINVAL; }
     if (y_t != KP_C64 && y_t != KP_C32_BF16 && y_t != KP_C32_FP16) { set_error("bad y type"); return KP_EINVAL; }
     cudaPointerAttributes at{};

@@ -18,6 +18,18 @@ namespace kp {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+#ifdef KP_CHECKED
+// The translation units' record readers (registered during static initialisation).
+static std::vector<cudaError_t (*)(unsigned int*, unsigned long long*)>& oob_readers() {
+    static std::vector<cudaError_t (*)(unsigned int*, unsigned long long*)> r;
+    return r;
+}
+bool oob_register(cudaError_t (*take)(unsigned int*, unsigned long long*)) {
+    oob_readers().push_back(take);
+    return true;
+}
+#endif
+
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ int wrap(int k, int g) { return k < 0 ? k + g : (k >= g ? k - g : k); }
 
@@ -838,6 +850,7 @@ const char* kp_status_string(kp_status s) {
 const char* kp_last_error(void) { return g_last_error.c_str(); }
 
 kp_status kp_plan_create(kp_plan* out, const kp_params* params, void* stream) {
+    KP_RANGE("kp_plan_create");
     g_last_error.clear();
     return plan_create_internal(out, params, false, (cudaStream_t)stream);
 }
@@ -845,12 +858,14 @@ kp_status kp_plan_create(kp_plan* out, const kp_params* params, void* stream) {
 kp_status kp_plan_destroy(kp_plan plan) { return plan_destroy_internal(plan); }
 
 kp_status kp_plan_set_trajectory(kp_plan plan, const float* traj_dev, void* stream) {
+    KP_RANGE("kp_plan_set_trajectory");
     g_last_error.clear();
     if (!plan) { set_error("null plan"); return KP_EINVAL; }
     return set_trajectory_internal(plan, traj_dev, 1.0f, (cudaStream_t)stream);
 }
 
 kp_status kp_plan_set_maps(kp_plan plan, const void* maps_dev, kp_cdtype maps_t, void* stream) {
+    KP_RANGE("kp_plan_set_maps");
     g_last_error.clear();
     if (!plan || !maps_dev) { set_error("null argument"); return KP_EINVAL; }
     if (plan->unit_maps) { set_error("plan has unit maps"); return KP_EINVAL; }
@@ -880,6 +895,28 @@ kp_status kp_plan_set_wait_limit(kp_plan plan, long long cycles) {
     if (cycles < 0) { set_error("the wait limit must be >= 0"); return KP_EINVAL; }
     plan->wait_cycles = cycles;
     drop_graphs(plan);
+    return KP_OK;
+}
+
+kp_status kp_bounds_report(int* checked, uint32_t* count, uint32_t* first_site, int64_t* first_index) {
+    uint32_t n = 0;
+    unsigned long long first = 0;
+#ifdef KP_CHECKED
+    KP_TRY_CUDA(cudaDeviceSynchronize());
+    for (auto take : oob_readers()) {
+        unsigned int c = 0;
+        unsigned long long f = 0;
+        KP_TRY_CUDA(take(&c, &f));
+        if (c && !n) first = f;
+        n += c;
+    }
+    if (checked) *checked = 1;
+#else
+    if (checked) *checked = 0;
+#endif
+    if (count) *count = n;
+    if (first_site) *first_site = n ? (uint32_t)(first >> 48) : 0u;
+    if (first_index) *first_index = n ? (int64_t)(first & 0xFFFFFFFFFFFFull) : 0;
     return KP_OK;
 }
 

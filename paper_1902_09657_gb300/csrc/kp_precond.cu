@@ -233,6 +233,7 @@ __global__ void k_accum_all(const float2* __restrict__ Q, int C, int D, int nb0,
     if ((int64_t)m >= Nb) return;
     const int c = blockIdx.y;
     const unsigned mneg = neg_index(m, D, (unsigned)nb0, (unsigned)nb1, (unsigned)nb2);
+    if (!KP_INB(14, mneg, Nb)) return;
     ff32 acc = {0.f, 0.f};
     for (int d = 0; d < c; ++d)
         acc = ff_add(acc, ff_abs2(Q[(size_t)(d * C - d * (d - 1) / 2 + c - d) * Nb + mneg]));
@@ -265,7 +266,7 @@ __global__ void k_rh(const float2* __restrict__ r, const float2* __restrict__ h,
         ri += idx * stride;
         stride *= (unsigned)nb[d];
     }
-    v[j] = cmul(r[ri], h[j]);
+    if (KP_INB(14, ri, Nb)) v[j] = cmul(r[ri], h[j]);
 }
 
 template <typename MT>
@@ -329,15 +330,19 @@ __global__ void k_den_p(const float2* __restrict__ Vhat, const int* __restrict__
         for (int b = 0; b < KW; ++b) {
             const ff32 wab = ff_two_prod(w[0][a], w[1 % D][b]);
             if (D == 2) {
-                acc = ff_add(acc, ff_mul(wab, Vhat[off[0][a] + off[1 % D][b]].x));
+                const int ix = off[0][a] + off[1 % D][b];
+                acc = ff_add(acc, ff_mul(wab, KP_INB(15, ix, g2.G) ? Vhat[ix].x : 0.f));
             } else {
 #pragma unroll
-                for (int e = 0; e < KW; ++e)
-                    acc = ff_add(acc, ff_mul(ff_mul(wab, w[D - 1][e]), Vhat[off[0][a] + off[1 % D][b] + off[D - 1][e]].x));
+                for (int e = 0; e < KW; ++e) {
+                    const int ix = off[0][a] + off[1 % D][b] + off[D - 1][e];
+                    acc = ff_add(acc, ff_mul(ff_mul(wab, w[D - 1][e]), KP_INB(15, ix, g2.G) ? Vhat[ix].x : 0.f));
+                }
             }
         }
     const double dv = ff_to_double(acc) * (double)(1 << D) / sqrt((double)g2.N);
     const int64_t i = perm[s];
+    if (!KP_INB(15, i, g2.M)) return;
     float val;
     if (dv > 0 && isfinite(dv)) {
         val = (float)(norm[cnorm] / dv);
@@ -492,6 +497,7 @@ kp_status kp::circulant_enqueue(kp_plan plan, cudaStream_t st) {
 // Enqueues the whole construction on st without waiting; the number of non-positive
 // denominators (entries set to 0) is left in d_flag[7].
 kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float* p_dev, cudaStream_t st) {
+    KP_PHASE("preconditioner");
     if (!plan || !p_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || (multichannel && !plan->maps_set)) { set_error("trajectory (and maps) must be set"); return KP_EINVAL; }
     if (plan->unit_maps) { set_error("not available on an internal plan"); return KP_EINVAL; }
@@ -594,6 +600,7 @@ kp_status kp::make_preconditioner_enqueue(kp_plan plan, int multichannel, float*
 }
 
 extern "C" kp_status kp_make_preconditioner(kp_plan plan, int multichannel, float* p_dev, void* stream) {
+    KP_RANGE("kp_make_preconditioner");
     cudaStream_t st = (cudaStream_t)stream;
     KP_TRY(kp::make_preconditioner_enqueue(plan, multichannel, p_dev, st));
     int bad = 0;

@@ -198,6 +198,7 @@ using namespace kp;
 extern "C" {
 
 kp_status kp_sense_forward_traj_grad(kp_plan plan, const void* x_dev, const void* gy_dev, float* gtraj_dev, void* stream) {
+    KP_RANGE("kp_sense_forward_traj_grad");
     if (!plan || !x_dev || !gy_dev || !gtraj_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
@@ -206,6 +207,7 @@ kp_status kp_sense_forward_traj_grad(kp_plan plan, const void* x_dev, const void
 }
 
 kp_status kp_sense_adjoint_traj_grad(kp_plan plan, const void* u_dev, const void* gx_dev, float* gtraj_dev, void* stream) {
+    KP_RANGE("kp_sense_adjoint_traj_grad");
     if (!plan || !u_dev || !gx_dev || !gtraj_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
@@ -215,6 +217,7 @@ kp_status kp_sense_adjoint_traj_grad(kp_plan plan, const void* u_dev, const void
 
 kp_status kp_unrolled_forward(kp_plan plan, const void* y_dev, const float* p_dev, float lambda, int iters, double lmax,
                               void* x_dev, void* stream) {
+    KP_RANGE("kp_unrolled_forward");
     if (!plan || !y_dev || !x_dev) { set_error("null argument"); return KP_EINVAL; }
     if (!plan->traj_set || !plan->maps_set) { set_error("trajectory and maps must be set"); return KP_EINVAL; }
     if (iters < 1) { set_error("iters must be >= 1"); return KP_EINVAL; }
@@ -245,6 +248,7 @@ kp_status kp_unrolled_forward(kp_plan plan, const void* y_dev, const float* p_de
 
 kp_status kp_unrolled_backward(kp_plan plan, const void* gx_dev, void* gy_dev, double* glambda, float* gtraj_dev,
                                void* stream) {
+    KP_RANGE("kp_unrolled_backward");
     if (!plan || !gx_dev) { set_error("null argument"); return KP_EINVAL; }
     if (plan->tape_iters < 1) { set_error("kp_unrolled_forward must run first"); return KP_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;

@@ -303,6 +303,7 @@ __device__ __forceinline__ void inv_level_tile(const LevelArgs& a, int tile, flo
         if (!ok) continue;
         const float2 v = in[o];
         const int64_t off = voff<D>(a.dst, j);
+        if (a.lev_first && a.x && !KP_INB(13, off, a.geo.N)) continue;
         if (a.lev_first && a.x) {
             const float2 xo = a.x[off];
             const float2 xb = make_float2(v.x + th * (v.x - xo.x), v.y + th * (v.y - xo.y));
@@ -800,7 +801,7 @@ __device__ void zero_split_tiles(const PrimalArgs& a) {
                 if (lidx[d] >= e[d]) in = false;
                 gflat = gflat * g.g[d] + tunshift(o[d] + lidx[d], tl.sh[d], g.g[d]);
             }
-            if (in) a.grid2w[(size_t)c * g.G + gflat] = make_float2(0.f, 0.f);
+            if (in && KP_INB(13, gflat, g.G)) a.grid2w[(size_t)c * g.G + gflat] = make_float2(0.f, 0.f);
         }
     }
 }

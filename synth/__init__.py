@@ -191,6 +191,10 @@ WORKLOADS = {
     # the L2 cache but keep a profiler capture within a few GB of device memory
     "ute3d_160": Workload("ute3d_160", (160, 160, 160), 8, 1.25, 4, "l1_wavelet", 1e-3, 30, 3,
                           "radial3d", dict(n_spokes=16000, n_readout=208, kmax=80.0)),
+    # the 192^3 family's grid (240^3 passes, 8^3 tiles) with 2 coils and a quarter of the spokes:
+    # 221 MB grids, above the L2 cache, and under 3 GB on the device for profiler captures
+    "ute3d_192_c2": Workload("ute3d_192_c2", (192, 192, 192), 2, 1.25, 4, "l1_wavelet", 1e-3, 30, 3,
+                             "radial3d", dict(n_spokes=6000, n_readout=256, kmax=96.0)),
     # differentiable unrolled solver: 2D spiral 256^2, 16 coils, 16 x 4096, l2 lambda 1e-2
     "spiral2d_256_unrolled": Workload("spiral2d_256_unrolled", (256, 256), 16, 1.25, 4, "l2", 1e-2, 10, 0,
                                       "spiral", dict(n_interleaves=16, n_samples=4096, kmax=128.0)),

@@ -66,3 +66,25 @@ def test_struct_layout_matches_header():
 def test_sources_use_blackwell_target():
     from paper_1902_09657_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+def test_release_bounds_report_without_gpu(lib):
+    """The release build has no bounds checks: its report is empty and touches no device."""
+    from paper_1902_09657_gb300 import _lib
+    ck, n, site, idx = ctypes.c_int(7), ctypes.c_uint32(7), ctypes.c_uint32(7), ctypes.c_int64(7)
+    assert lib.kp_bounds_report(ctypes.byref(ck), ctypes.byref(n), ctypes.byref(site), ctypes.byref(idx)) == _lib.KP_OK
+    assert (ck.value, n.value, site.value, idx.value) == (0, 0, 0, 0)
+    assert lib.kp_bounds_report(None, None, None, None) == _lib.KP_OK
+
+
+def test_checked_build_flag_and_library_choice():
+    """`_build --checked` compiles with -DKP_CHECKED into its own library and object folder;
+    KPDHG_CHECKED=1 makes the binding load that library."""
+    import subprocess
+    import sys
+    from paper_1902_09657_gb300 import _build
+    assert _build.LIB_CHECKED != _build.LIB and _build.BUILD_CHECKED != _build.BUILD
+    code = "from paper_1902_09657_gb300 import _lib; print(_lib.LIB_PATH)"
+    env = dict(__import__("os").environ, KPDHG_CHECKED="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True).stdout
+    assert out.strip().endswith("libkpdhg_checked.so")
