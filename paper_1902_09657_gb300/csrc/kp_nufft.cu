@@ -181,7 +181,7 @@ __global__ void k_fwd_pre(const float2* __restrict__ x, const MT* __restrict__ m
 // copies (cp.async.bulk, one or two per grid row, completing on an mbarrier), then each
 // thread interpolates one sample for the group's coils from shared memory.
 constexpr int IP_CH = 4;           // coils per CTA (blockIdx.y selects the group)
-constexpr int IP_THREADS = 256;
+constexpr int IP_THREADS = 256;     // four CTAs per SM (64 registers; 3D: 4 x 46.5 KB staged)
 
 struct InterpIO {
     void* out;           // mode 0: [C][M] storage type T, index perm[s] (or s)
@@ -466,7 +466,7 @@ __device__ __forceinline__ void interp_tile_body(const int4* __restrict__ items,
 }
 
 template <int D, int MODE, typename T>
-__global__ void __launch_bounds__(IP_THREADS, D == 3 ? 3 : 4)
+__global__ void __launch_bounds__(IP_THREADS, 4)
 k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const float* __restrict__ wt,
               const float2* __restrict__ grid, Geom geo, Tiles tl, InterpIO io) {
     interp_tile_body<D, MODE, T>(items, k0t, wt, grid, geo, tl, io, blockIdx.x, blockIdx.y);
@@ -475,7 +475,7 @@ k_interp_tile(const int4* __restrict__ items, const int* __restrict__ k0t, const
 // The same over the cases of a batch: block b belongs to the case c with boff[c] <= b <
 // boff[c + 1]; within it, item (b - boff[c]) mod n_items of coil group (b - boff[c]) / n_items.
 template <int D, int MODE, typename T>
-__global__ void __launch_bounds__(IP_THREADS, D == 3 ? 3 : 4)
+__global__ void __launch_bounds__(IP_THREADS, 4)
 k_interp_tile_b(const BInterp* __restrict__ cs, const int* __restrict__ boff, int ncase) {
     const int c = batch_case(boff, ncase, (int)blockIdx.x);
     const BInterp& a = cs[c];
@@ -1029,7 +1029,6 @@ k_spread_z(const int* __restrict__ k0t, const float* __restrict__ wt, const UT* 
 // stores every grid point as the sum of its tile's slots and, for points within W - 1 of a low
 // face, of the lower neighbours' halos (periodic): no atomics, no clearing, fixed sum order.
 constexpr int PT = 8 + KW - 1;                 // padded tile edge
-constexpr int PT3 = PT * PT * PT;
 constexpr int OT_RS = 12;                      // float4 per padded row: x padded to 12 so that a quarter-warp's
 constexpr int OT_PS = PT * OT_RS;              // lanes (4 consecutive x, 2 rows) hit 8 different bank groups
 constexpr int OT_PAIR = PT * OT_PS;            // float4 per coil pair
