@@ -371,7 +371,7 @@ NCU_TRAFFIC = {
 # the same 16-bit values; "storage error": oracle on the unrounded inputs.  The tests hold the
 # pass/fail tolerances (1e-5 float32, 2e-3 storage).
 ORACLE_ERRORS = {
-    "ute3d_192_operators": {"forward": 3.08e-07, "adjoint": 7.37e-07,
+    "ute3d_192_operators": {"forward": 3.08e-07, "adjoint": 7.44e-07,
                             "test": "test_gpu_nufft.py::test_forward_adjoint_3d_ute_full_size (every sample)"},
     "ute3d_own_fft_passes": {"forward": 6.9e-07, "adjoint": 6.19e-07,
                              "test": "test_gpu_nufft.py::test_own_fft_passes_match_oracle_and_cufft (every compiled length, 20-480)"},
