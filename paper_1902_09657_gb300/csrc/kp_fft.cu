@@ -32,7 +32,7 @@ namespace kp {
 
 constexpr int FF_LINES = 16;     // lines per CTA (at most)
 // lines per CTA for length N: 16 up to 256 points (16 x = 128-byte row segments), else 8 so
-// that the two buffers stay near 64 KB and several CTAs share an SM
+// that the buffer of lines stays near 32 KB and five CTAs share an SM
 constexpr int ff_lines(int N) { return N <= 256 ? 16 : 8; }
 constexpr int FF_T = 256;        // threads per CTA
 constexpr int FF_MAXN = 512;     // longest axis handled
