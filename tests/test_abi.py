@@ -88,3 +88,13 @@ def test_checked_build_flag_and_library_choice():
     env = dict(__import__("os").environ, KPDHG_CHECKED="1")
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True).stdout
     assert out.strip().endswith("libkpdhg_checked.so")
+
+
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    """The bounds-checked variant (-DKP_CHECKED) builds for sm_103a without a GPU and exports
+    every symbol the header declares (the checks only add code inside the kernels)."""
+    from paper_1902_09657_gb300 import _build
+    path = _build.build(checked=True)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
