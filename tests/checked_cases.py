@@ -5,7 +5,8 @@ reach every instrumented kernel: bin-sort, forward and adjoint NUFFT (the one-ph
 spreading and the two-phase 3D spreading with its own phase and gather, the interpolation,
 the library's own 3D FFT passes), the MC preconditioner, the power method and PDHG with the
 fused primal step (l1-wavelet and l2).  Run as a script (``python -m tests.checked_cases
-OUT.npz``, with KPDHG_CHECKED=1 for the checked build) it saves the results and prints the
+OUT.npz``, with KPDHG_CHECKED=1 for the checked build; ``--workload NAME`` runs one whole
+reconstruction of a named workload at full size instead) it saves the results and prints the
 library's bounds report as one JSON line.
 """
 import json
@@ -61,12 +62,35 @@ def run_cases():
     return out
 
 
-def main(path):
+def run_workload(name):
+    """One whole reconstruction of a named workload (bin-sort, MC preconditioner, 30 power
+    iterations, the workload's PDHG iterations) at its full size, with the storage types the
+    bench uses; returns the image."""
+    import torch
+    from paper_1902_09657_gb300.api import Plan, to_storage
+    w = synth.workload(name)
+    traj = w.traj()
+    plan = Plan(w.img_shape, w.ncoils, traj.shape[0], oversamp=w.oversamp, wavelet_levels=w.wavelet_levels)
+    maps = torch.from_numpy(w.maps()).cuda()
+    maps_st = to_storage(maps, "fp16") if len(w.img_shape) == 3 else maps
+    plan.set_trajectory(torch.from_numpy(traj).cuda()).set_maps(maps_st)
+    y = plan.sense_forward(torch.from_numpy(w.phantom()).cuda())
+    lam = 1e-3 * float(plan.sense_adjoint(y).abs().max())
+    x, _, _ = plan.pdhg_solve(y, None, w.reg, lam, w.iters)
+    out = x.cpu().numpy()
+    plan.close()
+    return out
+
+
+def main(argv):
     from paper_1902_09657_gb300.api import bounds_report
-    res = run_cases()
-    np.savez(path, **res)
+    if len(argv) > 2 and argv[2] == "--workload":
+        res = {"x": run_workload(argv[3])}
+    else:
+        res = run_cases()
+    np.savez(argv[1], **res)
     print(json.dumps(bounds_report()), flush=True)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    main(sys.argv)
